@@ -1,0 +1,349 @@
+"""Pins of the oracle against facts fixed outside it (no GPU).
+
+Each test ties one part of the oracle to something other than its own code:
+an independent formula (pairwise modularity in exact fractions), a library
+(networkx), brute force over all partitions, closed forms, invariants, and
+runs worked by hand (tests/golden/hand_runs.json).  Together they are chosen
+so that a dropped term, a wrong sign, a swapped index or a wrong tie rule in
+the oracle fails at least one of them.
+"""
+import itertools
+import json
+import os
+import random
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "hand_runs.json")
+
+
+# ---------------------------------------------------------------- helpers
+
+def dense(g):
+    """Dense adjacency (CSR entry values; a self-loop appears once on the diagonal)."""
+    A = [[0] * g.n for _ in range(g.n)]
+    for u in range(g.n):
+        for e in range(int(g.off[u]), int(g.off[u + 1])):
+            A[u][int(g.col[e])] += int(g.w[e])
+    return A
+
+
+def q_pairwise(A, memb):
+    """Newman-Girvan in its pairwise form, exact: (1/M) sum_ij [A_ij - K_i K_j / M] delta(c_i, c_j)."""
+    n = len(A)
+    K = [sum(r) for r in A]
+    M = sum(K)
+    if M == 0:
+        return Fraction(0)
+    tot = Fraction(0)
+    for i in range(n):
+        for j in range(n):
+            if memb[i] == memb[j]:
+                tot += Fraction(A[i][j]) - Fraction(K[i] * K[j], M)
+    return tot / M
+
+
+def random_graph(rng, n, p, wmax=5, loops=True):
+    edges = []
+    for u in range(n):
+        for v in range(u + 1, n):
+            if rng.random() < p:
+                edges.append((u, v, rng.randint(1, wmax)))
+        if loops and rng.random() < 0.2:
+            edges.append((u, u, rng.randint(1, wmax)))
+    return gg.from_weighted_edges(n, edges)
+
+
+def bell(n):
+    row = [1]
+    for _ in range(n - 1):
+        nxt = [row[-1]]
+        for x in row:
+            nxt.append(nxt[-1] + x)
+        row = nxt
+    return row[-1]
+
+
+def cliques(k, s, ring=False):
+    edges = []
+    for c in range(k):
+        base = c * s
+        for a in range(s):
+            for b in range(a + 1, s):
+                edges.append((base + a, base + b, 1))
+        if ring and k > 1:
+            edges.append((base + s - 1, ((c + 1) % k) * s, 1))
+    return gg.from_weighted_edges(k * s, edges)
+
+
+def run(g, **kw):
+    return oracle.louvain(g.off, g.col, g.w, **kw)
+
+
+# ----------------------------------------------------------- modularity (a9)
+
+def test_modularity_matches_pairwise_form_exactly():
+    rng = random.Random(1)
+    for _ in range(40):
+        n = rng.randint(1, 9)
+        g = random_graph(rng, n, 0.5)
+        A = dense(g)
+        memb = [rng.randrange(n) for _ in range(n)]
+        q, num, M = oracle.modularity(g.off, g.col, g.w, memb)
+        exact = q_pairwise(A, memb)
+        if M:
+            assert Fraction(num, M * M) == exact
+        assert M == sum(map(sum, A))
+
+
+def test_modularity_matches_networkx_without_self_loops():
+    nx = pytest.importorskip("networkx")
+    rng = random.Random(2)
+    for _ in range(20):
+        n = rng.randint(2, 30)
+        g = random_graph(rng, n, 0.3, loops=False)
+        if g.nnz == 0:
+            continue
+        G = nx.Graph()
+        G.add_nodes_from(range(n))
+        for u in range(n):
+            for e in range(int(g.off[u]), int(g.off[u + 1])):
+                v = int(g.col[e])
+                if u < v:
+                    G.add_edge(u, v, weight=int(g.w[e]))
+        memb = [rng.randrange(min(4, n)) for _ in range(n)]
+        comms = [set(i for i in range(n) if memb[i] == c) for c in set(memb)]
+        q, _, _ = oracle.modularity(g.off, g.col, g.w, memb)
+        assert abs(q - nx.community.modularity(G, comms, weight="weight")) < 1e-12
+
+
+def test_modularity_closed_form_disjoint_cliques():
+    for k, s in [(2, 3), (4, 5), (7, 4), (16, 6)]:
+        g = cliques(k, s)
+        memb = np.repeat(np.arange(k), s)
+        _, num, M = oracle.modularity(g.off, g.col, g.w, memb)
+        assert Fraction(num, M * M) == 1 - Fraction(1, k)
+
+
+def test_modularity_closed_form_ring_of_cliques():
+    for k, s in [(3, 4), (8, 5), (30, 3)]:
+        g = cliques(k, s, ring=True)
+        memb = np.repeat(np.arange(k), s)
+        _, num, M = oracle.modularity(g.off, g.col, g.w, memb)
+        assert Fraction(num, M * M) == Fraction(s * (s - 1), s * (s - 1) + 2) - Fraction(1, k)
+
+
+def test_modularity_singletons_and_one_community():
+    rng = random.Random(3)
+    g = random_graph(rng, 8, 0.6, loops=False)
+    A = dense(g)
+    K = [sum(r) for r in A]
+    M = sum(K)
+    _, num, _ = oracle.modularity(g.off, g.col, g.w, np.arange(8))
+    assert Fraction(num, M * M) == -Fraction(sum(k * k for k in K), M * M)
+    _, num, _ = oracle.modularity(g.off, g.col, g.w, np.zeros(8, np.int32))
+    assert num == 0
+
+
+# ----------------------------------------------------------- gain (a3)
+
+def test_gain_equals_exact_modularity_difference():
+    """For every vertex and candidate: gain * 2 / M^2 == Q(after) - Q(before), exactly."""
+    rng = random.Random(4)
+    checked = 0
+    for _ in range(30):
+        n = rng.randint(2, 9)
+        g = random_graph(rng, n, 0.5)
+        A = dense(g)
+        M = sum(map(sum, A))
+        if M == 0:
+            continue
+        memb = [rng.randrange(n) for _ in range(n)]
+        q0 = q_pairwise(A, memb)
+        for i in range(n):
+            gains = oracle.vertex_gains(g.off, g.col, g.w, memb, i)
+            nb = {memb[int(g.col[e])] for e in range(int(g.off[i]), int(g.off[i + 1])) if int(g.col[e]) != i}
+            assert set(gains) == nb - {memb[i]}
+            for c, gain in gains.items():
+                after = list(memb)
+                after[i] = c
+                assert Fraction(2 * gain, M * M) == q_pairwise(A, after) - q0
+                checked += 1
+    assert checked > 100
+
+
+# ------------------------------------------------------ brute force (O2)
+
+def test_brute_force_enumerates_bell_numbers_and_known_optima():
+    for n in range(1, 9):
+        g = gg.from_weighted_edges(n, [(i, i + 1, 1) for i in range(n - 1)])
+        _, _, cnt = oracle.brute_best(g.off, g.col, g.w)
+        assert cnt == bell(n)
+    with open(GOLDEN) as f:
+        case = [c for c in json.load(f)["cases"] if c["name"] == "two_triangles_bridge_optimum"][0]
+    g = gg.from_weighted_edges(case["n"], [tuple(e) for e in case["edges"]])
+    best, memb, cnt = oracle.brute_best(g.off, g.col, g.w)
+    assert best == case["expect"]["best_q_num"] and cnt == case["expect"]["partitions"]
+    assert len(set(memb[:3])) == 1 and len(set(memb[3:])) == 1 and memb[0] != memb[3]
+    # complete graph: nothing beats one community (Q = 0)
+    g = cliques(1, 6)
+    best, _, _ = oracle.brute_best(g.off, g.col, g.w)
+    assert best == 0
+
+
+def test_brute_force_agrees_with_exhaustive_pairwise_search():
+    rng = random.Random(5)
+    for _ in range(5):
+        n = rng.randint(2, 6)
+        g = random_graph(rng, n, 0.5)
+        A = dense(g)
+        M = sum(map(sum, A))
+        if M == 0:
+            continue
+        best_exact = max(q_pairwise(A, m) for m in itertools.product(range(n), repeat=n))
+        best, _, _ = oracle.brute_best(g.off, g.col, g.w)
+        assert Fraction(best, M * M) == best_exact
+
+
+# ---------------------------------------------------------- Louvain runs
+
+def test_hand_worked_runs():
+    with open(GOLDEN) as f:
+        cases = json.load(f)["cases"]
+    for case in cases:
+        if case["options"] is None:
+            continue
+        g = gg.from_weighted_edges(case["n"], [tuple(e) for e in case["edges"]])
+        o = dict(case["options"])
+        mode = oracle.SYNC if o.pop("mode") == "sync" else oracle.ASYNC
+        for prune in (0, 1):
+            r = run(g, mode=mode, prune=prune, **o)
+            ex = case["expect"]
+            assert list(r.top) == ex["top"], case["name"]
+            assert r.q_num == ex["q_num"] and r.M == ex["M"], case["name"]
+            assert r.Q == ex["Q"], case["name"]
+            assert [list(t) for t in r.iterations] == ex["iterations"], case["name"]
+
+
+@pytest.mark.parametrize("mode", [oracle.SYNC, oracle.ASYNC])
+def test_louvain_never_beats_brute_force_and_finds_clique_optimum(mode):
+    rng = random.Random(6)
+    for _ in range(25):
+        n = rng.randint(2, 10)
+        g = random_graph(rng, n, 0.4)
+        if g.nnz == 0:
+            continue
+        r = run(g, mode=mode)
+        best, _, _ = oracle.brute_best(g.off, g.col, g.w)
+        assert r.q_num <= best
+        _, num, _ = oracle.modularity(g.off, g.col, g.w, r.top)
+        assert num == r.q_num
+    for k, s in [(2, 4), (3, 3), (5, 5)]:
+        g = cliques(k, s)
+        r = run(g, mode=mode)
+        assert Fraction(r.q_num, r.M * r.M) == 1 - Fraction(1, k)
+        best, _, _ = oracle.brute_best(g.off, g.col, g.w) if k * s <= 10 else (r.q_num, None, None)
+        assert r.q_num == best
+
+
+@pytest.mark.parametrize("mode", [oracle.SYNC, oracle.ASYNC])
+def test_louvain_ring_of_cliques_reaches_clique_partition(mode):
+    for k, s in [(6, 5), (12, 4)]:
+        g = cliques(k, s, ring=True)
+        r = run(g, mode=mode)
+        clique_q = Fraction(s * (s - 1), s * (s - 1) + 2) - Fraction(1, k)
+        assert Fraction(r.q_num, r.M * r.M) >= clique_q
+
+
+@pytest.mark.parametrize("mode", [oracle.SYNC, oracle.ASYNC])
+@pytest.mark.parametrize("prune", [0, 1])
+@pytest.mark.parametrize("subrounds", [1, 4])
+def test_pass_invariants(mode, prune, subrounds):
+    """Aggregation keeps M and Q; levels compose to the top membership; k shrinks."""
+    g = gg.sbm(11, 600, 12, 0.15, 0.01, wmin=1, wmax=9)
+    r = run(g, mode=mode, prune=prune, subrounds=subrounds, record_levels=True)
+    assert r.Q > 0.3
+    off, col, w = g.off, g.col, g.w.astype(np.int64)
+    top = np.arange(g.n)
+    for p, ps in enumerate(r.passes):
+        assert ps.n == len(off) - 1
+        if ps.level is None:
+            break
+        k = ps.k
+        assert sorted(set(ps.level.tolist())) == list(range(k))
+        # Q numerator after the pass equals the modularity of the level on the pass graph
+        _, num, M = oracle.modularity(off, col, w, ps.level)
+        assert num == ps.n_after and M == r.M
+        top = ps.level[top]
+        if ps.coarse is not None:
+            co, cc, cw = ps.coarse
+            assert int(cw.sum()) == r.M                     # total weight preserved
+            _, num_c, _ = oracle.modularity(co, cc, cw, np.arange(k))
+            assert num_c == ps.n_after                     # Q preserved exactly
+            oo, oc, ow = oracle.aggregate(off, col, w, ps.level, k)
+            assert np.array_equal(oo, co) and np.array_equal(oc, cc) and np.array_equal(ow, cw)
+            for C in range(k):                             # canonical rows
+                row = cc[co[C]:co[C + 1]]
+                assert np.all(np.diff(row) > 0)
+            # coarse degrees are the community totals Sigma_C of the fine graph
+            K = np.array([w[off[i]:off[i + 1]].sum() for i in range(len(off) - 1)], np.int64)
+            sig = np.bincount(ps.level, weights=K, minlength=k).astype(np.int64)
+            coarse_K = np.array([cw[co[C]:co[C + 1]].sum() for C in range(k)], np.int64)
+            assert np.array_equal(sig, coarse_K)
+            off, col, w = co, cc, cw
+            assert p + 1 < len(r.passes)
+            assert r.passes[p + 1].n == k and k < ps.n
+    assert np.array_equal(top, r.top)
+    _, num, _ = oracle.modularity(g.off, g.col, g.w, r.top)
+    assert num == r.q_num
+
+
+def test_async_gains_sum_to_the_exact_modularity_change():
+    """Sequential Gauss-Seidel: S of an iteration equals the true Q change * M^2 / 2."""
+    g = gg.sbm(12, 400, 8, 0.2, 0.02)
+    for iters in (1, 2, 3):
+        r = run(g, mode=oracle.ASYNC, max_iterations=iters, max_passes=1, tolerance=0.0)
+        total_S = sum(S for (p, m, S) in r.iterations if p == 0)
+        assert 2 * total_S == r.passes[0].n_after - r.passes[0].n_before
+
+
+def test_modularity_range_and_sync_async_quality():
+    """Q stays in [-1/2, 1] (Section 1); sync and async reach equivalent quality (Section 3.2)."""
+    g = gg.sbm(0x5EED, 2048, 16, 0.1, 0.002)
+    rs = run(g, mode=oracle.SYNC, prune=1)
+    rp = run(g, mode=oracle.SYNC, prune=1, subrounds=8)
+    ra = run(g, mode=oracle.ASYNC, prune=1)
+    for r in (rs, rp, ra):
+        assert -0.5 <= r.Q <= 1.0
+    assert abs(rs.Q - ra.Q) < 0.05 and abs(rp.Q - ra.Q) < 0.02
+    # the planted partition is (near) optimal here; Louvain should come close to it
+    q_truth, _, _ = oracle.modularity(g.off, g.col, g.w, g.truth)
+    assert ra.Q >= q_truth - 0.02
+
+
+def test_plain_jacobi_oscillates_and_guard_fixes_it():
+    """Plain Jacobi swaps singleton pairs (the slow sync convergence of Section 3.2);
+    the singleton guard restores quality close to the sequential (async) run."""
+    g = gg.sbm(11, 600, 12, 0.15, 0.01, wmin=1, wmax=9)
+    plain = run(g, mode=oracle.SYNC, singleton_guard=0)
+    guard = run(g, mode=oracle.SYNC, singleton_guard=1)
+    seq = run(g, mode=oracle.ASYNC)
+    assert plain.iterations[0][1] == g.n and plain.passes[0].iterations == 20
+    assert guard.Q > plain.Q + 0.2 and guard.Q > seq.Q - 0.02
+
+
+def test_empty_and_edgeless_graphs():
+    g = gg.from_weighted_edges(0, [])
+    r = run(g)
+    assert r.Q == 0.0 and len(r.top) == 0 and r.passes == []
+    g = gg.from_weighted_edges(5, [])
+    r = run(g)
+    assert r.Q == 0.0 and list(r.top) == list(range(5))
+    g = gg.from_weighted_edges(3, [(1, 1, 4)])   # a lone self-loop: nothing to move to
+    r = run(g)
+    assert list(r.top) == [0, 1, 2] and r.passes[0].moves == 0
