@@ -1,0 +1,185 @@
+/*
+ * louvain.h — C ABI of the GB300 (sm_103a) Louvain community-detection engine.
+ *
+ * The engine runs the data-parallel hot path of the Louvain method as the
+ * paper describes it (Sahu, "Enhancing Efficiency in Parallel Louvain
+ * Algorithm for Community Detection", Section 3.2): the local-moving phase,
+ * where every vertex moves to the neighbouring community of greatest
+ * modularity gain, repeated while an iteration's total gain exceeds
+ * `tolerance`; the aggregation phase, which collapses each community into a
+ * super-vertex (inter-community edges merged with summed weights, intra-
+ * community edges into a summed self-loop); passes of the two phases until the
+ * pass gain is <= `pass_tolerance`; threshold scaling (tolerance 0.01 divided
+ * by the decline factor 10 after every pass); synchronous (Jacobi) and
+ * asynchronous (Gauss-Seidel) variants.  The result is the top level of the
+ * dendrogram and its modularity.
+ *
+ * Modularity (Newman-Girvan, resolution 1; the paper states no formula) in
+ * this CSR convention: an undirected edge {u,v}, u != v, is stored as (u,v) and
+ * (v,u) with equal weight; a self-loop once.  K_i = row sum, M = sum K_i,
+ * Sigma_c = sum of K_i over c, L_c = sum of entries inside c,
+ * Q = (M sum L_c - sum Sigma_c^2) / M^2.  All gains and sums are exact
+ * integers (128-bit where needed); Q is the correctly rounded quotient of the
+ * exact numerator and M^2 as doubles.
+ *
+ * Conventions for every function below:
+ *   - return 0 on success or a negative LOUVAIN_ERR_* code; the message of
+ *     the last error of a context is louvain_last_error(ctx);
+ *   - pointers whose kind is given by a `louvain_ptr_kind` argument are host
+ *     or device (cuda:device of the context) memory of that kind;
+ *   - the engine copies every input: the caller keeps ownership of its
+ *     buffers and may free them once the call returns;
+ *   - outputs go to caller-owned buffers of the stated length;
+ *   - a context is not thread-safe; several contexts may share one device;
+ *   - all device work is ordered on the context's stream; calls that return
+ *     results synchronise that stream.
+ */
+#ifndef GB_LOUVAIN_H
+#define GB_LOUVAIN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ errors */
+#define LOUVAIN_OK 0
+#define LOUVAIN_ERR_INVALID_ARG (-1)   /* null pointer, negative size, bad option */
+#define LOUVAIN_ERR_NOT_SYMMETRIC (-2) /* some (u,v,w) has no (v,u,w) */
+#define LOUVAIN_ERR_BAD_CSR (-3)       /* offsets not monotone / col out of range / weight <= 0 */
+#define LOUVAIN_ERR_OOM (-4)           /* device allocation failed */
+#define LOUVAIN_ERR_CUDA (-5)          /* a CUDA runtime call or kernel failed */
+#define LOUVAIN_ERR_TIMEOUT (-6)       /* a bounded device-side wait ran out */
+#define LOUVAIN_ERR_STATE (-7)         /* e.g. run before load, result before run */
+#define LOUVAIN_ERR_OVERFLOW (-8)      /* total weight M >= 2^62 or n >= 2^31 */
+#define LOUVAIN_ERR_INTERNAL (-9)      /* a device-side consistency check failed */
+
+typedef enum { LOUVAIN_SYNC = 0, LOUVAIN_ASYNC = 1 } louvain_mode;
+typedef enum { LOUVAIN_PTR_HOST = 0, LOUVAIN_PTR_DEVICE = 1 } louvain_ptr_kind;
+
+/* Run options.  Defaults (louvain_default_options) are the paper's:
+ * tolerance 0.01, decline factor 10, pass tolerance 0 (Section 3.2), with
+ * 20 iterations per pass and 10 passes at most. */
+typedef struct {
+  int32_t mode;               /* louvain_mode */
+  double tolerance;           /* an iteration ends the phase when its total gain 2S/M^2 <= tolerance */
+  double tolerance_decline;   /* tolerance is divided by this after every pass (threshold scaling) */
+  double pass_tolerance;      /* the run ends after a pass whose modularity gain is <= this */
+  int32_t max_iterations;     /* local-moving iterations per pass (>= 1) */
+  int32_t max_passes;         /* passes (>= 0, <= 64) */
+  int32_t prune;              /* 1: after the first iteration of a pass, only vertices that moved or
+                                 have a neighbour that moved in the previous iteration are visited */
+  int32_t singleton_guard;    /* 1: a vertex alone in its community does not move to another
+                                 single-vertex community of higher id (minimum-label rule, Grappolo;
+                                 stops Jacobi updates from swapping pairs forever) */
+  int32_t subrounds;          /* P >= 1: the vertices are split into classes i mod P processed one
+                                 after the other in each iteration; 1 = every vertex at once */
+  int32_t validate;           /* 1: louvain_load_csr checks symmetry and CSR form (costs a pass) */
+  int32_t record_levels;      /* 1: keep each pass's membership and coarse CSR for louvain_get_level /
+                                 louvain_get_coarse (copies them to host memory) */
+  int32_t reserved_i[5];
+  double reserved_d[4];
+} louvain_options;
+
+/* Per-run statistics. */
+typedef struct {
+  int32_t passes;             /* passes whose local-moving phase ran */
+  int32_t iterations;         /* local-moving iterations over all passes */
+  int64_t moves;              /* vertex moves over all iterations */
+  int64_t lm_edges;           /* CSR entries scanned by local-moving (vertices visited x degree) */
+  int64_t communities;        /* communities in the final membership */
+  double q;                   /* final modularity */
+  double lm_ms;               /* device time of local-moving kernels (CUDA events) */
+  double agg_ms;              /* device time of renumbering + aggregation */
+  double other_ms;            /* pass set-up, modularity, bucketing */
+  double total_ms;            /* device time of louvain_run */
+  int64_t reserved[8];
+} louvain_stats;
+
+/* Per-pass record. */
+typedef struct {
+  int64_t n, nnz;             /* vertices and CSR entries of the pass graph */
+  int64_t k;                  /* communities after the pass (its level's size) */
+  int64_t moves;
+  int32_t iterations;
+  int32_t level_recorded;     /* louvain_get_level available for this pass */
+  int32_t coarse_built;       /* aggregation ran after this pass (another pass followed) */
+  int32_t pad;
+  int64_t coarse_nnz;         /* entries of the coarse CSR built from this pass */
+  int64_t n_before_hi;        /* exact Q numerator before the pass, as hi * 2^64 + lo */
+  uint64_t n_before_lo;
+  int64_t n_after_hi;         /* exact Q numerator after the pass's local-moving */
+  uint64_t n_after_lo;
+  double lm_ms, agg_ms;
+} louvain_pass_info;
+
+typedef struct louvain_ctx louvain_ctx;
+
+/* Fill *opt with the defaults above. */
+int louvain_default_options(louvain_options *opt);
+
+/* Create a context on CUDA device `device` using CUDA stream `cuda_stream`
+ * (a cudaStream_t; NULL = the context creates and owns a non-blocking
+ * stream).  `opt` is copied; NULL = defaults. */
+int louvain_create(louvain_ctx **out, const louvain_options *opt, int device, void *cuda_stream);
+
+/* Replace the options of a context (takes effect at the next run). */
+int louvain_set_options(louvain_ctx *ctx, const louvain_options *opt);
+
+/* Load a graph: n vertices, nnz CSR entries; offsets[n+1] (int64, offsets[0] = 0,
+ * non-decreasing, offsets[n] = nnz), cols[nnz] (int32 in [0,n)), weights[nnz]
+ * (int32 > 0), all of kind `ptr_kind`.  The CSR must be symmetric as described
+ * above (checked when opt.validate = 1).  Copies the graph to the device and
+ * sizes the context's device memory for it; a previous graph and its results
+ * are dropped.  Errors: INVALID_ARG, BAD_CSR, NOT_SYMMETRIC, OVERFLOW, OOM, CUDA. */
+int louvain_load_csr(louvain_ctx *ctx, int64_t n, int64_t nnz, const int64_t *offsets, const int32_t *cols,
+                     const int32_t *weights, int ptr_kind);
+
+/* Run the Louvain method on the loaded graph.  Errors: STATE (no graph), CUDA,
+ * INTERNAL, TIMEOUT. */
+int louvain_run(louvain_ctx *ctx);
+
+/* Top-level community of every input vertex into out[n] (kind `ptr_kind`);
+ * community ids are dense in [0, k) in order of first appearance by the
+ * renumbering rule (ascending old id at every pass).  n must equal the loaded n. */
+int louvain_get_membership(louvain_ctx *ctx, int32_t *out, int64_t n, int ptr_kind);
+
+/* Modularity of the result (see the convention above). */
+int louvain_get_modularity(louvain_ctx *ctx, double *q);
+
+/* Exact modularity of the result: Q = num / M^2 with num = num_hi * 2^64 + num_lo. */
+int louvain_get_modularity_exact(louvain_ctx *ctx, int64_t *num_hi, uint64_t *num_lo, int64_t *M);
+
+/* Modularity of an arbitrary membership memb[n] (kind `ptr_kind`, values in
+ * [0, n)) of the loaded graph, computed on the device; exact numerator too
+ * (num_hi / num_lo / M may be NULL). */
+int louvain_modularity(louvain_ctx *ctx, const int32_t *memb, int64_t n, int ptr_kind, double *q, int64_t *num_hi,
+                       uint64_t *num_lo, int64_t *M);
+
+int louvain_get_stats(louvain_ctx *ctx, louvain_stats *out);
+int louvain_get_pass_info(louvain_ctx *ctx, int pass, louvain_pass_info *out);
+
+/* Iteration t of the last run (all passes, in order): out[0] = pass,
+ * out[1] = moves, out[2..3] = S (sum of the gains of the moves, as hi, lo). */
+int louvain_get_iteration(louvain_ctx *ctx, int64_t t, int64_t out[4]);
+
+/* Renumbered membership of pass `pass`'s graph (record_levels = 1), out[n] host. */
+int louvain_get_level(louvain_ctx *ctx, int pass, int32_t *out, int64_t n);
+
+/* Coarse CSR built after pass `pass` (record_levels = 1): off[k+1], col[nnz],
+ * w[nnz] (int64), host.  Columns within a row are in no particular order. */
+int louvain_get_coarse(louvain_ctx *ctx, int pass, int64_t *off, int64_t k, int32_t *col, int64_t *w,
+                       int64_t nnz);
+
+/* Device bytes the context holds (arena). */
+int louvain_get_device_bytes(louvain_ctx *ctx, int64_t *bytes);
+
+void louvain_destroy(louvain_ctx *ctx);
+const char *louvain_last_error(const louvain_ctx *ctx);
+const char *louvain_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB_LOUVAIN_H */

@@ -1,0 +1,209 @@
+// common.cuh — device-side building blocks shared by the engine's kernels.
+//
+// Exact integer arithmetic for the modularity gain (Section 3.2 of the paper:
+// each vertex moves to the neighbouring community of greatest modularity
+// increase), hashing for per-vertex community-weight tables, and warp
+// reductions.  Nothing here is shared with the CPU oracle.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gbl {
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+constexpr int kWarp = 32;
+constexpr int32_t kEmpty = -1;
+
+// ---------------------------------------------------------------- errors
+
+// Device-side error codes, OR-ed into DevCounters::error.
+enum : int {
+  kErrProbe = 1,      // a hash table ran out of free slots (capacity too small)
+  kErrRange = 2,      // an index was out of range (bad input that slipped through)
+};
+
+// Per-iteration counters written by the local-moving kernels.
+struct DevCounters {
+  unsigned long long moves;
+  unsigned long long s_lo, s_hi;   // sum of the gains of the moves (u128)
+  unsigned long long edges;        // CSR entries scanned
+  unsigned long long nmoves_list;  // entries in the synchronous move list
+  int error;
+  int pad;
+};
+
+// ---------------------------------------------------------- 128-bit sums
+
+// Unsigned 128-bit atomic add from two 64-bit atomics: the low word wraps
+// modulo 2^64 and the add that wraps it carries one into the high word, so
+// the pair always ends at the exact total.
+__device__ __forceinline__ void atomic_add_u128(unsigned long long* lo, unsigned long long* hi, u128 v) {
+  unsigned long long vlo = (unsigned long long)v, vhi = (unsigned long long)(v >> 64);
+  if (vlo) {
+    unsigned long long old = atomicAdd(lo, vlo);
+    if (old + vlo < old) vhi += 1ull;
+  }
+  if (vhi) atomicAdd(hi, vhi);
+}
+
+// ------------------------------------------------------------- the gain
+
+// score(x) = M * K_{i->x} - K_i * Sigma'_x, Sigma'_x the total of community x
+// without vertex i; moving i from d to c gains score(c) - score(d), which is
+// M^2/2 times the modularity change.  With M^2 < 2^62 every term fits in
+// int64 (Narrow); otherwise 128-bit (Wide).
+template <bool WIDE> struct Arith;
+template <> struct Arith<false> {
+  typedef long long S;
+  __device__ __forceinline__ static S score(long long M, long long kix, long long Ki, long long sig) {
+    return M * kix - Ki * sig;
+  }
+  __device__ __forceinline__ static u128 to_u128(S g) { return (u128)(unsigned long long)g; }
+};
+template <> struct Arith<true> {
+  typedef i128 S;
+  __device__ __forceinline__ static S score(long long M, long long kix, long long Ki, long long sig) {
+    return (i128)M * kix - (i128)Ki * sig;
+  }
+  __device__ __forceinline__ static u128 to_u128(S g) { return (u128)g; }
+};
+
+// (gain, community) ordering: larger gain first, ties to the lower id.
+template <typename S>
+__device__ __forceinline__ bool better(S g1, int32_t c1, S g2, int32_t c2) {
+  return g1 > g2 || (g1 == g2 && (unsigned)c1 < (unsigned)c2);
+}
+
+__device__ __forceinline__ long long shfl_xor_ll(long long v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ i128 shfl_xor_i128(i128 v, int m) {
+  unsigned long long lo = (unsigned long long)v;
+  long long hi = (long long)(v >> 64);
+  lo = __shfl_xor_sync(0xffffffffu, lo, m);
+  hi = __shfl_xor_sync(0xffffffffu, hi, m);
+  return ((i128)hi << 64) | (i128)lo;
+}
+__device__ __forceinline__ long long shfl_xor_s(long long v, int m) { return shfl_xor_ll(v, m); }
+__device__ __forceinline__ i128 shfl_xor_s(i128 v, int m) { return shfl_xor_i128(v, m); }
+
+// Warp-wide argmax of (gain, community) with the tie rule; every lane ends
+// with the result.
+template <typename S>
+__device__ __forceinline__ void warp_argmax(S& g, int32_t& c) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    S g2 = shfl_xor_s(g, m);
+    int32_t c2 = __shfl_xor_sync(0xffffffffu, c, m);
+    if (better(g2, c2, g, c)) { g = g2; c = c2; }
+  }
+}
+
+// ---------------------------------------------------------------- hashing
+
+__device__ __forceinline__ uint32_t hash32(uint32_t x) {
+  x ^= x >> 16; x *= 0x7feb352du;
+  x ^= x >> 15; x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+
+// Open-addressing insert-or-add into a power-of-two table (shared or global
+// memory): keys int32 (kEmpty = free), values u64.  Returns false if the
+// table is full (the caller records kErrProbe).
+template <int CAP>
+__device__ __forceinline__ bool table_add_pow2(int32_t* keys, unsigned long long* vals, int32_t key,
+                                               unsigned long long w) {
+  uint32_t h = hash32((uint32_t)key) & (CAP - 1);
+#pragma unroll 1
+  for (int probe = 0; probe < CAP; ++probe) {
+    int32_t k = keys[h];
+    if (k == kEmpty) k = atomicCAS(&keys[h], kEmpty, key);
+    if (k == kEmpty || k == key) {
+      atomicAdd(&vals[h], w);
+      return true;
+    }
+    h = (h + 1) & (CAP - 1);
+  }
+  return false;
+}
+
+// Lookup in a power-of-two table; 0 if absent.
+template <int CAP>
+__device__ __forceinline__ unsigned long long table_get_pow2(const int32_t* keys, const unsigned long long* vals,
+                                                             int32_t key) {
+  uint32_t h = hash32((uint32_t)key) & (CAP - 1);
+#pragma unroll 1
+  for (int probe = 0; probe < CAP; ++probe) {
+    int32_t k = keys[h];
+    if (k == key) return vals[h];
+    if (k == kEmpty) return 0;
+    h = (h + 1) & (CAP - 1);
+  }
+  return 0;
+}
+
+// Same for a table of arbitrary capacity `cap` in global memory; the slot is
+// the high half of hash * cap.  `fresh` reports a key seen for the first time.
+__device__ __forceinline__ bool gtable_add(int32_t* keys, unsigned long long* vals, uint32_t cap, int32_t key,
+                                           unsigned long long w, bool* fresh) {
+  uint32_t h = __umulhi(hash32((uint32_t)key), cap);
+  *fresh = false;
+#pragma unroll 1
+  for (uint32_t probe = 0; probe < cap; ++probe) {
+    int32_t k = *(volatile int32_t*)&keys[h];
+    if (k == kEmpty) {
+      k = atomicCAS(&keys[h], kEmpty, key);
+      if (k == kEmpty) *fresh = true;
+    }
+    if (k == kEmpty || k == key) {
+      atomicAdd(&vals[h], w);
+      return true;
+    }
+    h = (h + 1 == cap) ? 0 : h + 1;
+  }
+  return false;
+}
+
+__device__ __forceinline__ unsigned long long gtable_get(const int32_t* keys, const unsigned long long* vals,
+                                                         uint32_t cap, int32_t key) {
+  uint32_t h = __umulhi(hash32((uint32_t)key), cap);
+#pragma unroll 1
+  for (uint32_t probe = 0; probe < cap; ++probe) {
+    int32_t k = keys[h];
+    if (k == key) return vals[h];
+    if (k == kEmpty) return 0;
+    h = (h + 1 == cap) ? 0 : h + 1;
+  }
+  return 0;
+}
+
+// ------------------------------------------------------ kernel parameters
+
+// What every local-moving launch needs for one (class, bucket) list.
+template <typename W>
+struct LMArgs {
+  const int64_t* off;
+  const int32_t* col;
+  const W* wt;
+  const long long* K;        // vertex degrees (row sums)
+  int32_t* memb;             // community of each vertex
+  long long* sig;            // community totals Sigma_c
+  int32_t* csize;            // community sizes (for the singleton guard)
+  const int32_t* stamp_r;    // active in this iteration iff stamp_r[i] == iter (when pruning)
+  int32_t* stamp_w;          // set to iter + 1 for vertices active in the next iteration
+  int2* moves;               // synchronous: (vertex, target) of every move of the class
+  DevCounters* ctr;
+  long long M;
+  int iter;
+  int prune;
+  int guard;
+  // hub path: per-hub global tables
+  int32_t* hkeys;
+  unsigned long long* hvals;
+  const int64_t* hbase;      // table offset of hub h (scan of capacities)
+  int32_t* hcount;           // distinct keys of hub h
+  int32_t* hslots;           // touched slots of hub h (at hbase[h])
+};
+
+}  // namespace gbl

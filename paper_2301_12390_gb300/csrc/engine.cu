@@ -1,0 +1,815 @@
+// engine.cu — the pass driver and the C ABI (include/louvain.h).
+//
+// A run follows Section 3.2 of the paper: passes of a local-moving phase
+// (iterations until the iteration gain is <= tolerance, at most
+// max_iterations) and an aggregation phase; tolerance divided by the decline
+// factor after every pass; the run ends after a pass with no move, a pass
+// whose modularity gain is <= pass_tolerance, or max_passes.  Every decision
+// that a floating-point value takes is made on exact integers converted
+// once: the iteration test is (2.0 * dbl(S)) / dbl(M^2) <= tolerance and the
+// pass test dbl(N_after - N_before) / dbl(M^2) <= pass_tolerance, dbl() the
+// correctly rounded int128 -> double conversion.
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+#include "engine.h"
+#include "../../include/louvain.h"
+
+using namespace gbl;
+
+namespace {
+
+struct IterRec {
+  int pass;
+  int64_t moves;
+  u128 S;
+};
+
+struct PassRec {
+  louvain_pass_info info;
+  std::vector<int32_t> level;
+  std::vector<int64_t> coff;
+  std::vector<int32_t> ccol;
+  std::vector<int64_t> cw;
+};
+
+}  // namespace
+
+struct louvain_ctx {
+  louvain_options opt;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+
+  // graph
+  bool loaded = false, ran = false;
+  int64_t n0 = 0, nnz0 = 0;
+  int64_t bytes = 0;
+  std::vector<void*> allocs;
+
+  // device buffers
+  int64_t* off0 = nullptr;
+  int32_t* col0 = nullptr;
+  int32_t* w0 = nullptr;
+  int64_t* offX[2] = {nullptr, nullptr};
+  int32_t* colX[2] = {nullptr, nullptr};
+  unsigned char* wX[2] = {nullptr, nullptr};   // int64-sized storage, used as int32 when M < 2^31
+  long long* K0 = nullptr;            // input row sums (for louvain_modularity)
+  long long* K = nullptr;
+  long long* Knext = nullptr;
+  int32_t* memb = nullptr;
+  long long* sig = nullptr;
+  int32_t* csize = nullptr;
+  int32_t* stamp[2] = {nullptr, nullptr};
+  int32_t* key = nullptr;
+  int32_t* list = nullptr;
+  int32_t* used = nullptr;
+  int32_t* newid = nullptr;
+  int32_t* level = nullptr;
+  int32_t* top = nullptr;
+  int2* moves = nullptr;
+  int64_t* key_off = nullptr;
+  int64_t* cnt = nullptr;
+  int64_t* cstart = nullptr;
+  int64_t* fill = nullptr;
+  int32_t* members = nullptr;
+  int64_t* mdeg = nullptr;
+  int64_t* mpre = nullptr;
+  int64_t* rlen = nullptr;
+  int32_t* tcol = nullptr;
+  unsigned char* tw = nullptr;
+  int32_t* gkeys = nullptr;
+  unsigned long long* gvals = nullptr;
+  int32_t* gslots = nullptr;
+  int32_t* gcount = nullptr;
+  int64_t* gbase = nullptr;
+  int64_t* chunk_pre = nullptr;
+  unsigned char* tmp = nullptr;
+  size_t tmp_bytes = 0;
+  int64_t M0 = 0;                      // total weight of the loaded graph
+  DevCounters* ctr = nullptr;
+  unsigned long long* acc = nullptr;   // 8 words of reduction scratch
+  int* flags = nullptr;
+  int64_t* scal = nullptr;             // small device scalars
+  // pinned host mirror
+  DevCounters* h_ctr = nullptr;
+  unsigned long long* h_acc = nullptr;
+  int64_t* h_scal = nullptr;
+
+  // results
+  int64_t M = 0;
+  i128 qnum = 0;
+  double Q = 0.0;
+  int64_t k_final = 0;
+  std::vector<IterRec> iters;
+  std::vector<PassRec> passes;
+  louvain_stats stats;
+  cudaEvent_t ev[8] = {};
+};
+
+namespace {
+
+int fail(louvain_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                                    \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess)                                                                          \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? LOUVAIN_ERR_OOM : LOUVAIN_ERR_CUDA,          \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                             \
+  } while (0)
+
+#define CKLAUNCH() CK(cudaGetLastError())
+
+double dbl(i128 x) { return (double)x; }
+
+void free_all(louvain_ctx* c) {
+  for (void* p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+  c->bytes = 0;
+  c->loaded = false;
+  c->ran = false;
+}
+
+template <typename T>
+int dalloc(louvain_ctx* c, T** p, int64_t count) {
+  size_t b = (size_t)(count > 0 ? count : 1) * sizeof(T);
+  b = (b + 255) & ~(size_t)255;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, b);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, LOUVAIN_ERR_OOM, "cudaMalloc of " + std::to_string(b) + " bytes failed");
+  }
+  c->allocs.push_back(q);
+  c->bytes += (int64_t)b;
+  *p = (T*)q;
+  return 0;
+}
+
+#define ALLOC(ptr, count)                          \
+  do {                                             \
+    int r_ = dalloc(c, &(ptr), (int64_t)(count));  \
+    if (r_) { free_all(c); return r_; }            \
+  } while (0)
+
+int check_options(const louvain_options* o) {
+  if (o->mode != LOUVAIN_SYNC && o->mode != LOUVAIN_ASYNC) return 1;
+  if (!(o->tolerance >= 0) || !(o->tolerance_decline > 0) || !(o->pass_tolerance == o->pass_tolerance)) return 1;
+  if (o->max_iterations < 1 || o->max_passes < 0 || o->max_passes > 64) return 1;
+  if (o->subrounds < 1 || o->subrounds > 64) return 1;
+  return 0;
+}
+
+// Copy a small device array to host (synchronises the stream).
+int fetch(louvain_ctx* c, void* host, const void* dev, size_t bytes) {
+  CK(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return 0;
+}
+
+// --------------------------------------------------------------- a pass
+
+struct PassState {
+  int64_t n, nnz;
+  int64_t* off;
+  int32_t* col;
+  void* w;
+  int widx;   // which coarse buffer holds this graph (-1 = input)
+};
+
+template <typename W>
+int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool wide, int64_t* pass_moves,
+                 int* iters_out, int64_t* edges_out) {
+  const int P = c->opt.subrounds;
+  const bool async = c->opt.mode == LOUVAIN_ASYNC;
+  const int nkeys = kBuckets * P + 1;
+  cudaStream_t s = c->stream;
+  // bucket lists: key = bucket * P + class
+  lm_keys(g.off, g.n, P, c->key, s);
+  stable_partition(c->key, g.n, nkeys, c->list, c->key_off, c->tmp, s);
+  CKLAUNCH();
+  std::vector<int64_t> ko(nkeys + 1);
+  if (int r = fetch(c, ko.data(), c->key_off, ko.size() * sizeof(int64_t))) return r;
+  // hubs: all classes' hub lists are contiguous
+  const int64_t hub0 = ko[kHubBucket * P], hub1 = ko[kHubBucket * P + P];
+  const int64_t nhubs = hub1 - hub0;
+  std::vector<int64_t> hchunks;
+  if (nhubs > 0) {
+    hub_layout(g.off, c->list + hub0, nhubs, c->gbase, c->chunk_pre, c->tmp, s);
+    CKLAUNCH();
+    hchunks.resize(nhubs + 1);
+    if (int r = fetch(c, hchunks.data(), c->chunk_pre, hchunks.size() * sizeof(int64_t))) return r;
+  }
+  LMArgs<W> a;
+  memset(&a, 0, sizeof(a));
+  a.off = g.off;
+  a.col = g.col;
+  a.wt = (const W*)g.w;
+  a.K = c->K;
+  a.memb = c->memb;
+  a.sig = c->sig;
+  a.csize = c->csize;
+  a.moves = c->moves;
+  a.ctr = c->ctr;
+  a.M = c->M;
+  a.prune = c->opt.prune;
+  a.guard = c->opt.singleton_guard;
+  a.hkeys = c->gkeys;
+  a.hvals = c->gvals;
+  a.hslots = c->gslots;
+  const i128 M2 = (i128)c->M * c->M;
+  int64_t moves_total = 0, edges_total = 0;
+  int it = 0;
+  for (; it < c->opt.max_iterations; ++it) {
+    CK(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), s));
+    a.iter = it;
+    a.stamp_r = c->stamp[it & 1];
+    a.stamp_w = c->stamp[(it + 1) & 1];
+    for (int ch = 0; ch < P; ++ch) {
+      for (int b = 0; b < kHubBucket; ++b) {
+        int64_t s0 = ko[b * P + ch], s1 = ko[b * P + ch + 1];
+        lm_launch_bucket<W>(a, wide, async, b, c->list + s0, (int)(s1 - s0), s);
+      }
+      int64_t h0 = ko[kHubBucket * P + ch] - hub0, h1 = ko[kHubBucket * P + ch + 1] - hub0;
+      if (h1 > h0) {
+        LMArgs<W> ah = a;
+        ah.hbase = c->gbase + h0;
+        ah.hcount = c->gcount + h0;
+        lm_launch_hubs<W>(ah, wide, async, c->list + hub0 + h0, (int)(h1 - h0), c->chunk_pre + h0,
+                          hchunks[h1] - hchunks[h0], s);
+      }
+      if (!async) {
+        int64_t cls = 0;
+        for (int b = 0; b <= kHubBucket; ++b) cls += ko[b * P + ch + 1] - ko[b * P + ch];
+        lm_launch_commit<W>(a, cls, s);
+      }
+      CKLAUNCH();
+    }
+    if (int r = fetch(c, c->h_ctr, c->ctr, sizeof(DevCounters))) return r;
+    if (c->h_ctr->error) return fail(c, LOUVAIN_ERR_INTERNAL, "local-moving: hash table overflow");
+    u128 S = ((u128)c->h_ctr->s_hi << 64) | (u128)c->h_ctr->s_lo;
+    int64_t mv = (int64_t)c->h_ctr->moves;
+    c->iters.push_back(IterRec{pass, mv, S});
+    moves_total += mv;
+    edges_total += (int64_t)c->h_ctr->edges;
+    if ((2.0 * (double)S) / dbl(M2) <= tol) { ++it; break; }
+  }
+  *pass_moves = moves_total;
+  *iters_out = it;
+  *edges_out = edges_total;
+  return 0;
+}
+
+// Exact Q numerator of the current membership on the pass graph.
+template <typename W>
+int q_numerator(louvain_ctx* c, const PassState& g, i128* out) {
+  CK(cudaMemsetAsync(c->acc, 0, 4 * sizeof(unsigned long long), c->stream));
+  modularity_parts<W>(g.off, g.col, (const W*)g.w, g.n, c->memb, c->sig, c->acc, c->stream);
+  CKLAUNCH();
+  if (int r = fetch(c, c->h_acc, c->acc, 4 * sizeof(unsigned long long))) return r;
+  u128 L = ((u128)c->h_acc[3] << 64) | (u128)c->h_acc[0];
+  u128 SS = ((u128)c->h_acc[2] << 64) | (u128)c->h_acc[1];
+  *out = (i128)c->M * (i128)L - (i128)SS;
+  return 0;
+}
+
+template <typename W, typename W2>
+int aggregate(louvain_ctx* c, const PassState& g, int64_t k, PassState* next) {
+  cudaStream_t s = c->stream;
+  const int dst = g.widx == 0 ? 1 : 0;
+  coarse_degrees(c->used, c->newid, c->sig, g.n, c->Knext, s);
+  agg_group_members(c->level, g.n, k, c->cnt, c->cstart, c->fill, c->members, c->tmp, s);
+  agg_member_prefix(g.off, c->members, g.n, c->mdeg, c->mpre, c->tmp, s);
+  agg_keys(c->cstart, c->mpre, k, c->key, s);
+  stable_partition(c->key, k, kAggBuckets + 1, c->list, c->key_off, c->tmp, s);
+  CKLAUNCH();
+  int64_t ko[kAggBuckets + 2];
+  if (int r = fetch(c, ko, c->key_off, sizeof(ko))) return r;
+  CK(cudaMemsetAsync(c->flags, 0, sizeof(int), s));
+  AggArgs a;
+  a.off = g.off;
+  a.col = g.col;
+  a.wt = g.w;
+  a.level = c->level;
+  a.n = g.n;
+  a.k = k;
+  a.cstart = c->cstart;
+  a.members = c->members;
+  a.mpre = c->mpre;
+  a.tcol = c->tcol;
+  a.tw = c->tw;
+  a.rlen = c->rlen;
+  a.gkeys = c->gkeys;
+  a.gvals = c->gvals;
+  a.gcount = c->gcount;
+  a.gslots = c->gslots;
+  a.error = c->flags;
+  // communities whose members have no edge get empty rows
+  CK(cudaMemsetAsync(c->rlen, 0, (k + 1) * sizeof(int64_t), s));
+  for (int b = 0; b < kAggGlobal; ++b)
+    agg_launch_bucket<W, W2>(a, b, c->list + ko[b], (int)(ko[b + 1] - ko[b]), s);
+  const int64_t ng = ko[kAggGlobal + 1] - ko[kAggGlobal];
+  if (ng > 0) {
+    agg_global_layout(c->cstart, c->mpre, c->list + ko[kAggGlobal], ng, c->gbase, c->chunk_pre, c->tmp, s);
+    int64_t nchunks = 0;
+    CKLAUNCH();
+    if (int r = fetch(c, &nchunks, c->chunk_pre + ng, sizeof(int64_t))) return r;
+    agg_launch_global<W, W2>(a, c->list + ko[kAggGlobal], (int)ng, c->gbase, c->chunk_pre, nchunks, s);
+  }
+  CKLAUNCH();
+  // coarse offsets = scan of row lengths, written straight into the next graph
+  scan_i64(c->rlen, c->offX[dst], k, c->offX[dst] + k, c->tmp, s);
+  CKLAUNCH();
+  int64_t nnz2 = 0;
+  if (int r = fetch(c, &nnz2, c->offX[dst] + k, sizeof(int64_t))) return r;
+  int flag = 0;
+  if (int r = fetch(c, &flag, c->flags, sizeof(int))) return r;
+  if (flag) return fail(c, LOUVAIN_ERR_INTERNAL, "aggregation: hash table overflow");
+  agg_compact<W2>(c->cstart, c->mpre, c->rlen, c->offX[dst], k, c->tcol, (const W2*)c->tw, c->colX[dst],
+                  (W2*)c->wX[dst], s);
+  CKLAUNCH();
+  next->n = k;
+  next->nnz = nnz2;
+  next->off = c->offX[dst];
+  next->col = c->colX[dst];
+  next->w = (void*)c->wX[dst];
+  next->widx = dst;
+  return 0;
+}
+
+template <typename W2>
+int record_coarse(louvain_ctx* c, PassRec& pr, const PassState& h) {
+  pr.coff.resize(h.n + 1);
+  pr.ccol.resize(h.nnz);
+  pr.cw.resize(h.nnz);
+  std::vector<W2> w(h.nnz);
+  CK(cudaMemcpyAsync(pr.coff.data(), h.off, (h.n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+  if (h.nnz) {
+    CK(cudaMemcpyAsync(pr.ccol.data(), h.col, h.nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(w.data(), h.w, h.nnz * sizeof(W2), cudaMemcpyDeviceToHost, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  for (int64_t i = 0; i < h.nnz; ++i) pr.cw[i] = (int64_t)w[i];
+  return 0;
+}
+
+// One pass on graph g (weights W), coarse graphs use W2.  Returns 0 and sets
+// *stop; on continuing, *next holds the coarse graph.
+template <typename W, typename W2>
+int run_pass(louvain_ctx* c, const PassState& g, int pass, double* tol, bool wide, bool* stop, PassState* next) {
+  cudaStream_t s = c->stream;
+  PassRec pr;
+  memset(&pr.info, 0, sizeof(pr.info));
+  pr.info.n = g.n;
+  pr.info.nnz = g.nnz;
+  CK(cudaEventRecord(c->ev[0], s));
+  pass_init(g.n, c->K, c->memb, c->sig, c->csize, c->stamp[0], c->stamp[1], s);
+  CKLAUNCH();
+  const i128 nbefore = c->qnum;
+  const i128 M2 = (i128)c->M * c->M;
+  int64_t pmoves = 0, edges = 0;
+  int iters = 0;
+  CK(cudaEventRecord(c->ev[1], s));
+  if (int r = local_moving<W>(c, g, pass, *tol, wide, &pmoves, &iters, &edges)) return r;
+  CK(cudaEventRecord(c->ev[2], s));
+  pr.info.moves = pmoves;
+  pr.info.iterations = iters;
+  pr.info.n_before_hi = (int64_t)(nbefore >> 64);
+  pr.info.n_before_lo = (uint64_t)nbefore;
+  c->stats.lm_edges += edges;
+  c->stats.moves += pmoves;
+  c->stats.iterations += iters;
+  c->stats.passes = pass + 1;
+  float ms_init = 0, ms_lm = 0;
+  if (pmoves == 0) {
+    CK(cudaEventSynchronize(c->ev[2]));
+    cudaEventElapsedTime(&ms_init, c->ev[0], c->ev[1]);
+    cudaEventElapsedTime(&ms_lm, c->ev[1], c->ev[2]);
+    pr.info.k = g.n;
+    pr.info.n_after_hi = pr.info.n_before_hi;
+    pr.info.n_after_lo = pr.info.n_before_lo;
+    pr.info.lm_ms = ms_lm;
+    c->stats.lm_ms += ms_lm;
+    c->stats.other_ms += ms_init;
+    c->passes.push_back(std::move(pr));
+    *stop = true;
+    return 0;
+  }
+  // renumber by ascending old id and compose the top level
+  mark_used(c->memb, g.n, c->used, s);
+  scan_i32(c->used, c->newid, g.n, c->scal, c->tmp, s);
+  apply_level(c->memb, c->newid, g.n, c->level, s);
+  compose_top(c->top, c->n0, c->level, s);
+  CKLAUNCH();
+  int64_t k = 0;
+  if (int r = fetch(c, &k, c->scal, sizeof(int64_t))) return r;
+  i128 nafter = 0;
+  if (int r = q_numerator<W>(c, g, &nafter)) return r;
+  CK(cudaEventRecord(c->ev[3], s));
+  pr.info.k = k;
+  pr.info.n_after_hi = (int64_t)(nafter >> 64);
+  pr.info.n_after_lo = (uint64_t)nafter;
+  pr.info.level_recorded = c->opt.record_levels ? 1 : 0;
+  if (c->opt.record_levels) {
+    pr.level.resize(g.n);
+    CK(cudaMemcpyAsync(pr.level.data(), c->level, g.n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  c->qnum = nafter;
+  c->k_final = k;
+  *stop = dbl(nafter - nbefore) / dbl(M2) <= c->opt.pass_tolerance || pass + 1 == c->opt.max_passes;
+  float ms_agg = 0;
+  if (!*stop) {
+    if (int r = aggregate<W, W2>(c, g, k, next)) return r;
+    CK(cudaEventRecord(c->ev[4], s));
+    pr.info.coarse_built = 1;
+    pr.info.coarse_nnz = next->nnz;
+    if (c->opt.record_levels)
+      if (int r = record_coarse<W2>(c, pr, *next)) return r;
+    CK(cudaEventSynchronize(c->ev[4]));
+    cudaEventElapsedTime(&ms_agg, c->ev[2], c->ev[4]);
+    *tol = *tol / c->opt.tolerance_decline;
+  } else {
+    CK(cudaEventSynchronize(c->ev[3]));
+    cudaEventElapsedTime(&ms_agg, c->ev[2], c->ev[3]);
+  }
+  cudaEventElapsedTime(&ms_init, c->ev[0], c->ev[1]);
+  cudaEventElapsedTime(&ms_lm, c->ev[1], c->ev[2]);
+  pr.info.lm_ms = ms_lm;
+  pr.info.agg_ms = ms_agg;
+  c->stats.lm_ms += ms_lm;
+  c->stats.agg_ms += ms_agg;
+  c->stats.other_ms += ms_init;
+  c->passes.push_back(std::move(pr));
+  return 0;
+}
+
+int run_all(louvain_ctx* c) {
+  cudaStream_t s = c->stream;
+  c->iters.clear();
+  c->passes.clear();
+  memset(&c->stats, 0, sizeof(c->stats));
+  c->qnum = 0;
+  c->Q = 0;
+  c->k_final = c->n0;
+  CK(cudaEventRecord(c->ev[6], s));
+  iota_i32(c->top, c->n0, s);
+  // pass-0 degrees, M and the singleton numerator
+  CK(cudaMemsetAsync(c->acc, 0, 8 * sizeof(unsigned long long), s));
+  row_sums<int32_t>(c->off0, c->col0, c->w0, c->n0, c->K, c->acc + 4, s);
+  CKLAUNCH();
+  if (int r = fetch(c, c->h_acc, c->acc, 8 * sizeof(unsigned long long))) return r;
+  if (c->h_acc[5] != 0 || c->h_acc[4] >= (1ull << 62))
+    return fail(c, LOUVAIN_ERR_OVERFLOW, "total weight M must be below 2^62");
+  c->M = (int64_t)c->h_acc[4];
+  const bool wide = c->M >= (1ll << 31);           // M^2 >= 2^62: 128-bit gains
+  const bool coarse64 = c->M >= (1ll << 31) - 1;   // coarse weights can exceed int32
+  PassState g{c->n0, c->nnz0, c->off0, c->col0, (void*)c->w0, -1};
+  pass_init(g.n, c->K, c->memb, c->sig, c->csize, c->stamp[0], c->stamp[1], s);
+  if (int r = q_numerator<int32_t>(c, g, &c->qnum)) return r;
+  double tol = c->opt.tolerance;
+  for (int p = 0; p < c->opt.max_passes && c->M > 0; ++p) {
+    bool stop = false;
+    PassState next{};
+    int r;
+    if (g.widx < 0)
+      r = coarse64 ? run_pass<int32_t, int64_t>(c, g, p, &tol, wide, &stop, &next)
+                   : run_pass<int32_t, int32_t>(c, g, p, &tol, wide, &stop, &next);
+    else
+      r = coarse64 ? run_pass<int64_t, int64_t>(c, g, p, &tol, wide, &stop, &next)
+                   : run_pass<int32_t, int32_t>(c, g, p, &tol, wide, &stop, &next);
+    if (r) return r;
+    if (stop) break;
+    std::swap(c->K, c->Knext);
+    g = next;
+  }
+  CK(cudaEventRecord(c->ev[7], s));
+  CK(cudaEventSynchronize(c->ev[7]));
+  float tot = 0;
+  cudaEventElapsedTime(&tot, c->ev[6], c->ev[7]);
+  c->stats.total_ms = tot;
+  const i128 M2 = (i128)c->M * c->M;
+  c->Q = c->M == 0 ? 0.0 : dbl(c->qnum) / dbl(M2);
+  c->stats.q = c->Q;
+  c->stats.communities = c->k_final;
+  return 0;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+
+extern "C" {
+
+int louvain_default_options(louvain_options* o) {
+  if (!o) return LOUVAIN_ERR_INVALID_ARG;
+  memset(o, 0, sizeof(*o));
+  o->mode = LOUVAIN_SYNC;
+  o->tolerance = 0.01;
+  o->tolerance_decline = 10.0;
+  o->pass_tolerance = 0.0;
+  o->max_iterations = 20;
+  o->max_passes = 10;
+  o->prune = 0;
+  o->singleton_guard = 1;
+  o->subrounds = 1;
+  o->validate = 1;
+  o->record_levels = 0;
+  return 0;
+}
+
+int louvain_create(louvain_ctx** out, const louvain_options* opt, int device, void* cuda_stream) {
+  if (!out) return LOUVAIN_ERR_INVALID_ARG;
+  *out = nullptr;
+  louvain_ctx* c = new louvain_ctx();
+  if (opt) c->opt = *opt; else louvain_default_options(&c->opt);
+  if (check_options(&c->opt)) { delete c; return LOUVAIN_ERR_INVALID_ARG; }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    delete c;
+    return LOUVAIN_ERR_CUDA;
+  }
+  c->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) { delete c; return LOUVAIN_ERR_CUDA; }
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return LOUVAIN_ERR_CUDA; }
+    c->own_stream = true;
+  }
+  for (auto& e : c->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) { delete c; return LOUVAIN_ERR_CUDA; }
+  if (cudaMallocHost(&c->h_ctr, sizeof(DevCounters)) != cudaSuccess ||
+      cudaMallocHost(&c->h_acc, 8 * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMallocHost(&c->h_scal, 8 * sizeof(int64_t)) != cudaSuccess) {
+    delete c;
+    return LOUVAIN_ERR_OOM;
+  }
+  memset(&c->stats, 0, sizeof(c->stats));
+  *out = c;
+  return 0;
+}
+
+int louvain_set_options(louvain_ctx* c, const louvain_options* opt) {
+  if (!c || !opt) return LOUVAIN_ERR_INVALID_ARG;
+  if (check_options(opt)) return fail(c, LOUVAIN_ERR_INVALID_ARG, "invalid options");
+  c->opt = *opt;
+  return 0;
+}
+
+int louvain_load_csr(louvain_ctx* c, int64_t n, int64_t nnz, const int64_t* offsets, const int32_t* cols,
+                     const int32_t* weights, int ptr_kind) {
+  if (!c) return LOUVAIN_ERR_INVALID_ARG;
+  if (n < 0 || nnz < 0 || (ptr_kind != LOUVAIN_PTR_HOST && ptr_kind != LOUVAIN_PTR_DEVICE))
+    return fail(c, LOUVAIN_ERR_INVALID_ARG, "negative size or bad pointer kind");
+  if (!offsets || (nnz > 0 && (!cols || !weights))) return fail(c, LOUVAIN_ERR_INVALID_ARG, "null pointer");
+  if (n >= (1ll << 31) - 1) return fail(c, LOUVAIN_ERR_OVERFLOW, "n must be below 2^31 - 1");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, LOUVAIN_ERR_CUDA, "cudaSetDevice failed");
+  if (ptr_kind == LOUVAIN_PTR_HOST) {
+    // cheap host checks first
+    if (offsets[0] != 0 || offsets[n] != nnz) return fail(c, LOUVAIN_ERR_BAD_CSR, "offsets[0] != 0 or offsets[n] != nnz");
+  }
+  free_all(c);
+  c->n0 = n;
+  c->nnz0 = nnz;
+  const int64_t N1 = n + 1;
+  ALLOC(c->off0, N1);
+  ALLOC(c->col0, nnz);
+  ALLOC(c->w0, nnz);
+  for (int i = 0; i < 2; ++i) {
+    ALLOC(c->offX[i], N1);
+    ALLOC(c->colX[i], nnz);
+    ALLOC(c->wX[i], nnz * 8);   // bytes
+  }
+  ALLOC(c->K0, n);
+  ALLOC(c->K, n);
+  ALLOC(c->Knext, n);
+  ALLOC(c->memb, n);
+  ALLOC(c->sig, n);
+  ALLOC(c->csize, n);
+  ALLOC(c->stamp[0], n);
+  ALLOC(c->stamp[1], n);
+  ALLOC(c->key, n);
+  ALLOC(c->list, n);
+  ALLOC(c->used, n);
+  ALLOC(c->newid, n);
+  ALLOC(c->level, n);
+  ALLOC(c->top, n);
+  ALLOC(c->moves, n);
+  ALLOC(c->key_off, kBuckets * 64 + 8);
+  ALLOC(c->cnt, N1);
+  ALLOC(c->cstart, N1);
+  ALLOC(c->fill, N1);
+  ALLOC(c->members, n);
+  ALLOC(c->mdeg, n);
+  ALLOC(c->mpre, N1);
+  ALLOC(c->rlen, N1);
+  ALLOC(c->tcol, nnz);
+  ALLOC(c->tw, nnz * 8);
+  ALLOC(c->gkeys, 2 * nnz);
+  ALLOC(c->gvals, 2 * nnz);
+  ALLOC(c->gslots, 2 * nnz);
+  ALLOC(c->gcount, N1);
+  ALLOC(c->gbase, N1);
+  ALLOC(c->chunk_pre, N1);
+  {
+    size_t t1 = partition_tmp_bytes(n, kBuckets * 64 + 1);
+    size_t t2 = (size_t)N1 * 16 + scan_tmp_bytes(N1);
+    size_t t3 = scan_tmp_bytes(nnz + 1);
+    c->tmp_bytes = std::max(t1, std::max(t2, t3));
+    ALLOC(c->tmp, (int64_t)c->tmp_bytes);
+  }
+  ALLOC(c->ctr, 1);
+  ALLOC(c->acc, 8);
+  ALLOC(c->flags, 4);
+  ALLOC(c->scal, 8);
+  cudaStream_t s = c->stream;
+  cudaMemcpyKind kind = ptr_kind == LOUVAIN_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(c->off0, offsets, N1 * sizeof(int64_t), kind, s));
+  if (nnz) {
+    CK(cudaMemcpyAsync(c->col0, cols, nnz * sizeof(int32_t), kind, s));
+    CK(cudaMemcpyAsync(c->w0, weights, nnz * sizeof(int32_t), kind, s));
+  }
+  CK(cudaMemsetAsync(c->gkeys, 0xff, 2 * nnz * sizeof(int32_t), s));
+  CK(cudaMemsetAsync(c->gvals, 0, 2 * nnz * sizeof(unsigned long long), s));
+  CK(cudaMemsetAsync(c->gcount, 0, N1 * sizeof(int32_t), s));
+  if (c->opt.validate) {
+    validate_csr(c->off0, c->col0, c->w0, n, nnz, c->flags, c->acc, s);
+    CKLAUNCH();
+    int flags = 0;
+    unsigned long long h[2];
+    if (int r = fetch(c, &flags, c->flags, sizeof(int))) { free_all(c); return r; }
+    if (int r = fetch(c, h, c->acc, sizeof(h))) { free_all(c); return r; }
+    if (flags & 1) { free_all(c); return fail(c, LOUVAIN_ERR_BAD_CSR, "offsets not monotone or wrong ends"); }
+    if (flags & 2) { free_all(c); return fail(c, LOUVAIN_ERR_BAD_CSR, "column index out of range"); }
+    if (flags & 4) { free_all(c); return fail(c, LOUVAIN_ERR_BAD_CSR, "weight <= 0"); }
+    if (h[0] != h[1]) { free_all(c); return fail(c, LOUVAIN_ERR_NOT_SYMMETRIC, "CSR is not symmetric"); }
+  }
+  // input degrees (for louvain_modularity)
+  CK(cudaMemsetAsync(c->acc, 0, 8 * sizeof(unsigned long long), s));
+  row_sums<int32_t>(c->off0, c->col0, c->w0, n, c->K0, c->acc, s);
+  CKLAUNCH();
+  if (int r = fetch(c, c->h_acc, c->acc, 4 * sizeof(unsigned long long))) { free_all(c); return r; }
+  if (c->h_acc[1] != 0 || c->h_acc[0] >= (1ull << 62)) {
+    free_all(c);
+    return fail(c, LOUVAIN_ERR_OVERFLOW, "total weight M must be below 2^62");
+  }
+  c->M0 = (int64_t)c->h_acc[0];
+  c->loaded = true;
+  c->ran = false;
+  return 0;
+}
+
+int louvain_run(louvain_ctx* c) {
+  if (!c) return LOUVAIN_ERR_INVALID_ARG;
+  if (!c->loaded) return fail(c, LOUVAIN_ERR_STATE, "no graph loaded");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, LOUVAIN_ERR_CUDA, "cudaSetDevice failed");
+  c->ran = false;
+  int r = run_all(c);
+  if (r) return r;
+  c->ran = true;
+  return 0;
+}
+
+int louvain_get_membership(louvain_ctx* c, int32_t* out, int64_t n, int ptr_kind) {
+  if (!c) return LOUVAIN_ERR_INVALID_ARG;
+  if (!c->ran) return fail(c, LOUVAIN_ERR_STATE, "no result (run first)");
+  if (n != c->n0 || (!out && n > 0)) return fail(c, LOUVAIN_ERR_INVALID_ARG, "n must equal the loaded n");
+  if (n == 0) return 0;
+  cudaMemcpyKind kind = ptr_kind == LOUVAIN_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(out, c->top, n * sizeof(int32_t), kind, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return 0;
+}
+
+int louvain_get_modularity(louvain_ctx* c, double* q) {
+  if (!c || !q) return LOUVAIN_ERR_INVALID_ARG;
+  if (!c->ran) return fail(c, LOUVAIN_ERR_STATE, "no result (run first)");
+  *q = c->Q;
+  return 0;
+}
+
+int louvain_get_modularity_exact(louvain_ctx* c, int64_t* num_hi, uint64_t* num_lo, int64_t* M) {
+  if (!c || !num_hi || !num_lo || !M) return LOUVAIN_ERR_INVALID_ARG;
+  if (!c->ran) return fail(c, LOUVAIN_ERR_STATE, "no result (run first)");
+  *num_hi = (int64_t)(c->qnum >> 64);
+  *num_lo = (uint64_t)c->qnum;
+  *M = c->M;
+  return 0;
+}
+
+int louvain_modularity(louvain_ctx* c, const int32_t* memb, int64_t n, int ptr_kind, double* q, int64_t* num_hi,
+                       uint64_t* num_lo, int64_t* Mout) {
+  if (!c || !q) return LOUVAIN_ERR_INVALID_ARG;
+  if (!c->loaded) return fail(c, LOUVAIN_ERR_STATE, "no graph loaded");
+  if (n != c->n0 || (!memb && n > 0)) return fail(c, LOUVAIN_ERR_INVALID_ARG, "n must equal the loaded n");
+  cudaStream_t s = c->stream;
+  if (ptr_kind == LOUVAIN_PTR_HOST) {
+    for (int64_t i = 0; i < n; ++i)
+      if (memb[i] < 0 || memb[i] >= n) return fail(c, LOUVAIN_ERR_INVALID_ARG, "membership out of range");
+  }
+  cudaMemcpyKind kind = ptr_kind == LOUVAIN_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (n) CK(cudaMemcpyAsync(c->used, memb, n * sizeof(int32_t), kind, s));
+  community_totals(c->K0, c->used, n, c->Knext, s);
+  CK(cudaMemsetAsync(c->acc, 0, 8 * sizeof(unsigned long long), s));
+  modularity_parts<int32_t>(c->off0, c->col0, c->w0, n, c->used, c->Knext, c->acc, s);
+  CKLAUNCH();
+  if (int r = fetch(c, c->h_acc, c->acc, 4 * sizeof(unsigned long long))) return r;
+  const int64_t M = c->M0;
+  u128 L = ((u128)c->h_acc[3] << 64) | (u128)c->h_acc[0];
+  u128 SS = ((u128)c->h_acc[2] << 64) | (u128)c->h_acc[1];
+  i128 N = (i128)M * (i128)L - (i128)SS;
+  *q = M == 0 ? 0.0 : dbl(N) / dbl((i128)M * M);
+  if (num_hi) *num_hi = (int64_t)(N >> 64);
+  if (num_lo) *num_lo = (uint64_t)N;
+  if (Mout) *Mout = M;
+  return 0;
+}
+
+int louvain_get_stats(louvain_ctx* c, louvain_stats* out) {
+  if (!c || !out) return LOUVAIN_ERR_INVALID_ARG;
+  if (!c->ran) return fail(c, LOUVAIN_ERR_STATE, "no result (run first)");
+  *out = c->stats;
+  return 0;
+}
+
+int louvain_get_pass_info(louvain_ctx* c, int pass, louvain_pass_info* out) {
+  if (!c || !out) return LOUVAIN_ERR_INVALID_ARG;
+  if (!c->ran) return fail(c, LOUVAIN_ERR_STATE, "no result (run first)");
+  if (pass < 0 || pass >= (int)c->passes.size()) return fail(c, LOUVAIN_ERR_INVALID_ARG, "no such pass");
+  *out = c->passes[pass].info;
+  return 0;
+}
+
+int louvain_get_iteration(louvain_ctx* c, int64_t t, int64_t out[4]) {
+  if (!c || !out) return LOUVAIN_ERR_INVALID_ARG;
+  if (!c->ran) return fail(c, LOUVAIN_ERR_STATE, "no result (run first)");
+  if (t < 0 || t >= (int64_t)c->iters.size()) return fail(c, LOUVAIN_ERR_INVALID_ARG, "no such iteration");
+  const IterRec& r = c->iters[t];
+  out[0] = r.pass;
+  out[1] = r.moves;
+  out[2] = (int64_t)(r.S >> 64);
+  out[3] = (int64_t)(uint64_t)r.S;
+  return 0;
+}
+
+int louvain_get_level(louvain_ctx* c, int pass, int32_t* out, int64_t n) {
+  if (!c || !out) return LOUVAIN_ERR_INVALID_ARG;
+  if (!c->ran) return fail(c, LOUVAIN_ERR_STATE, "no result (run first)");
+  if (pass < 0 || pass >= (int)c->passes.size() || !c->passes[pass].info.level_recorded)
+    return fail(c, LOUVAIN_ERR_STATE, "level not recorded (record_levels = 1)");
+  const PassRec& p = c->passes[pass];
+  if (n != (int64_t)p.level.size()) return fail(c, LOUVAIN_ERR_INVALID_ARG, "n must equal the pass graph size");
+  memcpy(out, p.level.data(), n * sizeof(int32_t));
+  return 0;
+}
+
+int louvain_get_coarse(louvain_ctx* c, int pass, int64_t* off, int64_t k, int32_t* col, int64_t* w, int64_t nnz) {
+  if (!c || !off) return LOUVAIN_ERR_INVALID_ARG;
+  if (!c->ran) return fail(c, LOUVAIN_ERR_STATE, "no result (run first)");
+  if (pass < 0 || pass >= (int)c->passes.size() || !c->passes[pass].info.coarse_built || c->passes[pass].coff.empty())
+    return fail(c, LOUVAIN_ERR_STATE, "coarse graph not recorded (record_levels = 1)");
+  const PassRec& p = c->passes[pass];
+  if (k + 1 != (int64_t)p.coff.size() || nnz != (int64_t)p.ccol.size())
+    return fail(c, LOUVAIN_ERR_INVALID_ARG, "sizes must equal the coarse graph's");
+  memcpy(off, p.coff.data(), (k + 1) * sizeof(int64_t));
+  if (nnz) {
+    if (!col || !w) return LOUVAIN_ERR_INVALID_ARG;
+    memcpy(col, p.ccol.data(), nnz * sizeof(int32_t));
+    memcpy(w, p.cw.data(), nnz * sizeof(int64_t));
+  }
+  return 0;
+}
+
+int louvain_get_device_bytes(louvain_ctx* c, int64_t* bytes) {
+  if (!c || !bytes) return LOUVAIN_ERR_INVALID_ARG;
+  *bytes = c->bytes;
+  return 0;
+}
+
+void louvain_destroy(louvain_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_all(c);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  if (c->h_ctr) cudaFreeHost(c->h_ctr);
+  if (c->h_acc) cudaFreeHost(c->h_acc);
+  if (c->h_scal) cudaFreeHost(c->h_scal);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+const char* louvain_last_error(const louvain_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+const char* louvain_version(void) { return "gb-louvain 0.1 (sm_103a)"; }
+
+}  // extern "C"

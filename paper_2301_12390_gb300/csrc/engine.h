@@ -1,0 +1,129 @@
+// engine.h — host-side declarations shared by the engine's translation units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace gbl {
+
+// Degree classes of the local-moving phase (see local_move.cu).
+constexpr int kBuckets = 6;          // 0 thread, 1 warp/64, 2 warp/256, 3 block/2k, 4 block/8k, 5 hub
+constexpr int kHubBucket = 5;
+__host__ __device__ inline int lm_bucket_of(int64_t deg) {
+  return deg <= 0 ? -1 : deg <= 8 ? 0 : deg <= 32 ? 1 : deg <= 128 ? 2 : deg <= 1024 ? 3 : deg <= 4096 ? 4 : 5;
+}
+constexpr int64_t kHubChunkEntries = 2048;
+
+// Community classes of the aggregation phase by total member degree.
+constexpr int kAggBuckets = 5;       // 0 warp/64, 1 warp/256, 2 block/2k, 3 block/8k, 4 global
+constexpr int kAggGlobal = 4;
+__host__ __device__ inline int agg_bucket_of(int64_t dsum) {
+  return dsum <= 0 ? -1 : dsum <= 32 ? 0 : dsum <= 128 ? 1 : dsum <= 1024 ? 2 : dsum <= 4096 ? 3 : 4;
+}
+constexpr int64_t kAggChunkEntries = 2048;
+
+// ------------------------------------------------------ local_move.cu
+template <typename W>
+void lm_launch_bucket(const LMArgs<W>& a, bool wide, bool async, int bucket, const int32_t* verts, int nverts,
+                      cudaStream_t s);
+template <typename W>
+void lm_launch_hubs(const LMArgs<W>& a, bool wide, bool async, const int32_t* hubs, int nhubs,
+                    const int64_t* chunk_pre, int64_t nchunks, cudaStream_t s);
+template <typename W>
+void lm_launch_commit(const LMArgs<W>& a, int64_t max_moves, cudaStream_t s);
+
+// ------------------------------------------------------- graph_ops.cu
+
+// Exclusive scan of n values into out (out may alias in); if total != nullptr
+// the sum of all values is stored there (device).  tmp needs scan_tmp_bytes(n).
+size_t scan_tmp_bytes(int64_t n);
+void scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, int64_t* total, void* tmp, cudaStream_t s);
+void scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total, void* tmp, cudaStream_t s);
+void scan_i32(const int32_t* in, int32_t* out, int64_t n, int64_t* total, void* tmp, cudaStream_t s);
+
+// Stable partition of [0, n) by key[i] in [0, nkeys): out lists the ids in key
+// order, ascending within a key; key_off[nkeys + 1] (device) gets the offsets.
+size_t partition_tmp_bytes(int64_t n, int nkeys);
+void stable_partition(const int32_t* key, int64_t n, int nkeys, int32_t* out, int64_t* key_off, void* tmp,
+                      cudaStream_t s);
+
+// Keys for the local-moving lists: bucket-major, then class (i mod P); vertices
+// of degree 0 get the trailing key nb * P.
+void lm_keys(const int64_t* off, int64_t n, int P, int32_t* key, cudaStream_t s);
+// For the hub list: per hub its table base (2 * degree slots) and chunk prefix.
+void hub_layout(const int64_t* off, const int32_t* hubs, int64_t nhubs, int64_t* hbase, int64_t* chunk_pre,
+                void* tmp, cudaStream_t s);
+
+// Row sums K (int64) of a CSR, the total M (u128 lo/hi) and the self-loop total.
+template <typename W>
+void row_sums(const int64_t* off, const int32_t* col, const W* wt, int64_t n, long long* K,
+              unsigned long long* acc /* [0..1] M lo/hi, [2] self-loop total */, cudaStream_t s);
+
+// Pass set-up: memb = identity, Sigma = K, sizes 1, stamps -1.
+void pass_init(int64_t n, const long long* K, int32_t* memb, long long* sig, int32_t* csize, int32_t* stampA,
+               int32_t* stampB, cudaStream_t s);
+
+// Modularity numerator parts: sumL (u64) += weights inside communities,
+// ss (u128 lo/hi) += sum over c < n of sig[c]^2.
+template <typename W>
+void modularity_parts(const int64_t* off, const int32_t* col, const W* wt, int64_t n, const int32_t* memb,
+                      const long long* sig, unsigned long long* acc /* [0] L, [1..2] ss lo/hi */, cudaStream_t s);
+// Community totals for an arbitrary membership (Sigma_c = sum K_i over c).
+void community_totals(const long long* K, const int32_t* memb, int64_t n, long long* sig, cudaStream_t s);
+
+// Renumbering: used flags, dense ids by ascending old id, level = newid[memb],
+// top = level[top].
+void mark_used(const int32_t* memb, int64_t n, int32_t* used, cudaStream_t s);
+void apply_level(const int32_t* memb, const int32_t* newid, int64_t n, int32_t* level, cudaStream_t s);
+void compose_top(int32_t* top, int64_t n0, const int32_t* level, cudaStream_t s);
+void coarse_degrees(const int32_t* used, const int32_t* newid, const long long* sig, int64_t n, long long* Knext,
+                    cudaStream_t s);
+
+// Aggregation.  members grouped by community (counting sort), mpre = prefix
+// of member degrees, then per community the (D, w) sums into tmp rows at
+// mpre[cstart[C]], row lengths into rlen; finally compaction into the coarse CSR.
+struct AggArgs {
+  const int64_t* off;
+  const int32_t* col;
+  const void* wt;          // W
+  const int32_t* level;    // community of each vertex, in [0, k)
+  int64_t n, k;
+  const int64_t* cstart;   // k + 1
+  const int32_t* members;  // n
+  const int64_t* mpre;     // n + 1
+  int32_t* tcol;           // nnz (tmp rows)
+  void* tw;                // nnz (W2)
+  int64_t* rlen;           // k
+  int32_t* gkeys;          // global tables
+  unsigned long long* gvals;
+  int32_t* gcount;
+  int32_t* gslots;
+  int* error;
+};
+void agg_group_members(const int32_t* level, int64_t n, int64_t k, int64_t* cnt /* k+1 */, int64_t* cstart,
+                       int64_t* fill, int32_t* members, void* tmp, cudaStream_t s);
+void agg_member_prefix(const int64_t* off, const int32_t* members, int64_t n, int64_t* mdeg, int64_t* mpre,
+                       void* tmp, cudaStream_t s);
+void agg_keys(const int64_t* cstart, const int64_t* mpre, int64_t k, int32_t* key, cudaStream_t s);
+template <typename W, typename W2>
+void agg_launch_bucket(const AggArgs& a, int bucket, const int32_t* comms, int ncomms, cudaStream_t s);
+template <typename W, typename W2>
+void agg_launch_global(const AggArgs& a, const int32_t* comms, int ncomms, const int64_t* gbase,
+                       const int64_t* chunk_pre, int64_t nchunks, cudaStream_t s);
+void agg_global_layout(const int64_t* cstart, const int64_t* mpre, const int32_t* comms, int64_t ncomms,
+                       int64_t* gbase, int64_t* chunk_pre, void* tmp, cudaStream_t s);
+template <typename W2>
+void agg_compact(const int64_t* cstart, const int64_t* mpre, const int64_t* rlen, const int64_t* coff, int64_t k,
+                 const int32_t* tcol, const W2* tw, int32_t* ocol, W2* ow, cudaStream_t s);
+
+// Input checks: flags |= 1 offsets not monotone / bad ends, 2 col out of
+// range, 4 weight <= 0; hashes[0..1] = sums of mix(u,v,w) and mix(v,u,w).
+void validate_csr(const int64_t* off, const int32_t* col, const int32_t* wt, int64_t n, int64_t nnz, int* flags,
+                  unsigned long long* hashes, cudaStream_t s);
+
+// Copies with conversion.
+void widen_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
+void fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t s);
+void iota_i32(int32_t* p, int64_t n, cudaStream_t s);
+
+}  // namespace gbl

@@ -1,0 +1,864 @@
+// graph_ops.cu — everything around local-moving: scans, partitions, row
+// sums, modularity, renumbering and the aggregation phase (Section 3.2 of the
+// paper: each community becomes a super-vertex, edges between communities
+// are merged with summed weights, edges inside one become a summed
+// self-loop).  No library primitives: scan and partition are our own.
+#include "common.cuh"
+#include "engine.h"
+
+namespace gbl {
+
+constexpr int kT = 256;          // threads of the generic kernels
+constexpr int kScanTile = 2048;  // elements per scan / partition tile (8 per thread)
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Inclusive block scan of one value per thread (kT threads); returns the
+// thread's inclusive prefix and the block total in *total.
+__device__ __forceinline__ long long block_inclusive_scan(long long v, long long* total) {
+  __shared__ long long wsum[kT / kWarp];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    long long u = __shfl_up_sync(0xffffffffu, v, d);
+    if (lane >= d) v += u;
+  }
+  if (lane == 31) wsum[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    long long s = lane < kT / kWarp ? wsum[lane] : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      long long u = __shfl_up_sync(0xffffffffu, s, d);
+      if (lane >= d) s += u;
+    }
+    if (lane < kT / kWarp) wsum[lane] = s;
+  }
+  __syncthreads();
+  long long add = wid > 0 ? wsum[wid - 1] : 0;
+  *total = wsum[kT / kWarp - 1];
+  __syncthreads();
+  return v + add;
+}
+
+// Sum of a u128 per thread into the block; thread 0 adds it to lo/hi.
+__device__ __forceinline__ void block_add_u128(u128 v, unsigned long long* lo, unsigned long long* hi) {
+  __shared__ unsigned long long slo[kT / kWarp], shi[kT / kWarp];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    unsigned long long a = __shfl_xor_sync(0xffffffffu, (unsigned long long)v, m);
+    unsigned long long b = __shfl_xor_sync(0xffffffffu, (unsigned long long)(v >> 64), m);
+    v += ((u128)b << 64) | (u128)a;
+  }
+  if (lane == 0) { slo[wid] = (unsigned long long)v; shi[wid] = (unsigned long long)(v >> 64); }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    u128 s = 0;
+    for (int w = 0; w < kT / kWarp; ++w) s += ((u128)shi[w] << 64) | (u128)slo[w];
+    if (s) atomic_add_u128(lo, hi, s);
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- scans
+
+template <typename Tin>
+__global__ void __launch_bounds__(kT) scan_reduce_k(const Tin* __restrict__ in, int64_t n, long long* bsum) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  long long s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanTile / kT; ++k) {
+    int64_t idx = base + k * kT + threadIdx.x;
+    if (idx < n) s += (long long)in[idx];
+  }
+  long long tot;
+  block_inclusive_scan(s, &tot);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kT) scan_bsums_k(long long* bsum, int64_t nb, int64_t* total) {
+  long long carry = 0;
+  for (int64_t c0 = 0; c0 < nb; c0 += kT) {
+    int64_t idx = c0 + threadIdx.x;
+    long long v = idx < nb ? bsum[idx] : 0;
+    long long tot;
+    long long inc = block_inclusive_scan(v, &tot);
+    if (idx < nb) bsum[idx] = carry + inc - v;
+    carry += tot;
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(kT) scan_final_k(const Tin* in, Tout* out, int64_t n, const long long* bsum) {
+  __shared__ long long tile[kScanTile];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  constexpr int PER = kScanTile / kT;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    int64_t idx = base + k * kT + threadIdx.x;
+    tile[k * kT + threadIdx.x] = idx < n ? (long long)in[idx] : 0;
+  }
+  __syncthreads();
+  long long loc[PER], s = 0;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) { loc[k] = s; s += tile[threadIdx.x * PER + k]; }
+  long long tot;
+  long long inc = block_inclusive_scan(s, &tot);
+  long long ex = inc - s + bsum[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) tile[threadIdx.x * PER + k] = ex + loc[k];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    int64_t idx = base + k * kT + threadIdx.x;
+    if (idx < n) out[idx] = (Tout)tile[k * kT + threadIdx.x];
+  }
+}
+
+size_t scan_tmp_bytes(int64_t n) { return (size_t)((n + kScanTile - 1) / kScanTile + 1) * sizeof(long long); }
+
+template <typename Tin, typename Tout>
+static void scan_any(const Tin* in, Tout* out, int64_t n, int64_t* total, void* tmp, cudaStream_t s) {
+  if (n <= 0) {
+    if (total) cudaMemsetAsync(total, 0, sizeof(int64_t), s);
+    return;
+  }
+  int64_t nb = (n + kScanTile - 1) / kScanTile;
+  long long* bsum = (long long*)tmp;
+  scan_reduce_k<Tin><<<(unsigned)nb, kT, 0, s>>>(in, n, bsum);
+  scan_bsums_k<<<1, kT, 0, s>>>(bsum, nb, total);
+  scan_final_k<Tin, Tout><<<(unsigned)nb, kT, 0, s>>>(in, out, n, bsum);
+}
+
+void scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, int64_t* total, void* tmp, cudaStream_t s) {
+  scan_any<int32_t, int64_t>(in, out, n, total, tmp, s);
+}
+void scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total, void* tmp, cudaStream_t s) {
+  scan_any<int64_t, int64_t>(in, out, n, total, tmp, s);
+}
+void scan_i32(const int32_t* in, int32_t* out, int64_t n, int64_t* total, void* tmp, cudaStream_t s) {
+  scan_any<int32_t, int32_t>(in, out, n, total, tmp, s);
+}
+
+// ------------------------------------------------------ stable partition
+
+__global__ void __launch_bounds__(kT) part_count_k(const int32_t* __restrict__ key, int64_t n, int nkeys,
+                                                   int64_t* counts, int64_t nblk) {
+  extern __shared__ int hist[];
+  for (int t = threadIdx.x; t < nkeys; t += kT) hist[t] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  for (int k = 0; k < kScanTile / kT; ++k) {
+    int64_t idx = base + k * kT + threadIdx.x;
+    if (idx < n) atomicAdd(&hist[key[idx]], 1);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nkeys; t += kT) counts[(int64_t)t * nblk + blockIdx.x] = hist[t];
+}
+
+__global__ void part_key_off_k(const int64_t* offs, int nkeys, int64_t nblk, int64_t n, int64_t* key_off) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t <= nkeys; t += gridDim.x * blockDim.x)
+    key_off[t] = t < nkeys ? offs[(int64_t)t * nblk] : n;
+}
+
+__global__ void __launch_bounds__(kT) part_scatter_k(const int32_t* __restrict__ key, int64_t n, int nkeys,
+                                                     const int64_t* offs, int64_t nblk, int32_t* out) {
+  extern __shared__ long long psm[];
+  long long* running = psm;               // nkeys
+  long long* wcnt = psm + nkeys;          // (kT / 32) * nkeys
+  constexpr int NW = kT / kWarp;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int t = threadIdx.x; t < nkeys; t += kT) running[t] = offs[(int64_t)t * nblk + blockIdx.x];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  for (int r = 0; r < kScanTile / kT; ++r) {
+    for (int t = threadIdx.x; t < NW * nkeys; t += kT) wcnt[t] = 0;
+    __syncthreads();
+    int64_t idx = base + r * kT + threadIdx.x;
+    bool valid = idx < n;
+    int k = valid ? key[idx] : -1;
+    unsigned peers = __match_any_sync(0xffffffffu, k);
+    int rank = __popc(peers & lanemask_lt());
+    if (valid && rank == 0) wcnt[wid * nkeys + k] = __popc(peers);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nkeys; t += kT) {
+      long long b = running[t];
+      for (int w = 0; w < NW; ++w) {
+        long long c = wcnt[w * nkeys + t];
+        wcnt[w * nkeys + t] = b;
+        b += c;
+      }
+      running[t] = b;
+    }
+    __syncthreads();
+    if (valid) out[wcnt[wid * nkeys + k] + rank] = (int32_t)idx;
+    __syncthreads();
+  }
+}
+
+size_t partition_tmp_bytes(int64_t n, int nkeys) {
+  int64_t nblk = (n + kScanTile - 1) / kScanTile;
+  if (nblk < 1) nblk = 1;
+  int64_t m = (int64_t)nkeys * nblk;
+  return (size_t)m * 8 * 2 + scan_tmp_bytes(m) + 256;
+}
+
+void stable_partition(const int32_t* key, int64_t n, int nkeys, int32_t* out, int64_t* key_off, void* tmp,
+                      cudaStream_t s) {
+  int64_t nblk = (n + kScanTile - 1) / kScanTile;
+  if (nblk < 1) nblk = 1;
+  int64_t m = (int64_t)nkeys * nblk;
+  int64_t* counts = (int64_t*)tmp;
+  int64_t* offs = counts + m;
+  void* stmp = (void*)(offs + m);
+  if (n > 0) {
+    part_count_k<<<(unsigned)nblk, kT, nkeys * sizeof(int), s>>>(key, n, nkeys, counts, nblk);
+    scan_i64(counts, offs, m, nullptr, stmp, s);
+  } else {
+    cudaMemsetAsync(offs, 0, m * sizeof(int64_t), s);
+  }
+  part_key_off_k<<<(nkeys + 1 + 255) / 256, 256, 0, s>>>(offs, nkeys, nblk, n, key_off);
+  if (n > 0) {
+    size_t smem = (size_t)nkeys * (1 + kT / kWarp) * sizeof(long long);
+    part_scatter_k<<<(unsigned)nblk, kT, smem, s>>>(key, n, nkeys, offs, nblk, out);
+  }
+}
+
+// --------------------------------------------------- local-moving lists
+
+__global__ void lm_keys_k(const int64_t* __restrict__ off, int64_t n, int P, int32_t* key) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int b = lm_bucket_of(off[i + 1] - off[i]);
+    key[i] = b < 0 ? kBuckets * P : b * P + (int)(i % P);
+  }
+}
+
+static unsigned grid1d(int64_t n, int per = kT) {
+  int64_t b = (n + per - 1) / per;
+  if (b > 152 * 32) b = 152 * 32;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+void lm_keys(const int64_t* off, int64_t n, int P, int32_t* key, cudaStream_t s) {
+  if (n > 0) lm_keys_k<<<grid1d(n), kT, 0, s>>>(off, n, P, key);
+}
+
+__global__ void hub_sizes_k(const int64_t* off, const int32_t* hubs, int64_t nhubs, int64_t* cap, int64_t* chunks) {
+  for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < nhubs; h += (int64_t)gridDim.x * blockDim.x) {
+    int64_t d = off[hubs[h] + 1] - off[hubs[h]];
+    cap[h] = 2 * d;
+    chunks[h] = (d + kHubChunkEntries - 1) / kHubChunkEntries;
+  }
+}
+
+void hub_layout(const int64_t* off, const int32_t* hubs, int64_t nhubs, int64_t* hbase, int64_t* chunk_pre,
+                void* tmp, cudaStream_t s) {
+  if (nhubs <= 0) {
+    cudaMemsetAsync(hbase, 0, sizeof(int64_t), s);
+    cudaMemsetAsync(chunk_pre, 0, sizeof(int64_t), s);
+    return;
+  }
+  int64_t* cap = (int64_t*)tmp;
+  int64_t* chunks = cap + nhubs;
+  void* stmp = (void*)(chunks + nhubs);
+  hub_sizes_k<<<grid1d(nhubs), kT, 0, s>>>(off, hubs, nhubs, cap, chunks);
+  scan_i64(cap, hbase, nhubs, hbase + nhubs, stmp, s);
+  scan_i64(chunks, chunk_pre, nhubs, chunk_pre + nhubs, stmp, s);
+}
+
+// -------------------------------------------- row-range load balancing
+
+// A block takes rows [v0, v0 + kT); its threads stride over the rows'
+// entries and find each entry's row by binary search in a shared copy of
+// the offsets, so a hub row is spread over all threads of its block.
+__device__ __forceinline__ int row_of(const int64_t* soff, int nr, int64_t x) {
+  int lo = 0, hi = nr;  // soff[lo] <= x < soff[hi]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (soff[mid] <= x) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+template <typename W>
+__global__ void __launch_bounds__(kT) row_sums_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                                                 const W* __restrict__ wt, int64_t n, long long* K,
+                                                 unsigned long long* acc) {
+  __shared__ int64_t soff[kT + 1];
+  __shared__ unsigned long long ks[kT];
+  const int64_t v0 = (int64_t)blockIdx.x * kT;
+  const int nr = (int)min((int64_t)kT, n - v0);
+  for (int t = threadIdx.x; t <= nr; t += kT) soff[t] = off[v0 + t];
+  ks[threadIdx.x] = 0;
+  __syncthreads();
+  unsigned long long loops = 0;
+  for (int64_t x = soff[0] + threadIdx.x; x < soff[nr]; x += kT) {
+    int r = row_of(soff, nr, x);
+    unsigned long long w = (unsigned long long)wt[x];
+    atomicAdd(&ks[r], w);
+    if (col[x] == v0 + r) loops += w;
+  }
+  __syncthreads();
+  u128 mine = 0;
+  if (threadIdx.x < nr) {
+    K[v0 + threadIdx.x] = (long long)ks[threadIdx.x];
+    mine = ks[threadIdx.x];
+  }
+  block_add_u128(mine, acc, acc + 1);
+  block_add_u128((u128)loops, acc + 2, acc + 3);
+}
+
+template <typename W>
+void row_sums(const int64_t* off, const int32_t* col, const W* wt, int64_t n, long long* K, unsigned long long* acc,
+              cudaStream_t s) {
+  if (n <= 0) return;
+  row_sums_k<W><<<(unsigned)((n + kT - 1) / kT), kT, 0, s>>>(off, col, wt, n, K, acc);
+}
+template void row_sums<int32_t>(const int64_t*, const int32_t*, const int32_t*, int64_t, long long*,
+                                unsigned long long*, cudaStream_t);
+template void row_sums<int64_t>(const int64_t*, const int32_t*, const int64_t*, int64_t, long long*,
+                                unsigned long long*, cudaStream_t);
+
+__global__ void pass_init_k(int64_t n, const long long* K, int32_t* memb, long long* sig, int32_t* csize,
+                            int32_t* sa, int32_t* sb) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    memb[i] = (int32_t)i;
+    sig[i] = K[i];
+    csize[i] = 1;
+    sa[i] = -1;
+    sb[i] = -1;
+  }
+}
+
+void pass_init(int64_t n, const long long* K, int32_t* memb, long long* sig, int32_t* csize, int32_t* stampA,
+               int32_t* stampB, cudaStream_t s) {
+  if (n > 0) pass_init_k<<<grid1d(n), kT, 0, s>>>(n, K, memb, sig, csize, stampA, stampB);
+}
+
+template <typename W>
+__global__ void __launch_bounds__(kT) intra_weight_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                                                     const W* __restrict__ wt, int64_t n,
+                                                     const int32_t* __restrict__ memb, unsigned long long* acc) {
+  __shared__ int64_t soff[kT + 1];
+  const int64_t v0 = (int64_t)blockIdx.x * kT;
+  const int nr = (int)min((int64_t)kT, n - v0);
+  for (int t = threadIdx.x; t <= nr; t += kT) soff[t] = off[v0 + t];
+  __syncthreads();
+  unsigned long long L = 0;
+  for (int64_t x = soff[0] + threadIdx.x; x < soff[nr]; x += kT) {
+    int r = row_of(soff, nr, x);
+    if (memb[col[x]] == memb[v0 + r]) L += (unsigned long long)wt[x];
+  }
+  block_add_u128((u128)L, acc, acc + 3);   // acc[0] lo; hi unused beyond 2^64 (L <= M < 2^62)
+}
+
+__global__ void __launch_bounds__(kT) sum_squares_k(const long long* __restrict__ sig, int64_t n,
+                                                    unsigned long long* acc) {
+  u128 ss = 0;
+  for (int64_t c = blockIdx.x * (int64_t)kT + threadIdx.x; c < n; c += (int64_t)gridDim.x * kT) {
+    long long v = sig[c];
+    ss += (u128)((unsigned long long)v) * (u128)((unsigned long long)v);
+  }
+  block_add_u128(ss, acc + 1, acc + 2);
+}
+
+template <typename W>
+void modularity_parts(const int64_t* off, const int32_t* col, const W* wt, int64_t n, const int32_t* memb,
+                      const long long* sig, unsigned long long* acc, cudaStream_t s) {
+  if (n <= 0) return;
+  intra_weight_k<W><<<(unsigned)((n + kT - 1) / kT), kT, 0, s>>>(off, col, wt, n, memb, acc);
+  sum_squares_k<<<grid1d(n), kT, 0, s>>>(sig, n, acc);
+}
+template void modularity_parts<int32_t>(const int64_t*, const int32_t*, const int32_t*, int64_t, const int32_t*,
+                                        const long long*, unsigned long long*, cudaStream_t);
+template void modularity_parts<int64_t>(const int64_t*, const int32_t*, const int64_t*, int64_t, const int32_t*,
+                                        const long long*, unsigned long long*, cudaStream_t);
+
+__global__ void community_totals_k(const long long* K, const int32_t* memb, int64_t n, long long* sig) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd((unsigned long long*)(sig + memb[i]), (unsigned long long)K[i]);
+}
+void community_totals(const long long* K, const int32_t* memb, int64_t n, long long* sig, cudaStream_t s) {
+  if (n <= 0) return;
+  cudaMemsetAsync(sig, 0, n * sizeof(long long), s);
+  community_totals_k<<<grid1d(n), kT, 0, s>>>(K, memb, n, sig);
+}
+
+// ------------------------------------------------------------ renumber
+
+__global__ void mark_used_k(const int32_t* memb, int64_t n, int32_t* used) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    used[memb[i]] = 1;
+}
+void mark_used(const int32_t* memb, int64_t n, int32_t* used, cudaStream_t s) {
+  if (n <= 0) return;
+  cudaMemsetAsync(used, 0, n * sizeof(int32_t), s);
+  mark_used_k<<<grid1d(n), kT, 0, s>>>(memb, n, used);
+}
+
+__global__ void apply_level_k(const int32_t* memb, const int32_t* newid, int64_t n, int32_t* level) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    level[i] = newid[memb[i]];
+}
+void apply_level(const int32_t* memb, const int32_t* newid, int64_t n, int32_t* level, cudaStream_t s) {
+  if (n > 0) apply_level_k<<<grid1d(n), kT, 0, s>>>(memb, newid, n, level);
+}
+
+__global__ void compose_top_k(int32_t* top, int64_t n0, const int32_t* level) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n0; v += (int64_t)gridDim.x * blockDim.x)
+    top[v] = level[top[v]];
+}
+void compose_top(int32_t* top, int64_t n0, const int32_t* level, cudaStream_t s) {
+  if (n0 > 0) compose_top_k<<<grid1d(n0), kT, 0, s>>>(top, n0, level);
+}
+
+__global__ void coarse_degrees_k(const int32_t* used, const int32_t* newid, const long long* sig, int64_t n,
+                                 long long* Knext) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+    if (used[c]) Knext[newid[c]] = sig[c];
+}
+void coarse_degrees(const int32_t* used, const int32_t* newid, const long long* sig, int64_t n, long long* Knext,
+                    cudaStream_t s) {
+  if (n > 0) coarse_degrees_k<<<grid1d(n), kT, 0, s>>>(used, newid, sig, n, Knext);
+}
+
+// ------------------------------------------------------------ aggregation
+
+__global__ void count_members_k(const int32_t* level, int64_t n, int64_t* cnt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd((unsigned long long*)(cnt + level[i]), 1ull);
+}
+__global__ void place_members_k(const int32_t* level, int64_t n, const int64_t* cstart, int64_t* fill,
+                                int32_t* members) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t C = level[i];
+    int64_t pos = cstart[C] + (int64_t)atomicAdd((unsigned long long*)(fill + C), 1ull);
+    members[pos] = (int32_t)i;
+  }
+}
+
+void agg_group_members(const int32_t* level, int64_t n, int64_t k, int64_t* cnt, int64_t* cstart, int64_t* fill,
+                       int32_t* members, void* tmp, cudaStream_t s) {
+  cudaMemsetAsync(cnt, 0, (k + 1) * sizeof(int64_t), s);
+  cudaMemsetAsync(fill, 0, (k + 1) * sizeof(int64_t), s);
+  if (n > 0) count_members_k<<<grid1d(n), kT, 0, s>>>(level, n, cnt);
+  scan_i64(cnt, cstart, k, cstart + k, tmp, s);
+  if (n > 0) place_members_k<<<grid1d(n), kT, 0, s>>>(level, n, cstart, fill, members);
+}
+
+__global__ void member_degrees_k(const int64_t* off, const int32_t* members, int64_t n, int64_t* mdeg) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    int32_t u = members[p];
+    mdeg[p] = off[u + 1] - off[u];
+  }
+}
+void agg_member_prefix(const int64_t* off, const int32_t* members, int64_t n, int64_t* mdeg, int64_t* mpre,
+                       void* tmp, cudaStream_t s) {
+  if (n > 0) member_degrees_k<<<grid1d(n), kT, 0, s>>>(off, members, n, mdeg);
+  scan_i64(mdeg, mpre, n, mpre + n, tmp, s);
+}
+
+__global__ void agg_keys_k(const int64_t* cstart, const int64_t* mpre, int64_t k, int32_t* key) {
+  for (int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; C < k; C += (int64_t)gridDim.x * blockDim.x) {
+    int64_t dsum = mpre[cstart[C + 1]] - mpre[cstart[C]];
+    int b = agg_bucket_of(dsum);
+    key[C] = b < 0 ? kAggBuckets : b;
+  }
+}
+void agg_keys(const int64_t* cstart, const int64_t* mpre, int64_t k, int32_t* key, cudaStream_t s) {
+  if (k > 0) agg_keys_k<<<grid1d(k), kT, 0, s>>>(cstart, mpre, k, key);
+}
+
+// Member position of virtual entry t of a community: the last p in [lo, hi)
+// with mpre[p] <= t.
+__device__ __forceinline__ int64_t member_of(const int64_t* __restrict__ mpre, int64_t lo, int64_t hi, int64_t t) {
+  while (hi - lo > 1) {
+    int64_t mid = (lo + hi) >> 1;
+    if (mpre[mid] <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+template <typename W>
+__device__ __forceinline__ void virtual_entry(const AggArgs& a, int64_t cs, int64_t ce, int64_t t, int32_t* D,
+                                              unsigned long long* w) {
+  int64_t p = member_of(a.mpre, cs, ce, t);
+  int32_t u = a.members[p];
+  int64_t x = a.off[u] + (t - a.mpre[p]);
+  *D = a.level[a.col[x]];
+  *w = (unsigned long long)((const W*)a.wt)[x];
+}
+
+template <typename W, typename W2, int CAP>
+__global__ void __launch_bounds__(256) agg_warp_k(AggArgs a, const int32_t* __restrict__ comms, int ncomms) {
+  constexpr int WPB = 8;
+  __shared__ int32_t skeys[WPB][CAP];
+  __shared__ unsigned long long svals[WPB][CAP];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  int32_t* keys = skeys[wib];
+  unsigned long long* vals = svals[wib];
+  for (int t = lane; t < CAP; t += kWarp) { keys[t] = kEmpty; vals[t] = 0; }
+  __syncwarp();
+  bool ok = true;
+  for (int ci = blockIdx.x * WPB + wib; ci < ncomms; ci += gridDim.x * WPB) {
+    int32_t C = comms[ci];
+    int64_t cs = a.cstart[C], ce = a.cstart[C + 1];
+    int64_t vs = a.mpre[cs], ve = a.mpre[ce];
+    for (int64_t t = vs + lane; t < ve; t += kWarp) {
+      int32_t D;
+      unsigned long long w;
+      virtual_entry<W>(a, cs, ce, t, &D, &w);
+      ok &= table_add_pow2<CAP>(keys, vals, D, w);
+    }
+    __syncwarp();
+    int64_t base = 0;
+    for (int t = lane; t < CAP; t += kWarp) {
+      int32_t key = keys[t];
+      bool occ = key != kEmpty;
+      unsigned m = __ballot_sync(0xffffffffu, occ);
+      if (occ) {
+        int64_t pos = vs + base + __popc(m & lanemask_lt());
+        a.tcol[pos] = key;
+        ((W2*)a.tw)[pos] = (W2)vals[t];
+        keys[t] = kEmpty;
+        vals[t] = 0;
+      }
+      base += __popc(m);
+    }
+    if (lane == 0) a.rlen[C] = base;
+    __syncwarp();
+  }
+  if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicOr(a.error, kErrProbe);
+}
+
+template <typename W, typename W2, int CAP, int THREADS>
+__global__ void __launch_bounds__(THREADS) agg_block_k(AggArgs a, const int32_t* __restrict__ comms, int ncomms) {
+  extern __shared__ unsigned long long adyn[];
+  unsigned long long* vals = adyn;
+  int32_t* keys = (int32_t*)(adyn + CAP);
+  __shared__ int wtot[THREADS / kWarp];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int t = threadIdx.x; t < CAP; t += THREADS) { keys[t] = kEmpty; vals[t] = 0; }
+  __syncthreads();
+  bool ok = true;
+  for (int ci = blockIdx.x; ci < ncomms; ci += gridDim.x) {
+    int32_t C = comms[ci];
+    int64_t cs = a.cstart[C], ce = a.cstart[C + 1];
+    int64_t vs = a.mpre[cs], ve = a.mpre[ce];
+    for (int64_t t = vs + threadIdx.x; t < ve; t += THREADS) {
+      int32_t D;
+      unsigned long long w;
+      virtual_entry<W>(a, cs, ce, t, &D, &w);
+      ok &= table_add_pow2<CAP>(keys, vals, D, w);
+    }
+    __syncthreads();
+    int64_t base = 0;
+    for (int t0 = 0; t0 < CAP; t0 += THREADS) {
+      int t = t0 + threadIdx.x;
+      int32_t key = keys[t];
+      bool occ = key != kEmpty;
+      unsigned m = __ballot_sync(0xffffffffu, occ);
+      if (lane == 0) wtot[wid] = __popc(m);
+      __syncthreads();
+      int before = 0, all = 0;
+      for (int w = 0; w < THREADS / kWarp; ++w) {
+        if (w < wid) before += wtot[w];
+        all += wtot[w];
+      }
+      if (occ) {
+        int64_t pos = vs + base + before + __popc(m & lanemask_lt());
+        a.tcol[pos] = key;
+        ((W2*)a.tw)[pos] = (W2)vals[t];
+        keys[t] = kEmpty;
+        vals[t] = 0;
+      }
+      base += all;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) a.rlen[C] = base;
+  }
+  if (!ok) atomicOr(a.error, kErrProbe);
+}
+
+template <typename W>
+__global__ void __launch_bounds__(256) agg_global_insert_k(AggArgs a, const int32_t* __restrict__ comms, int ncomms,
+                                                           const int64_t* __restrict__ gbase,
+                                                           const int64_t* __restrict__ chunk_pre) {
+  int lo = 0, hi = ncomms;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (chunk_pre[mid] <= (int64_t)blockIdx.x) lo = mid; else hi = mid;
+  }
+  const int h = lo;
+  const int32_t C = comms[h];
+  const int64_t cs = a.cstart[C], ce = a.cstart[C + 1];
+  const int64_t vs = a.mpre[cs], ve = a.mpre[ce];
+  const int64_t q = (int64_t)blockIdx.x - chunk_pre[h];
+  const int64_t base = gbase[h];
+  const uint32_t cap = (uint32_t)(gbase[h + 1] - base);
+  int32_t* keys = a.gkeys + base;
+  unsigned long long* vals = a.gvals + base;
+  const int64_t t0 = vs + q * kAggChunkEntries, t1 = min(ve, t0 + kAggChunkEntries);
+  bool ok = true;
+  for (int64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+    int32_t D;
+    unsigned long long w;
+    virtual_entry<W>(a, cs, ce, t, &D, &w);
+    bool fresh;
+    ok &= gtable_add(keys, vals, cap, D, w, &fresh);
+    if (fresh) {
+      int pos = atomicAdd(a.gcount + h, 1);
+      a.gslots[base + pos] = D;
+    }
+  }
+  if (!ok) atomicOr(a.error, kErrProbe);
+}
+
+template <typename W2>
+__global__ void __launch_bounds__(256) agg_global_write_k(AggArgs a, const int32_t* __restrict__ comms, int ncomms,
+                                                          const int64_t* __restrict__ gbase) {
+  for (int h = blockIdx.x; h < ncomms; h += gridDim.x) {
+    const int32_t C = comms[h];
+    const int64_t vs = a.mpre[a.cstart[C]];
+    const int64_t base = gbase[h];
+    const uint32_t cap = (uint32_t)(gbase[h + 1] - base);
+    int32_t* keys = a.gkeys + base;
+    unsigned long long* vals = a.gvals + base;
+    const int cnt = a.gcount[h];
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      int32_t D = a.gslots[base + t];
+      a.tcol[vs + t] = D;
+      ((W2*)a.tw)[vs + t] = (W2)gtable_get(keys, vals, cap, D);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      int32_t D = a.gslots[base + t];
+      uint32_t hs = __umulhi(hash32((uint32_t)D), cap);
+      for (uint32_t probe = 0; probe < cap; ++probe) {
+        if (keys[hs] == D) { keys[hs] = kEmpty; vals[hs] = 0; break; }
+        hs = (hs + 1 == cap) ? 0 : hs + 1;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      a.rlen[C] = cnt;
+      a.gcount[h] = 0;
+    }
+  }
+}
+
+namespace {
+template <typename K>
+int agrid(K kernel, int threads, size_t smem, int work) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess || per < 1) per = 1;
+  int g = sms * per;
+  if (work < g) g = work;
+  return g < 1 ? 1 : g;
+}
+}  // namespace
+
+template <typename W, typename W2>
+void agg_launch_bucket(const AggArgs& a, int bucket, const int32_t* comms, int ncomms, cudaStream_t s) {
+  if (ncomms <= 0) return;
+  switch (bucket) {
+    case 0: {
+      auto k = agg_warp_k<W, W2, 64>;
+      k<<<agrid(k, 256, 0, (ncomms + 7) / 8), 256, 0, s>>>(a, comms, ncomms);
+      break;
+    }
+    case 1: {
+      auto k = agg_warp_k<W, W2, 256>;
+      k<<<agrid(k, 256, 0, (ncomms + 7) / 8), 256, 0, s>>>(a, comms, ncomms);
+      break;
+    }
+    case 2: {
+      constexpr int CAP = 2048;
+      size_t smem = (size_t)CAP * 12;
+      auto k = agg_block_k<W, W2, CAP, 128>;
+      k<<<agrid(k, 128, smem, ncomms), 128, smem, s>>>(a, comms, ncomms);
+      break;
+    }
+    case 3: {
+      constexpr int CAP = 8192;
+      size_t smem = (size_t)CAP * 12;
+      auto k = agg_block_k<W, W2, CAP, 256>;
+      static bool attr = false;
+      if (!attr) {
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+      }
+      k<<<agrid(k, 256, smem, ncomms), 256, smem, s>>>(a, comms, ncomms);
+      break;
+    }
+    default: break;
+  }
+}
+
+template <typename W, typename W2>
+void agg_launch_global(const AggArgs& a, const int32_t* comms, int ncomms, const int64_t* gbase,
+                       const int64_t* chunk_pre, int64_t nchunks, cudaStream_t s) {
+  if (ncomms <= 0 || nchunks <= 0) return;
+  agg_global_insert_k<W><<<(unsigned)nchunks, 256, 0, s>>>(a, comms, ncomms, gbase, chunk_pre);
+  agg_global_write_k<W2><<<ncomms < 4096 ? ncomms : 4096, 256, 0, s>>>(a, comms, ncomms, gbase);
+}
+
+#define AGG_INST(W, W2)                                                                                        \
+  template void agg_launch_bucket<W, W2>(const AggArgs&, int, const int32_t*, int, cudaStream_t);            \
+  template void agg_launch_global<W, W2>(const AggArgs&, const int32_t*, int, const int64_t*, const int64_t*, \
+                                         int64_t, cudaStream_t);
+AGG_INST(int32_t, int32_t)
+AGG_INST(int32_t, int64_t)
+AGG_INST(int64_t, int64_t)
+
+__global__ void agg_global_sizes_k(const int64_t* cstart, const int64_t* mpre, const int32_t* comms, int64_t ncomms,
+                                   int64_t* cap, int64_t* chunks) {
+  for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < ncomms; h += (int64_t)gridDim.x * blockDim.x) {
+    int32_t C = comms[h];
+    int64_t dsum = mpre[cstart[C + 1]] - mpre[cstart[C]];
+    cap[h] = 2 * dsum;
+    chunks[h] = (dsum + kAggChunkEntries - 1) / kAggChunkEntries;
+  }
+}
+
+void agg_global_layout(const int64_t* cstart, const int64_t* mpre, const int32_t* comms, int64_t ncomms,
+                       int64_t* gbase, int64_t* chunk_pre, void* tmp, cudaStream_t s) {
+  if (ncomms <= 0) {
+    cudaMemsetAsync(gbase, 0, sizeof(int64_t), s);
+    cudaMemsetAsync(chunk_pre, 0, sizeof(int64_t), s);
+    return;
+  }
+  int64_t* cap = (int64_t*)tmp;
+  int64_t* chunks = cap + ncomms;
+  void* stmp = (void*)(chunks + ncomms);
+  agg_global_sizes_k<<<grid1d(ncomms), kT, 0, s>>>(cstart, mpre, comms, ncomms, cap, chunks);
+  scan_i64(cap, gbase, ncomms, gbase + ncomms, stmp, s);
+  scan_i64(chunks, chunk_pre, ncomms, chunk_pre + ncomms, stmp, s);
+}
+
+// Copy each community's tmp row (at mpre[cstart[C]], rlen[C] long) to its
+// coarse position coff[C]; blocks take kT communities each.
+template <typename W2>
+__global__ void __launch_bounds__(kT) agg_compact_k(const int64_t* __restrict__ cstart,
+                                                    const int64_t* __restrict__ mpre, const int64_t* __restrict__ coff,
+                                                    int64_t k, const int32_t* __restrict__ tcol,
+                                                    const W2* __restrict__ tw, int32_t* ocol, W2* ow) {
+  __shared__ int64_t soff[kT + 1];
+  __shared__ int64_t ssrc[kT];
+  const int64_t C0 = (int64_t)blockIdx.x * kT;
+  const int nr = (int)min((int64_t)kT, k - C0);
+  for (int t = threadIdx.x; t <= nr; t += kT) soff[t] = coff[C0 + t];
+  if (threadIdx.x < nr) ssrc[threadIdx.x] = mpre[cstart[C0 + threadIdx.x]];
+  __syncthreads();
+  for (int64_t o = soff[0] + threadIdx.x; o < soff[nr]; o += kT) {
+    int r = row_of(soff, nr, o);
+    int64_t src = ssrc[r] + (o - soff[r]);
+    ocol[o] = tcol[src];
+    ow[o] = tw[src];
+  }
+}
+
+template <typename W2>
+void agg_compact(const int64_t* cstart, const int64_t* mpre, const int64_t* rlen, const int64_t* coff, int64_t k,
+                 const int32_t* tcol, const W2* tw, int32_t* ocol, W2* ow, cudaStream_t s) {
+  (void)rlen;
+  if (k <= 0) return;
+  agg_compact_k<W2><<<(unsigned)((k + kT - 1) / kT), kT, 0, s>>>(cstart, mpre, coff, k, tcol, tw, ocol, ow);
+}
+template void agg_compact<int32_t>(const int64_t*, const int64_t*, const int64_t*, const int64_t*, int64_t,
+                                   const int32_t*, const int32_t*, int32_t*, int32_t*, cudaStream_t);
+template void agg_compact<int64_t>(const int64_t*, const int64_t*, const int64_t*, const int64_t*, int64_t,
+                                   const int32_t*, const int64_t*, int32_t*, int64_t*, cudaStream_t);
+
+// -------------------------------------------------------------- validation
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ unsigned long long entry_hash(uint32_t u, uint32_t v, uint32_t w) {
+  return mix64((((unsigned long long)u << 32) | v) ^ mix64(0xC0FFEEull + w));
+}
+
+__global__ void validate_off_k(const int64_t* off, int64_t n, int64_t nnz, int* flags) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (off[i] > off[i + 1]) atomicOr(flags, 1);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (off[0] != 0 || off[n] != nnz)) atomicOr(flags, 1);
+}
+
+__global__ void __launch_bounds__(kT) validate_rows_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                                                      const int32_t* __restrict__ wt, int64_t n, int* flags,
+                                                      unsigned long long* hashes) {
+  __shared__ int64_t soff[kT + 1];
+  const int64_t v0 = (int64_t)blockIdx.x * kT;
+  const int nr = (int)min((int64_t)kT, n - v0);
+  for (int t = threadIdx.x; t <= nr; t += kT) soff[t] = off[v0 + t];
+  __syncthreads();
+  unsigned long long h1 = 0, h2 = 0;
+  int f = 0;
+  for (int64_t x = soff[0] + threadIdx.x; x < soff[nr]; x += kT) {
+    int r = row_of(soff, nr, x);
+    int32_t v = col[x], w = wt[x];
+    if (v < 0 || v >= n) { f |= 2; continue; }
+    if (w <= 0) f |= 4;
+    uint32_t u = (uint32_t)(v0 + r);
+    h1 += entry_hash(u, (uint32_t)v, (uint32_t)w);
+    h2 += entry_hash((uint32_t)v, u, (uint32_t)w);
+  }
+  if (f) atomicOr(flags, f);
+  atomicAdd(hashes, h1);
+  atomicAdd(hashes + 1, h2);
+}
+
+void validate_csr(const int64_t* off, const int32_t* col, const int32_t* wt, int64_t n, int64_t nnz, int* flags,
+                  unsigned long long* hashes, cudaStream_t s) {
+  cudaMemsetAsync(flags, 0, sizeof(int), s);
+  cudaMemsetAsync(hashes, 0, 2 * sizeof(unsigned long long), s);
+  if (n <= 0) return;
+  validate_off_k<<<grid1d(n), kT, 0, s>>>(off, n, nnz, flags);
+  int hf = 0;
+  cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  if (hf) return;
+  validate_rows_k<<<(unsigned)((n + kT - 1) / kT), kT, 0, s>>>(off, col, wt, n, flags, hashes);
+}
+
+// ------------------------------------------------------------ conversions
+
+__global__ void widen_k(const int32_t* in, int64_t* out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[i];
+}
+void widen_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s) {
+  if (n > 0) widen_k<<<grid1d(n), kT, 0, s>>>(in, out, n);
+}
+__global__ void fill_k(int32_t* p, int32_t v, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+void fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t s) {
+  if (n > 0) fill_k<<<grid1d(n), kT, 0, s>>>(p, v, n);
+}
+__global__ void iota_k(int32_t* p, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = (int32_t)i;
+}
+void iota_i32(int32_t* p, int64_t n, cudaStream_t s) {
+  if (n > 0) iota_k<<<grid1d(n), kT, 0, s>>>(p, n);
+}
+
+}  // namespace gbl

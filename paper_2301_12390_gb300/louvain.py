@@ -1,0 +1,273 @@
+"""ctypes binding of the engine's C ABI (include/louvain.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+libgblouvain.so.  If that library is missing this module raises; there is no
+CPU fallback.  Function names are the C names; :class:`Louvain` is a small
+convenience wrapper over them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import List, Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgblouvain.so")
+
+SYNC, ASYNC = 0, 1
+PTR_HOST, PTR_DEVICE = 0, 1
+
+ERRORS = {
+    -1: "INVALID_ARG", -2: "NOT_SYMMETRIC", -3: "BAD_CSR", -4: "OOM", -5: "CUDA", -6: "TIMEOUT", -7: "STATE",
+    -8: "OVERFLOW", -9: "INTERNAL",
+}
+
+
+class LouvainError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("tolerance", ctypes.c_double), ("tolerance_decline", ctypes.c_double),
+                ("pass_tolerance", ctypes.c_double), ("max_iterations", ctypes.c_int32),
+                ("max_passes", ctypes.c_int32), ("prune", ctypes.c_int32), ("singleton_guard", ctypes.c_int32),
+                ("subrounds", ctypes.c_int32), ("validate", ctypes.c_int32), ("record_levels", ctypes.c_int32),
+                ("reserved_i", ctypes.c_int32 * 5), ("reserved_d", ctypes.c_double * 4)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("passes", ctypes.c_int32), ("iterations", ctypes.c_int32), ("moves", ctypes.c_int64),
+                ("lm_edges", ctypes.c_int64), ("communities", ctypes.c_int64), ("q", ctypes.c_double),
+                ("lm_ms", ctypes.c_double), ("agg_ms", ctypes.c_double), ("other_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double), ("reserved", ctypes.c_int64 * 8)]
+
+
+class PassInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("k", ctypes.c_int64), ("moves", ctypes.c_int64),
+                ("iterations", ctypes.c_int32), ("level_recorded", ctypes.c_int32), ("coarse_built", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("coarse_nnz", ctypes.c_int64), ("n_before_hi", ctypes.c_int64),
+                ("n_before_lo", ctypes.c_uint64), ("n_after_hi", ctypes.c_int64), ("n_after_lo", ctypes.c_uint64),
+                ("lm_ms", ctypes.c_double), ("agg_ms", ctypes.c_double)]
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported function
+_VP, _I64, _I32, _U64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64
+SIGNATURES = [
+    ("louvain_default_options", _I32, [ctypes.POINTER(Options)]),
+    ("louvain_create", _I32, [ctypes.POINTER(_VP), ctypes.POINTER(Options), _I32, _VP]),
+    ("louvain_set_options", _I32, [_VP, ctypes.POINTER(Options)]),
+    ("louvain_load_csr", _I32, [_VP, _I64, _I64, _VP, _VP, _VP, _I32]),
+    ("louvain_run", _I32, [_VP]),
+    ("louvain_get_membership", _I32, [_VP, _VP, _I64, _I32]),
+    ("louvain_get_modularity", _I32, [_VP, ctypes.POINTER(ctypes.c_double)]),
+    ("louvain_get_modularity_exact", _I32, [_VP, ctypes.POINTER(_I64), ctypes.POINTER(_U64), ctypes.POINTER(_I64)]),
+    ("louvain_modularity", _I32, [_VP, _VP, _I64, _I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64),
+                                  ctypes.POINTER(_U64), ctypes.POINTER(_I64)]),
+    ("louvain_get_stats", _I32, [_VP, ctypes.POINTER(Stats)]),
+    ("louvain_get_pass_info", _I32, [_VP, _I32, ctypes.POINTER(PassInfo)]),
+    ("louvain_get_iteration", _I32, [_VP, _I64, _VP]),
+    ("louvain_get_level", _I32, [_VP, _I32, _VP, _I64]),
+    ("louvain_get_coarse", _I32, [_VP, _I32, _VP, _I64, _VP, _VP, _I64]),
+    ("louvain_get_device_bytes", _I32, [_VP, ctypes.POINTER(_I64)]),
+    ("louvain_destroy", None, [_VP]),
+    ("louvain_last_error", ctypes.c_char_p, [_VP]),
+    ("louvain_version", ctypes.c_char_p, []),
+]
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libgblouvain.so and declare its functions; raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA engine library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load_library().louvain_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(a) -> int:
+    """Address of a numpy array or a torch tensor (host or device)."""
+    if a is None:
+        return 0
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return int(a.data_ptr())
+
+
+def _is_device(a) -> bool:
+    return not isinstance(a, np.ndarray) and getattr(a, "is_cuda", False)
+
+
+@dataclass
+class PassRecord:
+    n: int
+    nnz: int
+    k: int
+    moves: int
+    iterations: int
+    n_before: int
+    n_after: int
+    coarse_built: bool
+    coarse_nnz: int
+    lm_ms: float
+    agg_ms: float
+
+
+def _i128(hi, lo) -> int:
+    return (int(hi) << 64) + (int(lo) & ((1 << 64) - 1))
+
+
+class Louvain:
+    """One engine context on a CUDA device.
+
+    Inputs may be numpy arrays (host) or CUDA torch tensors (device); the
+    engine copies them.  `stream` is a cudaStream_t handle (int) or None.
+    """
+
+    def __init__(self, device: int = 0, stream: Optional[int] = None, **options):
+        self.lib = load_library()
+        self.opt = default_options(**options)
+        h = ctypes.c_void_p()
+        rc = self.lib.louvain_create(ctypes.byref(h), ctypes.byref(self.opt), device, stream or None)
+        if rc:
+            raise LouvainError(rc, "louvain_create failed")
+        self.h = h
+        self.n = None
+
+    def _check(self, rc):
+        if rc:
+            raise LouvainError(rc, self.lib.louvain_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.louvain_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_options(self, **options):
+        for k, v in options.items():
+            if not hasattr(self.opt, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(self.opt, k, v)
+        self._check(self.lib.louvain_set_options(self.h, ctypes.byref(self.opt)))
+
+    def load_csr(self, off, col, w):
+        dev = _is_device(off)
+        if not dev:
+            off = np.ascontiguousarray(off, dtype=np.int64)
+            col = np.ascontiguousarray(col, dtype=np.int32)
+            w = np.ascontiguousarray(w, dtype=np.int32)
+        n = len(off) - 1
+        nnz = len(col)
+        self._keep = (off, col, w)
+        self._check(self.lib.louvain_load_csr(self.h, n, nnz, _ptr(off), _ptr(col), _ptr(w),
+                                              PTR_DEVICE if dev else PTR_HOST))
+        self._keep = None
+        self.n = n
+
+    def run(self):
+        self._check(self.lib.louvain_run(self.h))
+
+    def membership(self, out=None) -> np.ndarray:
+        if out is None:
+            out = np.empty(self.n, np.int32)
+        self._check(self.lib.louvain_get_membership(self.h, _ptr(out), self.n,
+                                                    PTR_DEVICE if _is_device(out) else PTR_HOST))
+        return out
+
+    def modularity(self) -> float:
+        q = ctypes.c_double()
+        self._check(self.lib.louvain_get_modularity(self.h, ctypes.byref(q)))
+        return q.value
+
+    def modularity_exact(self):
+        hi, lo, M = ctypes.c_int64(), ctypes.c_uint64(), ctypes.c_int64()
+        self._check(self.lib.louvain_get_modularity_exact(self.h, ctypes.byref(hi), ctypes.byref(lo), ctypes.byref(M)))
+        return _i128(hi.value, lo.value), M.value
+
+    def modularity_of(self, memb):
+        """(Q, exact numerator, M) of an arbitrary membership of the loaded graph, on the device."""
+        dev = _is_device(memb)
+        if not dev:
+            memb = np.ascontiguousarray(memb, dtype=np.int32)
+        q, hi, lo, M = ctypes.c_double(), ctypes.c_int64(), ctypes.c_uint64(), ctypes.c_int64()
+        self._check(self.lib.louvain_modularity(self.h, _ptr(memb), self.n, PTR_DEVICE if dev else PTR_HOST,
+                                                ctypes.byref(q), ctypes.byref(hi), ctypes.byref(lo), ctypes.byref(M)))
+        return q.value, _i128(hi.value, lo.value), M.value
+
+    def stats(self) -> Stats:
+        s = Stats()
+        self._check(self.lib.louvain_get_stats(self.h, ctypes.byref(s)))
+        return s
+
+    def passes(self) -> List[PassRecord]:
+        out = []
+        st = self.stats()
+        for p in range(st.passes):
+            pi = PassInfo()
+            self._check(self.lib.louvain_get_pass_info(self.h, p, ctypes.byref(pi)))
+            out.append(PassRecord(pi.n, pi.nnz, pi.k, pi.moves, pi.iterations, _i128(pi.n_before_hi, pi.n_before_lo),
+                                  _i128(pi.n_after_hi, pi.n_after_lo), bool(pi.coarse_built), pi.coarse_nnz,
+                                  pi.lm_ms, pi.agg_ms))
+        return out
+
+    def iterations(self):
+        """[(pass, moves, S exact)] of every local-moving iteration of the last run."""
+        st = self.stats()
+        buf = np.zeros(4, np.int64)
+        out = []
+        for t in range(st.iterations):
+            self._check(self.lib.louvain_get_iteration(self.h, t, buf.ctypes.data))
+            out.append((int(buf[0]), int(buf[1]), _i128(buf[2], buf[3])))
+        return out
+
+    def level(self, p: int, n: int) -> np.ndarray:
+        out = np.empty(n, np.int32)
+        self._check(self.lib.louvain_get_level(self.h, p, out.ctypes.data, n))
+        return out
+
+    def coarse(self, p: int, k: int, nnz: int):
+        off = np.empty(k + 1, np.int64)
+        col = np.empty(max(nnz, 1), np.int32)
+        w = np.empty(max(nnz, 1), np.int64)
+        self._check(self.lib.louvain_get_coarse(self.h, p, off.ctypes.data, k, col.ctypes.data, w.ctypes.data, nnz))
+        return off, col[:nnz], w[:nnz]
+
+    def device_bytes(self) -> int:
+        b = ctypes.c_int64()
+        self._check(self.lib.louvain_get_device_bytes(self.h, ctypes.byref(b)))
+        return b.value

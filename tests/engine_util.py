@@ -1,0 +1,72 @@
+"""Helpers shared by the GPU tests: run the engine and the oracle on one graph and compare."""
+import numpy as np
+
+import oracle
+from paper_2301_12390_gb300 import Louvain
+
+
+def sorted_rows(off, col, w):
+    """Rows of a CSR with entries sorted by column (coarse rows come out in no particular order)."""
+    off = np.asarray(off)
+    col2 = np.empty_like(col)
+    w2 = np.empty_like(w)
+    for r in range(len(off) - 1):
+        a, b = int(off[r]), int(off[r + 1])
+        o = np.argsort(col[a:b], kind="stable")
+        col2[a:b] = col[a:b][o]
+        w2[a:b] = w[a:b][o]
+    return col2, w2
+
+
+def engine_run(g, **opt):
+    with Louvain(device=0, **opt) as lv:
+        lv.load_csr(g.off, g.col, g.w)
+        lv.run()
+        out = {
+            "top": lv.membership(),
+            "q": lv.modularity(),
+            "exact": lv.modularity_exact(),
+            "iters": lv.iterations(),
+            "passes": lv.passes(),
+            "stats": lv.stats(),
+        }
+        if opt.get("record_levels"):
+            lv_levels, coarse = [], []
+            for p, ps in enumerate(out["passes"]):
+                lv_levels.append(lv.level(p, ps.n) if ps.moves > 0 else None)
+                coarse.append(lv.coarse(p, ps.k, ps.coarse_nnz) if ps.coarse_built else None)
+            out["levels"] = lv_levels
+            out["coarse"] = coarse
+        return out
+
+
+def assert_sync_parity(g, **opt):
+    """Bit-exact synchronous parity: top membership, exact Q, every iteration's (moves, S),
+    every pass's level and coarse CSR."""
+    kw = dict(opt)
+    kw["mode"] = 0
+    kw["record_levels"] = 1
+    got = engine_run(g, **kw)
+    ref = oracle.louvain(g.off, g.col, g.w, mode=oracle.SYNC, record_levels=True,
+                         prune=kw.get("prune", 0), singleton_guard=kw.get("singleton_guard", 1),
+                         subrounds=kw.get("subrounds", 1), max_iterations=kw.get("max_iterations", 20),
+                         max_passes=kw.get("max_passes", 10), tolerance=kw.get("tolerance", 0.01),
+                         tolerance_decline=kw.get("tolerance_decline", 10.0))
+    assert got["iters"] == list(ref.iterations), "per-iteration (pass, moves, S) differ"
+    assert len(got["passes"]) == len(ref.passes)
+    for p, (gp, rp) in enumerate(zip(got["passes"], ref.passes)):
+        assert (gp.n, gp.nnz, gp.k, gp.moves, gp.iterations) == (rp.n, rp.nnz, rp.k, rp.moves, rp.iterations), p
+        assert gp.n_before == rp.n_before and gp.n_after == rp.n_after, p
+        if rp.level is not None:
+            assert np.array_equal(got["levels"][p], rp.level), f"level of pass {p} differs"
+        assert gp.coarse_built == (rp.coarse is not None), p
+        if rp.coarse is not None:
+            co, cc, cw = got["coarse"][p]
+            ro, rc, rw = rp.coarse
+            assert np.array_equal(co, ro), f"coarse offsets of pass {p} differ"
+            cc2, cw2 = sorted_rows(co, cc, cw)
+            assert np.array_equal(cc2, rc) and np.array_equal(cw2, rw), f"coarse rows of pass {p} differ"
+    assert np.array_equal(got["top"], ref.top)
+    assert got["exact"] == (ref.q_num, ref.M)
+    assert got["q"] == ref.Q
+    return got, ref

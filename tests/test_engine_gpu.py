@@ -1,0 +1,213 @@
+"""GPU parity of the CUDA engine against the oracle, through the C ABI.
+
+Synchronous mode: bit-exact (top membership, exact modularity numerator,
+every iteration's move count and gain sum S, every pass's level and coarse
+CSR).  Asynchronous mode: final modularity no lower than the oracle's minus
+0.01.  Inputs are the seeded synthetic graphs of the benchmark configurations
+at sizes the oracle finishes in seconds, chosen so that every degree class of
+the local-moving phase (thread, warp, block, hub) and of the aggregation
+phase is used, plus edge cases.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from engine_util import assert_sync_parity, engine_run
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "hand_runs.json")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _engine():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def graphs():
+    return {
+        "sbm600": gg.sbm(11, 600, 12, 0.15, 0.01, wmin=1, wmax=9),
+        "sbm8192": gg.sbm(0x5EED, 8192, 64, 0.1, 0.0005),          # the small benchmark configuration
+        "rmat14": gg.rmat(0x5EED + 1, 14, 16, wmin=1, wmax=8),
+        "rmat16": gg.rmat(0x5EED + 1, 16, 16, wmin=1, wmax=8),     # hubs of degree > 4096
+        "road128": gg.grid_road(0x5EED + 2, 128),
+    }
+
+
+G = graphs()
+
+
+# ------------------------------------------------------------- hand runs
+
+def test_hand_worked_runs_on_gpu():
+    with open(GOLDEN) as f:
+        cases = json.load(f)["cases"]
+    for case in cases:
+        if case["options"] is None:
+            continue
+        g = gg.from_weighted_edges(case["n"], [tuple(e) for e in case["edges"]])
+        o = dict(case["options"])
+        mode = 0 if o.pop("mode") == "sync" else 1
+        ex = case["expect"]
+        for prune in (0, 1):
+            got = engine_run(g, mode=mode, prune=prune, **o)
+            if mode == 0:
+                assert list(got["top"]) == ex["top"], case["name"]
+                assert got["exact"] == (ex["q_num"], ex["M"]), case["name"]
+                assert [list(t) for t in got["iters"]] == ex["iterations"], case["name"]
+            else:
+                assert got["q"] >= ex["Q"] - 0.01, case["name"]
+
+
+# --------------------------------------------------------- sync parity
+
+@pytest.mark.parametrize("name", list(G))
+@pytest.mark.parametrize("prune", [0, 1])
+def test_sync_parity(name, prune):
+    assert_sync_parity(G[name], prune=prune)
+
+
+@pytest.mark.parametrize("name", ["sbm8192", "rmat16", "road128"])
+@pytest.mark.parametrize("subrounds", [4, 16])
+def test_sync_parity_subrounds(name, subrounds):
+    assert_sync_parity(G[name], prune=1, subrounds=subrounds)
+
+
+@pytest.mark.parametrize("name", ["sbm600", "rmat14"])
+def test_sync_parity_plain_jacobi(name):
+    assert_sync_parity(G[name], singleton_guard=0)
+
+
+def test_sync_parity_wide_arithmetic():
+    """Weights near the int32 maximum: M >= 2^31, so gains need 128 bits and
+    coarse weights 64 bits."""
+    base = gg.sbm(5, 700, 10, 0.12, 0.01)
+    # weights from the unordered pair keep the CSR symmetric
+    rows = np.repeat(np.arange(base.n), np.diff(base.off))
+    lo, hi = np.minimum(rows, base.col), np.maximum(rows, base.col)
+    w = (2**31 - 1 - ((lo.astype(np.int64) * 131 + hi) % 1000)).astype(np.int32)
+    g = gg.CSR(base.n, base.off, base.col, w)
+    got, ref = assert_sync_parity(g, prune=1)
+    assert ref.M >= 2**31
+
+
+def test_sync_parity_max_iterations_and_passes():
+    g = G["sbm8192"]
+    assert_sync_parity(g, max_iterations=1)
+    assert_sync_parity(g, max_passes=1)
+    assert_sync_parity(g, max_passes=2, tolerance=0.0)
+
+
+# ------------------------------------------------------- async quality
+
+@pytest.mark.parametrize("name", list(G))
+@pytest.mark.parametrize("prune,subrounds", [(0, 1), (1, 1), (1, 8)])
+def test_async_quality(name, prune, subrounds):
+    g = G[name]
+    got = engine_run(g, mode=1, prune=prune, subrounds=subrounds)
+    ref = oracle.louvain(g.off, g.col, g.w, mode=oracle.ASYNC, prune=prune)
+    assert got["q"] >= ref.Q - 0.01, (got["q"], ref.Q)
+    # the reported modularity is that of the reported membership, exactly
+    _, num, M = oracle.modularity(g.off, g.col, g.w, got["top"])
+    assert got["exact"] == (num, M)
+
+
+# ---------------------------------------------------------- edge cases
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_edge_cases(mode):
+    cases = [
+        gg.from_weighted_edges(1, []),
+        gg.from_weighted_edges(5, []),
+        gg.from_weighted_edges(3, [(1, 1, 4)]),
+        gg.from_weighted_edges(6, [(0, 1, 1), (2, 2, 3), (4, 5, 2)]),
+        gg.from_weighted_edges(4, [(0, 1, 5), (1, 2, 5), (2, 3, 5), (3, 0, 5), (0, 0, 2)]),
+    ]
+    for g in cases:
+        got = engine_run(g, mode=mode)
+        ref = oracle.louvain(g.off, g.col, g.w, mode=mode)
+        if mode == 0:
+            assert np.array_equal(got["top"], ref.top)
+            assert got["exact"] == (ref.q_num, ref.M)
+        else:
+            assert got["q"] >= ref.Q - 0.01
+
+
+def test_empty_graph():
+    from paper_2301_12390_gb300 import Louvain
+    with Louvain(device=0) as lv:
+        lv.load_csr(np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int32))
+        lv.run()
+        assert lv.modularity() == 0.0 and len(lv.membership()) == 0
+
+
+# ------------------------------------------------------ modularity API
+
+def test_modularity_of_arbitrary_memberships():
+    from paper_2301_12390_gb300 import Louvain
+    rng = np.random.default_rng(3)
+    for g in (G["sbm600"], G["rmat14"]):
+        with Louvain(device=0) as lv:
+            lv.load_csr(g.off, g.col, g.w)
+            for k in (1, 7, g.n):
+                memb = rng.integers(0, k, g.n).astype(np.int32)
+                q, num, M = lv.modularity_of(memb)
+                rq, rnum, rM = oracle.modularity(g.off, g.col, g.w, memb)
+                assert (num, M) == (rnum, rM) and q == rq
+
+
+# ---------------------------------------------------------- input errors
+
+def test_input_errors():
+    from paper_2301_12390_gb300 import Louvain, LouvainError
+    g = G["sbm600"]
+    with Louvain(device=0) as lv:
+        with pytest.raises(LouvainError) as e:
+            lv.run()
+        assert e.value.code == -7                                   # STATE: run before load
+        bad = g.w.copy()
+        bad[0] += 1                                                 # (u,v) and (v,u) weights differ
+        with pytest.raises(LouvainError) as e:
+            lv.load_csr(g.off, g.col, bad)
+        assert e.value.code == -2
+        bad = g.w.copy()
+        bad[3] = 0
+        with pytest.raises(LouvainError) as e:
+            lv.load_csr(g.off, g.col, bad)
+        assert e.value.code == -3
+        badc = g.col.copy()
+        badc[5] = g.n
+        with pytest.raises(LouvainError) as e:
+            lv.load_csr(g.off, badc, g.w)
+        assert e.value.code == -3
+        bado = g.off.copy()
+        bado[10], bado[11] = bado[11], bado[10] + 5
+        with pytest.raises(LouvainError) as e:
+            lv.load_csr(bado, g.col, g.w)
+        assert e.value.code == -3
+        lv.load_csr(g.off, g.col, g.w)                              # still usable afterwards
+        lv.run()
+        assert lv.modularity() > 0.3
+
+
+# ------------------------------------------------------- device inputs
+
+def test_device_pointers_match_host():
+    import torch
+    from paper_2301_12390_gb300 import Louvain
+    g = G["rmat14"]
+    host = engine_run(g, mode=0)
+    with Louvain(device=0, mode=0) as lv:
+        lv.load_csr(torch.from_numpy(g.off).cuda(), torch.from_numpy(g.col).cuda(), torch.from_numpy(g.w).cuda())
+        lv.run()
+        out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        lv.membership(out)
+        assert np.array_equal(out.cpu().numpy(), host["top"])
