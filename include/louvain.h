@@ -74,7 +74,8 @@ typedef struct {
                                  single-vertex community of higher id (minimum-label rule, Grappolo;
                                  stops Jacobi updates from swapping pairs forever) */
   int32_t subrounds;          /* P >= 1: the vertices are split into classes i mod P processed one
-                                 after the other in each iteration; 1 = every vertex at once */
+                                 after the other in each iteration; 1 = every vertex at once;
+                                 0 = automatic (synchronous 1, asynchronous 16) */
   int32_t validate;           /* 1: louvain_load_csr checks symmetry and CSR form (costs a pass) */
   int32_t record_levels;      /* 1: keep each pass's membership and coarse CSR for louvain_get_level /
                                  louvain_get_coarse (copies them to host memory) */

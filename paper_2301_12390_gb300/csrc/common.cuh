@@ -128,6 +128,29 @@ __device__ __forceinline__ bool table_add_pow2(int32_t* keys, unsigned long long
   return false;
 }
 
+// Same, also reporting the slot and whether the key is new (for touched-slot
+// lists).  Returns -1 if the table is full.
+template <int CAP>
+__device__ __forceinline__ int table_add_pow2_slot(int32_t* keys, unsigned long long* vals, int32_t key,
+                                                   unsigned long long w, bool* fresh) {
+  uint32_t h = hash32((uint32_t)key) & (CAP - 1);
+  *fresh = false;
+#pragma unroll 1
+  for (int probe = 0; probe < CAP; ++probe) {
+    int32_t k = keys[h];
+    if (k == kEmpty) {
+      k = atomicCAS(&keys[h], kEmpty, key);
+      if (k == kEmpty) *fresh = true;
+    }
+    if (k == kEmpty || k == key) {
+      atomicAdd(&vals[h], w);
+      return (int)h;
+    }
+    h = (h + 1) & (CAP - 1);
+  }
+  return -1;
+}
+
 // Lookup in a power-of-two table; 0 if absent.
 template <int CAP>
 __device__ __forceinline__ unsigned long long table_get_pow2(const int32_t* keys, const unsigned long long* vals,

@@ -285,23 +285,41 @@ __device__ __forceinline__ int row_of(const int64_t* soff, int nr, int64_t x) {
   return lo;
 }
 
+// Row sums: warps take consecutive 32-entry chunks of the block's rows; a
+// segmented scan across the warp (rows are non-decreasing along the chunk)
+// leaves each row's chunk total on the row's last lane, which adds it to the
+// row in shared memory — one atomic per (row, chunk) instead of per entry.
 template <typename W>
 __global__ void __launch_bounds__(kT) row_sums_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
                                                  const W* __restrict__ wt, int64_t n, long long* K,
                                                  unsigned long long* acc) {
   __shared__ int64_t soff[kT + 1];
   __shared__ unsigned long long ks[kT];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t v0 = (int64_t)blockIdx.x * kT;
   const int nr = (int)min((int64_t)kT, n - v0);
   for (int t = threadIdx.x; t <= nr; t += kT) soff[t] = off[v0 + t];
   ks[threadIdx.x] = 0;
   __syncthreads();
   unsigned long long loops = 0;
-  for (int64_t x = soff[0] + threadIdx.x; x < soff[nr]; x += kT) {
-    int r = row_of(soff, nr, x);
-    unsigned long long w = (unsigned long long)wt[x];
-    atomicAdd(&ks[r], w);
-    if (col[x] == v0 + r) loops += w;
+  const int64_t e0 = soff[0], e1 = soff[nr];
+  for (int64_t c0 = e0 + (int64_t)wid * kWarp; c0 < e1; c0 += (int64_t)(kT / kWarp) * kWarp) {
+    const int64_t x = c0 + lane;
+    int r = -1;
+    unsigned long long v = 0;
+    if (x < e1) {
+      r = row_of(soff, nr, x);
+      v = (unsigned long long)wt[x];
+      if (col[x] == v0 + r) loops += v;
+    }
+#pragma unroll
+    for (int d = 1; d < kWarp; d <<= 1) {
+      unsigned long long u = __shfl_up_sync(0xffffffffu, v, d);
+      int ru = __shfl_up_sync(0xffffffffu, r, d);
+      if (lane >= d && ru == r) v += u;
+    }
+    int rn = __shfl_down_sync(0xffffffffu, r, 1);
+    if (r >= 0 && (lane == kWarp - 1 || rn != r)) atomicAdd(&ks[r], v);
   }
   __syncthreads();
   u128 mine = 0;

@@ -27,19 +27,23 @@ namespace gbl {
 
 // --------------------------------------------------------- small helpers
 
+// Synchronous launches never write memberships, totals or sizes, so they
+// read them through the read-only path; asynchronous launches use plain
+// loads, which may return a value that another vertex has since changed —
+// exactly the staleness the asynchronous variant allows.
 template <bool ASYNC>
 __device__ __forceinline__ int32_t ld_memb(const int32_t* p) {
-  if (ASYNC) return *(const volatile int32_t*)p;
+  if (ASYNC) return *p;
   return __ldg(p);
 }
 template <bool ASYNC>
 __device__ __forceinline__ long long ld_sig(const long long* p) {
-  if (ASYNC) return *(const volatile long long*)p;
+  if (ASYNC) return *p;
   return __ldg(p);
 }
 template <bool ASYNC>
 __device__ __forceinline__ int32_t ld_size(const int32_t* p) {
-  if (ASYNC) return *(const volatile int32_t*)p;
+  if (ASYNC) return *p;
   return __ldg(p);
 }
 
@@ -218,16 +222,19 @@ template <typename W, bool WIDE, bool ASYNC, int CAP, int THREADS>
 __global__ void __launch_bounds__(THREADS) lm_block(LMArgs<W> a, const int32_t* __restrict__ verts, int nverts) {
   typedef typename Arith<WIDE>::S S;
   constexpr int NW = THREADS / kWarp;
+  // dynamic shared memory: values (CAP u64), keys (CAP i32), touched slots (CAP/2 i32)
   extern __shared__ unsigned long long dyn[];
   unsigned long long* vals = dyn;
   int32_t* keys = (int32_t*)(dyn + CAP);
+  int32_t* touched = keys + CAP;
   __shared__ BlockAcc acc;
   __shared__ S red_g[NW];
   __shared__ int32_t red_c[NW];
   __shared__ unsigned long long s_kid;
-  __shared__ int s_moved;
+  __shared__ int s_moved, s_nt;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   acc_init(acc);
+  if (threadIdx.x == 0) s_nt = 0;
   for (int t = threadIdx.x; t < CAP; t += THREADS) { keys[t] = kEmpty; vals[t] = 0; }
   __syncthreads();
   bool ok = true;
@@ -239,24 +246,29 @@ __global__ void __launch_bounds__(THREADS) lm_block(LMArgs<W> a, const int32_t* 
     long long Ki = a.K[i];
     for (int64_t x = b + threadIdx.x; x < e; x += THREADS) {
       int32_t j = a.col[x];
-      if (j != i) ok &= table_add_pow2<CAP>(keys, vals, ld_memb<ASYNC>(a.memb + j), (unsigned long long)a.wt[x]);
+      if (j != i) {
+        bool fresh;
+        int h = table_add_pow2_slot<CAP>(keys, vals, ld_memb<ASYNC>(a.memb + j), (unsigned long long)a.wt[x], &fresh);
+        if (h < 0) ok = false;
+        else if (fresh) touched[atomicAdd(&s_nt, 1)] = h;
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) s_kid = table_get_pow2<CAP>(keys, vals, d);
     __syncthreads();
+    const int nt = s_nt;
     S score_d = Arith<WIDE>::score(a.M, (long long)s_kid, Ki, ld_sig<ASYNC>(a.sig + d) - Ki);
     S bg = 0;
     int32_t bc = -1;
-    for (int t = threadIdx.x; t < CAP; t += THREADS) {
-      int32_t c = keys[t];
-      if (c != kEmpty) {
-        if (c != d) {
-          S g = Arith<WIDE>::score(a.M, (long long)vals[t], Ki, ld_sig<ASYNC>(a.sig + c)) - score_d;
-          if (better(g, c, bg, bc)) { bg = g; bc = c; }
-        }
-        keys[t] = kEmpty;
-        vals[t] = 0;
+    for (int t = threadIdx.x; t < nt; t += THREADS) {
+      int h = touched[t];
+      int32_t c = keys[h];
+      if (c != d) {
+        S g = Arith<WIDE>::score(a.M, (long long)vals[h], Ki, ld_sig<ASYNC>(a.sig + c)) - score_d;
+        if (better(g, c, bg, bc)) { bg = g; bc = c; }
       }
+      keys[h] = kEmpty;
+      vals[h] = 0;
     }
     warp_argmax(bg, bc);
     if (lane == 0) { red_g[wid] = bg; red_c[wid] = bc; }
@@ -268,6 +280,7 @@ __global__ void __launch_bounds__(THREADS) lm_block(LMArgs<W> a, const int32_t* 
       if (lane == 0) {
         atomicAdd(&acc.edges, (unsigned long long)(e - b));
         s_moved = commit_choice<W, WIDE, ASYNC>(a, acc, i, d, Ki, bg, bc);
+        s_nt = 0;
       }
     }
     __syncthreads();
@@ -290,6 +303,12 @@ constexpr int kHubChunk = 2048;
 template <typename W, bool ASYNC>
 __global__ void __launch_bounds__(256) lm_hub_insert(LMArgs<W> a, const int32_t* __restrict__ hubs, int nhubs,
                                                      const int64_t* __restrict__ chunk_pre) {
+  // a chunk's entries are first summed per community in a shared table, then
+  // each distinct community is added once to the hub's global table
+  constexpr int CAP = 2 * kHubChunk;
+  extern __shared__ unsigned long long hdyn[];
+  unsigned long long* svals = hdyn;
+  int32_t* skeys = (int32_t*)(hdyn + CAP);
   // find the hub of this block: last h with chunk_pre[h] - chunk_pre[0] <= blockIdx.x
   const int64_t cb = chunk_pre[0];
   int lo = 0, hi = nhubs;
@@ -299,8 +318,10 @@ __global__ void __launch_bounds__(256) lm_hub_insert(LMArgs<W> a, const int32_t*
   }
   const int h = lo;
   const int32_t i = hubs[h];
-  if (!is_active(a, i)) return;
+  if (!is_active(a, i)) return;   // uniform across the block
   const int64_t q = (int64_t)blockIdx.x - (chunk_pre[h] - cb);
+  for (int t = threadIdx.x; t < CAP; t += blockDim.x) { skeys[t] = kEmpty; svals[t] = 0; }
+  __syncthreads();
   const int64_t b = a.off[i], e = a.off[i + 1];
   const int64_t base = a.hbase[h];
   const uint32_t cap = (uint32_t)(2 * (e - b));
@@ -311,9 +332,14 @@ __global__ void __launch_bounds__(256) lm_hub_insert(LMArgs<W> a, const int32_t*
   for (int64_t x = x0 + threadIdx.x; x < x1; x += blockDim.x) {
     int32_t j = a.col[x];
     if (j == i) continue;
-    int32_t c = ld_memb<ASYNC>(a.memb + j);
+    ok &= table_add_pow2<CAP>(skeys, svals, ld_memb<ASYNC>(a.memb + j), (unsigned long long)a.wt[x]);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < CAP; t += blockDim.x) {
+    int32_t c = skeys[t];
+    if (c == kEmpty) continue;
     bool fresh;
-    ok &= gtable_add(keys, vals, cap, c, (unsigned long long)a.wt[x], &fresh);
+    ok &= gtable_add(keys, vals, cap, c, svals[t], &fresh);
     if (fresh) {
       int pos = atomicAdd(a.hcount + h, 1);
       a.hslots[base + pos] = c;   // record the key; the decide step looks it up
@@ -452,14 +478,14 @@ void launch_bucket_t(const LMArgs<W>& a, int bucket, const int32_t* verts, int n
     }
     case 3: {
       constexpr int CAP = 2048;
-      size_t smem = (size_t)CAP * 12;
+      size_t smem = (size_t)CAP * 14;
       auto k = lm_block<W, WIDE, ASYNC, CAP, 128>;
       k<<<grid_for(k, 128, smem, nverts), 128, smem, s>>>(a, verts, nverts);
       break;
     }
     case 4: {
       constexpr int CAP = 8192;
-      size_t smem = (size_t)CAP * 12;
+      size_t smem = (size_t)CAP * 14;
       auto k = lm_block<W, WIDE, ASYNC, CAP, 256>;
       static bool attr = false;
       if (!attr) {
@@ -491,8 +517,9 @@ template <typename W>
 void lm_launch_hubs(const LMArgs<W>& a, bool wide, bool async, const int32_t* hubs, int nhubs,
                     const int64_t* chunk_pre, int64_t nchunks, cudaStream_t s) {
   if (nhubs <= 0 || nchunks <= 0) return;
-  if (async) lm_hub_insert<W, true><<<(unsigned)nchunks, 256, 0, s>>>(a, hubs, nhubs, chunk_pre);
-  else lm_hub_insert<W, false><<<(unsigned)nchunks, 256, 0, s>>>(a, hubs, nhubs, chunk_pre);
+  const size_t smem = (size_t)(2 * kHubChunk) * 12;
+  if (async) lm_hub_insert<W, true><<<(unsigned)nchunks, 256, smem, s>>>(a, hubs, nhubs, chunk_pre);
+  else lm_hub_insert<W, false><<<(unsigned)nchunks, 256, smem, s>>>(a, hubs, nhubs, chunk_pre);
   int g = nhubs < 4096 ? nhubs : 4096;
   if (wide) {
     if (async) lm_hub_decide<W, true, true><<<g, 256, 0, s>>>(a, hubs, nhubs);

@@ -109,7 +109,7 @@ def test_sync_parity_max_iterations_and_passes():
 # ------------------------------------------------------- async quality
 
 @pytest.mark.parametrize("name", list(G))
-@pytest.mark.parametrize("prune,subrounds", [(0, 1), (1, 1), (1, 8)])
+@pytest.mark.parametrize("prune,subrounds", [(0, 0), (1, 0), (1, 32)])
 def test_async_quality(name, prune, subrounds):
     g = G[name]
     got = engine_run(g, mode=1, prune=prune, subrounds=subrounds)
