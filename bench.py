@@ -1,0 +1,313 @@
+#!/usr/bin/env python3
+"""Benchmark of the Louvain hot path (local-moving + aggregation) on one GB300.
+
+One step = one full Louvain run (every pass: local-moving iterations,
+renumbering, aggregation) on a graph already resident in HBM.  The metric is
+local-moving throughput: CSR entries scanned by the local-moving phase per
+second of whole-step device time.  The default workload is the R-MAT scale-22
+graph (4,194,304 vertices, edge factor 16, a/b/c/d = .57/.19/.19/.05,
+symmetrised, self-loops and duplicates merged, weights uniform in 1..8) in the
+asynchronous mode the paper recommends (tolerance 0.01, decline factor 10).
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle
+(single-threaded C, the correctness reference) on a bounded sample of the same
+workload instead.  Under torchrun each rank runs its own replica of the
+workload on its own GPU (a single graph does not shard; replicas only) and
+value = all ranks' entries / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import graphgen as gg  # noqa: E402
+
+SEED = 0x5EED
+WORKLOADS = {
+    # name: (builder, description)
+    "rmat22": (lambda: gg.rmat(SEED + 1, 22, 16, 0.57, 0.19, 0.19, wmin=1, wmax=8),
+               "R-MAT scale 22 (4,194,304 vertices, edge factor 16, a,b,c,d = .57,.19,.19,.05), symmetrised, "
+               "self-loops and duplicates merged, int32 weights uniform 1..8"),
+    "sbm8192": (lambda: gg.sbm(SEED, 8192, 64, 0.1, 0.0005),
+                "planted-partition SBM: 8,192 vertices in 64 blocks of 128, p_in 0.1, p_out 0.0005, weight 1"),
+    "road4096": (lambda: gg.grid_road(SEED + 2, 4096, 0.1, 0.001, wmin=1, wmax=100),
+                 "road-like 4096x4096 grid, 10% of edges dropped, 0.1% long-range shortcuts, weights 1..100"),
+}
+METRIC = "edges/sec in local-moving"
+UNIT = "edges/s"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join("/tmp", f"gbl_clocks_{os.getpid()}.csv")
+
+    def _smi_id(self) -> str:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").strip()
+        if vis:
+            ids = [x.strip() for x in vis.split(",") if x.strip()]
+            if self.device < len(ids):
+                return ids[self.device]
+        return str(self.device)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self._smi_id()}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() in ("active", "1", "yes"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg, device):
+    if pg is not None:
+        import torch
+        pg.barrier(device_ids=[device]) if pg.get_backend() == "nccl" else pg.barrier()
+        torch.cuda.synchronize()
+
+
+def max_over_ranks(pg, x: float, device) -> float:
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=f"cuda:{device}")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(pg, x: float, device) -> float:
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=f"cuda:{device}")
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+def run_oracle_sample(g, mode, max_passes=10, max_iterations=20):
+    """One oracle run; returns (local-moving entries scanned, seconds, Q)."""
+    import oracle
+    t = time.perf_counter()
+    r = oracle.louvain(g.off, g.col, g.w, mode=mode, prune=0, max_passes=max_passes, max_iterations=max_iterations)
+    dt = time.perf_counter() - t
+    entries = sum(p.nnz * p.iterations for p in r.passes)   # prune off: every vertex visited every iteration
+    return entries, dt, r.Q
+
+
+def bench_reference(args):
+    """CPU oracle arm: each step is one local-moving iteration of the oracle over the whole graph."""
+    world, rank, _, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0, None
+    if rank != 0:
+        return
+    import oracle
+    g = WORKLOADS[args.workload][0]()
+    mode = oracle.ASYNC if args.mode == "async" else oracle.SYNC
+    for _ in range(args.warmup):
+        run_oracle_sample(g, mode, max_passes=1, max_iterations=1)
+    tot_e, tot_t, q = 0, 0.0, None
+    for _ in range(args.steps):
+        e, dt, q = run_oracle_sample(g, mode, max_passes=1, max_iterations=1)
+        tot_e += e
+        tot_t += dt
+    value = tot_e / tot_t
+    sample = f"first local-moving iteration (pass 0) over all {g.n} vertices / {g.nnz} entries, per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload][1], "mode": args.mode,
+                   "n": g.n, "nnz": g.nnz},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def bench_ours(args):
+    import torch
+    world, rank, local, pg = dist_setup()
+    device = local
+    torch.cuda.set_device(device)
+    from paper_2301_12390_gb300 import Louvain, SYNC, ASYNC
+    g = WORKLOADS[args.workload][0]()
+    mode = ASYNC if args.mode == "async" else SYNC
+    stream = torch.cuda.Stream(device=device)
+    lv = Louvain(device=device, stream=stream.cuda_stream, mode=mode, prune=1, validate=0)
+    # inputs resident in HBM before the timed region
+    d_off = torch.from_numpy(g.off).to(f"cuda:{device}")
+    d_col = torch.from_numpy(g.col).to(f"cuda:{device}")
+    d_w = torch.from_numpy(g.w).to(f"cuda:{device}")
+    torch.cuda.synchronize()
+    lv.load_csr(d_off, d_col, d_w)
+    for _ in range(args.warmup):
+        lv.run()
+    # timed region: K steps, CUDA events on the engine's stream
+    clocks = Clocks(device)
+    barrier(pg, device)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)   # let the sampler start before the load
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lm_edges = lm_bytes = launches = 0
+    lm_ms = agg_ms = 0.0
+    qs = []
+    start.record(stream)
+    for _ in range(args.steps):
+        lv.run()
+        st = lv.stats()
+        lm_edges += st.lm_edges
+        lm_bytes += st.lm_bytes
+        lm_ms += st.lm_ms
+        agg_ms += st.agg_ms
+        launches += st.kernel_launches
+        qs.append(st.q)
+    end.record(stream)
+    torch.cuda.synchronize()
+    barrier(pg, device)
+    ck = clocks.stop()
+    ms_local = start.elapsed_time(end)
+    ms = max_over_ranks(pg, ms_local, device)
+    all_edges = sum_over_ranks(pg, float(lm_edges), device)
+    value = all_edges / (ms / 1e3)
+    # roofline of the local-moving phase (the dominant part of the step)
+    hbm, peak_src = peaks()
+    achieved = lm_bytes / (lm_ms / 1e3) / 1e9
+    # end to end through the C ABI with host buffers: load (H2D), run, membership (D2H)
+    lv_e2e = Louvain(device=device, stream=stream.cuda_stream, mode=mode, prune=1)
+    memb = np.empty(g.n, np.int32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_edges = 0
+    e2e_steps = max(1, min(args.steps, 5))
+    for _ in range(e2e_steps):
+        lv_e2e.load_csr(g.off, g.col, g.w)
+        lv_e2e.run()
+        lv_e2e.membership(memb)
+        e2e_edges += lv_e2e.stats().lm_edges
+    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(pg, e2e_s, device)
+    e2e_value = sum_over_ranks(pg, float(e2e_edges), device) / e2e_s
+    h2d = g.off.nbytes + g.col.nbytes + g.w.nbytes
+    d2h = memb.nbytes
+    lv_e2e.close()
+    # CPU baseline: the oracle, as it stands, on rank 0 at N=1 only
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        e, dt, q_or = run_oracle_sample(g, oracle.ASYNC if mode == ASYNC else oracle.SYNC)
+        cpu = {"value": e / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one full oracle run ({args.mode}, prune off) of the same graph: "
+                         f"{e} local-moving entries in {dt:.1f} s, Q {q_or:.5f}"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": WORKLOADS[args.workload][1], "mode": args.mode,
+                       "n": g.n, "nnz": g.nnz, "prune": 1, "tolerance": 0.01, "tolerance_decline": 10,
+                       "parallelism": "replicas" if world > 1 else "single-gpu",
+                       "l2": "inputs larger than L2 (col+w %.0f MB)" % ((g.col.nbytes + g.w.nbytes) / 1e6),
+                       "modularity": qs[-1]},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": None, "kernel": "local-moving phase (all its kernels, CUDA events)",
+                         "peak_source": peak_src},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps},
+            "clocks": ck,
+            "gpu_launches": launches,
+            "breakdown": {"lm_ms_per_step": lm_ms / args.steps, "agg_ms_per_step": agg_ms / args.steps,
+                          "lm_edges_per_step": lm_edges / args.steps,
+                          "lm_only_edges_per_s": lm_edges / (lm_ms / 1e3)},
+        }
+        print(json.dumps(line), flush=True)
+    lv.close()
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS))
+    ap.add_argument("--mode", default="async", choices=["async", "sync"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

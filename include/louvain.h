@@ -95,7 +95,11 @@ typedef struct {
   double agg_ms;              /* device time of renumbering + aggregation */
   double other_ms;            /* pass set-up, modularity, bucketing */
   double total_ms;            /* device time of louvain_run */
-  int64_t reserved[8];
+  int64_t lm_vertices;        /* vertices visited by local-moving */
+  int64_t lm_bytes;           /* algorithmic bytes of local-moving: 8 + sizeof(weight) per scanned entry
+                                 (column, weight, neighbour membership) + 32 per visited vertex */
+  int64_t kernel_launches;    /* kernels the run launched */
+  int64_t reserved[5];
 } louvain_stats;
 
 /* Per-pass record. */

@@ -10,6 +10,11 @@
 
 namespace gbl {
 
+// Host-side count of the engine's kernel launches (every launch site is
+// written as `(count_launch(), kernel<<<...>>>(...))`).
+void count_launch();
+long long launches_so_far();
+
 typedef __int128 i128;
 typedef unsigned __int128 u128;
 
@@ -29,6 +34,7 @@ struct DevCounters {
   unsigned long long moves;
   unsigned long long s_lo, s_hi;   // sum of the gains of the moves (u128)
   unsigned long long edges;        // CSR entries scanned
+  unsigned long long visited;      // vertices visited
   unsigned long long nmoves_list;  // entries in the synchronous move list
   int error;
   int pad;
@@ -57,6 +63,7 @@ __device__ __forceinline__ void atomic_add_u128(unsigned long long* lo, unsigned
 template <bool WIDE> struct Arith;
 template <> struct Arith<false> {
   typedef long long S;
+  __device__ __forceinline__ static S lowest() { return (S)(-0x7fffffffffffffffll - 1); }
   __device__ __forceinline__ static S score(long long M, long long kix, long long Ki, long long sig) {
     return M * kix - Ki * sig;
   }
@@ -64,13 +71,16 @@ template <> struct Arith<false> {
 };
 template <> struct Arith<true> {
   typedef i128 S;
+  __device__ __forceinline__ static S lowest() { return (S)((u128)1 << 127); }
   __device__ __forceinline__ static S score(long long M, long long kix, long long Ki, long long sig) {
     return (i128)M * kix - (i128)Ki * sig;
   }
   __device__ __forceinline__ static u128 to_u128(S g) { return (u128)g; }
 };
 
-// (gain, community) ordering: larger gain first, ties to the lower id.
+// (score, community) ordering: larger first, ties to the lower id.  Since
+// every candidate's gain is its score minus the same score(d), the best score
+// is the best gain, and ties agree.
 template <typename S>
 __device__ __forceinline__ bool better(S g1, int32_t c1, S g2, int32_t c2) {
   return g1 > g2 || (g1 == g2 && (unsigned)c1 < (unsigned)c2);
@@ -221,12 +231,14 @@ struct LMArgs {
   int iter;
   int prune;
   int guard;
-  // hub path: per-hub global tables
+  // hub path: per-hub global tables (slots [hbase[h], hbase[h] + 2 deg))
   int32_t* hkeys;
   unsigned long long* hvals;
-  const int64_t* hbase;      // table offset of hub h (scan of capacities)
-  int32_t* hcount;           // distinct keys of hub h
-  int32_t* hslots;           // touched slots of hub h (at hbase[h])
+  const int64_t* hbase;      // table offset of hub h
+  const int64_t* spre;       // first slot chunk of hub h (absolute within the pass)
+  unsigned long long* hkid;  // K_{i->d} of hub h, looked up before the scan clears the table
+  long long* hpart;          // per slot chunk: best gain (lo, hi)
+  int32_t* hpart_c;          // per slot chunk: its community
 };
 
 }  // namespace gbl

@@ -18,6 +18,13 @@
 
 using namespace gbl;
 
+#include <atomic>
+namespace gbl {
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace gbl
+
 namespace {
 
 // Vertex classes per asynchronous iteration when the options leave it to the
@@ -89,13 +96,17 @@ struct louvain_ctx {
   unsigned char* tw = nullptr;
   int32_t* gkeys = nullptr;
   unsigned long long* gvals = nullptr;
-  int32_t* gslots = nullptr;
-  int32_t* gcount = nullptr;
   int64_t* gbase = nullptr;
   int64_t* chunk_pre = nullptr;
+  int64_t* spre = nullptr;
+  unsigned long long* hkid = nullptr;
+  long long* hpart = nullptr;
+  int32_t* hpart_c = nullptr;
+  int64_t npart = 0;
   unsigned char* tmp = nullptr;
   size_t tmp_bytes = 0;
   int64_t M0 = 0;                      // total weight of the loaded graph
+  i128 qnum0 = 0;                      // exact Q numerator of the singleton partition of the loaded graph
   DevCounters* ctr = nullptr;
   unsigned long long* acc = nullptr;   // 8 words of reduction scratch
   int* flags = nullptr;
@@ -110,6 +121,7 @@ struct louvain_ctx {
   i128 qnum = 0;
   double Q = 0.0;
   int64_t k_final = 0;
+  i128 agg_nafter = 0;                 // Q numerator found by the last aggregation
   std::vector<IterRec> iters;
   std::vector<PassRec> passes;
   louvain_stats stats;
@@ -192,7 +204,7 @@ struct PassState {
 
 template <typename W>
 int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool wide, int64_t* pass_moves,
-                 int* iters_out, int64_t* edges_out) {
+                 int* iters_out, int64_t* edges_out, int64_t* visited_out) {
   const bool async = c->opt.mode == LOUVAIN_ASYNC;
   const int P = c->opt.subrounds > 0 ? c->opt.subrounds : (async ? kAsyncSubrounds : 1);
   const int nkeys = kBuckets * P + 1;
@@ -206,12 +218,15 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
   // hubs: all classes' hub lists are contiguous
   const int64_t hub0 = ko[kHubBucket * P], hub1 = ko[kHubBucket * P + P];
   const int64_t nhubs = hub1 - hub0;
-  std::vector<int64_t> hchunks;
+  std::vector<int64_t> hchunks, hschunks;
   if (nhubs > 0) {
-    hub_layout(g.off, c->list + hub0, nhubs, c->gbase, c->chunk_pre, c->tmp, s);
+    hub_layout(g.off, c->list + hub0, nhubs, c->gbase, c->chunk_pre, c->spre, c->tmp, s);
     CKLAUNCH();
     hchunks.resize(nhubs + 1);
+    hschunks.resize(nhubs + 1);
     if (int r = fetch(c, hchunks.data(), c->chunk_pre, hchunks.size() * sizeof(int64_t))) return r;
+    if (int r = fetch(c, hschunks.data(), c->spre, hschunks.size() * sizeof(int64_t))) return r;
+    if (hschunks[nhubs] > c->npart) return fail(c, LOUVAIN_ERR_INTERNAL, "hub partial buffer too small");
   }
   LMArgs<W> a;
   memset(&a, 0, sizeof(a));
@@ -229,9 +244,10 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
   a.guard = c->opt.singleton_guard;
   a.hkeys = c->gkeys;
   a.hvals = c->gvals;
-  a.hslots = c->gslots;
+  a.hpart = c->hpart;
+  a.hpart_c = c->hpart_c;
   const i128 M2 = (i128)c->M * c->M;
-  int64_t moves_total = 0, edges_total = 0;
+  int64_t moves_total = 0, edges_total = 0, visited_total = 0;
   int it = 0;
   for (; it < c->opt.max_iterations; ++it) {
     CK(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), s));
@@ -247,9 +263,10 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
       if (h1 > h0) {
         LMArgs<W> ah = a;
         ah.hbase = c->gbase + h0;
-        ah.hcount = c->gcount + h0;
+        ah.spre = c->spre + h0;
+        ah.hkid = c->hkid + h0;
         lm_launch_hubs<W>(ah, wide, async, c->list + hub0 + h0, (int)(h1 - h0), c->chunk_pre + h0,
-                          hchunks[h1] - hchunks[h0], s);
+                          hchunks[h1] - hchunks[h0], c->spre + h0, hschunks[h1] - hschunks[h0], s);
       }
       if (!async) {
         int64_t cls = 0;
@@ -265,11 +282,13 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
     c->iters.push_back(IterRec{pass, mv, S});
     moves_total += mv;
     edges_total += (int64_t)c->h_ctr->edges;
+    visited_total += (int64_t)c->h_ctr->visited;
     if ((2.0 * (double)S) / dbl(M2) <= tol) { ++it; break; }
   }
   *pass_moves = moves_total;
   *iters_out = it;
   *edges_out = edges_total;
+  *visited_out = visited_total;
   return 0;
 }
 
@@ -314,20 +333,23 @@ int aggregate(louvain_ctx* c, const PassState& g, int64_t k, PassState* next) {
   a.rlen = c->rlen;
   a.gkeys = c->gkeys;
   a.gvals = c->gvals;
-  a.gcount = c->gcount;
-  a.gslots = c->gslots;
+  a.lsum = c->acc + 6;
   a.error = c->flags;
   // communities whose members have no edge get empty rows
   CK(cudaMemsetAsync(c->rlen, 0, (k + 1) * sizeof(int64_t), s));
+  CK(cudaMemsetAsync(c->acc, 0, 8 * sizeof(unsigned long long), s));
+  sum_squares(c->sig, g.n, c->acc + 4, s);   // sum of Sigma_c^2 for the pass's Q numerator
   for (int b = 0; b < kAggGlobal; ++b)
     agg_launch_bucket<W, W2>(a, b, c->list + ko[b], (int)(ko[b + 1] - ko[b]), s);
   const int64_t ng = ko[kAggGlobal + 1] - ko[kAggGlobal];
   if (ng > 0) {
-    agg_global_layout(c->cstart, c->mpre, c->list + ko[kAggGlobal], ng, c->gbase, c->chunk_pre, c->tmp, s);
-    int64_t nchunks = 0;
+    agg_global_layout(c->cstart, c->mpre, c->list + ko[kAggGlobal], ng, c->gbase, c->chunk_pre, c->spre, c->tmp, s);
+    int64_t nchunks = 0, nschunks = 0;
     CKLAUNCH();
     if (int r = fetch(c, &nchunks, c->chunk_pre + ng, sizeof(int64_t))) return r;
-    agg_launch_global<W, W2>(a, c->list + ko[kAggGlobal], (int)ng, c->gbase, c->chunk_pre, nchunks, s);
+    if (int r = fetch(c, &nschunks, c->spre + ng, sizeof(int64_t))) return r;
+    agg_launch_global<W, W2>(a, c->list + ko[kAggGlobal], (int)ng, c->gbase, c->chunk_pre, nchunks, c->spre,
+                             nschunks, s);
   }
   CKLAUNCH();
   // coarse offsets = scan of row lengths, written straight into the next graph
@@ -341,6 +363,12 @@ int aggregate(louvain_ctx* c, const PassState& g, int64_t k, PassState* next) {
   agg_compact<W2>(c->cstart, c->mpre, c->rlen, c->offX[dst], k, c->tcol, (const W2*)c->tw, c->colX[dst],
                   (W2*)c->wX[dst], s);
   CKLAUNCH();
+  // Q numerator after the pass: M * sum_C L_C (coarse self-loops) - sum_c Sigma_c^2
+  if (int r = fetch(c, c->h_acc, c->acc, 8 * sizeof(unsigned long long))) return r;
+  {
+    u128 SS = ((u128)c->h_acc[5] << 64) | (u128)c->h_acc[4];
+    c->agg_nafter = (i128)c->M * (i128)c->h_acc[6] - (i128)SS;
+  }
   next->n = k;
   next->nnz = nnz2;
   next->off = c->offX[dst];
@@ -380,16 +408,21 @@ int run_pass(louvain_ctx* c, const PassState& g, int pass, double* tol, bool wid
   CKLAUNCH();
   const i128 nbefore = c->qnum;
   const i128 M2 = (i128)c->M * c->M;
-  int64_t pmoves = 0, edges = 0;
+  int64_t pmoves = 0, edges = 0, visited = 0;
   int iters = 0;
   CK(cudaEventRecord(c->ev[1], s));
-  if (int r = local_moving<W>(c, g, pass, *tol, wide, &pmoves, &iters, &edges)) return r;
+  if (int r = local_moving<W>(c, g, pass, *tol, wide, &pmoves, &iters, &edges, &visited)) return r;
   CK(cudaEventRecord(c->ev[2], s));
   pr.info.moves = pmoves;
   pr.info.iterations = iters;
   pr.info.n_before_hi = (int64_t)(nbefore >> 64);
   pr.info.n_before_lo = (uint64_t)nbefore;
   c->stats.lm_edges += edges;
+  // algorithmic bytes of local-moving: per scanned entry its column, weight
+  // and neighbour membership; per visited vertex two offsets, its membership,
+  // degree, own community total and activity stamp (32 B)
+  c->stats.lm_vertices += visited;
+  c->stats.lm_bytes += edges * (int64_t)(4 + sizeof(W) + 4) + visited * 32;
   c->stats.moves += pmoves;
   c->stats.iterations += iters;
   c->stats.passes = pass + 1;
@@ -416,8 +449,18 @@ int run_pass(louvain_ctx* c, const PassState& g, int pass, double* tol, bool wid
   CKLAUNCH();
   int64_t k = 0;
   if (int r = fetch(c, &k, c->scal, sizeof(int64_t))) return r;
+  // If another pass may follow, aggregate first: the coarse self-loops give
+  // sum_C L_C, so the pass's Q numerator costs no extra scan of the graph; a
+  // coarse graph built for a pass that then stops is dropped.
   i128 nafter = 0;
-  if (int r = q_numerator<W>(c, g, &nafter)) return r;
+  bool built = false;
+  if (pass + 1 < c->opt.max_passes) {
+    if (int r = aggregate<W, W2>(c, g, k, next)) return r;
+    nafter = c->agg_nafter;
+    built = true;
+  } else {
+    if (int r = q_numerator<W>(c, g, &nafter)) return r;
+  }
   CK(cudaEventRecord(c->ev[3], s));
   pr.info.k = k;
   pr.info.n_after_hi = (int64_t)(nafter >> 64);
@@ -432,19 +475,14 @@ int run_pass(louvain_ctx* c, const PassState& g, int pass, double* tol, bool wid
   c->k_final = k;
   *stop = dbl(nafter - nbefore) / dbl(M2) <= c->opt.pass_tolerance || pass + 1 == c->opt.max_passes;
   float ms_agg = 0;
-  if (!*stop) {
-    if (int r = aggregate<W, W2>(c, g, k, next)) return r;
-    CK(cudaEventRecord(c->ev[4], s));
+  CK(cudaEventSynchronize(c->ev[3]));
+  cudaEventElapsedTime(&ms_agg, c->ev[2], c->ev[3]);
+  if (!*stop && built) {
     pr.info.coarse_built = 1;
     pr.info.coarse_nnz = next->nnz;
     if (c->opt.record_levels)
       if (int r = record_coarse<W2>(c, pr, *next)) return r;
-    CK(cudaEventSynchronize(c->ev[4]));
-    cudaEventElapsedTime(&ms_agg, c->ev[2], c->ev[4]);
     *tol = *tol / c->opt.tolerance_decline;
-  } else {
-    CK(cudaEventSynchronize(c->ev[3]));
-    cudaEventElapsedTime(&ms_agg, c->ev[2], c->ev[3]);
   }
   cudaEventElapsedTime(&ms_init, c->ev[0], c->ev[1]);
   cudaEventElapsedTime(&ms_lm, c->ev[1], c->ev[2]);
@@ -465,21 +503,17 @@ int run_all(louvain_ctx* c) {
   c->qnum = 0;
   c->Q = 0;
   c->k_final = c->n0;
+  const long long launches0 = launches_so_far();
   CK(cudaEventRecord(c->ev[6], s));
   iota_i32(c->top, c->n0, s);
-  // pass-0 degrees, M and the singleton numerator
-  CK(cudaMemsetAsync(c->acc, 0, 8 * sizeof(unsigned long long), s));
-  row_sums<int32_t>(c->off0, c->col0, c->w0, c->n0, c->K, c->acc + 4, s);
-  CKLAUNCH();
-  if (int r = fetch(c, c->h_acc, c->acc, 8 * sizeof(unsigned long long))) return r;
-  if (c->h_acc[5] != 0 || c->h_acc[4] >= (1ull << 62))
-    return fail(c, LOUVAIN_ERR_OVERFLOW, "total weight M must be below 2^62");
-  c->M = (int64_t)c->h_acc[4];
+  // pass-0 degrees, M and the singleton numerator were found when the graph
+  // was loaded
+  CK(cudaMemcpyAsync(c->K, c->K0, c->n0 * sizeof(long long), cudaMemcpyDeviceToDevice, s));
+  c->M = c->M0;
+  c->qnum = c->qnum0;
   const bool wide = c->M >= (1ll << 31);           // M^2 >= 2^62: 128-bit gains
   const bool coarse64 = c->M >= (1ll << 31) - 1;   // coarse weights can exceed int32
   PassState g{c->n0, c->nnz0, c->off0, c->col0, (void*)c->w0, -1};
-  pass_init(g.n, c->K, c->memb, c->sig, c->csize, c->stamp[0], c->stamp[1], s);
-  if (int r = q_numerator<int32_t>(c, g, &c->qnum)) return r;
   double tol = c->opt.tolerance;
   for (int p = 0; p < c->opt.max_passes && c->M > 0; ++p) {
     bool stop = false;
@@ -505,6 +539,7 @@ int run_all(louvain_ctx* c) {
   c->Q = c->M == 0 ? 0.0 : dbl(c->qnum) / dbl(M2);
   c->stats.q = c->Q;
   c->stats.communities = c->k_final;
+  c->stats.kernel_launches = launches_so_far() - launches0;
   return 0;
 }
 
@@ -622,13 +657,18 @@ int louvain_load_csr(louvain_ctx* c, int64_t n, int64_t nnz, const int64_t* offs
   ALLOC(c->tw, nnz * 8);
   ALLOC(c->gkeys, 2 * nnz);
   ALLOC(c->gvals, 2 * nnz);
-  ALLOC(c->gslots, 2 * nnz);
-  ALLOC(c->gcount, N1);
   ALLOC(c->gbase, N1);
   ALLOC(c->chunk_pre, N1);
+  ALLOC(c->spre, N1);
+  ALLOC(c->hkid, N1);
+  CK(cudaMemsetAsync(c->hkid, 0, N1 * sizeof(unsigned long long), c->stream));
+  // slot chunks of all hubs: sum of ceil(2 deg / kSlotChunk) <= 2 nnz / kSlotChunk + #hubs
+  c->npart = 2 * nnz / kSlotChunk + nnz / 4096 + 16;
+  ALLOC(c->hpart, 2 * c->npart);
+  ALLOC(c->hpart_c, c->npart);
   {
     size_t t1 = partition_tmp_bytes(n, kBuckets * 64 + 1);
-    size_t t2 = (size_t)N1 * 16 + scan_tmp_bytes(N1);
+    size_t t2 = (size_t)N1 * 24 + scan_tmp_bytes(N1);
     size_t t3 = scan_tmp_bytes(nnz + 1);
     c->tmp_bytes = std::max(t1, std::max(t2, t3));
     ALLOC(c->tmp, (int64_t)c->tmp_bytes);
@@ -646,7 +686,6 @@ int louvain_load_csr(louvain_ctx* c, int64_t n, int64_t nnz, const int64_t* offs
   }
   CK(cudaMemsetAsync(c->gkeys, 0xff, 2 * nnz * sizeof(int32_t), s));
   CK(cudaMemsetAsync(c->gvals, 0, 2 * nnz * sizeof(unsigned long long), s));
-  CK(cudaMemsetAsync(c->gcount, 0, N1 * sizeof(int32_t), s));
   if (c->opt.validate) {
     validate_csr(c->off0, c->col0, c->w0, n, nnz, c->flags, c->acc, s);
     CKLAUNCH();
@@ -669,6 +708,16 @@ int louvain_load_csr(louvain_ctx* c, int64_t n, int64_t nnz, const int64_t* offs
     return fail(c, LOUVAIN_ERR_OVERFLOW, "total weight M must be below 2^62");
   }
   c->M0 = (int64_t)c->h_acc[0];
+  {
+    // singleton partition: sum L_c = total self-loop weight, sum Sigma_c^2 = sum K_i^2
+    const u128 loops = ((u128)c->h_acc[3] << 64) | (u128)c->h_acc[2];
+    CK(cudaMemsetAsync(c->acc, 0, 2 * sizeof(unsigned long long), s));
+    sum_squares(c->K0, n, c->acc, s);
+    CKLAUNCH();
+    if (int r = fetch(c, c->h_acc, c->acc, 2 * sizeof(unsigned long long))) { free_all(c); return r; }
+    const u128 SS = ((u128)c->h_acc[1] << 64) | (u128)c->h_acc[0];
+    c->qnum0 = (i128)c->M0 * (i128)loops - (i128)SS;
+  }
   c->loaded = true;
   c->ran = false;
   return 0;

@@ -12,7 +12,8 @@ constexpr int kHubBucket = 5;
 __host__ __device__ inline int lm_bucket_of(int64_t deg) {
   return deg <= 0 ? -1 : deg <= 8 ? 0 : deg <= 32 ? 1 : deg <= 128 ? 2 : deg <= 1024 ? 3 : deg <= 4096 ? 4 : 5;
 }
-constexpr int64_t kHubChunkEntries = 2048;
+constexpr int64_t kHubChunkEntries = 2048;   // entries per insert block of a hub
+constexpr int64_t kSlotChunk = 4096;         // table slots per scan block (hubs and large communities)
 
 // Community classes of the aggregation phase by total member degree.
 constexpr int kAggBuckets = 5;       // 0 warp/64, 1 warp/256, 2 block/2k, 3 block/8k, 4 global
@@ -28,7 +29,8 @@ void lm_launch_bucket(const LMArgs<W>& a, bool wide, bool async, int bucket, con
                       cudaStream_t s);
 template <typename W>
 void lm_launch_hubs(const LMArgs<W>& a, bool wide, bool async, const int32_t* hubs, int nhubs,
-                    const int64_t* chunk_pre, int64_t nchunks, cudaStream_t s);
+                    const int64_t* chunk_pre, int64_t nchunks, const int64_t* spre, int64_t nslotchunks,
+                    cudaStream_t s);
 template <typename W>
 void lm_launch_commit(const LMArgs<W>& a, int64_t max_moves, cudaStream_t s);
 
@@ -50,9 +52,10 @@ void stable_partition(const int32_t* key, int64_t n, int nkeys, int32_t* out, in
 // Keys for the local-moving lists: bucket-major, then class (i mod P); vertices
 // of degree 0 get the trailing key nb * P.
 void lm_keys(const int64_t* off, int64_t n, int P, int32_t* key, cudaStream_t s);
-// For the hub list: per hub its table base (2 * degree slots) and chunk prefix.
+// For the hub list: per hub its table base (2 * degree slots), the prefix of
+// its insert chunks and the prefix of its slot chunks (each nhubs + 1 long).
 void hub_layout(const int64_t* off, const int32_t* hubs, int64_t nhubs, int64_t* hbase, int64_t* chunk_pre,
-                void* tmp, cudaStream_t s);
+                int64_t* spre, void* tmp, cudaStream_t s);
 
 // Row sums K (int64) of a CSR, the total M (u128 lo/hi) and the self-loop total.
 template <typename W>
@@ -68,6 +71,8 @@ void pass_init(int64_t n, const long long* K, int32_t* memb, long long* sig, int
 template <typename W>
 void modularity_parts(const int64_t* off, const int32_t* col, const W* wt, int64_t n, const int32_t* memb,
                       const long long* sig, unsigned long long* acc /* [0] L, [1..2] ss lo/hi */, cudaStream_t s);
+// ss (u128 lo/hi at acc[0..1]) += sum over i < n of v[i]^2.
+void sum_squares(const long long* v, int64_t n, unsigned long long* acc, cudaStream_t s);
 // Community totals for an arbitrary membership (Sigma_c = sum K_i over c).
 void community_totals(const long long* K, const int32_t* memb, int64_t n, long long* sig, cudaStream_t s);
 
@@ -96,8 +101,7 @@ struct AggArgs {
   int64_t* rlen;           // k
   int32_t* gkeys;          // global tables
   unsigned long long* gvals;
-  int32_t* gcount;
-  int32_t* gslots;
+  unsigned long long* lsum;  // += weight of every coarse self-loop (sum of L_C)
   int* error;
 };
 void agg_group_members(const int32_t* level, int64_t n, int64_t k, int64_t* cnt /* k+1 */, int64_t* cstart,
@@ -109,9 +113,10 @@ template <typename W, typename W2>
 void agg_launch_bucket(const AggArgs& a, int bucket, const int32_t* comms, int ncomms, cudaStream_t s);
 template <typename W, typename W2>
 void agg_launch_global(const AggArgs& a, const int32_t* comms, int ncomms, const int64_t* gbase,
-                       const int64_t* chunk_pre, int64_t nchunks, cudaStream_t s);
+                       const int64_t* chunk_pre, int64_t nchunks, const int64_t* spre, int64_t nslotchunks,
+                       cudaStream_t s);
 void agg_global_layout(const int64_t* cstart, const int64_t* mpre, const int32_t* comms, int64_t ncomms,
-                       int64_t* gbase, int64_t* chunk_pre, void* tmp, cudaStream_t s);
+                       int64_t* gbase, int64_t* chunk_pre, int64_t* spre, void* tmp, cudaStream_t s);
 template <typename W2>
 void agg_compact(const int64_t* cstart, const int64_t* mpre, const int64_t* rlen, const int64_t* coff, int64_t k,
                  const int32_t* tcol, const W2* tw, int32_t* ocol, W2* ow, cudaStream_t s);

@@ -131,9 +131,9 @@ static void scan_any(const Tin* in, Tout* out, int64_t n, int64_t* total, void* 
   }
   int64_t nb = (n + kScanTile - 1) / kScanTile;
   long long* bsum = (long long*)tmp;
-  scan_reduce_k<Tin><<<(unsigned)nb, kT, 0, s>>>(in, n, bsum);
-  scan_bsums_k<<<1, kT, 0, s>>>(bsum, nb, total);
-  scan_final_k<Tin, Tout><<<(unsigned)nb, kT, 0, s>>>(in, out, n, bsum);
+  (count_launch(), scan_reduce_k<Tin><<<(unsigned)nb, kT, 0, s>>>(in, n, bsum));
+  (count_launch(), scan_bsums_k<<<1, kT, 0, s>>>(bsum, nb, total));
+  (count_launch(), scan_final_k<Tin, Tout><<<(unsigned)nb, kT, 0, s>>>(in, out, n, bsum));
 }
 
 void scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, int64_t* total, void* tmp, cudaStream_t s) {
@@ -217,15 +217,15 @@ void stable_partition(const int32_t* key, int64_t n, int nkeys, int32_t* out, in
   int64_t* offs = counts + m;
   void* stmp = (void*)(offs + m);
   if (n > 0) {
-    part_count_k<<<(unsigned)nblk, kT, nkeys * sizeof(int), s>>>(key, n, nkeys, counts, nblk);
+    (count_launch(), part_count_k<<<(unsigned)nblk, kT, nkeys * sizeof(int), s>>>(key, n, nkeys, counts, nblk));
     scan_i64(counts, offs, m, nullptr, stmp, s);
   } else {
     cudaMemsetAsync(offs, 0, m * sizeof(int64_t), s);
   }
-  part_key_off_k<<<(nkeys + 1 + 255) / 256, 256, 0, s>>>(offs, nkeys, nblk, n, key_off);
+  (count_launch(), part_key_off_k<<<(nkeys + 1 + 255) / 256, 256, 0, s>>>(offs, nkeys, nblk, n, key_off));
   if (n > 0) {
     size_t smem = (size_t)nkeys * (1 + kT / kWarp) * sizeof(long long);
-    part_scatter_k<<<(unsigned)nblk, kT, smem, s>>>(key, n, nkeys, offs, nblk, out);
+    (count_launch(), part_scatter_k<<<(unsigned)nblk, kT, smem, s>>>(key, n, nkeys, offs, nblk, out));
   }
 }
 
@@ -245,30 +245,35 @@ static unsigned grid1d(int64_t n, int per = kT) {
 }
 
 void lm_keys(const int64_t* off, int64_t n, int P, int32_t* key, cudaStream_t s) {
-  if (n > 0) lm_keys_k<<<grid1d(n), kT, 0, s>>>(off, n, P, key);
+  if (n > 0) (count_launch(), lm_keys_k<<<grid1d(n), kT, 0, s>>>(off, n, P, key));
 }
 
-__global__ void hub_sizes_k(const int64_t* off, const int32_t* hubs, int64_t nhubs, int64_t* cap, int64_t* chunks) {
+__global__ void hub_sizes_k(const int64_t* off, const int32_t* hubs, int64_t nhubs, int64_t* cap, int64_t* chunks,
+                            int64_t* schunks) {
   for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < nhubs; h += (int64_t)gridDim.x * blockDim.x) {
     int64_t d = off[hubs[h] + 1] - off[hubs[h]];
     cap[h] = 2 * d;
     chunks[h] = (d + kHubChunkEntries - 1) / kHubChunkEntries;
+    schunks[h] = (2 * d + kSlotChunk - 1) / kSlotChunk;
   }
 }
 
 void hub_layout(const int64_t* off, const int32_t* hubs, int64_t nhubs, int64_t* hbase, int64_t* chunk_pre,
-                void* tmp, cudaStream_t s) {
+                int64_t* spre, void* tmp, cudaStream_t s) {
   if (nhubs <= 0) {
     cudaMemsetAsync(hbase, 0, sizeof(int64_t), s);
     cudaMemsetAsync(chunk_pre, 0, sizeof(int64_t), s);
+    cudaMemsetAsync(spre, 0, sizeof(int64_t), s);
     return;
   }
   int64_t* cap = (int64_t*)tmp;
   int64_t* chunks = cap + nhubs;
-  void* stmp = (void*)(chunks + nhubs);
-  hub_sizes_k<<<grid1d(nhubs), kT, 0, s>>>(off, hubs, nhubs, cap, chunks);
+  int64_t* schunks = chunks + nhubs;
+  void* stmp = (void*)(schunks + nhubs);
+  (count_launch(), hub_sizes_k<<<grid1d(nhubs), kT, 0, s>>>(off, hubs, nhubs, cap, chunks, schunks));
   scan_i64(cap, hbase, nhubs, hbase + nhubs, stmp, s);
   scan_i64(chunks, chunk_pre, nhubs, chunk_pre + nhubs, stmp, s);
+  scan_i64(schunks, spre, nhubs, spre + nhubs, stmp, s);
 }
 
 // -------------------------------------------- row-range load balancing
@@ -335,7 +340,7 @@ template <typename W>
 void row_sums(const int64_t* off, const int32_t* col, const W* wt, int64_t n, long long* K, unsigned long long* acc,
               cudaStream_t s) {
   if (n <= 0) return;
-  row_sums_k<W><<<(unsigned)((n + kT - 1) / kT), kT, 0, s>>>(off, col, wt, n, K, acc);
+  (count_launch(), row_sums_k<W><<<(unsigned)((n + kT - 1) / kT), kT, 0, s>>>(off, col, wt, n, K, acc));
 }
 template void row_sums<int32_t>(const int64_t*, const int32_t*, const int32_t*, int64_t, long long*,
                                 unsigned long long*, cudaStream_t);
@@ -355,7 +360,7 @@ __global__ void pass_init_k(int64_t n, const long long* K, int32_t* memb, long l
 
 void pass_init(int64_t n, const long long* K, int32_t* memb, long long* sig, int32_t* csize, int32_t* stampA,
                int32_t* stampB, cudaStream_t s) {
-  if (n > 0) pass_init_k<<<grid1d(n), kT, 0, s>>>(n, K, memb, sig, csize, stampA, stampB);
+  if (n > 0) (count_launch(), pass_init_k<<<grid1d(n), kT, 0, s>>>(n, K, memb, sig, csize, stampA, stampB));
 }
 
 template <typename W>
@@ -376,21 +381,21 @@ __global__ void __launch_bounds__(kT) intra_weight_k(const int64_t* __restrict__
 }
 
 __global__ void __launch_bounds__(kT) sum_squares_k(const long long* __restrict__ sig, int64_t n,
-                                                    unsigned long long* acc) {
+                                                    unsigned long long* lo, unsigned long long* hi) {
   u128 ss = 0;
   for (int64_t c = blockIdx.x * (int64_t)kT + threadIdx.x; c < n; c += (int64_t)gridDim.x * kT) {
     long long v = sig[c];
     ss += (u128)((unsigned long long)v) * (u128)((unsigned long long)v);
   }
-  block_add_u128(ss, acc + 1, acc + 2);
+  block_add_u128(ss, lo, hi);
 }
 
 template <typename W>
 void modularity_parts(const int64_t* off, const int32_t* col, const W* wt, int64_t n, const int32_t* memb,
                       const long long* sig, unsigned long long* acc, cudaStream_t s) {
   if (n <= 0) return;
-  intra_weight_k<W><<<(unsigned)((n + kT - 1) / kT), kT, 0, s>>>(off, col, wt, n, memb, acc);
-  sum_squares_k<<<grid1d(n), kT, 0, s>>>(sig, n, acc);
+  (count_launch(), intra_weight_k<W><<<(unsigned)((n + kT - 1) / kT), kT, 0, s>>>(off, col, wt, n, memb, acc));
+  (count_launch(), sum_squares_k<<<grid1d(n), kT, 0, s>>>(sig, n, acc + 1, acc + 2));
 }
 template void modularity_parts<int32_t>(const int64_t*, const int32_t*, const int32_t*, int64_t, const int32_t*,
                                         const long long*, unsigned long long*, cudaStream_t);
@@ -401,10 +406,14 @@ __global__ void community_totals_k(const long long* K, const int32_t* memb, int6
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     atomicAdd((unsigned long long*)(sig + memb[i]), (unsigned long long)K[i]);
 }
+void sum_squares(const long long* v, int64_t n, unsigned long long* acc, cudaStream_t s) {
+  if (n > 0) (count_launch(), sum_squares_k<<<grid1d(n), kT, 0, s>>>(v, n, acc, acc + 1));
+}
+
 void community_totals(const long long* K, const int32_t* memb, int64_t n, long long* sig, cudaStream_t s) {
   if (n <= 0) return;
   cudaMemsetAsync(sig, 0, n * sizeof(long long), s);
-  community_totals_k<<<grid1d(n), kT, 0, s>>>(K, memb, n, sig);
+  (count_launch(), community_totals_k<<<grid1d(n), kT, 0, s>>>(K, memb, n, sig));
 }
 
 // ------------------------------------------------------------ renumber
@@ -416,7 +425,7 @@ __global__ void mark_used_k(const int32_t* memb, int64_t n, int32_t* used) {
 void mark_used(const int32_t* memb, int64_t n, int32_t* used, cudaStream_t s) {
   if (n <= 0) return;
   cudaMemsetAsync(used, 0, n * sizeof(int32_t), s);
-  mark_used_k<<<grid1d(n), kT, 0, s>>>(memb, n, used);
+  (count_launch(), mark_used_k<<<grid1d(n), kT, 0, s>>>(memb, n, used));
 }
 
 __global__ void apply_level_k(const int32_t* memb, const int32_t* newid, int64_t n, int32_t* level) {
@@ -424,7 +433,7 @@ __global__ void apply_level_k(const int32_t* memb, const int32_t* newid, int64_t
     level[i] = newid[memb[i]];
 }
 void apply_level(const int32_t* memb, const int32_t* newid, int64_t n, int32_t* level, cudaStream_t s) {
-  if (n > 0) apply_level_k<<<grid1d(n), kT, 0, s>>>(memb, newid, n, level);
+  if (n > 0) (count_launch(), apply_level_k<<<grid1d(n), kT, 0, s>>>(memb, newid, n, level));
 }
 
 __global__ void compose_top_k(int32_t* top, int64_t n0, const int32_t* level) {
@@ -432,7 +441,7 @@ __global__ void compose_top_k(int32_t* top, int64_t n0, const int32_t* level) {
     top[v] = level[top[v]];
 }
 void compose_top(int32_t* top, int64_t n0, const int32_t* level, cudaStream_t s) {
-  if (n0 > 0) compose_top_k<<<grid1d(n0), kT, 0, s>>>(top, n0, level);
+  if (n0 > 0) (count_launch(), compose_top_k<<<grid1d(n0), kT, 0, s>>>(top, n0, level));
 }
 
 __global__ void coarse_degrees_k(const int32_t* used, const int32_t* newid, const long long* sig, int64_t n,
@@ -442,7 +451,7 @@ __global__ void coarse_degrees_k(const int32_t* used, const int32_t* newid, cons
 }
 void coarse_degrees(const int32_t* used, const int32_t* newid, const long long* sig, int64_t n, long long* Knext,
                     cudaStream_t s) {
-  if (n > 0) coarse_degrees_k<<<grid1d(n), kT, 0, s>>>(used, newid, sig, n, Knext);
+  if (n > 0) (count_launch(), coarse_degrees_k<<<grid1d(n), kT, 0, s>>>(used, newid, sig, n, Knext));
 }
 
 // ------------------------------------------------------------ aggregation
@@ -464,9 +473,9 @@ void agg_group_members(const int32_t* level, int64_t n, int64_t k, int64_t* cnt,
                        int32_t* members, void* tmp, cudaStream_t s) {
   cudaMemsetAsync(cnt, 0, (k + 1) * sizeof(int64_t), s);
   cudaMemsetAsync(fill, 0, (k + 1) * sizeof(int64_t), s);
-  if (n > 0) count_members_k<<<grid1d(n), kT, 0, s>>>(level, n, cnt);
+  if (n > 0) (count_launch(), count_members_k<<<grid1d(n), kT, 0, s>>>(level, n, cnt));
   scan_i64(cnt, cstart, k, cstart + k, tmp, s);
-  if (n > 0) place_members_k<<<grid1d(n), kT, 0, s>>>(level, n, cstart, fill, members);
+  if (n > 0) (count_launch(), place_members_k<<<grid1d(n), kT, 0, s>>>(level, n, cstart, fill, members));
 }
 
 __global__ void member_degrees_k(const int64_t* off, const int32_t* members, int64_t n, int64_t* mdeg) {
@@ -477,7 +486,7 @@ __global__ void member_degrees_k(const int64_t* off, const int32_t* members, int
 }
 void agg_member_prefix(const int64_t* off, const int32_t* members, int64_t n, int64_t* mdeg, int64_t* mpre,
                        void* tmp, cudaStream_t s) {
-  if (n > 0) member_degrees_k<<<grid1d(n), kT, 0, s>>>(off, members, n, mdeg);
+  if (n > 0) (count_launch(), member_degrees_k<<<grid1d(n), kT, 0, s>>>(off, members, n, mdeg));
   scan_i64(mdeg, mpre, n, mpre + n, tmp, s);
 }
 
@@ -489,7 +498,7 @@ __global__ void agg_keys_k(const int64_t* cstart, const int64_t* mpre, int64_t k
   }
 }
 void agg_keys(const int64_t* cstart, const int64_t* mpre, int64_t k, int32_t* key, cudaStream_t s) {
-  if (k > 0) agg_keys_k<<<grid1d(k), kT, 0, s>>>(cstart, mpre, k, key);
+  if (k > 0) (count_launch(), agg_keys_k<<<grid1d(k), kT, 0, s>>>(cstart, mpre, k, key));
 }
 
 // Member position of virtual entry t of a community: the last p in [lo, hi)
@@ -500,6 +509,39 @@ __device__ __forceinline__ int64_t member_of(const int64_t* __restrict__ mpre, i
     if (mpre[mid] <= t) lo = mid; else hi = mid;
   }
   return lo;
+}
+
+// Staged members of a tile of virtual entries: spre[j] = mpre of member
+// p0 + j, sstart[j] = off[member] - mpre, so entry t of member j is CSR entry
+// sstart[j] + t.  Lookups then search shared memory.
+__device__ __forceinline__ int staged_of(const int64_t* spre, int nm, int64_t t) {
+  int lo = 0, hi = nm;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (spre[mid] <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+template <typename W>
+__device__ __forceinline__ void staged_entry(const AggArgs& a, const int64_t* spre, const int64_t* sstart, int nm,
+                                             int64_t t, int32_t* D, unsigned long long* w) {
+  const int j = staged_of(spre, nm, t);
+  const int64_t x = sstart[j] + t;
+  *D = a.level[a.col[x]];
+  *w = (unsigned long long)((const W*)a.wt)[x];
+}
+
+// Stage members [p0, p0 + nm) (called by all threads of a group of `nthr`
+// threads with index `tid`).
+__device__ __forceinline__ void stage_members(const AggArgs& a, int64_t p0, int nm, int64_t* spre, int64_t* sstart,
+                                              int tid, int nthr) {
+  for (int j = tid; j < nm; j += nthr) {
+    const int64_t p = p0 + j;
+    const int64_t pre = a.mpre[p];
+    spre[j] = pre;
+    sstart[j] = a.off[a.members[p]] - pre;
+  }
 }
 
 template <typename W>
@@ -515,8 +557,10 @@ __device__ __forceinline__ void virtual_entry(const AggArgs& a, int64_t cs, int6
 template <typename W, typename W2, int CAP>
 __global__ void __launch_bounds__(256) agg_warp_k(AggArgs a, const int32_t* __restrict__ comms, int ncomms) {
   constexpr int WPB = 8;
+  constexpr int MAXM = CAP / 2;   // members <= dsum <= CAP / 2
   __shared__ int32_t skeys[WPB][CAP];
   __shared__ unsigned long long svals[WPB][CAP];
+  __shared__ int64_t sp[WPB][MAXM], ss[WPB][MAXM];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   int32_t* keys = skeys[wib];
   unsigned long long* vals = svals[wib];
@@ -527,11 +571,23 @@ __global__ void __launch_bounds__(256) agg_warp_k(AggArgs a, const int32_t* __re
     int32_t C = comms[ci];
     int64_t cs = a.cstart[C], ce = a.cstart[C + 1];
     int64_t vs = a.mpre[cs], ve = a.mpre[ce];
-    for (int64_t t = vs + lane; t < ve; t += kWarp) {
-      int32_t D;
-      unsigned long long w;
-      virtual_entry<W>(a, cs, ce, t, &D, &w);
-      ok &= table_add_pow2<CAP>(keys, vals, D, w);
+    const int nm = (int)(ce - cs);
+    if (nm <= MAXM) {
+      stage_members(a, cs, nm, sp[wib], ss[wib], lane, kWarp);
+      __syncwarp();
+      for (int64_t t = vs + lane; t < ve; t += kWarp) {
+        int32_t D;
+        unsigned long long w;
+        staged_entry<W>(a, sp[wib], ss[wib], nm, t, &D, &w);
+        ok &= table_add_pow2<CAP>(keys, vals, D, w);
+      }
+    } else {
+      for (int64_t t = vs + lane; t < ve; t += kWarp) {
+        int32_t D;
+        unsigned long long w;
+        virtual_entry<W>(a, cs, ce, t, &D, &w);
+        ok &= table_add_pow2<CAP>(keys, vals, D, w);
+      }
     }
     __syncwarp();
     int64_t base = 0;
@@ -543,6 +599,7 @@ __global__ void __launch_bounds__(256) agg_warp_k(AggArgs a, const int32_t* __re
         int64_t pos = vs + base + __popc(m & lanemask_lt());
         a.tcol[pos] = key;
         ((W2*)a.tw)[pos] = (W2)vals[t];
+        if (key == C) atomicAdd(a.lsum, vals[t]);
         keys[t] = kEmpty;
         vals[t] = 0;
       }
@@ -556,10 +613,17 @@ __global__ void __launch_bounds__(256) agg_warp_k(AggArgs a, const int32_t* __re
 
 template <typename W, typename W2, int CAP, int THREADS>
 __global__ void __launch_bounds__(THREADS) agg_block_k(AggArgs a, const int32_t* __restrict__ comms, int ncomms) {
+  constexpr int TILE = 2 * THREADS;
+  // dynamic shared memory: values (CAP u64), staged member prefixes and
+  // starts (TILE i64 each), keys (CAP i32)
   extern __shared__ unsigned long long adyn[];
   unsigned long long* vals = adyn;
-  int32_t* keys = (int32_t*)(adyn + CAP);
+  int64_t* spre = (int64_t*)(adyn + CAP);
+  int64_t* sstart = spre + TILE;
+  int32_t* keys = (int32_t*)(sstart + TILE);
   __shared__ int wtot[THREADS / kWarp];
+  __shared__ int64_t s_p0;
+  __shared__ int s_nm;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int t = threadIdx.x; t < CAP; t += THREADS) { keys[t] = kEmpty; vals[t] = 0; }
   __syncthreads();
@@ -568,13 +632,25 @@ __global__ void __launch_bounds__(THREADS) agg_block_k(AggArgs a, const int32_t*
     int32_t C = comms[ci];
     int64_t cs = a.cstart[C], ce = a.cstart[C + 1];
     int64_t vs = a.mpre[cs], ve = a.mpre[ce];
-    for (int64_t t = vs + threadIdx.x; t < ve; t += THREADS) {
-      int32_t D;
-      unsigned long long w;
-      virtual_entry<W>(a, cs, ce, t, &D, &w);
-      ok &= table_add_pow2<CAP>(keys, vals, D, w);
+    for (int64_t y = vs; y < ve; y += TILE) {
+      const int64_t y1 = min(ve, y + TILE);
+      if (threadIdx.x == 0) {
+        s_p0 = member_of(a.mpre, cs, ce, y);
+        s_nm = (int)(member_of(a.mpre, cs, ce, y1 - 1) - s_p0 + 1);
+      }
+      __syncthreads();
+      const int nm = s_nm;
+      if (nm <= TILE) stage_members(a, s_p0, nm, spre, sstart, threadIdx.x, THREADS);
+      __syncthreads();
+      for (int64_t t = y + threadIdx.x; t < y1; t += THREADS) {
+        int32_t D;
+        unsigned long long w;
+        if (nm <= TILE) staged_entry<W>(a, spre, sstart, nm, t, &D, &w);
+        else virtual_entry<W>(a, cs, ce, t, &D, &w);
+        ok &= table_add_pow2<CAP>(keys, vals, D, w);
+      }
+      __syncthreads();
     }
-    __syncthreads();
     int64_t base = 0;
     for (int t0 = 0; t0 < CAP; t0 += THREADS) {
       int t = t0 + threadIdx.x;
@@ -592,6 +668,7 @@ __global__ void __launch_bounds__(THREADS) agg_block_k(AggArgs a, const int32_t*
         int64_t pos = vs + base + before + __popc(m & lanemask_lt());
         a.tcol[pos] = key;
         ((W2*)a.tw)[pos] = (W2)vals[t];
+        if (key == C) atomicAdd(a.lsum, vals[t]);
         keys[t] = kEmpty;
         vals[t] = 0;
       }
@@ -603,69 +680,101 @@ __global__ void __launch_bounds__(THREADS) agg_block_k(AggArgs a, const int32_t*
   if (!ok) atomicOr(a.error, kErrProbe);
 }
 
+// Large communities: blocks are (community, 2048-virtual-entry chunk) pairs;
+// each sums its chunk per neighbour community in shared memory, then adds
+// each distinct one to the community's global table of 2 * dsum slots.
+__device__ __forceinline__ int find_item(const int64_t* __restrict__ pre, int nitems, int64_t blk) {
+  int lo = 0, hi = nitems;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (pre[mid] <= blk) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 template <typename W>
 __global__ void __launch_bounds__(256) agg_global_insert_k(AggArgs a, const int32_t* __restrict__ comms, int ncomms,
                                                            const int64_t* __restrict__ gbase,
                                                            const int64_t* __restrict__ chunk_pre) {
-  int lo = 0, hi = ncomms;
-  while (hi - lo > 1) {
-    int mid = (lo + hi) >> 1;
-    if (chunk_pre[mid] <= (int64_t)blockIdx.x) lo = mid; else hi = mid;
-  }
-  const int h = lo;
+  constexpr int CAP = 2 * (int)kAggChunkEntries;
+  // dynamic shared memory: values (CAP u64), staged prefixes and starts
+  // (chunk i64 each), keys (CAP i32)
+  extern __shared__ unsigned long long gdyn[];
+  unsigned long long* svals = gdyn;
+  int64_t* spre = (int64_t*)(gdyn + CAP);
+  int64_t* sstart = spre + kAggChunkEntries;
+  int32_t* skeys = (int32_t*)(sstart + kAggChunkEntries);
+  const int h = find_item(chunk_pre, ncomms, blockIdx.x);
   const int32_t C = comms[h];
   const int64_t cs = a.cstart[C], ce = a.cstart[C + 1];
   const int64_t vs = a.mpre[cs], ve = a.mpre[ce];
   const int64_t q = (int64_t)blockIdx.x - chunk_pre[h];
   const int64_t base = gbase[h];
   const uint32_t cap = (uint32_t)(gbase[h + 1] - base);
-  int32_t* keys = a.gkeys + base;
-  unsigned long long* vals = a.gvals + base;
+  for (int t = threadIdx.x; t < CAP; t += blockDim.x) { skeys[t] = kEmpty; svals[t] = 0; }
+  __syncthreads();
   const int64_t t0 = vs + q * kAggChunkEntries, t1 = min(ve, t0 + kAggChunkEntries);
+  __shared__ int64_t s_p0;
+  __shared__ int s_nm;
+  if (threadIdx.x == 0) {
+    s_p0 = member_of(a.mpre, cs, ce, t0);
+    s_nm = (int)(member_of(a.mpre, cs, ce, t1 - 1) - s_p0 + 1);
+  }
+  __syncthreads();
+  const int nm = s_nm;
+  constexpr int MAXM = (int)kAggChunkEntries;
+  if (nm <= MAXM) stage_members(a, s_p0, nm, spre, sstart, threadIdx.x, blockDim.x);
+  __syncthreads();
   bool ok = true;
   for (int64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
     int32_t D;
     unsigned long long w;
-    virtual_entry<W>(a, cs, ce, t, &D, &w);
+    if (nm <= MAXM) staged_entry<W>(a, spre, sstart, nm, t, &D, &w);
+    else virtual_entry<W>(a, cs, ce, t, &D, &w);
+    ok &= table_add_pow2<CAP>(skeys, svals, D, w);
+  }
+  __syncthreads();
+  int32_t* keys = a.gkeys + base;
+  unsigned long long* vals = a.gvals + base;
+  for (int t = threadIdx.x; t < CAP; t += blockDim.x) {
+    int32_t D = skeys[t];
+    if (D == kEmpty) continue;
     bool fresh;
-    ok &= gtable_add(keys, vals, cap, D, w, &fresh);
-    if (fresh) {
-      int pos = atomicAdd(a.gcount + h, 1);
-      a.gslots[base + pos] = D;
-    }
+    ok &= gtable_add(keys, vals, cap, D, svals[t], &fresh);
   }
   if (!ok) atomicOr(a.error, kErrProbe);
 }
 
+// Blocks are (community, 4096-slot chunk) pairs: every occupied slot is
+// appended to the community's tmp row (positions claimed once per warp) and
+// cleared.
 template <typename W2>
 __global__ void __launch_bounds__(256) agg_global_write_k(AggArgs a, const int32_t* __restrict__ comms, int ncomms,
-                                                          const int64_t* __restrict__ gbase) {
-  for (int h = blockIdx.x; h < ncomms; h += gridDim.x) {
-    const int32_t C = comms[h];
-    const int64_t vs = a.mpre[a.cstart[C]];
-    const int64_t base = gbase[h];
-    const uint32_t cap = (uint32_t)(gbase[h + 1] - base);
-    int32_t* keys = a.gkeys + base;
-    unsigned long long* vals = a.gvals + base;
-    const int cnt = a.gcount[h];
-    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-      int32_t D = a.gslots[base + t];
-      a.tcol[vs + t] = D;
-      ((W2*)a.tw)[vs + t] = (W2)gtable_get(keys, vals, cap, D);
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-      int32_t D = a.gslots[base + t];
-      uint32_t hs = __umulhi(hash32((uint32_t)D), cap);
-      for (uint32_t probe = 0; probe < cap; ++probe) {
-        if (keys[hs] == D) { keys[hs] = kEmpty; vals[hs] = 0; break; }
-        hs = (hs + 1 == cap) ? 0 : hs + 1;
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      a.rlen[C] = cnt;
-      a.gcount[h] = 0;
+                                                          const int64_t* __restrict__ gbase,
+                                                          const int64_t* __restrict__ spre) {
+  const int lane = threadIdx.x & 31;
+  const int h = find_item(spre, ncomms, blockIdx.x);
+  const int32_t C = comms[h];
+  const int64_t vs = a.mpre[a.cstart[C]];
+  const int64_t base = gbase[h];
+  const int64_t cap = gbase[h + 1] - base;
+  const int64_t q = (int64_t)blockIdx.x - spre[h];
+  const int64_t t0 = q * kSlotChunk, t1 = min(cap, t0 + kSlotChunk);
+  for (int64_t y = t0; y < t1; y += blockDim.x) {
+    const int64_t t = y + threadIdx.x;
+    int32_t D = t < t1 ? a.gkeys[base + t] : kEmpty;
+    const bool occ = D != kEmpty;
+    const unsigned m = __ballot_sync(0xffffffffu, occ);
+    int64_t wbase = 0;
+    if (lane == 0 && m) wbase = (int64_t)atomicAdd((unsigned long long*)(a.rlen + C), (unsigned long long)__popc(m));
+    wbase = __shfl_sync(0xffffffffu, wbase, 0);
+    if (occ) {
+      const int64_t pos = vs + wbase + __popc(m & lanemask_lt());
+      a.tcol[pos] = D;
+      ((W2*)a.tw)[pos] = (W2)a.gvals[base + t];
+      if (D == C) atomicAdd(a.lsum, a.gvals[base + t]);
+      a.gkeys[base + t] = kEmpty;
+      a.gvals[base + t] = 0;
     }
   }
 }
@@ -694,31 +803,31 @@ void agg_launch_bucket(const AggArgs& a, int bucket, const int32_t* comms, int n
   switch (bucket) {
     case 0: {
       auto k = agg_warp_k<W, W2, 64>;
-      k<<<agrid(k, 256, 0, (ncomms + 7) / 8), 256, 0, s>>>(a, comms, ncomms);
+      (count_launch(), k<<<agrid(k, 256, 0, (ncomms + 7) / 8), 256, 0, s>>>(a, comms, ncomms));
       break;
     }
     case 1: {
       auto k = agg_warp_k<W, W2, 256>;
-      k<<<agrid(k, 256, 0, (ncomms + 7) / 8), 256, 0, s>>>(a, comms, ncomms);
+      (count_launch(), k<<<agrid(k, 256, 0, (ncomms + 7) / 8), 256, 0, s>>>(a, comms, ncomms));
       break;
     }
     case 2: {
       constexpr int CAP = 2048;
-      size_t smem = (size_t)CAP * 12;
+      size_t smem = (size_t)CAP * 12 + 2 * 2 * 128 * 8;
       auto k = agg_block_k<W, W2, CAP, 128>;
-      k<<<agrid(k, 128, smem, ncomms), 128, smem, s>>>(a, comms, ncomms);
+      (count_launch(), k<<<agrid(k, 128, smem, ncomms), 128, smem, s>>>(a, comms, ncomms));
       break;
     }
     case 3: {
       constexpr int CAP = 8192;
-      size_t smem = (size_t)CAP * 12;
+      size_t smem = (size_t)CAP * 12 + 2 * 2 * 256 * 8;
       auto k = agg_block_k<W, W2, CAP, 256>;
       static bool attr = false;
       if (!attr) {
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
       }
-      k<<<agrid(k, 256, smem, ncomms), 256, smem, s>>>(a, comms, ncomms);
+      (count_launch(), k<<<agrid(k, 256, smem, ncomms), 256, smem, s>>>(a, comms, ncomms));
       break;
     }
     default: break;
@@ -727,43 +836,54 @@ void agg_launch_bucket(const AggArgs& a, int bucket, const int32_t* comms, int n
 
 template <typename W, typename W2>
 void agg_launch_global(const AggArgs& a, const int32_t* comms, int ncomms, const int64_t* gbase,
-                       const int64_t* chunk_pre, int64_t nchunks, cudaStream_t s) {
+                       const int64_t* chunk_pre, int64_t nchunks, const int64_t* spre, int64_t nslotchunks,
+                       cudaStream_t s) {
   if (ncomms <= 0 || nchunks <= 0) return;
-  agg_global_insert_k<W><<<(unsigned)nchunks, 256, 0, s>>>(a, comms, ncomms, gbase, chunk_pre);
-  agg_global_write_k<W2><<<ncomms < 4096 ? ncomms : 4096, 256, 0, s>>>(a, comms, ncomms, gbase);
+  const size_t smem = (size_t)(2 * kAggChunkEntries) * 12 + (size_t)kAggChunkEntries * 16;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(agg_global_insert_k<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  (count_launch(), agg_global_insert_k<W><<<(unsigned)nchunks, 256, smem, s>>>(a, comms, ncomms, gbase, chunk_pre));
+  (count_launch(), agg_global_write_k<W2><<<(unsigned)nslotchunks, 256, 0, s>>>(a, comms, ncomms, gbase, spre));
 }
 
 #define AGG_INST(W, W2)                                                                                        \
   template void agg_launch_bucket<W, W2>(const AggArgs&, int, const int32_t*, int, cudaStream_t);            \
   template void agg_launch_global<W, W2>(const AggArgs&, const int32_t*, int, const int64_t*, const int64_t*, \
-                                         int64_t, cudaStream_t);
+                                         int64_t, const int64_t*, int64_t, cudaStream_t);
 AGG_INST(int32_t, int32_t)
 AGG_INST(int32_t, int64_t)
 AGG_INST(int64_t, int64_t)
 
 __global__ void agg_global_sizes_k(const int64_t* cstart, const int64_t* mpre, const int32_t* comms, int64_t ncomms,
-                                   int64_t* cap, int64_t* chunks) {
+                                   int64_t* cap, int64_t* chunks, int64_t* schunks) {
   for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < ncomms; h += (int64_t)gridDim.x * blockDim.x) {
     int32_t C = comms[h];
     int64_t dsum = mpre[cstart[C + 1]] - mpre[cstart[C]];
     cap[h] = 2 * dsum;
     chunks[h] = (dsum + kAggChunkEntries - 1) / kAggChunkEntries;
+    schunks[h] = (2 * dsum + kSlotChunk - 1) / kSlotChunk;
   }
 }
 
 void agg_global_layout(const int64_t* cstart, const int64_t* mpre, const int32_t* comms, int64_t ncomms,
-                       int64_t* gbase, int64_t* chunk_pre, void* tmp, cudaStream_t s) {
+                       int64_t* gbase, int64_t* chunk_pre, int64_t* spre, void* tmp, cudaStream_t s) {
   if (ncomms <= 0) {
     cudaMemsetAsync(gbase, 0, sizeof(int64_t), s);
     cudaMemsetAsync(chunk_pre, 0, sizeof(int64_t), s);
+    cudaMemsetAsync(spre, 0, sizeof(int64_t), s);
     return;
   }
   int64_t* cap = (int64_t*)tmp;
   int64_t* chunks = cap + ncomms;
-  void* stmp = (void*)(chunks + ncomms);
-  agg_global_sizes_k<<<grid1d(ncomms), kT, 0, s>>>(cstart, mpre, comms, ncomms, cap, chunks);
+  int64_t* schunks = chunks + ncomms;
+  void* stmp = (void*)(schunks + ncomms);
+  (count_launch(), agg_global_sizes_k<<<grid1d(ncomms), kT, 0, s>>>(cstart, mpre, comms, ncomms, cap, chunks, schunks));
   scan_i64(cap, gbase, ncomms, gbase + ncomms, stmp, s);
   scan_i64(chunks, chunk_pre, ncomms, chunk_pre + ncomms, stmp, s);
+  scan_i64(schunks, spre, ncomms, spre + ncomms, stmp, s);
 }
 
 // Copy each community's tmp row (at mpre[cstart[C]], rlen[C] long) to its
@@ -793,7 +913,7 @@ void agg_compact(const int64_t* cstart, const int64_t* mpre, const int64_t* rlen
                  const int32_t* tcol, const W2* tw, int32_t* ocol, W2* ow, cudaStream_t s) {
   (void)rlen;
   if (k <= 0) return;
-  agg_compact_k<W2><<<(unsigned)((k + kT - 1) / kT), kT, 0, s>>>(cstart, mpre, coff, k, tcol, tw, ocol, ow);
+  (count_launch(), agg_compact_k<W2><<<(unsigned)((k + kT - 1) / kT), kT, 0, s>>>(cstart, mpre, coff, k, tcol, tw, ocol, ow));
 }
 template void agg_compact<int32_t>(const int64_t*, const int64_t*, const int64_t*, const int64_t*, int64_t,
                                    const int32_t*, const int32_t*, int32_t*, int32_t*, cudaStream_t);
@@ -847,12 +967,12 @@ void validate_csr(const int64_t* off, const int32_t* col, const int32_t* wt, int
   cudaMemsetAsync(flags, 0, sizeof(int), s);
   cudaMemsetAsync(hashes, 0, 2 * sizeof(unsigned long long), s);
   if (n <= 0) return;
-  validate_off_k<<<grid1d(n), kT, 0, s>>>(off, n, nnz, flags);
+  (count_launch(), validate_off_k<<<grid1d(n), kT, 0, s>>>(off, n, nnz, flags));
   int hf = 0;
   cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
   if (hf) return;
-  validate_rows_k<<<(unsigned)((n + kT - 1) / kT), kT, 0, s>>>(off, col, wt, n, flags, hashes);
+  (count_launch(), validate_rows_k<<<(unsigned)((n + kT - 1) / kT), kT, 0, s>>>(off, col, wt, n, flags, hashes));
 }
 
 // ------------------------------------------------------------ conversions
@@ -862,21 +982,21 @@ __global__ void widen_k(const int32_t* in, int64_t* out, int64_t n) {
     out[i] = in[i];
 }
 void widen_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s) {
-  if (n > 0) widen_k<<<grid1d(n), kT, 0, s>>>(in, out, n);
+  if (n > 0) (count_launch(), widen_k<<<grid1d(n), kT, 0, s>>>(in, out, n));
 }
 __global__ void fill_k(int32_t* p, int32_t v, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = v;
 }
 void fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t s) {
-  if (n > 0) fill_k<<<grid1d(n), kT, 0, s>>>(p, v, n);
+  if (n > 0) (count_launch(), fill_k<<<grid1d(n), kT, 0, s>>>(p, v, n));
 }
 __global__ void iota_k(int32_t* p, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = (int32_t)i;
 }
 void iota_i32(int32_t* p, int64_t n, cudaStream_t s) {
-  if (n > 0) iota_k<<<grid1d(n), kT, 0, s>>>(p, n);
+  if (n > 0) (count_launch(), iota_k<<<grid1d(n), kT, 0, s>>>(p, n));
 }
 
 }  // namespace gbl

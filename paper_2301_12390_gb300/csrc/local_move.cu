@@ -27,6 +27,12 @@ namespace gbl {
 
 // --------------------------------------------------------- small helpers
 
+__device__ __forceinline__ unsigned lanemask_lt_lm() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
 // Synchronous launches never write memberships, totals or sizes, so they
 // read them through the read-only path; asynchronous launches use plain
 // loads, which may return a value that another vertex has since changed —
@@ -49,17 +55,18 @@ __device__ __forceinline__ int32_t ld_size(const int32_t* p) {
 
 // Block-level accumulators, flushed once per block.
 struct BlockAcc {
-  unsigned long long moves, edges, s_lo, s_hi;
+  unsigned long long moves, edges, visited, s_lo, s_hi;
   int error;
 };
 
 __device__ __forceinline__ void acc_init(BlockAcc& b) {
-  if (threadIdx.x == 0) { b.moves = 0; b.edges = 0; b.s_lo = 0; b.s_hi = 0; b.error = 0; }
+  if (threadIdx.x == 0) { b.moves = 0; b.edges = 0; b.visited = 0; b.s_lo = 0; b.s_hi = 0; b.error = 0; }
 }
 __device__ __forceinline__ void acc_flush(BlockAcc& b, DevCounters* ctr) {
   if (threadIdx.x == 0) {
     if (b.moves) atomicAdd(&ctr->moves, b.moves);
     if (b.edges) atomicAdd(&ctr->edges, b.edges);
+    if (b.visited) atomicAdd(&ctr->visited, b.visited);
     u128 s = ((u128)b.s_hi << 64) | (u128)b.s_lo;
     if (s) atomic_add_u128(&ctr->s_lo, &ctr->s_hi, s);
     if (b.error) atomicOr(&ctr->error, b.error);
@@ -69,10 +76,15 @@ __device__ __forceinline__ void acc_flush(BlockAcc& b, DevCounters* ctr) {
 // Decide-and-apply for vertex i (called by one thread): guard, then either
 // an in-place move (asynchronous) or an entry in the move list (synchronous).
 // Returns whether the vertex moves.
+// `best` is the best candidate's score, `score_d` the vertex's own; the move
+// needs gain = best - score_d > 0.
 template <typename W, bool WIDE, bool ASYNC>
 __device__ __forceinline__ bool commit_choice(const LMArgs<W>& a, BlockAcc& acc, int32_t i, int32_t d, long long Ki,
-                                              typename Arith<WIDE>::S g, int32_t c) {
-  if (c < 0 || !(g > 0)) return false;
+                                              typename Arith<WIDE>::S best, int32_t c, unsigned long long kid) {
+  if (c < 0) return false;
+  typedef typename Arith<WIDE>::S S;
+  const S g = best - Arith<WIDE>::score(a.M, (long long)kid, Ki, ld_sig<ASYNC>(a.sig + d) - Ki);
+  if (!(g > 0)) return false;
   if (a.guard && c > d && ld_size<ASYNC>(a.csize + d) == 1 && ld_size<ASYNC>(a.csize + c) == 1) return false;
   if (ASYNC) {
     a.memb[i] = c;
@@ -97,8 +109,10 @@ __device__ __forceinline__ bool is_active(const LMArgs<W>& a, int32_t i) {
 
 // --------------------------------------------- bucket 0: thread per vertex
 
+// The row (<= 8 entries) is loaded first and its neighbours' communities
+// gathered with all loads in flight; duplicates are then merged in registers.
 template <typename W, bool WIDE, bool ASYNC>
-__global__ void __launch_bounds__(256) lm_thread(LMArgs<W> a, const int32_t* __restrict__ verts, int nverts) {
+__global__ void __launch_bounds__(256, 4) lm_thread(LMArgs<W> a, const int32_t* __restrict__ verts, int nverts) {
   typedef typename Arith<WIDE>::S S;
   __shared__ BlockAcc acc;
   acc_init(acc);
@@ -106,47 +120,46 @@ __global__ void __launch_bounds__(256) lm_thread(LMArgs<W> a, const int32_t* __r
   for (int vi = blockIdx.x * blockDim.x + threadIdx.x; vi < nverts; vi += gridDim.x * blockDim.x) {
     int32_t i = verts[vi];
     if (!is_active(a, i)) continue;
-    int64_t b = a.off[i], e = a.off[i + 1];
-    int32_t d = a.memb[i];
-    long long Ki = a.K[i];
-    int32_t ck[8];
-    unsigned long long cw[8];
+    const int64_t b = a.off[i], e = a.off[i + 1];
+    const int32_t d = a.memb[i];
+    const long long Ki = a.K[i];
+    int32_t cc[8];
+    unsigned long long ww[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) { ck[k] = kEmpty; cw[k] = 0; }
-    int cnt = 0;
-    for (int64_t x = b; x < e; ++x) {
-      int32_t j = a.col[x];
-      if (j == i) continue;
-      int32_t c = ld_memb<ASYNC>(a.memb + j);
-      unsigned long long w = (unsigned long long)a.wt[x];
-      bool found = false;
+    for (int k = 0; k < 8; ++k) {
+      const bool v = b + k < e;
+      cc[k] = v ? a.col[b + k] : i;
+      ww[k] = v ? (unsigned long long)a.wt[b + k] : 0ull;
+    }
 #pragma unroll
-      for (int k = 0; k < 8; ++k)
-        if (ck[k] == c) { cw[k] += w; found = true; }
-      if (!found) {
+    for (int k = 0; k < 8; ++k) cc[k] = cc[k] != i ? ld_memb<ASYNC>(a.memb + cc[k]) : kEmpty;
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if (k == cnt) { ck[k] = c; cw[k] = w; }
-        ++cnt;
-      }
+    for (int k = 1; k < 8; ++k) {
+      bool merged = false;
+#pragma unroll
+      for (int l = 0; l < k; ++l)
+        if (!merged && cc[k] != kEmpty && cc[l] == cc[k]) { ww[l] += ww[k]; merged = true; }
+      if (merged) cc[k] = kEmpty;
     }
     unsigned long long kid = 0;
 #pragma unroll
     for (int k = 0; k < 8; ++k)
-      if (ck[k] == d) kid = cw[k];
-    S score_d = Arith<WIDE>::score(a.M, (long long)kid, Ki, ld_sig<ASYNC>(a.sig + d) - Ki);
-    S bg = 0;
+      if (cc[k] == d) kid = ww[k];
+    long long sg[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sg[k] = (cc[k] != kEmpty && cc[k] != d) ? ld_sig<ASYNC>(a.sig + cc[k]) : 0;
+    S bg = Arith<WIDE>::lowest();
     int32_t bc = -1;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      int32_t c = ck[k];
-      if (c != kEmpty && c != d) {
-        S g = Arith<WIDE>::score(a.M, (long long)cw[k], Ki, ld_sig<ASYNC>(a.sig + c)) - score_d;
-        if (better(g, c, bg, bc)) { bg = g; bc = c; }
+      if (cc[k] != kEmpty && cc[k] != d) {
+        S g = Arith<WIDE>::score(a.M, (long long)ww[k], Ki, sg[k]);
+        if (better(g, cc[k], bg, bc)) { bg = g; bc = cc[k]; }
       }
     }
     atomicAdd(&acc.edges, (unsigned long long)(e - b));
-    if (commit_choice<W, WIDE, ASYNC>(a, acc, i, d, Ki, bg, bc) && a.prune) {
+        atomicAdd(&acc.visited, 1ull);
+    if (commit_choice<W, WIDE, ASYNC>(a, acc, i, d, Ki, bg, bc, kid) && a.prune) {
       a.stamp_w[i] = a.iter + 1;
       for (int64_t x = b; x < e; ++x) a.stamp_w[a.col[x]] = a.iter + 1;
     }
@@ -157,8 +170,10 @@ __global__ void __launch_bounds__(256) lm_thread(LMArgs<W> a, const int32_t* __r
 
 // ------------------------------------------ buckets 1-2: warp per vertex
 
-template <typename W, bool WIDE, bool ASYNC, int CAP>
-__global__ void __launch_bounds__(256) lm_warp(LMArgs<W> a, const int32_t* __restrict__ verts, int nverts) {
+// U entries per lane are loaded and gathered before any insert (U * 32 covers
+// the bucket's largest degree), so their memory latencies overlap.
+template <typename W, bool WIDE, bool ASYNC, int CAP, int U>
+__global__ void __launch_bounds__(256, 4) lm_warp(LMArgs<W> a, const int32_t* __restrict__ verts, int nverts) {
   typedef typename Arith<WIDE>::S S;
   constexpr int WPB = 8;
   __shared__ int32_t skeys[WPB][CAP];
@@ -174,35 +189,67 @@ __global__ void __launch_bounds__(256) lm_warp(LMArgs<W> a, const int32_t* __res
   for (int vi = blockIdx.x * WPB + wib; vi < nverts; vi += gridDim.x * WPB) {
     int32_t i = verts[vi];
     if (!is_active(a, i)) continue;
-    int64_t b = a.off[i], e = a.off[i + 1];
-    int32_t d = a.memb[i];
-    long long Ki = a.K[i];
-    for (int64_t x = b + lane; x < e; x += kWarp) {
-      int32_t j = a.col[x];
-      if (j != i) ok &= table_add_pow2<CAP>(keys, vals, ld_memb<ASYNC>(a.memb + j), (unsigned long long)a.wt[x]);
+    const int64_t b = a.off[i], e = a.off[i + 1];
+    const int32_t d = a.memb[i];
+    const long long Ki = a.K[i];
+    for (int64_t x0 = b; x0 < e; x0 += U * kWarp) {
+      int32_t cc[U];
+      unsigned long long ww[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t x = x0 + u * kWarp + lane;
+        const bool v = x < e;
+        cc[u] = v ? a.col[x] : i;
+        ww[u] = v ? (unsigned long long)a.wt[x] : 0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) cc[u] = cc[u] != i ? ld_memb<ASYNC>(a.memb + cc[u]) : kEmpty;
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (cc[u] != kEmpty) ok &= table_add_pow2<CAP>(keys, vals, cc[u], ww[u]);
     }
     __syncwarp();
-    unsigned long long kid = table_get_pow2<CAP>(keys, vals, d);
-    S score_d = Arith<WIDE>::score(a.M, (long long)kid, Ki, ld_sig<ASYNC>(a.sig + d) - Ki);
-    __syncwarp();
-    S bg = 0;
+    unsigned long long kid = 0;
+    S bg = Arith<WIDE>::lowest();
     int32_t bc = -1;
-    for (int t = lane; t < CAP; t += kWarp) {
-      int32_t c = keys[t];
-      if (c != kEmpty) {
-        if (c != d) {
-          S g = Arith<WIDE>::score(a.M, (long long)vals[t], Ki, ld_sig<ASYNC>(a.sig + c)) - score_d;
-          if (better(g, c, bg, bc)) { bg = g; bc = c; }
+#pragma unroll
+    for (int t0 = 0; t0 < CAP; t0 += kWarp * 4) {
+      int32_t cs[4];
+      long long sg[4];
+      unsigned long long vs[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int t = t0 + u * kWarp + lane;
+        cs[u] = t < CAP ? keys[t] : kEmpty;
+        vs[u] = t < CAP ? vals[t] : 0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) sg[u] = (cs[u] != kEmpty && cs[u] != d) ? ld_sig<ASYNC>(a.sig + cs[u]) : 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int t = t0 + u * kWarp + lane;
+        if (cs[u] != kEmpty) {
+          if (cs[u] != d) {
+            S g = Arith<WIDE>::score(a.M, (long long)vs[u], Ki, sg[u]);
+            if (better(g, cs[u], bg, bc)) { bg = g; bc = cs[u]; }
+          } else {
+            kid = vs[u];
+          }
+          keys[t] = kEmpty;
+          vals[t] = 0;
         }
-        keys[t] = kEmpty;
-        vals[t] = 0;
       }
     }
     warp_argmax(bg, bc);
+    {
+      const unsigned has = __ballot_sync(0xffffffffu, kid != 0);
+      kid = has ? __shfl_sync(0xffffffffu, kid, __ffs(has) - 1) : 0ull;
+    }
     bool moved = false;
     if (lane == 0) {
       atomicAdd(&acc.edges, (unsigned long long)(e - b));
-      moved = commit_choice<W, WIDE, ASYNC>(a, acc, i, d, Ki, bg, bc);
+        atomicAdd(&acc.visited, 1ull);
+      moved = commit_choice<W, WIDE, ASYNC>(a, acc, i, d, Ki, bg, bc, kid);
     }
     moved = __shfl_sync(0xffffffffu, moved, 0);
     if (moved && a.prune) {
@@ -222,6 +269,7 @@ template <typename W, bool WIDE, bool ASYNC, int CAP, int THREADS>
 __global__ void __launch_bounds__(THREADS) lm_block(LMArgs<W> a, const int32_t* __restrict__ verts, int nverts) {
   typedef typename Arith<WIDE>::S S;
   constexpr int NW = THREADS / kWarp;
+  constexpr int U = 4;
   // dynamic shared memory: values (CAP u64), keys (CAP i32), touched slots (CAP/2 i32)
   extern __shared__ unsigned long long dyn[];
   unsigned long long* vals = dyn;
@@ -234,53 +282,86 @@ __global__ void __launch_bounds__(THREADS) lm_block(LMArgs<W> a, const int32_t* 
   __shared__ int s_moved, s_nt;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   acc_init(acc);
-  if (threadIdx.x == 0) s_nt = 0;
+  if (threadIdx.x == 0) { s_nt = 0; s_kid = 0; }
   for (int t = threadIdx.x; t < CAP; t += THREADS) { keys[t] = kEmpty; vals[t] = 0; }
   __syncthreads();
   bool ok = true;
   for (int vi = blockIdx.x; vi < nverts; vi += gridDim.x) {
     int32_t i = verts[vi];
     if (!is_active(a, i)) continue;   // uniform across the block
-    int64_t b = a.off[i], e = a.off[i + 1];
-    int32_t d = a.memb[i];
-    long long Ki = a.K[i];
-    for (int64_t x = b + threadIdx.x; x < e; x += THREADS) {
-      int32_t j = a.col[x];
-      if (j != i) {
-        bool fresh;
-        int h = table_add_pow2_slot<CAP>(keys, vals, ld_memb<ASYNC>(a.memb + j), (unsigned long long)a.wt[x], &fresh);
-        if (h < 0) ok = false;
-        else if (fresh) touched[atomicAdd(&s_nt, 1)] = h;
+    const int64_t b = a.off[i], e = a.off[i + 1];
+    const int32_t d = a.memb[i];
+    const long long Ki = a.K[i];
+    for (int64_t x0 = b; x0 < e; x0 += U * THREADS) {
+      int32_t cc[U];
+      unsigned long long ww[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t x = x0 + u * THREADS + threadIdx.x;
+        const bool v = x < e;
+        cc[u] = v ? a.col[x] : i;
+        ww[u] = v ? (unsigned long long)a.wt[x] : 0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) cc[u] = cc[u] != i ? ld_memb<ASYNC>(a.memb + cc[u]) : kEmpty;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        bool fresh = false;
+        int h = -1;
+        if (cc[u] != kEmpty) {
+          h = table_add_pow2_slot<CAP>(keys, vals, cc[u], ww[u], &fresh);
+          if (h < 0) ok = false;
+        }
+        // one append per warp for the new keys of its lanes
+        const unsigned m = __ballot_sync(0xffffffffu, fresh);
+        int base = 0;
+        if (lane == 0 && m) base = atomicAdd(&s_nt, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (fresh) touched[base + __popc(m & lanemask_lt_lm())] = h;
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0) s_kid = table_get_pow2<CAP>(keys, vals, d);
-    __syncthreads();
     const int nt = s_nt;
-    S score_d = Arith<WIDE>::score(a.M, (long long)s_kid, Ki, ld_sig<ASYNC>(a.sig + d) - Ki);
-    S bg = 0;
+    S bg = Arith<WIDE>::lowest();
     int32_t bc = -1;
-    for (int t = threadIdx.x; t < nt; t += THREADS) {
-      int h = touched[t];
-      int32_t c = keys[h];
-      if (c != d) {
-        S g = Arith<WIDE>::score(a.M, (long long)vals[h], Ki, ld_sig<ASYNC>(a.sig + c)) - score_d;
-        if (better(g, c, bg, bc)) { bg = g; bc = c; }
+    for (int t0 = 0; t0 < nt; t0 += U * THREADS) {
+      int hs[U];
+      int32_t cs[U];
+      long long sg[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int t = t0 + u * THREADS + threadIdx.x;
+        hs[u] = t < nt ? touched[t] : -1;
+        cs[u] = hs[u] >= 0 ? keys[hs[u]] : kEmpty;
       }
-      keys[h] = kEmpty;
-      vals[h] = 0;
+#pragma unroll
+      for (int u = 0; u < U; ++u) sg[u] = (cs[u] != kEmpty && cs[u] != d) ? ld_sig<ASYNC>(a.sig + cs[u]) : 0;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (hs[u] < 0) continue;
+        if (cs[u] != d) {
+          S g = Arith<WIDE>::score(a.M, (long long)vals[hs[u]], Ki, sg[u]);
+          if (better(g, cs[u], bg, bc)) { bg = g; bc = cs[u]; }
+        } else {
+          s_kid = vals[hs[u]];
+        }
+        keys[hs[u]] = kEmpty;
+        vals[hs[u]] = 0;
+      }
     }
     warp_argmax(bg, bc);
     if (lane == 0) { red_g[wid] = bg; red_c[wid] = bc; }
     __syncthreads();
     if (wid == 0) {
-      bg = lane < NW ? red_g[lane] : (S)0;
+      bg = lane < NW ? red_g[lane] : Arith<WIDE>::lowest();
       bc = lane < NW ? red_c[lane] : -1;
       warp_argmax(bg, bc);
       if (lane == 0) {
         atomicAdd(&acc.edges, (unsigned long long)(e - b));
-        s_moved = commit_choice<W, WIDE, ASYNC>(a, acc, i, d, Ki, bg, bc);
+        atomicAdd(&acc.visited, 1ull);
+        s_moved = commit_choice<W, WIDE, ASYNC>(a, acc, i, d, Ki, bg, bc, s_kid);
         s_nt = 0;
+        s_kid = 0;
       }
     }
     __syncthreads();
@@ -295,68 +376,143 @@ __global__ void __launch_bounds__(THREADS) lm_block(LMArgs<W> a, const int32_t* 
 }
 
 // ------------------------------------------------- bucket 5: hub vertices
+//
+// Hub h of a launch owns global table slots [hbase[h], hbase[h] + 2 deg).
+// 1. insert: blocks are (hub, 2048-entry chunk) pairs; each sums its chunk
+//    per community in shared memory, then adds each distinct community once
+//    to the hub's global table;
+// 2. kid: K_{i->d} of each hub is read before anything clears the table;
+// 3. scan: blocks are (hub, 4096-slot chunk) pairs; each evaluates the gain
+//    of every occupied slot, clears it, and leaves its chunk's best;
+// 4. final: one block per hub reduces the chunk bests, commits, marks.
 
-constexpr int kHubChunk = 2048;
+constexpr int kHubChunk = (int)kHubChunkEntries;
 
-// hub h of the launch's list owns table slots [hbase[h], hbase[h] + 2 deg).
-// Blocks are (hub, chunk) pairs; chunk_pre[h] is the first block of hub h.
+__device__ __forceinline__ int find_item(const int64_t* __restrict__ pre, int nitems, int64_t blk) {
+  // last h with pre[h] - pre[0] <= blk
+  const int64_t p0 = pre[0];
+  int lo = 0, hi = nitems;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (pre[mid] - p0 <= blk) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 template <typename W, bool ASYNC>
 __global__ void __launch_bounds__(256) lm_hub_insert(LMArgs<W> a, const int32_t* __restrict__ hubs, int nhubs,
                                                      const int64_t* __restrict__ chunk_pre) {
-  // a chunk's entries are first summed per community in a shared table, then
-  // each distinct community is added once to the hub's global table
   constexpr int CAP = 2 * kHubChunk;
   extern __shared__ unsigned long long hdyn[];
   unsigned long long* svals = hdyn;
   int32_t* skeys = (int32_t*)(hdyn + CAP);
-  // find the hub of this block: last h with chunk_pre[h] - chunk_pre[0] <= blockIdx.x
-  const int64_t cb = chunk_pre[0];
-  int lo = 0, hi = nhubs;
-  while (hi - lo > 1) {
-    int mid = (lo + hi) >> 1;
-    if (chunk_pre[mid] - cb <= (int64_t)blockIdx.x) lo = mid; else hi = mid;
-  }
-  const int h = lo;
+  const int h = find_item(chunk_pre, nhubs, blockIdx.x);
   const int32_t i = hubs[h];
   if (!is_active(a, i)) return;   // uniform across the block
-  const int64_t q = (int64_t)blockIdx.x - (chunk_pre[h] - cb);
+  const int64_t q = (int64_t)blockIdx.x - (chunk_pre[h] - chunk_pre[0]);
   for (int t = threadIdx.x; t < CAP; t += blockDim.x) { skeys[t] = kEmpty; svals[t] = 0; }
   __syncthreads();
   const int64_t b = a.off[i], e = a.off[i + 1];
   const int64_t base = a.hbase[h];
   const uint32_t cap = (uint32_t)(2 * (e - b));
-  int32_t* keys = a.hkeys + base;
-  unsigned long long* vals = a.hvals + base;
   const int64_t x0 = b + q * kHubChunk, x1 = min(e, x0 + kHubChunk);
   bool ok = true;
-  for (int64_t x = x0 + threadIdx.x; x < x1; x += blockDim.x) {
-    int32_t j = a.col[x];
-    if (j == i) continue;
-    ok &= table_add_pow2<CAP>(skeys, svals, ld_memb<ASYNC>(a.memb + j), (unsigned long long)a.wt[x]);
+  constexpr int U = 4;
+  for (int64_t y = x0; y < x1; y += U * 256) {
+    int32_t cc[U];
+    unsigned long long ww[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t x = y + u * 256 + threadIdx.x;
+      const bool v = x < x1;
+      cc[u] = v ? a.col[x] : i;
+      ww[u] = v ? (unsigned long long)a.wt[x] : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) cc[u] = cc[u] != i ? ld_memb<ASYNC>(a.memb + cc[u]) : kEmpty;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (cc[u] != kEmpty) ok &= table_add_pow2<CAP>(skeys, svals, cc[u], ww[u]);
   }
   __syncthreads();
+  int32_t* keys = a.hkeys + base;
+  unsigned long long* vals = a.hvals + base;
   for (int t = threadIdx.x; t < CAP; t += blockDim.x) {
     int32_t c = skeys[t];
     if (c == kEmpty) continue;
     bool fresh;
     ok &= gtable_add(keys, vals, cap, c, svals[t], &fresh);
-    if (fresh) {
-      int pos = atomicAdd(a.hcount + h, 1);
-      a.hslots[base + pos] = c;   // record the key; the decide step looks it up
-    }
   }
   if (!ok) atomicOr(&a.ctr->error, kErrProbe);
 }
 
-// One block per hub: evaluate every distinct neighbour community, choose,
-// commit, reset the table.
 template <typename W, bool WIDE, bool ASYNC>
-__global__ void __launch_bounds__(256) lm_hub_decide(LMArgs<W> a, const int32_t* __restrict__ hubs, int nhubs) {
+__global__ void __launch_bounds__(256) lm_hub_scan(LMArgs<W> a, const int32_t* __restrict__ hubs, int nhubs) {
   typedef typename Arith<WIDE>::S S;
   constexpr int NW = 256 / kWarp;
-  __shared__ BlockAcc acc;
   __shared__ S red_g[NW];
   __shared__ int32_t red_c[NW];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int h = find_item(a.spre, nhubs, blockIdx.x);
+  const int32_t i = hubs[h];
+  if (!is_active(a, i)) return;   // uniform across the block
+  const int64_t q = (int64_t)blockIdx.x - (a.spre[h] - a.spre[0]);
+  const int64_t b = a.off[i], e = a.off[i + 1];
+  const int64_t cap = 2 * (e - b);
+  const int64_t base = a.hbase[h];
+  const int32_t d = a.memb[i];
+  const long long Ki = a.K[i];
+  const int64_t t0 = q * kSlotChunk, t1 = min(cap, t0 + kSlotChunk);
+  S bg = Arith<WIDE>::lowest();
+  int32_t bc = -1;
+  constexpr int U = 4;
+  for (int64_t y = t0; y < t1; y += U * 256) {
+    int32_t cs[U];
+    unsigned long long vs[U];
+    long long sg[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t t = y + u * 256 + threadIdx.x;
+      cs[u] = t < t1 ? a.hkeys[base + t] : kEmpty;
+      vs[u] = cs[u] != kEmpty ? a.hvals[base + t] : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) sg[u] = (cs[u] != kEmpty && cs[u] != d) ? ld_sig<ASYNC>(a.sig + cs[u]) : 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (cs[u] == kEmpty) continue;
+      const int64_t t = y + u * 256 + threadIdx.x;
+      if (cs[u] != d) {
+        S g = Arith<WIDE>::score(a.M, (long long)vs[u], Ki, sg[u]);
+        if (better(g, cs[u], bg, bc)) { bg = g; bc = cs[u]; }
+      } else {
+        a.hkid[h] = vs[u];   // K_{i->d}; only one slot holds d
+      }
+      a.hkeys[base + t] = kEmpty;
+      a.hvals[base + t] = 0;
+    }
+  }
+  warp_argmax(bg, bc);
+  if (lane == 0) { red_g[wid] = bg; red_c[wid] = bc; }
+  __syncthreads();
+  if (wid == 0) {
+    bg = lane < NW ? red_g[lane] : Arith<WIDE>::lowest();
+    bc = lane < NW ? red_c[lane] : -1;
+    warp_argmax(bg, bc);
+    if (lane == 0) {
+      const int64_t slot = a.spre[h] + q;
+      u128 gu = (u128)(i128)bg;
+      a.hpart[2 * slot] = (long long)(unsigned long long)gu;
+      a.hpart[2 * slot + 1] = (long long)(unsigned long long)(gu >> 64);
+      a.hpart_c[slot] = bc;
+    }
+  }
+}
+
+template <typename W, bool WIDE, bool ASYNC>
+__global__ void __launch_bounds__(256) lm_hub_final(LMArgs<W> a, const int32_t* __restrict__ hubs, int nhubs) {
+  typedef typename Arith<WIDE>::S S;
+  __shared__ BlockAcc acc;
   __shared__ int s_moved;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   acc_init(acc);
@@ -365,54 +521,29 @@ __global__ void __launch_bounds__(256) lm_hub_decide(LMArgs<W> a, const int32_t*
     const int32_t i = hubs[h];
     if (!is_active(a, i)) continue;
     const int64_t b = a.off[i], e = a.off[i + 1];
-    const int64_t base = a.hbase[h];
-    const uint32_t cap = (uint32_t)(2 * (e - b));
-    int32_t* keys = a.hkeys + base;
-    unsigned long long* vals = a.hvals + base;
-    const int32_t d = a.memb[i];
-    const long long Ki = a.K[i];
-    const int cnt = a.hcount[h];
-    unsigned long long kid = gtable_get(keys, vals, cap, d);
-    S score_d = Arith<WIDE>::score(a.M, (long long)kid, Ki, ld_sig<ASYNC>(a.sig + d) - Ki);
-    S bg = 0;
-    int32_t bc = -1;
-    for (int t = threadIdx.x; t < cnt; t += 256) {
-      int32_t c = a.hslots[base + t];
-      if (c == d) continue;
-      unsigned long long v = gtable_get(keys, vals, cap, c);
-      S g = Arith<WIDE>::score(a.M, (long long)v, Ki, ld_sig<ASYNC>(a.sig + c)) - score_d;
-      if (better(g, c, bg, bc)) { bg = g; bc = c; }
-    }
-    warp_argmax(bg, bc);
-    if (lane == 0) { red_g[wid] = bg; red_c[wid] = bc; }
-    __syncthreads();
     if (wid == 0) {
-      bg = lane < NW ? red_g[lane] : (S)0;
-      bc = lane < NW ? red_c[lane] : -1;
+      S bg = Arith<WIDE>::lowest();
+      int32_t bc = -1;
+      for (int64_t t = a.spre[h] + lane; t < a.spre[h + 1]; t += kWarp) {
+        i128 g = ((i128)a.hpart[2 * t + 1] << 64) | (i128)(unsigned long long)a.hpart[2 * t];
+        int32_t c = a.hpart_c[t];
+        if (c >= 0 && better((S)g, c, bg, bc)) { bg = (S)g; bc = c; }
+      }
       warp_argmax(bg, bc);
       if (lane == 0) {
         atomicAdd(&acc.edges, (unsigned long long)(e - b));
-        s_moved = commit_choice<W, WIDE, ASYNC>(a, acc, i, d, Ki, bg, bc);
+        atomicAdd(&acc.visited, 1ull);
+        s_moved = commit_choice<W, WIDE, ASYNC>(a, acc, i, a.memb[i], a.K[i], bg, bc, a.hkid[h]);
+        a.hkid[h] = 0;
       }
     }
     __syncthreads();
-    // reset the table: clear the slot of every recorded key
-    for (int t = threadIdx.x; t < cnt; t += 256) {
-      int32_t c = a.hslots[base + t];
-      uint32_t hs = __umulhi(hash32((uint32_t)c), cap);
-      for (uint32_t probe = 0; probe < cap; ++probe) {
-        if (keys[hs] == c) { keys[hs] = kEmpty; vals[hs] = 0; break; }
-        hs = (hs + 1 == cap) ? 0 : hs + 1;
-      }
-    }
     if (s_moved && a.prune) {
       if (threadIdx.x == 0) a.stamp_w[i] = a.iter + 1;
       for (int64_t x = b + threadIdx.x; x < e; x += 256) a.stamp_w[a.col[x]] = a.iter + 1;
     }
     __syncthreads();
-    if (threadIdx.x == 0) a.hcount[h] = 0;
   }
-  __syncthreads();
   acc_flush(acc, a.ctr);
 }
 
@@ -463,36 +594,36 @@ void launch_bucket_t(const LMArgs<W>& a, int bucket, const int32_t* verts, int n
   switch (bucket) {
     case 0: {
       auto k = lm_thread<W, WIDE, ASYNC>;
-      k<<<grid_for(k, 256, 0, (nverts + 255) / 256), 256, 0, s>>>(a, verts, nverts);
+      (count_launch(), k<<<grid_for(k, 256, 0, (nverts + 255) / 256), 256, 0, s>>>(a, verts, nverts));
       break;
     }
     case 1: {
-      auto k = lm_warp<W, WIDE, ASYNC, 64>;
-      k<<<grid_for(k, 256, 0, (nverts + 7) / 8), 256, 0, s>>>(a, verts, nverts);
+      auto k = lm_warp<W, WIDE, ASYNC, 64, 1>;
+      (count_launch(), k<<<grid_for(k, 256, 0, (nverts + 7) / 8), 256, 0, s>>>(a, verts, nverts));
       break;
     }
     case 2: {
-      auto k = lm_warp<W, WIDE, ASYNC, 256>;
-      k<<<grid_for(k, 256, 0, (nverts + 7) / 8), 256, 0, s>>>(a, verts, nverts);
+      auto k = lm_warp<W, WIDE, ASYNC, 256, 4>;
+      (count_launch(), k<<<grid_for(k, 256, 0, (nverts + 7) / 8), 256, 0, s>>>(a, verts, nverts));
       break;
     }
     case 3: {
       constexpr int CAP = 2048;
       size_t smem = (size_t)CAP * 14;
       auto k = lm_block<W, WIDE, ASYNC, CAP, 128>;
-      k<<<grid_for(k, 128, smem, nverts), 128, smem, s>>>(a, verts, nverts);
+      (count_launch(), k<<<grid_for(k, 128, smem, nverts), 128, smem, s>>>(a, verts, nverts));
       break;
     }
     case 4: {
       constexpr int CAP = 8192;
       size_t smem = (size_t)CAP * 14;
-      auto k = lm_block<W, WIDE, ASYNC, CAP, 256>;
+      auto k = lm_block<W, WIDE, ASYNC, CAP, 512>;
       static bool attr = false;
       if (!attr) {
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
       }
-      k<<<grid_for(k, 256, smem, nverts), 256, smem, s>>>(a, verts, nverts);
+      (count_launch(), k<<<grid_for(k, 512, smem, nverts), 512, smem, s>>>(a, verts, nverts));
       break;
     }
     default: break;
@@ -515,18 +646,29 @@ void lm_launch_bucket(const LMArgs<W>& a, bool wide, bool async, int bucket, con
 
 template <typename W>
 void lm_launch_hubs(const LMArgs<W>& a, bool wide, bool async, const int32_t* hubs, int nhubs,
-                    const int64_t* chunk_pre, int64_t nchunks, cudaStream_t s) {
+                    const int64_t* chunk_pre, int64_t nchunks, const int64_t* spre, int64_t nslotchunks,
+                    cudaStream_t s) {
   if (nhubs <= 0 || nchunks <= 0) return;
   const size_t smem = (size_t)(2 * kHubChunk) * 12;
-  if (async) lm_hub_insert<W, true><<<(unsigned)nchunks, 256, smem, s>>>(a, hubs, nhubs, chunk_pre);
-  else lm_hub_insert<W, false><<<(unsigned)nchunks, 256, smem, s>>>(a, hubs, nhubs, chunk_pre);
-  int g = nhubs < 4096 ? nhubs : 4096;
+  if (async) (count_launch(), lm_hub_insert<W, true><<<(unsigned)nchunks, 256, smem, s>>>(a, hubs, nhubs, chunk_pre));
+  else (count_launch(), lm_hub_insert<W, false><<<(unsigned)nchunks, 256, smem, s>>>(a, hubs, nhubs, chunk_pre));
+  const int g = nhubs < 4096 ? nhubs : 4096;
   if (wide) {
-    if (async) lm_hub_decide<W, true, true><<<g, 256, 0, s>>>(a, hubs, nhubs);
-    else lm_hub_decide<W, true, false><<<g, 256, 0, s>>>(a, hubs, nhubs);
+    if (async) {
+      (count_launch(), lm_hub_scan<W, true, true><<<(unsigned)nslotchunks, 256, 0, s>>>(a, hubs, nhubs));
+      (count_launch(), lm_hub_final<W, true, true><<<g, 256, 0, s>>>(a, hubs, nhubs));
+    } else {
+      (count_launch(), lm_hub_scan<W, true, false><<<(unsigned)nslotchunks, 256, 0, s>>>(a, hubs, nhubs));
+      (count_launch(), lm_hub_final<W, true, false><<<g, 256, 0, s>>>(a, hubs, nhubs));
+    }
   } else {
-    if (async) lm_hub_decide<W, false, true><<<g, 256, 0, s>>>(a, hubs, nhubs);
-    else lm_hub_decide<W, false, false><<<g, 256, 0, s>>>(a, hubs, nhubs);
+    if (async) {
+      (count_launch(), lm_hub_scan<W, false, true><<<(unsigned)nslotchunks, 256, 0, s>>>(a, hubs, nhubs));
+      (count_launch(), lm_hub_final<W, false, true><<<g, 256, 0, s>>>(a, hubs, nhubs));
+    } else {
+      (count_launch(), lm_hub_scan<W, false, false><<<(unsigned)nslotchunks, 256, 0, s>>>(a, hubs, nhubs));
+      (count_launch(), lm_hub_final<W, false, false><<<g, 256, 0, s>>>(a, hubs, nhubs));
+    }
   }
 }
 
@@ -535,16 +677,16 @@ void lm_launch_commit(const LMArgs<W>& a, int64_t max_moves, cudaStream_t s) {
   if (max_moves <= 0) return;
   int blocks = (int)((max_moves + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
-  lm_commit<W><<<blocks, 256, 0, s>>>(a);
-  reset_move_list<<<1, 1, 0, s>>>(a.ctr);
+  (count_launch(), lm_commit<W><<<blocks, 256, 0, s>>>(a));
+  (count_launch(), reset_move_list<<<1, 1, 0, s>>>(a.ctr));
 }
 
 template void lm_launch_bucket<int32_t>(const LMArgs<int32_t>&, bool, bool, int, const int32_t*, int, cudaStream_t);
 template void lm_launch_bucket<int64_t>(const LMArgs<int64_t>&, bool, bool, int, const int32_t*, int, cudaStream_t);
 template void lm_launch_hubs<int32_t>(const LMArgs<int32_t>&, bool, bool, const int32_t*, int, const int64_t*,
-                                      int64_t, cudaStream_t);
+                                      int64_t, const int64_t*, int64_t, cudaStream_t);
 template void lm_launch_hubs<int64_t>(const LMArgs<int64_t>&, bool, bool, const int32_t*, int, const int64_t*,
-                                      int64_t, cudaStream_t);
+                                      int64_t, const int64_t*, int64_t, cudaStream_t);
 template void lm_launch_commit<int32_t>(const LMArgs<int32_t>&, int64_t, cudaStream_t);
 template void lm_launch_commit<int64_t>(const LMArgs<int64_t>&, int64_t, cudaStream_t);
 

@@ -44,7 +44,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("passes", ctypes.c_int32), ("iterations", ctypes.c_int32), ("moves", ctypes.c_int64),
                 ("lm_edges", ctypes.c_int64), ("communities", ctypes.c_int64), ("q", ctypes.c_double),
                 ("lm_ms", ctypes.c_double), ("agg_ms", ctypes.c_double), ("other_ms", ctypes.c_double),
-                ("total_ms", ctypes.c_double), ("reserved", ctypes.c_int64 * 8)]
+                ("total_ms", ctypes.c_double), ("lm_vertices", ctypes.c_int64), ("lm_bytes", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("reserved", ctypes.c_int64 * 5)]
 
 
 class PassInfo(ctypes.Structure):
