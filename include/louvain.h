@@ -54,6 +54,10 @@ extern "C" {
 #define LOUVAIN_ERR_STATE (-7)         /* e.g. run before load, result before run */
 #define LOUVAIN_ERR_OVERFLOW (-8)      /* total weight M >= 2^62 or n >= 2^31 */
 #define LOUVAIN_ERR_INTERNAL (-9)      /* a device-side consistency check failed */
+#define LOUVAIN_ERR_CAPACITY (-10)     /* a size above a fixed capacity (louvain_modularity_static) */
+
+/* Vertex capacity of louvain_modularity_static's fixed scratch. */
+#define LOUVAIN_STATIC_MAX_VERTICES (1 << 20)
 
 typedef enum { LOUVAIN_SYNC = 0, LOUVAIN_ASYNC = 1 } louvain_mode;
 typedef enum { LOUVAIN_PTR_HOST = 0, LOUVAIN_PTR_DEVICE = 1 } louvain_ptr_kind;
@@ -161,6 +165,29 @@ int louvain_get_modularity_exact(louvain_ctx *ctx, int64_t *num_hi, uint64_t *nu
  * (num_hi / num_lo / M may be NULL). */
 int louvain_modularity(louvain_ctx *ctx, const int32_t *memb, int64_t n, int ptr_kind, double *q, int64_t *num_hi,
                        uint64_t *num_lo, int64_t *M);
+
+/* The paper has no counterpart to this entry point.  Exact modularity of
+ * memb[n] for a graph given entirely in device memory (offsets[n+1], cols,
+ * weights, memb: device pointers on the current device, in the CSR form that
+ * louvain_load_csr takes), computed on `cuda_stream` (a cudaStream_t, NULL =
+ * the default stream) without allocating any device memory: for callers that
+ * must not allocate, such as code whose allocator already owns the device's
+ * free memory, a service with a fixed memory plan, or a pipeline that cannot
+ * take the device-wide synchronisation of cudaMalloc / cudaFree.  Its
+ * scratch (degrees, community totals, sums) is a static device array of
+ * 16 * LOUVAIN_STATIC_MAX_VERTICES + 256 bytes (16 MiB + 256 B) that every GPU
+ * loading this library holds until the process exits.  The first call on a
+ * device finds that array's device address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  All calls
+ * share the array and each clears what it needs: calls that overlap on the
+ * GPU race and must not be issued.  Outputs are host pointers; num_hi,
+ * num_lo, M may be NULL.  The call synchronises `cuda_stream`.
+ * Errors: CAPACITY (n > LOUVAIN_STATIC_MAX_VERTICES), INVALID_ARG (null
+ * pointer, negative n, a membership outside [0, n)), OVERFLOW (M >= 2^62),
+ * CUDA. */
+int louvain_modularity_static(int64_t n, const int64_t *offsets, const int32_t *cols, const int32_t *weights,
+                              const int32_t *memb, void *cuda_stream, double *q, int64_t *num_hi, uint64_t *num_lo,
+                              int64_t *M);
 
 int louvain_get_stats(louvain_ctx *ctx, louvain_stats *out);
 int louvain_get_pass_info(louvain_ctx *ctx, int pass, louvain_pass_info *out);

@@ -22,8 +22,9 @@ PTR_HOST, PTR_DEVICE = 0, 1
 
 ERRORS = {
     -1: "INVALID_ARG", -2: "NOT_SYMMETRIC", -3: "BAD_CSR", -4: "OOM", -5: "CUDA", -6: "TIMEOUT", -7: "STATE",
-    -8: "OVERFLOW", -9: "INTERNAL",
+    -8: "OVERFLOW", -9: "INTERNAL", -10: "CAPACITY",
 }
+STATIC_MAX_VERTICES = 1 << 20   # LOUVAIN_STATIC_MAX_VERTICES
 
 
 class LouvainError(RuntimeError):
@@ -71,6 +72,8 @@ SIGNATURES = [
     ("louvain_get_modularity_exact", _I32, [_VP, ctypes.POINTER(_I64), ctypes.POINTER(_U64), ctypes.POINTER(_I64)]),
     ("louvain_modularity", _I32, [_VP, _VP, _I64, _I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64),
                                   ctypes.POINTER(_U64), ctypes.POINTER(_I64)]),
+    ("louvain_modularity_static", _I32, [_I64, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(_I64), ctypes.POINTER(_U64), ctypes.POINTER(_I64)]),
     ("louvain_get_stats", _I32, [_VP, ctypes.POINTER(Stats)]),
     ("louvain_get_pass_info", _I32, [_VP, _I32, ctypes.POINTER(PassInfo)]),
     ("louvain_get_iteration", _I32, [_VP, _I64, _VP]),
@@ -272,3 +275,18 @@ class Louvain:
         b = ctypes.c_int64()
         self._check(self.lib.louvain_get_device_bytes(self.h, ctypes.byref(b)))
         return b.value
+
+
+def modularity_static(off, col, w, memb, stream=None):
+    """louvain_modularity_static on CUDA tensors (device pointers): (Q, exact numerator, M).
+
+    Allocates no device memory; see include/louvain.h for who needs that and
+    for the limits (fixed capacity, calls must not overlap on the GPU)."""
+    lib = load_library()
+    q, hi, lo, M = ctypes.c_double(), ctypes.c_int64(), ctypes.c_uint64(), ctypes.c_int64()
+    n = len(off) - 1
+    rc = lib.louvain_modularity_static(n, _ptr(off), _ptr(col), _ptr(w), _ptr(memb), stream or None,
+                                       ctypes.byref(q), ctypes.byref(hi), ctypes.byref(lo), ctypes.byref(M))
+    if rc:
+        raise LouvainError(rc, "louvain_modularity_static failed")
+    return q.value, _i128(hi.value, lo.value), M.value
