@@ -111,31 +111,44 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_setup():
+def dist_setup(backend=None):
+    """Rank layout from the torchrun environment; a process group only when WORLD_SIZE > 1.
+
+    One rank per GPU, each with its own replica of the workload: the group
+    carries only the barrier and the max/sum of timings, no data."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     pg = None
     if world > 1:
+        import torch
         import torch.distributed as dist
-        backend = "nccl"
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
         dist.init_process_group(backend=backend)
         pg = dist
     return world, rank, local, pg
 
 
+def _reduce_device(pg, device):
+    return f"cuda:{device}" if pg.get_backend() == "nccl" else "cpu"
+
+
 def barrier(pg, device):
     if pg is not None:
         import torch
-        pg.barrier(device_ids=[device]) if pg.get_backend() == "nccl" else pg.barrier()
-        torch.cuda.synchronize()
+        if pg.get_backend() == "nccl":
+            pg.barrier(device_ids=[device])
+            torch.cuda.synchronize()
+        else:
+            pg.barrier()
 
 
 def max_over_ranks(pg, x: float, device) -> float:
     if pg is None:
         return x
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device=f"cuda:{device}")
+    t = torch.tensor([x], dtype=torch.float64, device=_reduce_device(pg, device))
     pg.all_reduce(t, op=pg.ReduceOp.MAX)
     return float(t.item())
 
@@ -144,7 +157,7 @@ def sum_over_ranks(pg, x: float, device) -> float:
     if pg is None:
         return x
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device=f"cuda:{device}")
+    t = torch.tensor([x], dtype=torch.float64, device=_reduce_device(pg, device))
     pg.all_reduce(t, op=pg.ReduceOp.SUM)
     return float(t.item())
 

@@ -83,7 +83,9 @@ typedef struct {
   int32_t validate;           /* 1: louvain_load_csr checks symmetry and CSR form (costs a pass) */
   int32_t record_levels;      /* 1: keep each pass's membership and coarse CSR for louvain_get_level /
                                  louvain_get_coarse (copies them to host memory) */
-  int32_t reserved_i[5];
+  int32_t cuda_graphs;        /* 1: from the third iteration of a pass, replay that pass's iteration
+                                 as one captured CUDA graph instead of individual launches */
+  int32_t reserved_i[4];
   double reserved_d[4];
 } louvain_options;
 
@@ -145,16 +147,45 @@ int louvain_set_options(louvain_ctx *ctx, const louvain_options *opt);
 int louvain_load_csr(louvain_ctx *ctx, int64_t n, int64_t nnz, const int64_t *offsets, const int32_t *cols,
                      const int32_t *weights, int ptr_kind);
 
+/* Load several independent graphs at once: graph g owns the vertices
+ * [graph_offsets[g], graph_offsets[g+1]) of one CSR laid out as in
+ * louvain_load_csr (block diagonal: no entry may join two graphs; checked).
+ * graph_offsets[num_graphs + 1] has the kind `ptr_kind`.  louvain_run then runs
+ * every graph as if alone — its own total weight M, its own iteration and
+ * pass control — in shared launches; results are per graph
+ * (louvain_batch_get_*, and louvain_get_membership with ids local to each
+ * graph).  The paper runs one graph at a time; batching fills the GPU with
+ * graphs that are each too small to fill it alone.
+ * Errors: as louvain_load_csr. */
+int louvain_load_batch(louvain_ctx *ctx, int64_t num_graphs, const int64_t *graph_offsets, int64_t n, int64_t nnz,
+                       const int64_t *offsets, const int32_t *cols, const int32_t *weights, int ptr_kind);
+
+/* Number of graphs loaded (1 after louvain_load_csr). */
+int louvain_get_num_graphs(louvain_ctx *ctx, int64_t *num_graphs);
+
+/* Per graph g < num_graphs: modularity q[g]; exact numerator and M
+ * (num_hi, num_lo, M may be NULL), host arrays of num_graphs entries. */
+int louvain_batch_get_modularity(louvain_ctx *ctx, double *q, int64_t *num_hi, uint64_t *num_lo, int64_t *M);
+
+/* Graph g: out[0] passes it took part in, out[1] iterations, out[2]
+ * communities, out[3] moves. */
+int louvain_batch_get_graph_info(louvain_ctx *ctx, int64_t g, int64_t out[4]);
+
+/* Iterations of graph g (as louvain_get_iteration, 4 values each) into
+ * out[4 * cap]; *count = how many there are. */
+int louvain_batch_get_iterations(louvain_ctx *ctx, int64_t g, int64_t *out, int64_t cap, int64_t *count);
+
 /* Run the Louvain method on the loaded graph.  Errors: STATE (no graph), CUDA,
  * INTERNAL, TIMEOUT. */
 int louvain_run(louvain_ctx *ctx);
 
 /* Top-level community of every input vertex into out[n] (kind `ptr_kind`);
- * community ids are dense in [0, k) in order of first appearance by the
- * renumbering rule (ascending old id at every pass).  n must equal the loaded n. */
+ * community ids are dense in [0, k) by the renumbering rule (ascending old id
+ * at every pass); with several graphs loaded, dense per graph.  n must equal
+ * the loaded n. */
 int louvain_get_membership(louvain_ctx *ctx, int32_t *out, int64_t n, int ptr_kind);
 
-/* Modularity of the result (see the convention above). */
+/* Modularity of the result (see the convention above); one graph loaded. */
 int louvain_get_modularity(louvain_ctx *ctx, double *q);
 
 /* Exact modularity of the result: Q = num / M^2 with num = num_hi * 2^64 + num_lo. */

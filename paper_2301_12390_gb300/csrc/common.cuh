@@ -223,12 +223,19 @@ struct LMArgs {
   int32_t* memb;             // community of each vertex
   long long* sig;            // community totals Sigma_c
   int32_t* csize;            // community sizes (for the singleton guard)
-  const int32_t* stamp_r;    // active in this iteration iff stamp_r[i] == iter (when pruning)
-  int32_t* stamp_w;          // set to iter + 1 for vertices active in the next iteration
+  const int* d_iter;         // the iteration number, read from device memory so that one
+                             // captured launch sequence serves every iteration of a pass
+  int32_t* stamps[2];        // pruning: active in iteration t iff stamps[t & 1][i] == t;
+                             // a move marks stamps[(t + 1) & 1] with t + 1
   int2* moves;               // synchronous: (vertex, target) of every move of the class
   DevCounters* ctr;
   long long M;
-  int iter;
+  // several graphs in one run (block-diagonal CSR); gid == nullptr means one graph
+  const int32_t* gid;        // graph of each vertex
+  const long long* Mg;       // total weight M of each graph
+  const int32_t* g_on;       // graph still iterating in this pass
+  unsigned long long* g_moves;  // per-graph moves of the iteration
+  unsigned long long* g_s;      // per-graph S of the iteration (lo, hi)
   int prune;
   int guard;
   // hub path: per-hub global tables (slots [hbase[h], hbase[h] + 2 deg))

@@ -22,6 +22,7 @@ using namespace gbl;
 namespace gbl {
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void add_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace gbl
 
@@ -38,6 +39,18 @@ struct IterRec {
   int pass;
   int64_t moves;
   u128 S;
+};
+
+// One graph of a run (a plain load is one graph; a batch load, several).
+struct GraphState {
+  int64_t M = 0;          // its total weight
+  i128 qnum = 0;          // exact Q numerator of its current partition
+  bool stopped = false;   // has left the run
+  int64_t k = 0;          // communities after its last pass
+  int passes = 0;         // passes whose local-moving it took part in
+  int64_t pass_moves = 0; // moves in the current pass
+  int pass_iters = 0;     // iterations in the current pass
+  std::vector<IterRec> iters;   // every iteration it took part in (several graphs only)
 };
 
 struct PassRec {
@@ -106,15 +119,49 @@ struct louvain_ctx {
   unsigned char* tmp = nullptr;
   size_t tmp_bytes = 0;
   int64_t M0 = 0;                      // total weight of the loaded graph
+  int64_t cap_n = 0, cap_nnz = 0;      // arena capacity
+  bool tables_dirty = true;            // global tables need clearing (new arena or a failed run)
   i128 qnum0 = 0;                      // exact Q numerator of the singleton partition of the loaded graph
   DevCounters* ctr = nullptr;
   unsigned long long* acc = nullptr;   // 8 words of reduction scratch
   int* flags = nullptr;
+  int* d_iter = nullptr;               // current local-moving iteration (device)
+  int* h_iter = nullptr;               // pinned staging for it
   int64_t* scal = nullptr;             // small device scalars
   // pinned host mirror
   DevCounters* h_ctr = nullptr;
   unsigned long long* h_acc = nullptr;
   int64_t* h_scal = nullptr;
+
+  // several graphs (block-diagonal CSR): G graphs, vertex ranges vo0
+  int64_t G = 1;
+  std::vector<GraphState> gst;
+  std::vector<int64_t> gM0, gn0;       // per graph: M and vertices of the loaded graph
+  std::vector<i128> gqnum0;            // per graph: singleton Q numerator of the loaded graph
+  int32_t* gid0 = nullptr;             // graph of every input vertex
+  int32_t* gid_a = nullptr;
+  int32_t* gid_b = nullptr;
+  int32_t* gid = nullptr;              // graph of every vertex of the pass graph
+  int32_t* gid_next = nullptr;         // ... of the coarse graph being built
+  int64_t* vo0 = nullptr;              // first input vertex of each graph (G + 1)
+  int64_t* vo_a = nullptr;
+  int64_t* vo_b = nullptr;
+  int64_t* vo = nullptr;               // first pass-graph vertex of each graph
+  int64_t* vo_next = nullptr;
+  int64_t* vo_top = nullptr;           // first community id of each graph in the top membership
+  int64_t* kcount = nullptr;
+  long long* d_Mg = nullptr;
+  int32_t* d_gon = nullptr;
+  unsigned long long* d_gmoves = nullptr;
+  unsigned long long* d_gs = nullptr;
+  unsigned long long* d_gL = nullptr;
+  unsigned long long* d_gSS = nullptr;
+  int64_t hcap = 0;                    // pinned per-graph host buffers below hold hcap graphs
+  int32_t* h_gon = nullptr;
+  unsigned long long* h_gmoves = nullptr;
+  unsigned long long* h_gs = nullptr;
+  unsigned long long* h_gL = nullptr;
+  unsigned long long* h_gSS = nullptr;
 
   // results
   int64_t M = 0;
@@ -126,6 +173,11 @@ struct louvain_ctx {
   std::vector<PassRec> passes;
   louvain_stats stats;
   cudaEvent_t ev[8] = {};
+  // the degree buckets of a vertex class run concurrently, one stream each
+  static constexpr int kAux = kBuckets;
+  cudaStream_t aux[kAux] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[kAux] = {};
 };
 
 namespace {
@@ -153,6 +205,8 @@ void free_all(louvain_ctx* c) {
   c->bytes = 0;
   c->loaded = false;
   c->ran = false;
+  c->cap_n = 0;
+  c->cap_nnz = 0;
 }
 
 template <typename T>
@@ -203,14 +257,16 @@ struct PassState {
 };
 
 template <typename W>
-int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool wide, int64_t* pass_moves,
-                 int* iters_out, int64_t* edges_out, int64_t* visited_out) {
+int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool wide, int* iters_out,
+                 int64_t* edges_out, int64_t* visited_out) {
   const bool async = c->opt.mode == LOUVAIN_ASYNC;
   const int P = c->opt.subrounds > 0 ? c->opt.subrounds : (async ? kAsyncSubrounds : 1);
   const int nkeys = kBuckets * P + 1;
+  const bool multi = c->G > 1;
+  const int64_t G = c->G;
   cudaStream_t s = c->stream;
-  // bucket lists: key = bucket * P + class
-  lm_keys(g.off, g.n, P, c->key, s);
+  // bucket lists: key = bucket * P + class (class by id within the graph)
+  lm_keys(g.off, g.n, P, c->key, multi ? c->gid : nullptr, multi ? c->vo : nullptr, s);
   stable_partition(c->key, g.n, nkeys, c->list, c->key_off, c->tmp, s);
   CKLAUNCH();
   std::vector<int64_t> ko(nkeys + 1);
@@ -246,27 +302,64 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
   a.hvals = c->gvals;
   a.hpart = c->hpart;
   a.hpart_c = c->hpart_c;
-  const i128 M2 = (i128)c->M * c->M;
-  int64_t moves_total = 0, edges_total = 0, visited_total = 0;
-  int it = 0;
-  for (; it < c->opt.max_iterations; ++it) {
+  a.d_iter = c->d_iter;
+  a.stamps[0] = c->stamp[0];
+  a.stamps[1] = c->stamp[1];
+  if (multi) {
+    a.gid = c->gid;
+    a.Mg = c->d_Mg;
+    a.g_on = c->d_gon;
+    a.g_moves = c->d_gmoves;
+    a.g_s = c->d_gs;
+  }
+  // the graphs that iterate in this pass
+  for (int64_t q = 0; q < G; ++q) {
+    c->gst[q].pass_moves = 0;
+    c->gst[q].pass_iters = 0;
+    c->h_gon[q] = c->gst[q].stopped ? 0 : 1;
+  }
+  if (multi) CK(cudaMemcpyAsync(c->d_gon, c->h_gon, G * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  int64_t edges_total = 0, visited_total = 0;
+
+  // One iteration's launch sequence: counters cleared, every class's buckets
+  // forked onto their streams and joined (synchronous: then committed), and
+  // the counters copied to pinned host memory.  The sequence depends on the
+  // iteration only through *d_iter (and, for several graphs, the device copy
+  // of which graphs still iterate), so after two direct iterations a pass
+  // captures it once into a CUDA graph and replays that.
+  auto iteration = [&]() -> int {
     CK(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), s));
-    a.iter = it;
-    a.stamp_r = c->stamp[it & 1];
-    a.stamp_w = c->stamp[(it + 1) & 1];
+    if (multi) {
+      CK(cudaMemsetAsync(c->d_gmoves, 0, G * sizeof(unsigned long long), s));
+      CK(cudaMemsetAsync(c->d_gs, 0, 2 * G * sizeof(unsigned long long), s));
+    }
     for (int ch = 0; ch < P; ++ch) {
+      // fork: every non-empty bucket of the class on its own stream
+      bool used[kBuckets] = {};
+      CK(cudaEventRecord(c->ev_fork, s));
       for (int b = 0; b < kHubBucket; ++b) {
         int64_t s0 = ko[b * P + ch], s1 = ko[b * P + ch + 1];
-        lm_launch_bucket<W>(a, wide, async, b, c->list + s0, (int)(s1 - s0), s);
+        if (s1 <= s0) continue;
+        used[b] = true;
+        CK(cudaStreamWaitEvent(c->aux[b], c->ev_fork, 0));
+        lm_launch_bucket<W>(a, wide, async, b, c->list + s0, (int)(s1 - s0), c->aux[b]);
       }
       int64_t h0 = ko[kHubBucket * P + ch] - hub0, h1 = ko[kHubBucket * P + ch + 1] - hub0;
       if (h1 > h0) {
+        used[kHubBucket] = true;
+        CK(cudaStreamWaitEvent(c->aux[kHubBucket], c->ev_fork, 0));
         LMArgs<W> ah = a;
         ah.hbase = c->gbase + h0;
         ah.spre = c->spre + h0;
         ah.hkid = c->hkid + h0;
         lm_launch_hubs<W>(ah, wide, async, c->list + hub0 + h0, (int)(h1 - h0), c->chunk_pre + h0,
-                          hchunks[h1] - hchunks[h0], c->spre + h0, hschunks[h1] - hschunks[h0], s);
+                          hchunks[h1] - hchunks[h0], c->spre + h0, hschunks[h1] - hschunks[h0], c->aux[kHubBucket]);
+      }
+      // join
+      for (int b = 0; b < kBuckets; ++b) {
+        if (!used[b]) continue;
+        CK(cudaEventRecord(c->ev_join[b], c->aux[b]));
+        CK(cudaStreamWaitEvent(s, c->ev_join[b], 0));
       }
       if (!async) {
         int64_t cls = 0;
@@ -275,39 +368,149 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
       }
       CKLAUNCH();
     }
-    if (int r = fetch(c, c->h_ctr, c->ctr, sizeof(DevCounters))) return r;
-    if (c->h_ctr->error) return fail(c, LOUVAIN_ERR_INTERNAL, "local-moving: hash table overflow");
-    u128 S = ((u128)c->h_ctr->s_hi << 64) | (u128)c->h_ctr->s_lo;
-    int64_t mv = (int64_t)c->h_ctr->moves;
-    c->iters.push_back(IterRec{pass, mv, S});
-    moves_total += mv;
+    CK(cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+    if (multi) {
+      CK(cudaMemcpyAsync(c->h_gmoves, c->d_gmoves, G * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(c->h_gs, c->d_gs, 2 * G * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    }
+    return 0;
+  };
+
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  long long graph_launches = 0;   // kernels in the captured graph
+  int it = 0;
+  int rc = 0;
+  for (; it < c->opt.max_iterations; ++it) {
+    *c->h_iter = it;
+    if ((rc = [&]() -> int {
+           CK(cudaMemcpyAsync(c->d_iter, c->h_iter, sizeof(int), cudaMemcpyHostToDevice, s));
+           return 0;
+         }()))
+      break;
+    if (c->opt.cuda_graphs && it >= 2) {
+      if (!gexec) {
+        if ((rc = [&]() -> int {
+               CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+               return 0;
+             }()))
+          break;
+        const long long l0 = launches_so_far();
+        int r1 = iteration();
+        cudaError_t e = cudaStreamEndCapture(s, &graph);
+        graph_launches = launches_so_far() - l0;
+        if (r1 || e != cudaSuccess) {
+          cudaGetLastError();
+          rc = r1 ? r1 : fail(c, LOUVAIN_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+          break;
+        }
+        if ((rc = [&]() -> int {
+               CK(cudaGraphInstantiate(&gexec, graph, 0));
+               return 0;
+             }()))
+          break;
+      } else {
+        add_launches(graph_launches);   // a replay runs the captured kernels again
+      }
+      if ((rc = [&]() -> int {
+             CK(cudaGraphLaunch(gexec, s));
+             return 0;
+           }()))
+        break;
+    } else {
+      if ((rc = iteration())) break;
+    }
+    if ((rc = [&]() -> int {
+           CK(cudaStreamSynchronize(s));
+           return 0;
+         }()))
+      break;
+    if (c->h_ctr->error) {
+      rc = fail(c, LOUVAIN_ERR_INTERNAL, "local-moving: hash table overflow");
+      break;
+    }
     edges_total += (int64_t)c->h_ctr->edges;
     visited_total += (int64_t)c->h_ctr->visited;
-    if ((2.0 * (double)S) / dbl(M2) <= tol) { ++it; break; }
+    bool any_on = false;
+    if (!multi) {
+      const u128 S = ((u128)c->h_ctr->s_hi << 64) | (u128)c->h_ctr->s_lo;
+      const int64_t mv = (int64_t)c->h_ctr->moves;
+      c->iters.push_back(IterRec{pass, mv, S});
+      c->gst[0].pass_moves += mv;
+      c->gst[0].pass_iters++;
+      any_on = !((2.0 * (double)S) / dbl((i128)c->M * c->M) <= tol);
+    } else {
+      u128 Stot = 0;
+      int64_t mvtot = 0;
+      for (int64_t q = 0; q < G; ++q) {
+        if (!c->h_gon[q]) continue;
+        GraphState& st = c->gst[q];
+        const u128 S = ((u128)c->h_gs[2 * q + 1] << 64) | (u128)c->h_gs[2 * q];
+        const int64_t mv = (int64_t)c->h_gmoves[q];
+        st.iters.push_back(IterRec{pass, mv, S});
+        st.pass_moves += mv;
+        st.pass_iters++;
+        Stot += S;
+        mvtot += mv;
+        if ((2.0 * (double)S) / dbl((i128)st.M * st.M) <= tol) c->h_gon[q] = 0;
+        else any_on = true;
+      }
+      c->iters.push_back(IterRec{pass, mvtot, Stot});
+      if (any_on)
+        if ((rc = [&]() -> int {
+               CK(cudaMemcpyAsync(c->d_gon, c->h_gon, G * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+               return 0;
+             }()))
+          break;
+    }
+    if (!any_on) {
+      ++it;
+      break;
+    }
   }
-  *pass_moves = moves_total;
+  if (gexec) cudaGraphExecDestroy(gexec);
+  if (graph) cudaGraphDestroy(graph);
+  if (rc) return rc;
   *iters_out = it;
   *edges_out = edges_total;
   *visited_out = visited_total;
   return 0;
 }
 
-// Exact Q numerator of the current membership on the pass graph.
+// Exact Q numerator of every graph's current membership on the pass graph.
 template <typename W>
-int q_numerator(louvain_ctx* c, const PassState& g, i128* out) {
-  CK(cudaMemsetAsync(c->acc, 0, 4 * sizeof(unsigned long long), c->stream));
-  modularity_parts<W>(g.off, g.col, (const W*)g.w, g.n, c->memb, c->sig, c->acc, c->stream);
+int q_numerators(louvain_ctx* c, const PassState& g, std::vector<i128>& out) {
+  cudaStream_t s = c->stream;
+  if (c->G == 1) {
+    CK(cudaMemsetAsync(c->acc, 0, 4 * sizeof(unsigned long long), s));
+    modularity_parts<W>(g.off, g.col, (const W*)g.w, g.n, c->memb, c->sig, c->acc, s);
+    CKLAUNCH();
+    if (int r = fetch(c, c->h_acc, c->acc, 4 * sizeof(unsigned long long))) return r;
+    u128 L = ((u128)c->h_acc[3] << 64) | (u128)c->h_acc[0];
+    u128 SS = ((u128)c->h_acc[2] << 64) | (u128)c->h_acc[1];
+    out[0] = (i128)c->M * (i128)L - (i128)SS;
+    return 0;
+  }
+  const int64_t G = c->G;
+  CK(cudaMemsetAsync(c->d_gL, 0, 2 * G * sizeof(unsigned long long), s));
+  CK(cudaMemsetAsync(c->d_gSS, 0, 2 * G * sizeof(unsigned long long), s));
+  graph_modularity_parts<W>(g.off, g.col, (const W*)g.w, g.n, c->memb, c->sig, c->gid, c->d_gL, c->d_gSS, s);
   CKLAUNCH();
-  if (int r = fetch(c, c->h_acc, c->acc, 4 * sizeof(unsigned long long))) return r;
-  u128 L = ((u128)c->h_acc[3] << 64) | (u128)c->h_acc[0];
-  u128 SS = ((u128)c->h_acc[2] << 64) | (u128)c->h_acc[1];
-  *out = (i128)c->M * (i128)L - (i128)SS;
+  if (int r = fetch(c, c->h_gL, c->d_gL, 2 * G * sizeof(unsigned long long))) return r;
+  if (int r = fetch(c, c->h_gSS, c->d_gSS, 2 * G * sizeof(unsigned long long))) return r;
+  for (int64_t q = 0; q < G; ++q) {
+    u128 L = ((u128)c->h_gL[2 * q + 1] << 64) | (u128)c->h_gL[2 * q];
+    u128 SS = ((u128)c->h_gSS[2 * q + 1] << 64) | (u128)c->h_gSS[2 * q];
+    out[q] = (i128)c->gst[q].M * (i128)L - (i128)SS;
+  }
   return 0;
 }
 
 template <typename W, typename W2>
-int aggregate(louvain_ctx* c, const PassState& g, int64_t k, PassState* next) {
+int aggregate(louvain_ctx* c, const PassState& g, int64_t k, PassState* next, std::vector<i128>& nafter) {
   cudaStream_t s = c->stream;
+  const bool multi = c->G > 1;
+  const int64_t G = c->G;
   const int dst = g.widx == 0 ? 1 : 0;
   coarse_degrees(c->used, c->newid, c->sig, g.n, c->Knext, s);
   agg_group_members(c->level, g.n, k, c->cnt, c->cstart, c->fill, c->members, c->tmp, s);
@@ -319,6 +522,7 @@ int aggregate(louvain_ctx* c, const PassState& g, int64_t k, PassState* next) {
   if (int r = fetch(c, ko, c->key_off, sizeof(ko))) return r;
   CK(cudaMemsetAsync(c->flags, 0, sizeof(int), s));
   AggArgs a;
+  memset(&a, 0, sizeof(a));
   a.off = g.off;
   a.col = g.col;
   a.wt = g.w;
@@ -338,7 +542,15 @@ int aggregate(louvain_ctx* c, const PassState& g, int64_t k, PassState* next) {
   // communities whose members have no edge get empty rows
   CK(cudaMemsetAsync(c->rlen, 0, (k + 1) * sizeof(int64_t), s));
   CK(cudaMemsetAsync(c->acc, 0, 8 * sizeof(unsigned long long), s));
-  sum_squares(c->sig, g.n, c->acc + 4, s);   // sum of Sigma_c^2 for the pass's Q numerator
+  if (multi) {
+    a.cgid = c->gid_next;
+    a.glsum = c->d_gL;
+    CK(cudaMemsetAsync(c->d_gL, 0, 2 * G * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(c->d_gSS, 0, 2 * G * sizeof(unsigned long long), s));
+    graph_squares(c->sig, c->gid, g.n, c->d_gSS, s);
+  } else {
+    sum_squares(c->sig, g.n, c->acc + 4, s);   // sum of Sigma_c^2 for the pass's Q numerator
+  }
   for (int b = 0; b < kAggGlobal; ++b)
     agg_launch_bucket<W, W2>(a, b, c->list + ko[b], (int)(ko[b + 1] - ko[b]), s);
   const int64_t ng = ko[kAggGlobal + 1] - ko[kAggGlobal];
@@ -364,10 +576,18 @@ int aggregate(louvain_ctx* c, const PassState& g, int64_t k, PassState* next) {
                   (W2*)c->wX[dst], s);
   CKLAUNCH();
   // Q numerator after the pass: M * sum_C L_C (coarse self-loops) - sum_c Sigma_c^2
-  if (int r = fetch(c, c->h_acc, c->acc, 8 * sizeof(unsigned long long))) return r;
-  {
+  if (!multi) {
+    if (int r = fetch(c, c->h_acc, c->acc, 8 * sizeof(unsigned long long))) return r;
     u128 SS = ((u128)c->h_acc[5] << 64) | (u128)c->h_acc[4];
-    c->agg_nafter = (i128)c->M * (i128)c->h_acc[6] - (i128)SS;
+    nafter[0] = (i128)c->M * (i128)c->h_acc[6] - (i128)SS;
+  } else {
+    if (int r = fetch(c, c->h_gL, c->d_gL, 2 * G * sizeof(unsigned long long))) return r;
+    if (int r = fetch(c, c->h_gSS, c->d_gSS, 2 * G * sizeof(unsigned long long))) return r;
+    for (int64_t q = 0; q < G; ++q) {
+      u128 L = ((u128)c->h_gL[2 * q + 1] << 64) | (u128)c->h_gL[2 * q];
+      u128 SS = ((u128)c->h_gSS[2 * q + 1] << 64) | (u128)c->h_gSS[2 * q];
+      nafter[q] = (i128)c->gst[q].M * (i128)L - (i128)SS;
+    }
   }
   next->n = k;
   next->nnz = nnz2;
@@ -394,11 +614,15 @@ int record_coarse(louvain_ctx* c, PassRec& pr, const PassState& h) {
   return 0;
 }
 
-// One pass on graph g (weights W), coarse graphs use W2.  Returns 0 and sets
-// *stop; on continuing, *next holds the coarse graph.
+// One pass on graph g (weights W), coarse graphs use W2.  Every graph that
+// has not stopped takes part; a graph stops after a pass with no move, a
+// pass whose gain is <= pass_tolerance, or the last pass.  Returns 0 and sets
+// *stop when every graph has stopped; otherwise *next holds the coarse graph.
 template <typename W, typename W2>
 int run_pass(louvain_ctx* c, const PassState& g, int pass, double* tol, bool wide, bool* stop, PassState* next) {
   cudaStream_t s = c->stream;
+  const bool multi = c->G > 1;
+  const int64_t G = c->G;
   PassRec pr;
   memset(&pr.info, 0, sizeof(pr.info));
   pr.info.n = g.n;
@@ -406,13 +630,14 @@ int run_pass(louvain_ctx* c, const PassState& g, int pass, double* tol, bool wid
   CK(cudaEventRecord(c->ev[0], s));
   pass_init(g.n, c->K, c->memb, c->sig, c->csize, c->stamp[0], c->stamp[1], s);
   CKLAUNCH();
-  const i128 nbefore = c->qnum;
-  const i128 M2 = (i128)c->M * c->M;
-  int64_t pmoves = 0, edges = 0, visited = 0;
+  const i128 nbefore = c->gst[0].qnum;
+  int64_t edges = 0, visited = 0;
   int iters = 0;
   CK(cudaEventRecord(c->ev[1], s));
-  if (int r = local_moving<W>(c, g, pass, *tol, wide, &pmoves, &iters, &edges, &visited)) return r;
+  if (int r = local_moving<W>(c, g, pass, *tol, wide, &iters, &edges, &visited)) return r;
   CK(cudaEventRecord(c->ev[2], s));
+  int64_t pmoves = 0;
+  for (int64_t q = 0; q < G; ++q) pmoves += c->gst[q].pass_moves;
   pr.info.moves = pmoves;
   pr.info.iterations = iters;
   pr.info.n_before_hi = (int64_t)(nbefore >> 64);
@@ -426,8 +651,11 @@ int run_pass(louvain_ctx* c, const PassState& g, int pass, double* tol, bool wid
   c->stats.moves += pmoves;
   c->stats.iterations += iters;
   c->stats.passes = pass + 1;
+  for (int64_t q = 0; q < G; ++q)
+    if (!c->gst[q].stopped) c->gst[q].passes++;
   float ms_init = 0, ms_lm = 0;
   if (pmoves == 0) {
+    // no graph moved: every graph stops, nothing to renumber
     CK(cudaEventSynchronize(c->ev[2]));
     cudaEventElapsedTime(&ms_init, c->ev[0], c->ev[1]);
     cudaEventElapsedTime(&ms_lm, c->ev[1], c->ev[2]);
@@ -438,42 +666,66 @@ int run_pass(louvain_ctx* c, const PassState& g, int pass, double* tol, bool wid
     c->stats.lm_ms += ms_lm;
     c->stats.other_ms += ms_init;
     c->passes.push_back(std::move(pr));
+    for (int64_t q = 0; q < G; ++q) c->gst[q].stopped = true;
     *stop = true;
     return 0;
   }
-  // renumber by ascending old id and compose the top level
+  // renumber by ascending old id and compose the top level; with several
+  // graphs each graph's communities stay contiguous and in order
   mark_used(c->memb, g.n, c->used, s);
   scan_i32(c->used, c->newid, g.n, c->scal, c->tmp, s);
   apply_level(c->memb, c->newid, g.n, c->level, s);
   compose_top(c->top, c->n0, c->level, s);
+  if (multi) {
+    CK(cudaMemsetAsync(c->kcount, 0, (G + 1) * sizeof(int64_t), s));
+    graph_renumber(c->used, c->newid, c->gid, g.n, c->kcount, c->gid_next, s);
+    scan_i64(c->kcount, c->vo_next, G, c->vo_next + G, c->tmp, s);
+    CK(cudaMemcpyAsync(c->vo_top, c->vo_next, (G + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  }
   CKLAUNCH();
   int64_t k = 0;
   if (int r = fetch(c, &k, c->scal, sizeof(int64_t))) return r;
+  std::vector<int64_t> vo_next;
+  if (multi) {
+    vo_next.resize(G + 1);
+    if (int r = fetch(c, vo_next.data(), c->vo_next, (G + 1) * sizeof(int64_t))) return r;
+  }
   // If another pass may follow, aggregate first: the coarse self-loops give
-  // sum_C L_C, so the pass's Q numerator costs no extra scan of the graph; a
-  // coarse graph built for a pass that then stops is dropped.
-  i128 nafter = 0;
+  // sum_C L_C, so the pass's Q numerators cost no extra scan of the graph; a
+  // coarse graph built for a pass after which every graph stops is dropped.
+  std::vector<i128> nafter(G, 0);
   bool built = false;
   if (pass + 1 < c->opt.max_passes) {
-    if (int r = aggregate<W, W2>(c, g, k, next)) return r;
-    nafter = c->agg_nafter;
+    if (int r = aggregate<W, W2>(c, g, k, next, nafter)) return r;
     built = true;
   } else {
-    if (int r = q_numerator<W>(c, g, &nafter)) return r;
+    if (int r = q_numerators<W>(c, g, nafter)) return r;
   }
   CK(cudaEventRecord(c->ev[3], s));
+  bool all_stopped = true;
+  for (int64_t q = 0; q < G; ++q) {
+    GraphState& st = c->gst[q];
+    if (st.stopped) continue;
+    if (st.pass_moves == 0) {
+      st.stopped = true;   // its level is the identity: nothing changes
+    } else {
+      const i128 gain = nafter[q] - st.qnum;
+      st.qnum = nafter[q];
+      st.k = multi ? vo_next[q + 1] - vo_next[q] : k;
+      st.stopped = dbl(gain) / dbl((i128)st.M * st.M) <= c->opt.pass_tolerance || pass + 1 == c->opt.max_passes;
+    }
+    all_stopped = all_stopped && st.stopped;
+  }
   pr.info.k = k;
-  pr.info.n_after_hi = (int64_t)(nafter >> 64);
-  pr.info.n_after_lo = (uint64_t)nafter;
+  pr.info.n_after_hi = (int64_t)(c->gst[0].qnum >> 64);
+  pr.info.n_after_lo = (uint64_t)c->gst[0].qnum;
   pr.info.level_recorded = c->opt.record_levels ? 1 : 0;
   if (c->opt.record_levels) {
     pr.level.resize(g.n);
     CK(cudaMemcpyAsync(pr.level.data(), c->level, g.n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
   }
-  c->qnum = nafter;
-  c->k_final = k;
-  *stop = dbl(nafter - nbefore) / dbl(M2) <= c->opt.pass_tolerance || pass + 1 == c->opt.max_passes;
+  *stop = all_stopped;
   float ms_agg = 0;
   CK(cudaEventSynchronize(c->ev[3]));
   cudaEventElapsedTime(&ms_agg, c->ev[2], c->ev[3]);
@@ -483,6 +735,10 @@ int run_pass(louvain_ctx* c, const PassState& g, int pass, double* tol, bool wid
     if (c->opt.record_levels)
       if (int r = record_coarse<W2>(c, pr, *next)) return r;
     *tol = *tol / c->opt.tolerance_decline;
+    if (multi) {
+      std::swap(c->gid, c->gid_next);
+      std::swap(c->vo, c->vo_next);
+    }
   }
   cudaEventElapsedTime(&ms_init, c->ev[0], c->ev[1]);
   cudaEventElapsedTime(&ms_lm, c->ev[1], c->ev[2]);
@@ -497,25 +753,46 @@ int run_pass(louvain_ctx* c, const PassState& g, int pass, double* tol, bool wid
 
 int run_all(louvain_ctx* c) {
   cudaStream_t s = c->stream;
+  const int64_t G = c->G;
   c->iters.clear();
   c->passes.clear();
   memset(&c->stats, 0, sizeof(c->stats));
-  c->qnum = 0;
   c->Q = 0;
-  c->k_final = c->n0;
   const long long launches0 = launches_so_far();
   CK(cudaEventRecord(c->ev[6], s));
   iota_i32(c->top, c->n0, s);
-  // pass-0 degrees, M and the singleton numerator were found when the graph
-  // was loaded
+  // pass-0 degrees, M and the singleton numerators were found when the
+  // graph was loaded
   CK(cudaMemcpyAsync(c->K, c->K0, c->n0 * sizeof(long long), cudaMemcpyDeviceToDevice, s));
   c->M = c->M0;
-  c->qnum = c->qnum0;
+  for (int64_t q = 0; q < G; ++q) {
+    GraphState& st = c->gst[q];
+    st.M = c->gM0[q];
+    st.qnum = c->gqnum0[q];
+    st.stopped = st.M == 0;      // a graph without edges never moves
+    st.k = c->gn0[q];
+    st.passes = 0;
+    st.iters.clear();
+  }
+  if (G > 1) {
+    c->gid = c->gid_a;
+    c->gid_next = c->gid_b;
+    c->vo = c->vo_a;
+    c->vo_next = c->vo_b;
+    CK(cudaMemcpyAsync(c->gid, c->gid0, c->n0 * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c->vo, c->vo0, (G + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c->vo_top, c->vo0, (G + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  }
   const bool wide = c->M >= (1ll << 31);           // M^2 >= 2^62: 128-bit gains
   const bool coarse64 = c->M >= (1ll << 31) - 1;   // coarse weights can exceed int32
   PassState g{c->n0, c->nnz0, c->off0, c->col0, (void*)c->w0, -1};
   double tol = c->opt.tolerance;
-  for (int p = 0; p < c->opt.max_passes && c->M > 0; ++p) {
+  auto any_running = [&]() {
+    for (int64_t q = 0; q < G; ++q)
+      if (!c->gst[q].stopped) return true;
+    return false;
+  };
+  for (int p = 0; p < c->opt.max_passes && any_running(); ++p) {
     bool stop = false;
     PassState next{};
     int r;
@@ -535,92 +812,22 @@ int run_all(louvain_ctx* c) {
   float tot = 0;
   cudaEventElapsedTime(&tot, c->ev[6], c->ev[7]);
   c->stats.total_ms = tot;
-  const i128 M2 = (i128)c->M * c->M;
-  c->Q = c->M == 0 ? 0.0 : dbl(c->qnum) / dbl(M2);
-  c->stats.q = c->Q;
-  c->stats.communities = c->k_final;
+  int64_t comms = 0;
+  for (int64_t q = 0; q < G; ++q) comms += c->gst[q].k;
+  c->qnum = c->gst[0].qnum;
+  c->Q = c->M == 0 ? 0.0 : dbl(c->qnum) / dbl((i128)c->M * c->M);
+  c->stats.q = G == 1 ? c->Q : 0.0;
+  c->stats.communities = comms;
   c->stats.kernel_launches = launches_so_far() - launches0;
   return 0;
 }
 
 }  // namespace
 
-// ================================================================== C ABI
-
-extern "C" {
-
-int louvain_default_options(louvain_options* o) {
-  if (!o) return LOUVAIN_ERR_INVALID_ARG;
-  memset(o, 0, sizeof(*o));
-  o->mode = LOUVAIN_SYNC;
-  o->tolerance = 0.01;
-  o->tolerance_decline = 10.0;
-  o->pass_tolerance = 0.0;
-  o->max_iterations = 20;
-  o->max_passes = 10;
-  o->prune = 0;
-  o->singleton_guard = 1;
-  o->subrounds = 0;
-  o->validate = 1;
-  o->record_levels = 0;
-  return 0;
-}
-
-int louvain_create(louvain_ctx** out, const louvain_options* opt, int device, void* cuda_stream) {
-  if (!out) return LOUVAIN_ERR_INVALID_ARG;
-  *out = nullptr;
-  louvain_ctx* c = new louvain_ctx();
-  if (opt) c->opt = *opt; else louvain_default_options(&c->opt);
-  if (check_options(&c->opt)) { delete c; return LOUVAIN_ERR_INVALID_ARG; }
-  int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
-    cudaGetLastError();
-    delete c;
-    return LOUVAIN_ERR_CUDA;
-  }
-  c->device = device;
-  if (cudaSetDevice(device) != cudaSuccess) { delete c; return LOUVAIN_ERR_CUDA; }
-  if (cuda_stream) {
-    c->stream = (cudaStream_t)cuda_stream;
-  } else {
-    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return LOUVAIN_ERR_CUDA; }
-    c->own_stream = true;
-  }
-  for (auto& e : c->ev)
-    if (cudaEventCreate(&e) != cudaSuccess) { delete c; return LOUVAIN_ERR_CUDA; }
-  if (cudaMallocHost(&c->h_ctr, sizeof(DevCounters)) != cudaSuccess ||
-      cudaMallocHost(&c->h_acc, 8 * sizeof(unsigned long long)) != cudaSuccess ||
-      cudaMallocHost(&c->h_scal, 8 * sizeof(int64_t)) != cudaSuccess) {
-    delete c;
-    return LOUVAIN_ERR_OOM;
-  }
-  memset(&c->stats, 0, sizeof(c->stats));
-  *out = c;
-  return 0;
-}
-
-int louvain_set_options(louvain_ctx* c, const louvain_options* opt) {
-  if (!c || !opt) return LOUVAIN_ERR_INVALID_ARG;
-  if (check_options(opt)) return fail(c, LOUVAIN_ERR_INVALID_ARG, "invalid options");
-  c->opt = *opt;
-  return 0;
-}
-
-int louvain_load_csr(louvain_ctx* c, int64_t n, int64_t nnz, const int64_t* offsets, const int32_t* cols,
-                     const int32_t* weights, int ptr_kind) {
-  if (!c) return LOUVAIN_ERR_INVALID_ARG;
-  if (n < 0 || nnz < 0 || (ptr_kind != LOUVAIN_PTR_HOST && ptr_kind != LOUVAIN_PTR_DEVICE))
-    return fail(c, LOUVAIN_ERR_INVALID_ARG, "negative size or bad pointer kind");
-  if (!offsets || (nnz > 0 && (!cols || !weights))) return fail(c, LOUVAIN_ERR_INVALID_ARG, "null pointer");
-  if (n >= (1ll << 31) - 1) return fail(c, LOUVAIN_ERR_OVERFLOW, "n must be below 2^31 - 1");
-  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, LOUVAIN_ERR_CUDA, "cudaSetDevice failed");
-  if (ptr_kind == LOUVAIN_PTR_HOST) {
-    // cheap host checks first
-    if (offsets[0] != 0 || offsets[n] != nnz) return fail(c, LOUVAIN_ERR_BAD_CSR, "offsets[0] != 0 or offsets[n] != nnz");
-  }
+// Device arena for graphs of up to n vertices and nnz entries (every buffer
+// is sized by one of the two); reused by later loads that fit.
+int alloc_arena(louvain_ctx* c, int64_t n, int64_t nnz) {
   free_all(c);
-  c->n0 = n;
-  c->nnz0 = nnz;
   const int64_t N1 = n + 1;
   ALLOC(c->off0, N1);
   ALLOC(c->col0, nnz);
@@ -661,7 +868,6 @@ int louvain_load_csr(louvain_ctx* c, int64_t n, int64_t nnz, const int64_t* offs
   ALLOC(c->chunk_pre, N1);
   ALLOC(c->spre, N1);
   ALLOC(c->hkid, N1);
-  CK(cudaMemsetAsync(c->hkid, 0, N1 * sizeof(unsigned long long), c->stream));
   // slot chunks of all hubs: sum of ceil(2 deg / kSlotChunk) <= 2 nnz / kSlotChunk + #hubs
   c->npart = 2 * nnz / kSlotChunk + nnz / 4096 + 16;
   ALLOC(c->hpart, 2 * c->npart);
@@ -676,7 +882,150 @@ int louvain_load_csr(louvain_ctx* c, int64_t n, int64_t nnz, const int64_t* offs
   ALLOC(c->ctr, 1);
   ALLOC(c->acc, 8);
   ALLOC(c->flags, 4);
+  ALLOC(c->d_iter, 4);
   ALLOC(c->scal, 8);
+  ALLOC(c->gid0, n);
+  ALLOC(c->gid_a, n);
+  ALLOC(c->gid_b, n);
+  ALLOC(c->vo0, N1 + 1);
+  ALLOC(c->vo_a, N1 + 1);
+  ALLOC(c->vo_b, N1 + 1);
+  ALLOC(c->vo_top, N1 + 1);
+  ALLOC(c->kcount, N1 + 1);
+  ALLOC(c->d_Mg, N1);
+  ALLOC(c->d_gon, N1);
+  ALLOC(c->d_gmoves, N1);
+  ALLOC(c->d_gs, 2 * N1);
+  ALLOC(c->d_gL, 2 * N1);
+  ALLOC(c->d_gSS, 2 * N1);
+  c->cap_n = n;
+  c->cap_nnz = nnz;
+  c->tables_dirty = true;
+  return 0;
+}
+
+void free_host_graph_buffers(louvain_ctx* c) {
+  if (c->h_gon) cudaFreeHost(c->h_gon);
+  if (c->h_gmoves) cudaFreeHost(c->h_gmoves);
+  if (c->h_gs) cudaFreeHost(c->h_gs);
+  if (c->h_gL) cudaFreeHost(c->h_gL);
+  if (c->h_gSS) cudaFreeHost(c->h_gSS);
+  c->h_gon = nullptr;
+  c->h_gmoves = c->h_gs = c->h_gL = c->h_gSS = nullptr;
+  c->hcap = 0;
+}
+
+int host_graph_buffers(louvain_ctx* c, int64_t G) {
+  if (c->hcap >= G) return 0;
+  free_host_graph_buffers(c);
+  if (cudaMallocHost(&c->h_gon, G * sizeof(int32_t)) != cudaSuccess ||
+      cudaMallocHost(&c->h_gmoves, G * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMallocHost(&c->h_gs, 2 * G * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMallocHost(&c->h_gL, 2 * G * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMallocHost(&c->h_gSS, 2 * G * sizeof(unsigned long long)) != cudaSuccess) {
+    free_host_graph_buffers(c);
+    return fail(c, LOUVAIN_ERR_OOM, "pinned host allocation failed");
+  }
+  c->hcap = G;
+  return 0;
+}
+
+// ================================================================== C ABI
+
+extern "C" {
+
+int louvain_default_options(louvain_options* o) {
+  if (!o) return LOUVAIN_ERR_INVALID_ARG;
+  memset(o, 0, sizeof(*o));
+  o->mode = LOUVAIN_SYNC;
+  o->tolerance = 0.01;
+  o->tolerance_decline = 10.0;
+  o->pass_tolerance = 0.0;
+  o->max_iterations = 20;
+  o->max_passes = 10;
+  o->prune = 0;
+  o->singleton_guard = 1;
+  o->subrounds = 0;
+  o->validate = 1;
+  o->record_levels = 0;
+  o->cuda_graphs = 1;
+  return 0;
+}
+
+int louvain_create(louvain_ctx** out, const louvain_options* opt, int device, void* cuda_stream) {
+  if (!out) return LOUVAIN_ERR_INVALID_ARG;
+  *out = nullptr;
+  louvain_ctx* c = new louvain_ctx();
+  if (opt) c->opt = *opt; else louvain_default_options(&c->opt);
+  if (check_options(&c->opt)) { delete c; return LOUVAIN_ERR_INVALID_ARG; }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    delete c;
+    return LOUVAIN_ERR_CUDA;
+  }
+  c->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) { delete c; return LOUVAIN_ERR_CUDA; }
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return LOUVAIN_ERR_CUDA; }
+    c->own_stream = true;
+  }
+  for (auto& e : c->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) { delete c; return LOUVAIN_ERR_CUDA; }
+  for (int i = 0; i < louvain_ctx::kAux; ++i)
+    if (cudaStreamCreateWithFlags(&c->aux[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming) != cudaSuccess) {
+      delete c;
+      return LOUVAIN_ERR_CUDA;
+    }
+  if (cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess) { delete c; return LOUVAIN_ERR_CUDA; }
+  if (cudaMallocHost(&c->h_ctr, sizeof(DevCounters)) != cudaSuccess ||
+      cudaMallocHost(&c->h_acc, 8 * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMallocHost(&c->h_scal, 8 * sizeof(int64_t)) != cudaSuccess ||
+      cudaMallocHost(&c->h_iter, 4 * sizeof(int)) != cudaSuccess) {
+    delete c;
+    return LOUVAIN_ERR_OOM;
+  }
+  memset(&c->stats, 0, sizeof(c->stats));
+  *out = c;
+  return 0;
+}
+
+int louvain_set_options(louvain_ctx* c, const louvain_options* opt) {
+  if (!c || !opt) return LOUVAIN_ERR_INVALID_ARG;
+  if (check_options(opt)) return fail(c, LOUVAIN_ERR_INVALID_ARG, "invalid options");
+  c->opt = *opt;
+  return 0;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Load one graph (G = 1) or G graphs whose vertices are the contiguous ranges
+// [vo[g], vo[g + 1]) of one CSR with no entry between ranges (vo: host).
+int load_graphs(louvain_ctx* c, int64_t G, const int64_t* vo, int64_t n, int64_t nnz, const int64_t* offsets,
+                const int32_t* cols, const int32_t* weights, int ptr_kind) {
+  if (!c) return LOUVAIN_ERR_INVALID_ARG;
+  if (n < 0 || nnz < 0 || (ptr_kind != LOUVAIN_PTR_HOST && ptr_kind != LOUVAIN_PTR_DEVICE))
+    return fail(c, LOUVAIN_ERR_INVALID_ARG, "negative size or bad pointer kind");
+  if (!offsets || (nnz > 0 && (!cols || !weights))) return fail(c, LOUVAIN_ERR_INVALID_ARG, "null pointer");
+  if (n >= (1ll << 31) - 1) return fail(c, LOUVAIN_ERR_OVERFLOW, "n must be below 2^31 - 1");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, LOUVAIN_ERR_CUDA, "cudaSetDevice failed");
+  if (ptr_kind == LOUVAIN_PTR_HOST) {
+    // cheap host checks first
+    if (offsets[0] != 0 || offsets[n] != nnz) return fail(c, LOUVAIN_ERR_BAD_CSR, "offsets[0] != 0 or offsets[n] != nnz");
+  }
+  if (!(c->cap_n >= n && c->cap_nnz >= nnz && !c->allocs.empty())) {
+    if (int r = alloc_arena(c, n, nnz)) return r;
+  }
+  c->loaded = false;
+  c->ran = false;
+  c->n0 = n;
+  c->nnz0 = nnz;
+  const int64_t N1 = n + 1;
   cudaStream_t s = c->stream;
   cudaMemcpyKind kind = ptr_kind == LOUVAIN_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   CK(cudaMemcpyAsync(c->off0, offsets, N1 * sizeof(int64_t), kind, s));
@@ -684,29 +1033,32 @@ int louvain_load_csr(louvain_ctx* c, int64_t n, int64_t nnz, const int64_t* offs
     CK(cudaMemcpyAsync(c->col0, cols, nnz * sizeof(int32_t), kind, s));
     CK(cudaMemcpyAsync(c->w0, weights, nnz * sizeof(int32_t), kind, s));
   }
-  CK(cudaMemsetAsync(c->gkeys, 0xff, 2 * nnz * sizeof(int32_t), s));
-  CK(cudaMemsetAsync(c->gvals, 0, 2 * nnz * sizeof(unsigned long long), s));
+  if (c->tables_dirty) {
+    // global tables start empty; every later use clears what it touched
+    CK(cudaMemsetAsync(c->gkeys, 0xff, 2 * c->cap_nnz * sizeof(int32_t), s));
+    CK(cudaMemsetAsync(c->gvals, 0, 2 * c->cap_nnz * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(c->hkid, 0, (c->cap_n + 1) * sizeof(unsigned long long), s));
+    c->tables_dirty = false;
+  }
   if (c->opt.validate) {
     validate_csr(c->off0, c->col0, c->w0, n, nnz, c->flags, c->acc, s);
     CKLAUNCH();
     int flags = 0;
     unsigned long long h[2];
-    if (int r = fetch(c, &flags, c->flags, sizeof(int))) { free_all(c); return r; }
-    if (int r = fetch(c, h, c->acc, sizeof(h))) { free_all(c); return r; }
-    if (flags & 1) { free_all(c); return fail(c, LOUVAIN_ERR_BAD_CSR, "offsets not monotone or wrong ends"); }
-    if (flags & 2) { free_all(c); return fail(c, LOUVAIN_ERR_BAD_CSR, "column index out of range"); }
-    if (flags & 4) { free_all(c); return fail(c, LOUVAIN_ERR_BAD_CSR, "weight <= 0"); }
-    if (h[0] != h[1]) { free_all(c); return fail(c, LOUVAIN_ERR_NOT_SYMMETRIC, "CSR is not symmetric"); }
+    if (int r = fetch(c, &flags, c->flags, sizeof(int))) return r;
+    if (int r = fetch(c, h, c->acc, sizeof(h))) return r;
+    if (flags & 1) return fail(c, LOUVAIN_ERR_BAD_CSR, "offsets not monotone or wrong ends");
+    if (flags & 2) return fail(c, LOUVAIN_ERR_BAD_CSR, "column index out of range");
+    if (flags & 4) return fail(c, LOUVAIN_ERR_BAD_CSR, "weight <= 0");
+    if (h[0] != h[1]) return fail(c, LOUVAIN_ERR_NOT_SYMMETRIC, "CSR is not symmetric");
   }
   // input degrees (for louvain_modularity)
   CK(cudaMemsetAsync(c->acc, 0, 8 * sizeof(unsigned long long), s));
   row_sums<int32_t>(c->off0, c->col0, c->w0, n, c->K0, c->acc, s);
   CKLAUNCH();
-  if (int r = fetch(c, c->h_acc, c->acc, 4 * sizeof(unsigned long long))) { free_all(c); return r; }
-  if (c->h_acc[1] != 0 || c->h_acc[0] >= (1ull << 62)) {
-    free_all(c);
+  if (int r = fetch(c, c->h_acc, c->acc, 4 * sizeof(unsigned long long))) return r;
+  if (c->h_acc[1] != 0 || c->h_acc[0] >= (1ull << 62))
     return fail(c, LOUVAIN_ERR_OVERFLOW, "total weight M must be below 2^62");
-  }
   c->M0 = (int64_t)c->h_acc[0];
   {
     // singleton partition: sum L_c = total self-loop weight, sum Sigma_c^2 = sum K_i^2
@@ -714,14 +1066,85 @@ int louvain_load_csr(louvain_ctx* c, int64_t n, int64_t nnz, const int64_t* offs
     CK(cudaMemsetAsync(c->acc, 0, 2 * sizeof(unsigned long long), s));
     sum_squares(c->K0, n, c->acc, s);
     CKLAUNCH();
-    if (int r = fetch(c, c->h_acc, c->acc, 2 * sizeof(unsigned long long))) { free_all(c); return r; }
+    if (int r = fetch(c, c->h_acc, c->acc, 2 * sizeof(unsigned long long))) return r;
     const u128 SS = ((u128)c->h_acc[1] << 64) | (u128)c->h_acc[0];
     c->qnum0 = (i128)c->M0 * (i128)loops - (i128)SS;
+  }
+  // per graph: M, vertices, singleton numerator
+  if (int r = host_graph_buffers(c, G)) return r;
+  c->G = G;
+  c->gst.assign(G, GraphState());
+  c->gM0.assign(G, 0);
+  c->gn0.assign(G, 0);
+  c->gqnum0.assign(G, 0);
+  for (int64_t q = 0; q < G; ++q) c->gn0[q] = vo[q + 1] - vo[q];
+  CK(cudaMemcpyAsync(c->vo0, vo, (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  if (G == 1) {
+    c->gM0[0] = c->M0;
+    c->gqnum0[0] = c->qnum0;
+  } else {
+    CK(cudaMemsetAsync(c->flags, 0, sizeof(int), s));
+    graph_ids(c->vo0, (int)G, n, c->gid0, c->off0, c->col0, c->flags, s);
+    int flags = 0;
+    CKLAUNCH();
+    if (int r = fetch(c, &flags, c->flags, sizeof(int))) return r;
+    if (flags & 8) return fail(c, LOUVAIN_ERR_BAD_CSR, "an entry joins two graphs of the batch");
+    CK(cudaMemsetAsync(c->d_gs, 0, 2 * G * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(c->d_gL, 0, 2 * G * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(c->d_gSS, 0, 2 * G * sizeof(unsigned long long), s));
+    graph_totals(c->K0, c->gid0, n, c->d_gs, s);
+    iota_i32(c->memb, n, s);
+    graph_modularity_parts<int32_t>(c->off0, c->col0, c->w0, n, c->memb, c->K0, c->gid0, c->d_gL, c->d_gSS, s);
+    CKLAUNCH();
+    if (int r = fetch(c, c->h_gs, c->d_gs, 2 * G * sizeof(unsigned long long))) return r;
+    if (int r = fetch(c, c->h_gL, c->d_gL, 2 * G * sizeof(unsigned long long))) return r;
+    if (int r = fetch(c, c->h_gSS, c->d_gSS, 2 * G * sizeof(unsigned long long))) return r;
+    std::vector<long long> Mg(G);
+    for (int64_t q = 0; q < G; ++q) {
+      const u128 M = ((u128)c->h_gs[2 * q + 1] << 64) | (u128)c->h_gs[2 * q];
+      const u128 L = ((u128)c->h_gL[2 * q + 1] << 64) | (u128)c->h_gL[2 * q];
+      const u128 SS = ((u128)c->h_gSS[2 * q + 1] << 64) | (u128)c->h_gSS[2 * q];
+      c->gM0[q] = (int64_t)M;
+      Mg[q] = (long long)M;
+      c->gqnum0[q] = (i128)(int64_t)M * (i128)L - (i128)SS;
+    }
+    CK(cudaMemcpyAsync(c->d_Mg, Mg.data(), G * sizeof(long long), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
   }
   c->loaded = true;
   c->ran = false;
   return 0;
 }
+
+}  // namespace
+
+extern "C" {
+
+int louvain_load_csr(louvain_ctx* c, int64_t n, int64_t nnz, const int64_t* offsets, const int32_t* cols,
+                     const int32_t* weights, int ptr_kind) {
+  if (n < 0) return c ? fail(c, LOUVAIN_ERR_INVALID_ARG, "negative size") : LOUVAIN_ERR_INVALID_ARG;
+  const int64_t vo[2] = {0, n};
+  return load_graphs(c, 1, vo, n, nnz, offsets, cols, weights, ptr_kind);
+}
+
+int louvain_load_batch(louvain_ctx* c, int64_t num_graphs, const int64_t* graph_offsets, int64_t n, int64_t nnz,
+                       const int64_t* offsets, const int32_t* cols, const int32_t* weights, int ptr_kind) {
+  if (!c) return LOUVAIN_ERR_INVALID_ARG;
+  if (num_graphs < 1 || num_graphs > n + 1 || !graph_offsets || n < 0)
+    return fail(c, LOUVAIN_ERR_INVALID_ARG, "num_graphs must be in [1, n] with graph_offsets given");
+  std::vector<int64_t> vo(num_graphs + 1);
+  if (ptr_kind == LOUVAIN_PTR_DEVICE) {
+    if (cudaMemcpy(vo.data(), graph_offsets, vo.size() * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(c, LOUVAIN_ERR_CUDA, "copying graph offsets failed");
+  } else {
+    memcpy(vo.data(), graph_offsets, vo.size() * sizeof(int64_t));
+  }
+  if (vo[0] != 0 || vo[num_graphs] != n) return fail(c, LOUVAIN_ERR_BAD_CSR, "graph offsets must run from 0 to n");
+  for (int64_t q = 0; q < num_graphs; ++q)
+    if (vo[q + 1] < vo[q]) return fail(c, LOUVAIN_ERR_BAD_CSR, "graph offsets must not decrease");
+  return load_graphs(c, num_graphs, vo.data(), n, nnz, offsets, cols, weights, ptr_kind);
+}
+
 
 int louvain_run(louvain_ctx* c) {
   if (!c) return LOUVAIN_ERR_INVALID_ARG;
@@ -729,7 +1152,11 @@ int louvain_run(louvain_ctx* c) {
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, LOUVAIN_ERR_CUDA, "cudaSetDevice failed");
   c->ran = false;
   int r = run_all(c);
-  if (r) return r;
+  if (r) {
+    c->tables_dirty = true;
+    c->loaded = false;   // load again before the next run
+    return r;
+  }
   c->ran = true;
   return 0;
 }
@@ -740,7 +1167,14 @@ int louvain_get_membership(louvain_ctx* c, int32_t* out, int64_t n, int ptr_kind
   if (n != c->n0 || (!out && n > 0)) return fail(c, LOUVAIN_ERR_INVALID_ARG, "n must equal the loaded n");
   if (n == 0) return 0;
   cudaMemcpyKind kind = ptr_kind == LOUVAIN_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-  CK(cudaMemcpyAsync(out, c->top, n * sizeof(int32_t), kind, c->stream));
+  const int32_t* src = c->top;
+  if (c->G > 1) {
+    // ids local to each graph: top - first community id of the vertex's graph
+    localize_membership(c->top, c->gid0, c->vo_top, n, c->key, c->stream);
+    CKLAUNCH();
+    src = c->key;
+  }
+  CK(cudaMemcpyAsync(out, src, n * sizeof(int32_t), kind, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return 0;
 }
@@ -748,6 +1182,7 @@ int louvain_get_membership(louvain_ctx* c, int32_t* out, int64_t n, int ptr_kind
 int louvain_get_modularity(louvain_ctx* c, double* q) {
   if (!c || !q) return LOUVAIN_ERR_INVALID_ARG;
   if (!c->ran) return fail(c, LOUVAIN_ERR_STATE, "no result (run first)");
+  if (c->G > 1) return fail(c, LOUVAIN_ERR_STATE, "several graphs loaded: use louvain_batch_get_modularity");
   *q = c->Q;
   return 0;
 }
@@ -755,6 +1190,7 @@ int louvain_get_modularity(louvain_ctx* c, double* q) {
 int louvain_get_modularity_exact(louvain_ctx* c, int64_t* num_hi, uint64_t* num_lo, int64_t* M) {
   if (!c || !num_hi || !num_lo || !M) return LOUVAIN_ERR_INVALID_ARG;
   if (!c->ran) return fail(c, LOUVAIN_ERR_STATE, "no result (run first)");
+  if (c->G > 1) return fail(c, LOUVAIN_ERR_STATE, "several graphs loaded: use louvain_batch_get_modularity");
   *num_hi = (int64_t)(c->qnum >> 64);
   *num_lo = (uint64_t)c->qnum;
   *M = c->M;
@@ -844,6 +1280,55 @@ int louvain_get_coarse(louvain_ctx* c, int pass, int64_t* off, int64_t k, int32_
   return 0;
 }
 
+int louvain_batch_get_modularity(louvain_ctx* c, double* q, int64_t* num_hi, uint64_t* num_lo, int64_t* M) {
+  if (!c || !q) return LOUVAIN_ERR_INVALID_ARG;
+  if (!c->ran) return fail(c, LOUVAIN_ERR_STATE, "no result (run first)");
+  for (int64_t g = 0; g < c->G; ++g) {
+    const GraphState& st = c->gst[g];
+    q[g] = st.M == 0 ? 0.0 : dbl(st.qnum) / dbl((i128)st.M * st.M);
+    if (num_hi) num_hi[g] = (int64_t)(st.qnum >> 64);
+    if (num_lo) num_lo[g] = (uint64_t)st.qnum;
+    if (M) M[g] = st.M;
+  }
+  return 0;
+}
+
+int louvain_batch_get_graph_info(louvain_ctx* c, int64_t g, int64_t out[4]) {
+  if (!c || !out) return LOUVAIN_ERR_INVALID_ARG;
+  if (!c->ran) return fail(c, LOUVAIN_ERR_STATE, "no result (run first)");
+  if (g < 0 || g >= c->G) return fail(c, LOUVAIN_ERR_INVALID_ARG, "no such graph");
+  const GraphState& st = c->gst[g];
+  int64_t moves = 0;
+  const std::vector<IterRec>& it = c->G > 1 ? st.iters : c->iters;
+  for (const IterRec& r : it) moves += r.moves;
+  out[0] = st.passes;
+  out[1] = (int64_t)it.size();
+  out[2] = st.k;
+  out[3] = moves;
+  return 0;
+}
+
+int louvain_batch_get_iterations(louvain_ctx* c, int64_t g, int64_t* out, int64_t cap, int64_t* count) {
+  if (!c || !count) return LOUVAIN_ERR_INVALID_ARG;
+  if (!c->ran) return fail(c, LOUVAIN_ERR_STATE, "no result (run first)");
+  if (g < 0 || g >= c->G) return fail(c, LOUVAIN_ERR_INVALID_ARG, "no such graph");
+  const std::vector<IterRec>& it = c->G > 1 ? c->gst[g].iters : c->iters;
+  *count = (int64_t)it.size();
+  for (int64_t t = 0; t < (int64_t)it.size() && t < cap && out; ++t) {
+    out[4 * t] = it[t].pass;
+    out[4 * t + 1] = it[t].moves;
+    out[4 * t + 2] = (int64_t)(it[t].S >> 64);
+    out[4 * t + 3] = (int64_t)(uint64_t)it[t].S;
+  }
+  return 0;
+}
+
+int louvain_get_num_graphs(louvain_ctx* c, int64_t* num_graphs) {
+  if (!c || !num_graphs) return LOUVAIN_ERR_INVALID_ARG;
+  *num_graphs = c->G;
+  return 0;
+}
+
 int louvain_get_device_bytes(louvain_ctx* c, int64_t* bytes) {
   if (!c || !bytes) return LOUVAIN_ERR_INVALID_ARG;
   *bytes = c->bytes;
@@ -857,9 +1342,16 @@ void louvain_destroy(louvain_ctx* c) {
   free_all(c);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
+  for (int i = 0; i < louvain_ctx::kAux; ++i) {
+    if (c->aux[i]) { cudaStreamSynchronize(c->aux[i]); cudaStreamDestroy(c->aux[i]); }
+    if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->h_ctr) cudaFreeHost(c->h_ctr);
   if (c->h_acc) cudaFreeHost(c->h_acc);
   if (c->h_scal) cudaFreeHost(c->h_scal);
+  if (c->h_iter) cudaFreeHost(c->h_iter);
+  free_host_graph_buffers(c);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }

@@ -51,7 +51,8 @@ void stable_partition(const int32_t* key, int64_t n, int nkeys, int32_t* out, in
 
 // Keys for the local-moving lists: bucket-major, then class (i mod P); vertices
 // of degree 0 get the trailing key nb * P.
-void lm_keys(const int64_t* off, int64_t n, int P, int32_t* key, cudaStream_t s);
+void lm_keys(const int64_t* off, int64_t n, int P, int32_t* key, const int32_t* gid, const int64_t* vo,
+             cudaStream_t s);
 // For the hub list: per hub its table base (2 * degree slots), the prefix of
 // its insert chunks and the prefix of its slot chunks (each nhubs + 1 long).
 void hub_layout(const int64_t* off, const int32_t* hubs, int64_t nhubs, int64_t* hbase, int64_t* chunk_pre,
@@ -102,6 +103,8 @@ struct AggArgs {
   int32_t* gkeys;          // global tables
   unsigned long long* gvals;
   unsigned long long* lsum;  // += weight of every coarse self-loop (sum of L_C)
+  const int32_t* cgid;       // several graphs: graph of each coarse vertex (else nullptr)
+  unsigned long long* glsum; // several graphs: per-graph sum of L_C (lo, hi)
   int* error;
 };
 void agg_group_members(const int32_t* level, int64_t n, int64_t k, int64_t* cnt /* k+1 */, int64_t* cstart,
@@ -120,6 +123,20 @@ void agg_global_layout(const int64_t* cstart, const int64_t* mpre, const int32_t
 template <typename W2>
 void agg_compact(const int64_t* cstart, const int64_t* mpre, const int64_t* rlen, const int64_t* coff, int64_t k,
                  const int32_t* tcol, const W2* tw, int32_t* ocol, W2* ow, cudaStream_t s);
+
+// Several graphs in one CSR (contiguous vertex ranges per graph).
+void graph_totals(const long long* K, const int32_t* gid, int64_t n, unsigned long long* Mg, cudaStream_t s);
+template <typename W>
+void graph_modularity_parts(const int64_t* off, const int32_t* col, const W* wt, int64_t n, const int32_t* memb,
+                            const long long* sig, const int32_t* gid, unsigned long long* Lg, unsigned long long* SSg,
+                            cudaStream_t s);
+void graph_squares(const long long* sig, const int32_t* gid, int64_t n, unsigned long long* SSg, cudaStream_t s);
+void graph_renumber(const int32_t* used, const int32_t* newid, const int32_t* gid, int64_t n, int64_t* kcount,
+                    int32_t* gid_next, cudaStream_t s);
+void localize_membership(const int32_t* top, const int32_t* gid0, const int64_t* vo, int64_t n0, int32_t* out,
+                         cudaStream_t s);
+void graph_ids(const int64_t* vo, int G, int64_t n, int32_t* gid, const int64_t* off, const int32_t* col, int* flags,
+               cudaStream_t s);
 
 // Input checks: flags |= 1 offsets not monotone / bad ends, 2 col out of
 // range, 4 weight <= 0; hashes[0..1] = sums of mix(u,v,w) and mix(v,u,w).

@@ -231,10 +231,12 @@ void stable_partition(const int32_t* key, int64_t n, int nkeys, int32_t* out, in
 
 // --------------------------------------------------- local-moving lists
 
-__global__ void lm_keys_k(const int64_t* __restrict__ off, int64_t n, int P, int32_t* key) {
+__global__ void lm_keys_k(const int64_t* __restrict__ off, int64_t n, int P, int32_t* key,
+                          const int32_t* __restrict__ gid, const int64_t* __restrict__ vo) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int b = lm_bucket_of(off[i + 1] - off[i]);
-    key[i] = b < 0 ? kBuckets * P : b * P + (int)(i % P);
+    const int64_t local = gid ? i - vo[gid[i]] : i;   // classes by id within the vertex's graph
+    key[i] = b < 0 ? kBuckets * P : b * P + (int)(local % P);
   }
 }
 
@@ -244,8 +246,9 @@ static unsigned grid1d(int64_t n, int per = kT) {
   return (unsigned)(b < 1 ? 1 : b);
 }
 
-void lm_keys(const int64_t* off, int64_t n, int P, int32_t* key, cudaStream_t s) {
-  if (n > 0) (count_launch(), lm_keys_k<<<grid1d(n), kT, 0, s>>>(off, n, P, key));
+void lm_keys(const int64_t* off, int64_t n, int P, int32_t* key, const int32_t* gid, const int64_t* vo,
+             cudaStream_t s) {
+  if (n > 0) (count_launch(), lm_keys_k<<<grid1d(n), kT, 0, s>>>(off, n, P, key, gid, vo));
 }
 
 __global__ void hub_sizes_k(const int64_t* off, const int32_t* hubs, int64_t nhubs, int64_t* cap, int64_t* chunks,
@@ -501,6 +504,13 @@ void agg_keys(const int64_t* cstart, const int64_t* mpre, int64_t k, int32_t* ke
   if (k > 0) (count_launch(), agg_keys_k<<<grid1d(k), kT, 0, s>>>(cstart, mpre, k, key));
 }
 
+// A coarse self-loop's weight is L_C: summed per graph when several graphs
+// run together, else into one total.
+__device__ __forceinline__ void add_self_loop(const AggArgs& a, int32_t C, unsigned long long w) {
+  if (a.cgid) atomic_add_u128(a.glsum + 2 * a.cgid[C], a.glsum + 2 * a.cgid[C] + 1, (u128)w);
+  else atomicAdd(a.lsum, w);
+}
+
 // Member position of virtual entry t of a community: the last p in [lo, hi)
 // with mpre[p] <= t.
 __device__ __forceinline__ int64_t member_of(const int64_t* __restrict__ mpre, int64_t lo, int64_t hi, int64_t t) {
@@ -599,7 +609,7 @@ __global__ void __launch_bounds__(256) agg_warp_k(AggArgs a, const int32_t* __re
         int64_t pos = vs + base + __popc(m & lanemask_lt());
         a.tcol[pos] = key;
         ((W2*)a.tw)[pos] = (W2)vals[t];
-        if (key == C) atomicAdd(a.lsum, vals[t]);
+        if (key == C) add_self_loop(a, C, vals[t]);
         keys[t] = kEmpty;
         vals[t] = 0;
       }
@@ -668,7 +678,7 @@ __global__ void __launch_bounds__(THREADS) agg_block_k(AggArgs a, const int32_t*
         int64_t pos = vs + base + before + __popc(m & lanemask_lt());
         a.tcol[pos] = key;
         ((W2*)a.tw)[pos] = (W2)vals[t];
-        if (key == C) atomicAdd(a.lsum, vals[t]);
+        if (key == C) add_self_loop(a, C, vals[t]);
         keys[t] = kEmpty;
         vals[t] = 0;
       }
@@ -772,7 +782,7 @@ __global__ void __launch_bounds__(256) agg_global_write_k(AggArgs a, const int32
       const int64_t pos = vs + wbase + __popc(m & lanemask_lt());
       a.tcol[pos] = D;
       ((W2*)a.tw)[pos] = (W2)a.gvals[base + t];
-      if (D == C) atomicAdd(a.lsum, a.gvals[base + t]);
+      if (D == C) add_self_loop(a, C, a.gvals[base + t]);
       a.gkeys[base + t] = kEmpty;
       a.gvals[base + t] = 0;
     }
@@ -919,6 +929,161 @@ template void agg_compact<int32_t>(const int64_t*, const int64_t*, const int64_t
                                    const int32_t*, const int32_t*, int32_t*, int32_t*, cudaStream_t);
 template void agg_compact<int64_t>(const int64_t*, const int64_t*, const int64_t*, const int64_t*, int64_t,
                                    const int32_t*, const int64_t*, int32_t*, int64_t*, cudaStream_t);
+
+// ----------------------------------------------------------- several graphs
+//
+// Vertices of one graph are contiguous, so the kT rows (or communities) of a
+// block span a contiguous range of graph ids: sums are gathered per graph in
+// shared memory (slot = graph - first graph of the block) and flushed with
+// one atomic per graph and block.
+
+__device__ __forceinline__ void flush_graph_sums(const unsigned long long* lo, const unsigned long long* hi, int g0,
+                                                 int ng, unsigned long long* out /* 2 per graph */) {
+  for (int t = threadIdx.x; t < ng; t += blockDim.x) {
+    u128 v = ((u128)hi[t] << 64) | (u128)lo[t];
+    if (v) atomic_add_u128(out + 2 * (g0 + t), out + 2 * (g0 + t) + 1, v);
+  }
+}
+
+// M of every graph: Mg[g] (lo, hi) += K[u] for u in g.
+__global__ void __launch_bounds__(kT) graph_totals_k(const long long* __restrict__ K, const int32_t* __restrict__ gid,
+                                                     int64_t n, unsigned long long* Mg) {
+  __shared__ unsigned long long lo[kT], hi[kT];
+  const int64_t v0 = (int64_t)blockIdx.x * kT;
+  if (v0 >= n) return;
+  const int64_t v1 = min(n, v0 + kT);
+  const int g0 = gid[v0], ng = gid[v1 - 1] - g0 + 1;
+  lo[threadIdx.x] = 0;
+  hi[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t u = v0 + threadIdx.x;
+  if (u < n) atomic_add_u128(&lo[gid[u] - g0], &hi[gid[u] - g0], (u128)(unsigned long long)K[u]);
+  __syncthreads();
+  flush_graph_sums(lo, hi, g0, ng, Mg);
+}
+
+void graph_totals(const long long* K, const int32_t* gid, int64_t n, unsigned long long* Mg, cudaStream_t s) {
+  if (n > 0) (count_launch(), graph_totals_k<<<(unsigned)((n + kT - 1) / kT), kT, 0, s>>>(K, gid, n, Mg));
+}
+
+// Per-graph modularity parts: L_g (lo, hi) over intra-community entries of
+// the graph's rows and SS_g (lo, hi) over its communities' Sigma^2.
+template <typename W>
+__global__ void __launch_bounds__(kT) graph_intra_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                                                    const W* __restrict__ wt, int64_t n, const int32_t* __restrict__ memb,
+                                                    const int32_t* __restrict__ gid, unsigned long long* Lg) {
+  __shared__ int64_t soff[kT + 1];
+  __shared__ unsigned long long lo[kT], hi[kT];
+  const int64_t v0 = (int64_t)blockIdx.x * kT;
+  const int nr = (int)min((int64_t)kT, n - v0);
+  for (int t = threadIdx.x; t <= nr; t += kT) soff[t] = off[v0 + t];
+  lo[threadIdx.x] = 0;
+  hi[threadIdx.x] = 0;
+  const int g0 = gid[v0], ng = gid[v0 + nr - 1] - g0 + 1;
+  __syncthreads();
+  for (int64_t x = soff[0] + threadIdx.x; x < soff[nr]; x += kT) {
+    int r = row_of(soff, nr, x);
+    if (memb[col[x]] == memb[v0 + r]) {
+      const int slot = gid[v0 + r] - g0;
+      atomic_add_u128(&lo[slot], &hi[slot], (u128)(unsigned long long)wt[x]);
+    }
+  }
+  __syncthreads();
+  flush_graph_sums(lo, hi, g0, ng, Lg);
+}
+
+__global__ void __launch_bounds__(kT) graph_squares_k(const long long* __restrict__ sig, const int32_t* __restrict__ gid,
+                                                      int64_t n, unsigned long long* SSg) {
+  __shared__ unsigned long long lo[kT], hi[kT];
+  const int64_t c0 = (int64_t)blockIdx.x * kT;
+  if (c0 >= n) return;
+  const int64_t c1 = min(n, c0 + kT);
+  const int g0 = gid[c0], ng = gid[c1 - 1] - g0 + 1;
+  lo[threadIdx.x] = 0;
+  hi[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t c = c0 + threadIdx.x;
+  if (c < n && sig[c]) {
+    const unsigned long long v = (unsigned long long)sig[c];
+    atomic_add_u128(&lo[gid[c] - g0], &hi[gid[c] - g0], (u128)v * (u128)v);
+  }
+  __syncthreads();
+  flush_graph_sums(lo, hi, g0, ng, SSg);
+}
+
+template <typename W>
+void graph_modularity_parts(const int64_t* off, const int32_t* col, const W* wt, int64_t n, const int32_t* memb,
+                            const long long* sig, const int32_t* gid, unsigned long long* Lg, unsigned long long* SSg,
+                            cudaStream_t s) {
+  if (n <= 0) return;
+  const unsigned nb = (unsigned)((n + kT - 1) / kT);
+  (count_launch(), graph_intra_k<W><<<nb, kT, 0, s>>>(off, col, wt, n, memb, gid, Lg));
+  (count_launch(), graph_squares_k<<<nb, kT, 0, s>>>(sig, gid, n, SSg));
+}
+template void graph_modularity_parts<int32_t>(const int64_t*, const int32_t*, const int32_t*, int64_t, const int32_t*,
+                                              const long long*, const int32_t*, unsigned long long*,
+                                              unsigned long long*, cudaStream_t);
+template void graph_modularity_parts<int64_t>(const int64_t*, const int32_t*, const int64_t*, int64_t, const int32_t*,
+                                              const long long*, const int32_t*, unsigned long long*,
+                                              unsigned long long*, cudaStream_t);
+
+void graph_squares(const long long* sig, const int32_t* gid, int64_t n, unsigned long long* SSg, cudaStream_t s) {
+  if (n > 0) (count_launch(), graph_squares_k<<<(unsigned)((n + kT - 1) / kT), kT, 0, s>>>(sig, gid, n, SSg));
+}
+
+// After renumbering: communities per graph (kcount[g] += used[c]) and the
+// graph of every coarse vertex (gid_next[newid[c]] = gid[c]).
+__global__ void graph_renumber_k(const int32_t* __restrict__ used, const int32_t* __restrict__ newid,
+                                 const int32_t* __restrict__ gid, int64_t n, int64_t* kcount, int32_t* gid_next) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+    if (used[c]) {
+      atomicAdd((unsigned long long*)(kcount + gid[c]), 1ull);
+      gid_next[newid[c]] = gid[c];
+    }
+}
+void graph_renumber(const int32_t* used, const int32_t* newid, const int32_t* gid, int64_t n, int64_t* kcount,
+                    int32_t* gid_next, cudaStream_t s) {
+  if (n > 0) (count_launch(), graph_renumber_k<<<grid1d(n), kT, 0, s>>>(used, newid, gid, n, kcount, gid_next));
+}
+
+// Final memberships as ids local to each graph.
+__global__ void localize_k(const int32_t* __restrict__ top, const int32_t* __restrict__ gid0,
+                           const int64_t* __restrict__ vo, int64_t n0, int32_t* out) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n0; v += (int64_t)gridDim.x * blockDim.x)
+    out[v] = (int32_t)(top[v] - vo[gid0[v]]);
+}
+void localize_membership(const int32_t* top, const int32_t* gid0, const int64_t* vo, int64_t n0, int32_t* out,
+                         cudaStream_t s) {
+  if (n0 > 0) (count_launch(), localize_k<<<grid1d(n0), kT, 0, s>>>(top, gid0, vo, n0, out));
+}
+
+// Graph of every input vertex from the graph vertex offsets, and a check that
+// no entry leaves its row's graph (flags |= 8).
+__global__ void graph_ids_k(const int64_t* __restrict__ vo, int G, int64_t n, int32_t* gid) {
+  for (int g = blockIdx.x; g < G; g += gridDim.x)
+    for (int64_t v = vo[g] + threadIdx.x; v < vo[g + 1]; v += blockDim.x) gid[v] = g;
+}
+__global__ void __launch_bounds__(kT) graph_check_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                                                    const int32_t* __restrict__ gid, int64_t n, int* flags) {
+  __shared__ int64_t soff[kT + 1];
+  const int64_t v0 = (int64_t)blockIdx.x * kT;
+  const int nr = (int)min((int64_t)kT, n - v0);
+  for (int t = threadIdx.x; t <= nr; t += kT) soff[t] = off[v0 + t];
+  __syncthreads();
+  int f = 0;
+  for (int64_t x = soff[0] + threadIdx.x; x < soff[nr]; x += kT) {
+    int r = row_of(soff, nr, x);
+    const int32_t v = col[x];
+    if (v < 0 || v >= n || gid[v] != gid[v0 + r]) f = 8;
+  }
+  if (f) atomicOr(flags, f);
+}
+void graph_ids(const int64_t* vo, int G, int64_t n, int32_t* gid, const int64_t* off, const int32_t* col, int* flags,
+               cudaStream_t s) {
+  if (G <= 0 || n <= 0) return;
+  (count_launch(), graph_ids_k<<<G < 65535 ? G : 65535, 256, 0, s>>>(vo, G, n, gid));
+  (count_launch(), graph_check_k<<<(unsigned)((n + kT - 1) / kT), kT, 0, s>>>(off, col, gid, n, flags));
+}
 
 // -------------------------------------------------------------- validation
 

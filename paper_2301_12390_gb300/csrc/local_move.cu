@@ -80,10 +80,11 @@ __device__ __forceinline__ void acc_flush(BlockAcc& b, DevCounters* ctr) {
 // needs gain = best - score_d > 0.
 template <typename W, bool WIDE, bool ASYNC>
 __device__ __forceinline__ bool commit_choice(const LMArgs<W>& a, BlockAcc& acc, int32_t i, int32_t d, long long Ki,
-                                              typename Arith<WIDE>::S best, int32_t c, unsigned long long kid) {
+                                              typename Arith<WIDE>::S best, int32_t c, unsigned long long kid,
+                                              long long M, int graph) {
   if (c < 0) return false;
   typedef typename Arith<WIDE>::S S;
-  const S g = best - Arith<WIDE>::score(a.M, (long long)kid, Ki, ld_sig<ASYNC>(a.sig + d) - Ki);
+  const S g = best - Arith<WIDE>::score(M, (long long)kid, Ki, ld_sig<ASYNC>(a.sig + d) - Ki);
   if (!(g > 0)) return false;
   if (a.guard && c > d && ld_size<ASYNC>(a.csize + d) == 1 && ld_size<ASYNC>(a.csize + c) == 1) return false;
   if (ASYNC) {
@@ -96,15 +97,49 @@ __device__ __forceinline__ bool commit_choice(const LMArgs<W>& a, BlockAcc& acc,
     unsigned long long pos = atomicAdd(&a.ctr->nmoves_list, 1ull);
     a.moves[pos] = make_int2(i, c);
   }
-  atomicAdd(&acc.moves, 1ull);
-  u128 gv = Arith<WIDE>::to_u128(g);
-  atomic_add_u128(&acc.s_lo, &acc.s_hi, gv);
+  u128 gv = Arith<WIDE>::to_u128(g);   // g > 0 here
+  if (a.gid) {
+    atomicAdd(a.g_moves + graph, 1ull);
+    atomic_add_u128(a.g_s + 2 * graph, a.g_s + 2 * graph + 1, gv);
+  } else {
+    atomicAdd(&acc.moves, 1ull);
+    atomic_add_u128(&acc.s_lo, &acc.s_hi, gv);
+  }
   return true;
 }
 
+// The graph of vertex i and its M; false if that graph has stopped
+// iterating in this pass.
 template <typename W>
-__device__ __forceinline__ bool is_active(const LMArgs<W>& a, int32_t i) {
-  return !a.prune || a.iter == 0 || a.stamp_r[i] == a.iter;
+__device__ __forceinline__ bool graph_of(const LMArgs<W>& a, int32_t i, long long* M, int* g) {
+  if (!a.gid) {
+    *M = a.M;
+    *g = 0;
+    return true;
+  }
+  const int gg = a.gid[i];
+  *g = gg;
+  if (!a.g_on[gg]) return false;
+  *M = a.Mg[gg];
+  return true;
+}
+
+// The iteration and its stamp buffers, read once at kernel start.
+struct IterView {
+  int iter;
+  const int32_t* sr;   // read: active in this iteration
+  int32_t* sw;         // write: active in the next one
+};
+
+template <typename W>
+__device__ __forceinline__ IterView iter_view(const LMArgs<W>& a) {
+  const int it = *a.d_iter;
+  return IterView{it, a.stamps[it & 1], a.stamps[(it + 1) & 1]};
+}
+
+template <typename W>
+__device__ __forceinline__ bool is_active(const LMArgs<W>& a, const IterView& iv, int32_t i) {
+  return !a.prune || iv.iter == 0 || iv.sr[i] == iv.iter;
 }
 
 // --------------------------------------------- bucket 0: thread per vertex
@@ -113,13 +148,17 @@ __device__ __forceinline__ bool is_active(const LMArgs<W>& a, int32_t i) {
 // gathered with all loads in flight; duplicates are then merged in registers.
 template <typename W, bool WIDE, bool ASYNC>
 __global__ void __launch_bounds__(256, 4) lm_thread(LMArgs<W> a, const int32_t* __restrict__ verts, int nverts) {
+  const IterView iv = iter_view(a);
   typedef typename Arith<WIDE>::S S;
   __shared__ BlockAcc acc;
   acc_init(acc);
   __syncthreads();
   for (int vi = blockIdx.x * blockDim.x + threadIdx.x; vi < nverts; vi += gridDim.x * blockDim.x) {
     int32_t i = verts[vi];
-    if (!is_active(a, i)) continue;
+    if (!is_active(a, iv, i)) continue;
+    long long M;
+    int graph;
+    if (!graph_of(a, i, &M, &graph)) continue;
     const int64_t b = a.off[i], e = a.off[i + 1];
     const int32_t d = a.memb[i];
     const long long Ki = a.K[i];
@@ -153,15 +192,15 @@ __global__ void __launch_bounds__(256, 4) lm_thread(LMArgs<W> a, const int32_t* 
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       if (cc[k] != kEmpty && cc[k] != d) {
-        S g = Arith<WIDE>::score(a.M, (long long)ww[k], Ki, sg[k]);
+        S g = Arith<WIDE>::score(M, (long long)ww[k], Ki, sg[k]);
         if (better(g, cc[k], bg, bc)) { bg = g; bc = cc[k]; }
       }
     }
     atomicAdd(&acc.edges, (unsigned long long)(e - b));
         atomicAdd(&acc.visited, 1ull);
-    if (commit_choice<W, WIDE, ASYNC>(a, acc, i, d, Ki, bg, bc, kid) && a.prune) {
-      a.stamp_w[i] = a.iter + 1;
-      for (int64_t x = b; x < e; ++x) a.stamp_w[a.col[x]] = a.iter + 1;
+    if (commit_choice<W, WIDE, ASYNC>(a, acc, i, d, Ki, bg, bc, kid, M, graph) && a.prune) {
+      iv.sw[i] = iv.iter + 1;
+      for (int64_t x = b; x < e; ++x) iv.sw[a.col[x]] = iv.iter + 1;
     }
   }
   __syncthreads();
@@ -174,6 +213,7 @@ __global__ void __launch_bounds__(256, 4) lm_thread(LMArgs<W> a, const int32_t* 
 // the bucket's largest degree), so their memory latencies overlap.
 template <typename W, bool WIDE, bool ASYNC, int CAP, int U>
 __global__ void __launch_bounds__(256, 4) lm_warp(LMArgs<W> a, const int32_t* __restrict__ verts, int nverts) {
+  const IterView iv = iter_view(a);
   typedef typename Arith<WIDE>::S S;
   constexpr int WPB = 8;
   __shared__ int32_t skeys[WPB][CAP];
@@ -188,7 +228,10 @@ __global__ void __launch_bounds__(256, 4) lm_warp(LMArgs<W> a, const int32_t* __
   bool ok = true;
   for (int vi = blockIdx.x * WPB + wib; vi < nverts; vi += gridDim.x * WPB) {
     int32_t i = verts[vi];
-    if (!is_active(a, i)) continue;
+    if (!is_active(a, iv, i)) continue;
+    long long M;
+    int graph;
+    if (!graph_of(a, i, &M, &graph)) continue;
     const int64_t b = a.off[i], e = a.off[i + 1];
     const int32_t d = a.memb[i];
     const long long Ki = a.K[i];
@@ -230,7 +273,7 @@ __global__ void __launch_bounds__(256, 4) lm_warp(LMArgs<W> a, const int32_t* __
         const int t = t0 + u * kWarp + lane;
         if (cs[u] != kEmpty) {
           if (cs[u] != d) {
-            S g = Arith<WIDE>::score(a.M, (long long)vs[u], Ki, sg[u]);
+            S g = Arith<WIDE>::score(M, (long long)vs[u], Ki, sg[u]);
             if (better(g, cs[u], bg, bc)) { bg = g; bc = cs[u]; }
           } else {
             kid = vs[u];
@@ -249,12 +292,12 @@ __global__ void __launch_bounds__(256, 4) lm_warp(LMArgs<W> a, const int32_t* __
     if (lane == 0) {
       atomicAdd(&acc.edges, (unsigned long long)(e - b));
         atomicAdd(&acc.visited, 1ull);
-      moved = commit_choice<W, WIDE, ASYNC>(a, acc, i, d, Ki, bg, bc, kid);
+      moved = commit_choice<W, WIDE, ASYNC>(a, acc, i, d, Ki, bg, bc, kid, M, graph);
     }
     moved = __shfl_sync(0xffffffffu, moved, 0);
     if (moved && a.prune) {
-      if (lane == 0) a.stamp_w[i] = a.iter + 1;
-      for (int64_t x = b + lane; x < e; x += kWarp) a.stamp_w[a.col[x]] = a.iter + 1;
+      if (lane == 0) iv.sw[i] = iv.iter + 1;
+      for (int64_t x = b + lane; x < e; x += kWarp) iv.sw[a.col[x]] = iv.iter + 1;
     }
     __syncwarp();
   }
@@ -267,6 +310,7 @@ __global__ void __launch_bounds__(256, 4) lm_warp(LMArgs<W> a, const int32_t* __
 
 template <typename W, bool WIDE, bool ASYNC, int CAP, int THREADS>
 __global__ void __launch_bounds__(THREADS) lm_block(LMArgs<W> a, const int32_t* __restrict__ verts, int nverts) {
+  const IterView iv = iter_view(a);
   typedef typename Arith<WIDE>::S S;
   constexpr int NW = THREADS / kWarp;
   constexpr int U = 4;
@@ -288,7 +332,10 @@ __global__ void __launch_bounds__(THREADS) lm_block(LMArgs<W> a, const int32_t* 
   bool ok = true;
   for (int vi = blockIdx.x; vi < nverts; vi += gridDim.x) {
     int32_t i = verts[vi];
-    if (!is_active(a, i)) continue;   // uniform across the block
+    if (!is_active(a, iv, i)) continue;   // uniform across the block
+    long long M;
+    int graph;
+    if (!graph_of(a, i, &M, &graph)) continue;
     const int64_t b = a.off[i], e = a.off[i + 1];
     const int32_t d = a.memb[i];
     const long long Ki = a.K[i];
@@ -340,7 +387,7 @@ __global__ void __launch_bounds__(THREADS) lm_block(LMArgs<W> a, const int32_t* 
       for (int u = 0; u < U; ++u) {
         if (hs[u] < 0) continue;
         if (cs[u] != d) {
-          S g = Arith<WIDE>::score(a.M, (long long)vals[hs[u]], Ki, sg[u]);
+          S g = Arith<WIDE>::score(M, (long long)vals[hs[u]], Ki, sg[u]);
           if (better(g, cs[u], bg, bc)) { bg = g; bc = cs[u]; }
         } else {
           s_kid = vals[hs[u]];
@@ -359,15 +406,15 @@ __global__ void __launch_bounds__(THREADS) lm_block(LMArgs<W> a, const int32_t* 
       if (lane == 0) {
         atomicAdd(&acc.edges, (unsigned long long)(e - b));
         atomicAdd(&acc.visited, 1ull);
-        s_moved = commit_choice<W, WIDE, ASYNC>(a, acc, i, d, Ki, bg, bc, s_kid);
+        s_moved = commit_choice<W, WIDE, ASYNC>(a, acc, i, d, Ki, bg, bc, s_kid, M, graph);
         s_nt = 0;
         s_kid = 0;
       }
     }
     __syncthreads();
     if (s_moved && a.prune) {
-      if (threadIdx.x == 0) a.stamp_w[i] = a.iter + 1;
-      for (int64_t x = b + threadIdx.x; x < e; x += THREADS) a.stamp_w[a.col[x]] = a.iter + 1;
+      if (threadIdx.x == 0) iv.sw[i] = iv.iter + 1;
+      for (int64_t x = b + threadIdx.x; x < e; x += THREADS) iv.sw[a.col[x]] = iv.iter + 1;
     }
   }
   if (!ok) atomicOr(&acc.error, kErrProbe);
@@ -402,13 +449,19 @@ __device__ __forceinline__ int find_item(const int64_t* __restrict__ pre, int ni
 template <typename W, bool ASYNC>
 __global__ void __launch_bounds__(256) lm_hub_insert(LMArgs<W> a, const int32_t* __restrict__ hubs, int nhubs,
                                                      const int64_t* __restrict__ chunk_pre) {
+  const IterView iv = iter_view(a);
   constexpr int CAP = 2 * kHubChunk;
   extern __shared__ unsigned long long hdyn[];
   unsigned long long* svals = hdyn;
   int32_t* skeys = (int32_t*)(hdyn + CAP);
   const int h = find_item(chunk_pre, nhubs, blockIdx.x);
   const int32_t i = hubs[h];
-  if (!is_active(a, i)) return;   // uniform across the block
+  if (!is_active(a, iv, i)) return;   // uniform across the block
+  {
+    long long M;
+    int graph;
+    if (!graph_of(a, i, &M, &graph)) return;
+  }
   const int64_t q = (int64_t)blockIdx.x - (chunk_pre[h] - chunk_pre[0]);
   for (int t = threadIdx.x; t < CAP; t += blockDim.x) { skeys[t] = kEmpty; svals[t] = 0; }
   __syncthreads();
@@ -448,6 +501,7 @@ __global__ void __launch_bounds__(256) lm_hub_insert(LMArgs<W> a, const int32_t*
 
 template <typename W, bool WIDE, bool ASYNC>
 __global__ void __launch_bounds__(256) lm_hub_scan(LMArgs<W> a, const int32_t* __restrict__ hubs, int nhubs) {
+  const IterView iv = iter_view(a);
   typedef typename Arith<WIDE>::S S;
   constexpr int NW = 256 / kWarp;
   __shared__ S red_g[NW];
@@ -455,7 +509,10 @@ __global__ void __launch_bounds__(256) lm_hub_scan(LMArgs<W> a, const int32_t* _
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int h = find_item(a.spre, nhubs, blockIdx.x);
   const int32_t i = hubs[h];
-  if (!is_active(a, i)) return;   // uniform across the block
+  if (!is_active(a, iv, i)) return;   // uniform across the block
+  long long M;
+  int graph;
+  if (!graph_of(a, i, &M, &graph)) return;
   const int64_t q = (int64_t)blockIdx.x - (a.spre[h] - a.spre[0]);
   const int64_t b = a.off[i], e = a.off[i + 1];
   const int64_t cap = 2 * (e - b);
@@ -483,7 +540,7 @@ __global__ void __launch_bounds__(256) lm_hub_scan(LMArgs<W> a, const int32_t* _
       if (cs[u] == kEmpty) continue;
       const int64_t t = y + u * 256 + threadIdx.x;
       if (cs[u] != d) {
-        S g = Arith<WIDE>::score(a.M, (long long)vs[u], Ki, sg[u]);
+        S g = Arith<WIDE>::score(M, (long long)vs[u], Ki, sg[u]);
         if (better(g, cs[u], bg, bc)) { bg = g; bc = cs[u]; }
       } else {
         a.hkid[h] = vs[u];   // K_{i->d}; only one slot holds d
@@ -511,6 +568,7 @@ __global__ void __launch_bounds__(256) lm_hub_scan(LMArgs<W> a, const int32_t* _
 
 template <typename W, bool WIDE, bool ASYNC>
 __global__ void __launch_bounds__(256) lm_hub_final(LMArgs<W> a, const int32_t* __restrict__ hubs, int nhubs) {
+  const IterView iv = iter_view(a);
   typedef typename Arith<WIDE>::S S;
   __shared__ BlockAcc acc;
   __shared__ int s_moved;
@@ -519,7 +577,10 @@ __global__ void __launch_bounds__(256) lm_hub_final(LMArgs<W> a, const int32_t* 
   __syncthreads();
   for (int h = blockIdx.x; h < nhubs; h += gridDim.x) {
     const int32_t i = hubs[h];
-    if (!is_active(a, i)) continue;
+    if (!is_active(a, iv, i)) continue;
+    long long M;
+    int graph;
+    if (!graph_of(a, i, &M, &graph)) continue;
     const int64_t b = a.off[i], e = a.off[i + 1];
     if (wid == 0) {
       S bg = Arith<WIDE>::lowest();
@@ -533,14 +594,14 @@ __global__ void __launch_bounds__(256) lm_hub_final(LMArgs<W> a, const int32_t* 
       if (lane == 0) {
         atomicAdd(&acc.edges, (unsigned long long)(e - b));
         atomicAdd(&acc.visited, 1ull);
-        s_moved = commit_choice<W, WIDE, ASYNC>(a, acc, i, a.memb[i], a.K[i], bg, bc, a.hkid[h]);
+        s_moved = commit_choice<W, WIDE, ASYNC>(a, acc, i, a.memb[i], a.K[i], bg, bc, a.hkid[h], M, graph);
         a.hkid[h] = 0;
       }
     }
     __syncthreads();
     if (s_moved && a.prune) {
-      if (threadIdx.x == 0) a.stamp_w[i] = a.iter + 1;
-      for (int64_t x = b + threadIdx.x; x < e; x += 256) a.stamp_w[a.col[x]] = a.iter + 1;
+      if (threadIdx.x == 0) iv.sw[i] = iv.iter + 1;
+      for (int64_t x = b + threadIdx.x; x < e; x += 256) iv.sw[a.col[x]] = iv.iter + 1;
     }
     __syncthreads();
   }

@@ -38,7 +38,7 @@ class Options(ctypes.Structure):
                 ("pass_tolerance", ctypes.c_double), ("max_iterations", ctypes.c_int32),
                 ("max_passes", ctypes.c_int32), ("prune", ctypes.c_int32), ("singleton_guard", ctypes.c_int32),
                 ("subrounds", ctypes.c_int32), ("validate", ctypes.c_int32), ("record_levels", ctypes.c_int32),
-                ("reserved_i", ctypes.c_int32 * 5), ("reserved_d", ctypes.c_double * 4)]
+                ("cuda_graphs", ctypes.c_int32), ("reserved_i", ctypes.c_int32 * 4), ("reserved_d", ctypes.c_double * 4)]
 
 
 class Stats(ctypes.Structure):
@@ -74,6 +74,11 @@ SIGNATURES = [
                                   ctypes.POINTER(_U64), ctypes.POINTER(_I64)]),
     ("louvain_modularity_static", _I32, [_I64, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(_I64), ctypes.POINTER(_U64), ctypes.POINTER(_I64)]),
+    ("louvain_load_batch", _I32, [_VP, _I64, _VP, _I64, _I64, _VP, _VP, _VP, _I32]),
+    ("louvain_get_num_graphs", _I32, [_VP, ctypes.POINTER(_I64)]),
+    ("louvain_batch_get_modularity", _I32, [_VP, _VP, _VP, _VP, _VP]),
+    ("louvain_batch_get_graph_info", _I32, [_VP, _I64, _VP]),
+    ("louvain_batch_get_iterations", _I32, [_VP, _I64, _VP, _I64, ctypes.POINTER(_I64)]),
     ("louvain_get_stats", _I32, [_VP, ctypes.POINTER(Stats)]),
     ("louvain_get_pass_info", _I32, [_VP, _I32, ctypes.POINTER(PassInfo)]),
     ("louvain_get_iteration", _I32, [_VP, _I64, _VP]),
@@ -202,6 +207,51 @@ class Louvain:
                                               PTR_DEVICE if dev else PTR_HOST))
         self._keep = None
         self.n = n
+
+    def load_batch(self, graph_offsets, off, col, w):
+        """Load graphs g = 0..G-1 owning vertices [graph_offsets[g], graph_offsets[g+1]) of one CSR."""
+        dev = _is_device(off)
+        if not dev:
+            off = np.ascontiguousarray(off, dtype=np.int64)
+            col = np.ascontiguousarray(col, dtype=np.int32)
+            w = np.ascontiguousarray(w, dtype=np.int32)
+            graph_offsets = np.ascontiguousarray(graph_offsets, dtype=np.int64)
+        n = len(off) - 1
+        G = len(graph_offsets) - 1
+        self._keep = (graph_offsets, off, col, w)
+        self._check(self.lib.louvain_load_batch(self.h, G, _ptr(graph_offsets), n, len(col), _ptr(off), _ptr(col),
+                                                _ptr(w), PTR_DEVICE if dev else PTR_HOST))
+        self._keep = None
+        self.n = n
+        self.G = G
+
+    def num_graphs(self) -> int:
+        g = ctypes.c_int64()
+        self._check(self.lib.louvain_get_num_graphs(self.h, ctypes.byref(g)))
+        return g.value
+
+    def batch_modularity(self):
+        """(q[G] float64, exact numerators [G] python ints, M[G])."""
+        G = self.num_graphs()
+        q = np.empty(G, np.float64)
+        hi = np.empty(G, np.int64)
+        lo = np.empty(G, np.uint64)
+        M = np.empty(G, np.int64)
+        self._check(self.lib.louvain_batch_get_modularity(self.h, q.ctypes.data, hi.ctypes.data, lo.ctypes.data,
+                                                          M.ctypes.data))
+        return q, [_i128(a, b) for a, b in zip(hi.tolist(), lo.tolist())], M
+
+    def batch_graph_info(self, g: int):
+        out = np.zeros(4, np.int64)
+        self._check(self.lib.louvain_batch_get_graph_info(self.h, g, out.ctypes.data))
+        return {"passes": int(out[0]), "iterations": int(out[1]), "communities": int(out[2]), "moves": int(out[3])}
+
+    def batch_iterations(self, g: int):
+        cnt = ctypes.c_int64()
+        self._check(self.lib.louvain_batch_get_iterations(self.h, g, None, 0, ctypes.byref(cnt)))
+        buf = np.zeros(4 * max(cnt.value, 1), np.int64)
+        self._check(self.lib.louvain_batch_get_iterations(self.h, g, buf.ctypes.data, cnt.value, ctypes.byref(cnt)))
+        return [(int(buf[4 * t]), int(buf[4 * t + 1]), _i128(buf[4 * t + 2], buf[4 * t + 3])) for t in range(cnt.value)]
 
     def run(self):
         self._check(self.lib.louvain_run(self.h))

@@ -1,0 +1,88 @@
+"""Several graphs in one run (louvain_load_batch) give, per graph, exactly
+what each graph gives alone: synchronous mode bit-exact against the plain
+engine run of the graph and against the oracle; asynchronous mode within 0.01
+of the oracle per graph."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from paper_2301_12390_gb300 import Louvain
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _engine():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def batch_graphs():
+    gs = []
+    for (seed, n, k, p_in, p_out) in gg.batch_sbm_specs(0x5EED, 24, nmin=64, nmax=3000, kmin=2, kmax=20,
+                                                       pin_lo=0.05, pin_hi=0.25, p_out=0.01):
+        gs.append(gg.sbm(seed, n, k, p_in, p_out, wmin=1, wmax=5))
+    gs.insert(3, gg.from_weighted_edges(5, []))                      # no edges
+    gs.insert(7, gg.from_weighted_edges(1, [(0, 0, 3)]))             # one vertex, a self-loop
+    gs.insert(11, gg.rmat(77, 13, 16, wmin=1, wmax=8))                # heavy-tailed, hubs
+    gs.insert(15, gg.grid_road(78, 40))                               # low degree, many passes
+    return gs
+
+
+GS = batch_graphs()
+
+
+def run_batch(gs, **opt):
+    big, vo = gg.concat(gs)
+    with Louvain(device=0, **opt) as lv:
+        lv.load_batch(vo, big.off, big.col, big.w)
+        lv.run()
+        memb = lv.membership()
+        q, nums, Ms = lv.batch_modularity()
+        iters = [lv.batch_iterations(g) for g in range(len(gs))]
+    return [memb[vo[g]:vo[g + 1]] for g in range(len(gs))], q, nums, Ms, iters
+
+
+def run_alone(g, **opt):
+    with Louvain(device=0, **opt) as lv:
+        lv.load_csr(g.off, g.col, g.w)
+        lv.run()
+        return lv.membership(), lv.modularity(), lv.modularity_exact(), lv.iterations()
+
+
+@pytest.mark.parametrize("prune,subrounds", [(0, 1), (1, 1), (1, 4)])
+def test_sync_batch_equals_each_graph_alone(prune, subrounds):
+    membs, q, nums, Ms, iters = run_batch(GS, mode=0, prune=prune, subrounds=subrounds)
+    for g, graph in enumerate(GS):
+        m1, q1, (num1, M1), it1 = run_alone(graph, mode=0, prune=prune, subrounds=subrounds)
+        assert np.array_equal(membs[g], m1), g
+        assert (nums[g], Ms[g]) == (num1, M1) and q[g] == q1, g
+        assert iters[g] == it1, g
+        ref = oracle.louvain(graph.off, graph.col, graph.w, mode=oracle.SYNC, prune=prune, subrounds=subrounds)
+        assert np.array_equal(membs[g], ref.top) and nums[g] == ref.q_num, g
+
+
+def test_async_batch_quality_per_graph():
+    membs, q, nums, Ms, iters = run_batch(GS, mode=1, prune=1)
+    for g, graph in enumerate(GS):
+        ref = oracle.louvain(graph.off, graph.col, graph.w, mode=oracle.ASYNC, prune=1)
+        assert q[g] >= ref.Q - 0.01, (g, q[g], ref.Q)
+        _, num, M = oracle.modularity(graph.off, graph.col, graph.w, membs[g])
+        assert (num, M) == (nums[g], Ms[g]), g
+
+
+def test_batch_rejects_entries_between_graphs():
+    from paper_2301_12390_gb300 import LouvainError
+    a, b = gg.sbm(1, 50, 2, 0.3, 0.05), gg.sbm(2, 60, 2, 0.3, 0.05)
+    big, vo = gg.concat([a, b])
+    with Louvain(device=0) as lv:
+        with pytest.raises(LouvainError) as e:
+            lv.load_batch(np.array([0, 40, big.n]), big.off, big.col, big.w)   # cuts graph a in two
+        assert e.value.code == -3
+        lv.load_batch(vo, big.off, big.col, big.w)
+        lv.run()
+        assert lv.num_graphs() == 2

@@ -81,6 +81,14 @@ def test_sync_parity_subrounds(name, subrounds):
     assert_sync_parity(G[name], prune=1, subrounds=subrounds)
 
 
+@pytest.mark.parametrize("name", ["road128", "sbm8192"])
+@pytest.mark.parametrize("graphs", [0, 1])
+def test_sync_parity_with_and_without_cuda_graphs(name, graphs):
+    """From the third iteration of a pass the engine replays a captured CUDA
+    graph; the result must not depend on it."""
+    assert_sync_parity(G[name], prune=1, subrounds=4, cuda_graphs=graphs)
+
+
 @pytest.mark.parametrize("name", ["sbm600", "rmat14"])
 def test_sync_parity_plain_jacobi(name):
     assert_sync_parity(G[name], singleton_guard=0)
