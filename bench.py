@@ -304,13 +304,216 @@ def bench_ours(args):
         pg.destroy_process_group()
 
 
+def bench_batched(args):
+    """Many small graphs: one batched run vs the same graphs one at a time.
+
+    Workload: args.batch_graphs planted-partition SBMs, n log-uniform in
+    [256, 16384], 4-64 blocks, p_in uniform in [0.05, 0.2], p_out 1e-3,
+    weight 1, packed as one block-diagonal CSR.  Both arms start from inputs
+    resident on the device and include load (validation, degrees), run and
+    membership read-back (device to device) per request.
+    """
+    import torch
+    from paper_2301_12390_gb300 import Louvain, SYNC, ASYNC
+    world, rank, local, pg = dist_setup()
+    device = local
+    torch.cuda.set_device(device)
+    mode = ASYNC if args.mode == "async" else SYNC
+    specs = gg.batch_sbm_specs(SEED + 3, args.batch_graphs)
+    big, vo = gg.sbm_batch(specs)
+    G = len(specs)
+    dev = f"cuda:{device}"
+    d_off = torch.from_numpy(big.off).to(dev)
+    d_col = torch.from_numpy(big.col).to(dev)
+    d_w = torch.from_numpy(big.w).to(dev)
+    d_vo = torch.from_numpy(vo).to(dev)
+    # per-graph device CSRs for the one-at-a-time arm
+    parts = []
+    for g in range(G):
+        v0, v1 = int(vo[g]), int(vo[g + 1])
+        e0, e1 = int(big.off[v0]), int(big.off[v1])
+        parts.append((d_off[v0:v1 + 1] - e0, d_col[e0:e1] - v0, d_w[e0:e1]))
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream(device=device)
+    opts = dict(mode=mode, prune=1, validate=1)
+    # one at a time
+    lv = Louvain(device=device, stream=stream.cuda_stream, **opts)
+    biggest = int(np.argmax(np.diff(big.off[vo])))
+    for _ in range(args.warmup):
+        lv.load_csr(*parts[biggest])
+        lv.run()
+    out_memb = torch.empty(int(big.n), dtype=torch.int32, device=dev)
+    lat = np.empty(G)
+    q_plain = np.empty(G)
+    t_all = time.perf_counter()
+    for g in range(G):
+        t0 = time.perf_counter()
+        lv.load_csr(*parts[g])
+        lv.run()
+        lv.membership(out_memb[int(vo[g]):int(vo[g + 1])])
+        lat[g] = time.perf_counter() - t0
+        q_plain[g] = lv.modularity()
+    plain_s = time.perf_counter() - t_all
+    lv.close()
+    # batched
+    lb = Louvain(device=device, stream=stream.cuda_stream, **opts)
+    for _ in range(args.warmup):
+        lb.load_batch(d_vo, d_off, d_col, d_w)
+        lb.run()
+    clocks = Clocks(device)
+    clocks.start()
+    time.sleep(0.3)
+    blat = []
+    lm_edges = 0
+    lm_ms = 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        lb.load_batch(d_vo, d_off, d_col, d_w)
+        lb.run()
+        lb.membership(out_memb)
+        blat.append(time.perf_counter() - t0)
+        st = lb.stats()
+        lm_edges += st.lm_edges
+        lm_ms += st.lm_ms
+    ck = clocks.stop()
+    q_batch, _, _ = lb.batch_modularity()
+    launches = lb.stats().kernel_launches
+    lb.close()
+    batch_s = float(np.median(blat))
+    value = G / batch_s
+    if rank == 0:
+        line = {
+            "metric": "graphs/sec batched vs plain, at equal Q", "value": value, "unit": "graphs/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * batch_s,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": "batched", "graphs": G, "n": int(big.n), "nnz": int(big.nnz), "mode": args.mode,
+                       "description": "SBM graphs, n log-uniform 256-16384, 4-64 blocks, p_in 0.05-0.2, "
+                                      "p_out 1e-3, weight 1, one block-diagonal CSR; each request = load "
+                                      "(validated) + run + membership, inputs resident on the device"},
+            "plain": {"graphs_per_s": G / plain_s, "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
+                      "latency_ms_p99": 1e3 * float(np.percentile(lat, 99)), "total_s": plain_s,
+                      "mean_q": float(q_plain.mean())},
+            "batched": {"graphs_per_s": value, "latency_ms_p50": 1e3 * float(np.percentile(blat, 50)),
+                        "latency_ms_p99": 1e3 * float(np.percentile(blat, 99)), "mean_q": float(q_batch.mean()),
+                        "lm_edges_per_s": lm_edges / (lm_ms / 1e3) if lm_ms else None},
+            "speedup_vs_plain": value / (G / plain_s),
+            "q_batched_minus_plain": {"mean": float((q_batch - q_plain).mean()),
+                                      "min": float((q_batch - q_plain).min())},
+            "clocks": ck, "gpu_launches": launches * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def serving_pool(seed: int, count: int, nmin: int, nmax: int):
+    """Request graphs: half planted-partition SBM, half R-MAT; n log-uniform in
+    [nmin, nmax], average degree uniform in [8, 32], weights uniform in 1..8."""
+    import math
+    pool = []
+    for i in range(count):
+        n = int(round(math.exp(math.log(nmin) + (math.log(nmax) - math.log(nmin)) * gg.uniform(seed, 30, i))))
+        d = 8 + 24 * gg.uniform(seed, 31, i)
+        if i % 2 == 0:
+            k = max(2, n // 512)
+            p_in = min(1.0, 0.8 * d / max(1.0, n / k))
+            p_out = 0.2 * d / n
+            pool.append(gg.sbm(seed * 7919 + i, n, k, p_in, p_out, wmin=1, wmax=8))
+        else:
+            scale = max(1, (n - 1).bit_length())
+            pool.append(gg.rmat(seed * 7919 + i, scale, d / 2, wmin=1, wmax=8, n=n))
+    return pool
+
+
+def bench_serving(args):
+    """A Poisson stream of requests served two ways: one request per run on one
+    slot (serial plain runs) and the continuous-batching server."""
+    import torch
+    from paper_2301_12390_gb300 import Louvain, Server, SYNC, ASYNC
+    torch.cuda.set_device(0)
+    mode = ASYNC if args.mode == "async" else SYNC
+    pool = serving_pool(SEED + 4, args.pool, args.serve_nmin, args.serve_nmax)
+    R = args.requests
+    pick = [int(gg.uniform(SEED + 4, 32, r) * len(pool)) for r in range(R)]
+    # serial capacity: each pool graph alone through the C ABI (host inputs)
+    lv = Louvain(device=0, mode=mode, prune=1)
+    lv.load_csr(pool[0].off, pool[0].col, pool[0].w)
+    lv.run()
+    svc = []
+    for g in pool:
+        t0 = time.perf_counter()
+        lv.load_csr(g.off, g.col, g.w)
+        lv.run()
+        lv.membership()
+        svc.append(time.perf_counter() - t0)
+    lv.close()
+    mean_svc = float(np.mean([svc[p] for p in pick]))
+    rate = args.rate_factor / mean_svc           # requests per second
+    gaps = [-np.log(1.0 - gg.uniform(SEED + 4, 33, r)) / rate for r in range(R)]
+    arrivals = np.cumsum(gaps)
+
+    def run_arm(**cfg):
+        results = {}
+        with Server(device=0, mode=mode, prune=1, **cfg) as srv:
+            t0 = time.perf_counter()
+            for r in range(R):
+                while time.perf_counter() - t0 < arrivals[r]:
+                    for x in srv.poll():
+                        results[x["id"]] = x
+                    time.sleep(0.0002)
+                g = pool[pick[r]]
+                srv.submit(r, g.off, g.col, g.w)
+            while len(results) < R:
+                for x in srv.poll(wait_ms=100):
+                    results[x["id"]] = x
+            st = srv.stats()
+        lat = np.array([results[r]["done_s"] - results[r]["submit_s"] for r in range(R)])
+        span = max(results[r]["done_s"] for r in range(R)) - min(results[r]["submit_s"] for r in range(R))
+        q = np.array([results[r]["q"] for r in range(R)])
+        ok = all(results[r]["status"] == 0 for r in range(R))
+        return {"graphs_per_s": R / span, "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
+                "latency_ms_p99": 1e3 * float(np.percentile(lat, 99)), "makespan_s": span, "runs": st["runs"],
+                "mean_q": float(q.mean()), "all_ok": ok, "peak_reserved_gb": st["peak_reserved_bytes"] / 1e9}, q
+
+    clocks = Clocks(0)
+    plain, q_plain = run_arm(slots=1, batch_max_entries=0)
+    clocks.start()
+    served, q_served = run_arm(slots=args.slots)
+    ck = clocks.stop()
+    line = {
+        "metric": "graphs/sec (p50/p99 latency) served with continuous batching vs serial plain runs, at equal Q",
+        "value": served["graphs_per_s"], "unit": "graphs/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": 1e3 * served["makespan_s"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "serving", "requests": R, "pool_graphs": len(pool), "mode": args.mode,
+                   "arrival_rate_per_s": rate, "rate_factor_of_serial_capacity": args.rate_factor,
+                   "description": f"Poisson arrivals; each request a graph drawn from {len(pool)} seeded graphs, "
+                                  f"half SBM half R-MAT, n log-uniform {args.serve_nmin}-{args.serve_nmax}, "
+                                  "average degree 8-32, weights 1..8; host CSR in, membership out",
+                   "pool_nnz_mean": float(np.mean([g.nnz for g in pool]))},
+        "served": served, "plain_serial": plain,
+        "speedup_vs_plain": served["graphs_per_s"] / plain["graphs_per_s"],
+        "q_served_minus_plain": {"mean": float((q_served - q_plain).mean()), "min": float((q_served - q_plain).min())},
+        "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS) + ["batched", "serving"])
+    ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--requests", type=int, default=1000)
+    ap.add_argument("--pool", type=int, default=64)
+    ap.add_argument("--serve-nmin", type=int, default=1000)
+    ap.add_argument("--serve-nmax", type=int, default=2_000_000)
+    ap.add_argument("--rate-factor", type=float, default=3.0)
+    ap.add_argument("--slots", type=int, default=2)
     ap.add_argument("--mode", default="async", choices=["async", "sync"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -318,6 +521,10 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         bench_reference(args)
+    elif args.workload == "batched":
+        bench_batched(args)
+    elif args.workload == "serving":
+        bench_serving(args)
     else:
         bench_ours(args)
 

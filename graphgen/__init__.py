@@ -54,6 +54,9 @@ def _load():
         lib.gg_grid_road.argtypes = [u64, i64, dbl, dbl, i32, i32, P]
         lib.gg_from_edges.argtypes = [i64, i64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, u64, i32, i32, P]
         lib.gg_free.argtypes = [P]
+        lib.gg_sbm_batch.argtypes = [i64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, i32, i32, P, ctypes.c_void_p]
+        lib.gg_sbm_batch.restype = ctypes.c_int
         lib.gg_uniform.argtypes = [u64, u64, u64]
         lib.gg_uniform.restype = dbl
         for f in (lib.gg_sbm, lib.gg_rmat, lib.gg_grid_road, lib.gg_from_edges):
@@ -178,6 +181,34 @@ def batch_sbm_specs(seed: int, count: int, nmin: int = 256, nmax: int = 16384, k
         p_in = pin_lo + (pin_hi - pin_lo) * uniform(seed, 22, g)
         specs.append((seed * 1000003 + g, n, k, p_in, p_out))
     return specs
+
+
+def sbm_batch(specs, wmin: int = 1, wmax: int = 1) -> Tuple[CSR, np.ndarray]:
+    """Build many SBM graphs (specs from batch_sbm_specs) on all host cores and pack them into one
+    block-diagonal CSR; returns it with the per-graph vertex offsets (int64, len(specs) + 1).
+    The graphs are identical to sbm(*spec) one by one."""
+    lib = _load()
+    cnt = len(specs)
+    seed = np.array([s[0] for s in specs], np.uint64)
+    n = np.array([s[1] for s in specs], np.int64)
+    k = np.array([s[2] for s in specs], np.int64)
+    pin = np.array([s[3] for s in specs], np.float64)
+    pout = np.array([s[4] for s in specs], np.float64)
+    vo = np.zeros(cnt + 1, np.int64)
+    c = _CSR()
+    _check(lib.gg_sbm_batch(cnt, seed.ctypes.data, n.ctypes.data, k.ctypes.data, pin.ctypes.data, pout.ctypes.data,
+                            wmin, wmax, ctypes.byref(c), vo.ctypes.data), "sbm_batch")
+    return _take(c, lib), vo
+
+
+def split(big: CSR, vo: np.ndarray) -> List[CSR]:
+    """The graphs of a block-diagonal CSR, each with its own ids."""
+    out = []
+    for g in range(len(vo) - 1):
+        v0, v1 = int(vo[g]), int(vo[g + 1])
+        e0, e1 = int(big.off[v0]), int(big.off[v1])
+        out.append(CSR(v1 - v0, big.off[v0:v1 + 1] - e0, big.col[e0:e1] - v0, big.w[e0:e1]))
+    return out
 
 
 def concat(graphs: Sequence[CSR]) -> Tuple[CSR, np.ndarray]:

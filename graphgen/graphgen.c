@@ -95,12 +95,15 @@ static int gg_threads(void) {
   return (int)t;
 }
 
+/* Set in worker threads of gg_sbm_batch: their builds run serially. */
+static __thread int gg_in_worker = 0;
+
 /* Split [0, total) into `nt` contiguous chunks, chunk i to thread i. */
 static void parallel_for(int nt, int64_t total, range_fn fn, void *ctx) {
   pthread_t th[64];
   range_job jobs[64];
   int ok[64];
-  if (total < 65536 || nt < 1) nt = 1;
+  if (total < 65536 || nt < 1 || gg_in_worker) nt = 1;
   if (nt > 64) nt = 64;
   for (int i = 0; i < nt; ++i) {
     jobs[i].fn = fn; jobs[i].ctx = ctx; jobs[i].tid = i;
@@ -151,7 +154,7 @@ static void rdx_scatter(void *c, int64_t lo, int64_t hi, int tid) {
 
 static int radix_sort_u64(uint64_t *a, int64_t E, int bits) {
   int nt = gg_threads();
-  if (E < 65536) nt = 1;
+  if (E < 65536 || gg_in_worker) nt = 1;
   uint64_t *t = (uint64_t *)malloc((size_t)(E ? E : 1) * 8);
   int64_t(*h)[RDX] = (int64_t(*)[RDX])malloc((size_t)nt * RDX * 8);
   if (!t || !h) { free(t); free(h); return -1; }
@@ -423,3 +426,93 @@ oom:
  * generators (log-uniform sizes, Poisson arrivals) so they share the stream. */
 double gg_uniform(uint64_t seed, uint64_t stream, uint64_t i) { return u01(rnd(stream_key(seed, stream), i)); }
 double gg_logn(double x) { return gg_log(x); }
+
+/* Many SBM graphs at once, built on a pool of threads (one graph per task),
+ * then packed into one block-diagonal CSR: graph g owns vertices
+ * [vo[g], vo[g+1]).  Specs per graph: seed, n, k, p_in, p_out. */
+typedef struct {
+  int64_t count;
+  const uint64_t *seed;
+  const int64_t *n, *k;
+  const double *p_in, *p_out;
+  int32_t wmin, wmax;
+  gg_csr *parts;
+  int64_t next;
+  pthread_mutex_t mu;
+  int failed;
+} batch_job;
+
+static void *batch_worker(void *p) {
+  batch_job *b = (batch_job *)p;
+  gg_in_worker = 1;
+  for (;;) {
+    pthread_mutex_lock(&b->mu);
+    int64_t g = b->next++;
+    pthread_mutex_unlock(&b->mu);
+    if (g >= b->count) break;
+    if (gg_sbm(b->seed[g], b->n[g], b->k[g], b->p_in[g], b->p_out[g], b->wmin, b->wmax, &b->parts[g])) {
+      pthread_mutex_lock(&b->mu);
+      b->failed = 1;
+      pthread_mutex_unlock(&b->mu);
+    }
+  }
+  return NULL;
+}
+
+int gg_sbm_batch(int64_t count, const uint64_t *seed, const int64_t *n, const int64_t *k, const double *p_in,
+                 const double *p_out, int32_t wmin, int32_t wmax, gg_csr *out, int64_t *vo) {
+  memset(out, 0, sizeof(*out));
+  batch_job b;
+  memset(&b, 0, sizeof(b));
+  b.count = count; b.seed = seed; b.n = n; b.k = k; b.p_in = p_in; b.p_out = p_out;
+  b.wmin = wmin; b.wmax = wmax;
+  b.parts = (gg_csr *)calloc((size_t)(count ? count : 1), sizeof(gg_csr));
+  if (!b.parts) return -1;
+  pthread_mutex_init(&b.mu, NULL);
+  int nt = gg_threads();
+  pthread_t th[64];
+  int ok[64];
+  for (int i = 0; i < nt; ++i) ok[i] = pthread_create(&th[i], NULL, batch_worker, &b) == 0;
+  for (int i = 0; i < nt; ++i)
+    if (ok[i]) pthread_join(th[i], NULL);
+  batch_worker(&b); /* finishes whatever threads could not be started */
+  pthread_mutex_destroy(&b.mu);
+  int rc = b.failed ? -1 : 0;
+  int64_t N = 0, E = 0;
+  vo[0] = 0;
+  for (int64_t g = 0; g < count && !rc; ++g) {
+    N += b.parts[g].n;
+    E += b.parts[g].nnz;
+    vo[g + 1] = N;
+  }
+  if (!rc) {
+    out->n = N;
+    out->nnz = E;
+    out->off = (int64_t *)malloc((size_t)(N + 1) * 8);
+    out->col = (int32_t *)malloc((size_t)(E ? E : 1) * 4);
+    out->w = (int32_t *)malloc((size_t)(E ? E : 1) * 4);
+    out->truth = (int32_t *)malloc((size_t)(N ? N : 1) * 4);
+    if (!out->off || !out->col || !out->w || !out->truth) rc = -1;
+  }
+  if (!rc) {
+    int64_t e0 = 0;
+    out->off[0] = 0;
+    for (int64_t g = 0; g < count; ++g) {
+      gg_csr *p = &b.parts[g];
+      int64_t v0 = vo[g];
+      for (int64_t i = 0; i < p->n; ++i) {
+        out->off[v0 + i + 1] = p->off[i + 1] + e0;
+        out->truth[v0 + i] = p->truth ? p->truth[i] : 0;
+      }
+      for (int64_t x = 0; x < p->nnz; ++x) {
+        out->col[e0 + x] = p->col[x] + (int32_t)v0;
+        out->w[e0 + x] = p->w[x];
+      }
+      e0 += p->nnz;
+    }
+  }
+  for (int64_t g = 0; g < count; ++g) gg_free(&b.parts[g]);
+  free(b.parts);
+  if (rc) gg_free(out);
+  return rc;
+}

@@ -84,7 +84,8 @@ typedef struct {
   int32_t record_levels;      /* 1: keep each pass's membership and coarse CSR for louvain_get_level /
                                  louvain_get_coarse (copies them to host memory) */
   int32_t cuda_graphs;        /* 1: from the third iteration of a pass, replay that pass's iteration
-                                 as one captured CUDA graph instead of individual launches */
+                                 as one captured CUDA graph instead of individual launches (default 0:
+                                 measured slower on the benchmark graphs) */
   int32_t reserved_i[4];
   double reserved_d[4];
 } louvain_options;
@@ -237,6 +238,61 @@ int louvain_get_coarse(louvain_ctx *ctx, int pass, int64_t *off, int64_t k, int3
 
 /* Device bytes the context holds (arena). */
 int louvain_get_device_bytes(louvain_ctx *ctx, int64_t *bytes);
+
+/* Device bytes a context's arena needs for a graph (or a batch) of n
+ * vertices and nnz entries, without allocating anything. */
+int louvain_arena_bytes(int64_t n, int64_t nnz, int64_t *bytes);
+
+/* ------------------------------------------------------------ server
+ * Requests (graphs) submitted at any time wait in arrival order.  Each worker
+ * slot owns one context on its own stream, so slots' device work overlaps.
+ * A free slot takes the oldest waiting request and every request behind it
+ * while their CSR entries stay within batch_max_entries (and their count
+ * within batch_max_graphs), and runs them as one batch (louvain_load_batch),
+ * so each result equals the graph's result alone (synchronous: bit for bit).
+ * Slot arenas stay resident between runs; admission keeps all slots' arenas
+ * within hbm_budget_bytes: a slot that cannot grow waits for busy slots to
+ * finish, takes back the arenas of idle slots, and a request that does not fit
+ * even alone is answered with LOUVAIN_ERR_OOM.  Not in the paper (it runs one
+ * graph at a time on the CPU); the server is how the engine serves many. */
+typedef struct louvain_server louvain_server;
+typedef struct {
+  int32_t slots;              /* worker slots (contexts), default 2 */
+  int32_t batch_max_graphs;   /* at most this many requests per run, default 1024 */
+  int64_t batch_max_entries;  /* at most this many CSR entries per run, default 64 Mi; 0 = one request per run */
+  int64_t hbm_budget_bytes;   /* device bytes all slots' arenas may hold; 0 = 90% of free memory at creation */
+  int64_t reserved[5];
+} louvain_server_config;
+
+typedef struct {
+  int64_t request_id;
+  int32_t status;             /* 0 or a LOUVAIN_ERR_* code */
+  int32_t batch_size;         /* requests in the run that served it */
+  int64_t n;                  /* vertices: the length of its membership */
+  int64_t communities;
+  double q;                   /* modularity; exact: (num_hi * 2^64 + num_lo) / M^2 */
+  int64_t num_hi;
+  uint64_t num_lo;
+  int64_t M;
+  double submit_s, start_s, done_s;   /* seconds since the server was created */
+} louvain_server_result;
+
+int louvain_server_default_config(louvain_server_config *cfg);
+/* opt: the engine options every slot runs with (NULL = defaults). */
+int louvain_server_create(louvain_server **out, const louvain_options *opt, const louvain_server_config *cfg,
+                          int device);
+/* Submit graph `request_id` (host CSR as in louvain_load_csr; copied). */
+int louvain_server_submit(louvain_server *srv, int64_t request_id, int64_t n, int64_t nnz, const int64_t *offsets,
+                          const int32_t *cols, const int32_t *weights);
+/* Up to cap finished results into out (host); waits up to wait_ms for the
+ * first if none is ready.  *count = results returned. */
+int louvain_server_poll(louvain_server *srv, louvain_server_result *out, int64_t cap, int64_t *count, int32_t wait_ms);
+/* Copy a finished request's membership (n entries) and forget it. */
+int louvain_server_membership(louvain_server *srv, int64_t request_id, int32_t *out, int64_t n);
+/* out: submitted, finished, runs, queued, reserved bytes, peak reserved, budget, slots. */
+int louvain_server_stats(louvain_server *srv, int64_t out[8]);
+/* Finishes every queued request, then frees everything. */
+void louvain_server_destroy(louvain_server *srv);
 
 void louvain_destroy(louvain_ctx *ctx);
 const char *louvain_last_error(const louvain_ctx *ctx);

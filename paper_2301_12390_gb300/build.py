@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgblouvain.so")
-SOURCES = ["local_move.cu", "graph_ops.cu", "engine.cu", "noalloc.cu"]
+SOURCES = ["local_move.cu", "graph_ops.cu", "engine.cu", "noalloc.cu", "serve.cu"]
 HEADERS = ["common.cuh", "engine.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -120,6 +120,7 @@ struct louvain_ctx {
   size_t tmp_bytes = 0;
   int64_t M0 = 0;                      // total weight of the loaded graph
   int64_t cap_n = 0, cap_nnz = 0;      // arena capacity
+  bool dry_run = false;                // alloc_arena only adds up the bytes
   bool tables_dirty = true;            // global tables need clearing (new arena or a failed run)
   i128 qnum0 = 0;                      // exact Q numerator of the singleton partition of the loaded graph
   DevCounters* ctr = nullptr;
@@ -213,6 +214,11 @@ template <typename T>
 int dalloc(louvain_ctx* c, T** p, int64_t count) {
   size_t b = (size_t)(count > 0 ? count : 1) * sizeof(T);
   b = (b + 255) & ~(size_t)255;
+  if (c->dry_run) {   // size the arena only
+    c->bytes += (int64_t)b;
+    *p = nullptr;
+    return 0;
+  }
   void* q = nullptr;
   cudaError_t e = cudaMalloc(&q, b);
   if (e != cudaSuccess) {
@@ -948,7 +954,7 @@ int louvain_default_options(louvain_options* o) {
   o->subrounds = 0;
   o->validate = 1;
   o->record_levels = 0;
-  o->cuda_graphs = 1;
+  o->cuda_graphs = 0;
   return 0;
 }
 
@@ -1321,6 +1327,15 @@ int louvain_batch_get_iterations(louvain_ctx* c, int64_t g, int64_t* out, int64_
     out[4 * t + 3] = (int64_t)(uint64_t)it[t].S;
   }
   return 0;
+}
+
+int louvain_arena_bytes(int64_t n, int64_t nnz, int64_t* bytes) {
+  if (n < 0 || nnz < 0 || !bytes) return LOUVAIN_ERR_INVALID_ARG;
+  louvain_ctx c;
+  c.dry_run = true;
+  int r = alloc_arena(&c, n, nnz);
+  *bytes = c.bytes;
+  return r;
 }
 
 int louvain_get_num_graphs(louvain_ctx* c, int64_t* num_graphs) {

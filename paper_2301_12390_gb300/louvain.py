@@ -340,3 +340,111 @@ def modularity_static(off, col, w, memb, stream=None):
     if rc:
         raise LouvainError(rc, "louvain_modularity_static failed")
     return q.value, _i128(hi.value, lo.value), M.value
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("batch_max_graphs", ctypes.c_int32), ("batch_max_entries", ctypes.c_int64),
+                ("hbm_budget_bytes", ctypes.c_int64), ("reserved", ctypes.c_int64 * 5)]
+
+
+class ServerResult(ctypes.Structure):
+    _fields_ = [("request_id", ctypes.c_int64), ("status", ctypes.c_int32), ("batch_size", ctypes.c_int32),
+                ("n", ctypes.c_int64), ("communities", ctypes.c_int64), ("q", ctypes.c_double),
+                ("num_hi", ctypes.c_int64), ("num_lo", ctypes.c_uint64), ("M", ctypes.c_int64),
+                ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double), ("done_s", ctypes.c_double)]
+
+
+SIGNATURES += [
+    ("louvain_arena_bytes", _I32, [_I64, _I64, ctypes.POINTER(_I64)]),
+    ("louvain_server_default_config", _I32, [ctypes.POINTER(ServerConfig)]),
+    ("louvain_server_create", _I32, [ctypes.POINTER(_VP), ctypes.POINTER(Options), ctypes.POINTER(ServerConfig), _I32]),
+    ("louvain_server_submit", _I32, [_VP, _I64, _I64, _I64, _VP, _VP, _VP]),
+    ("louvain_server_poll", _I32, [_VP, ctypes.POINTER(ServerResult), _I64, ctypes.POINTER(_I64), _I32]),
+    ("louvain_server_membership", _I32, [_VP, _I64, _VP, _I64]),
+    ("louvain_server_stats", _I32, [_VP, _VP]),
+    ("louvain_server_destroy", None, [_VP]),
+]
+
+
+class Server:
+    """Continuous-batching request server (louvain_server_*): submit host CSR graphs at any
+    time, poll finished results; each result equals the graph's result alone."""
+
+    def __init__(self, device: int = 0, slots: int = 2, batch_max_entries=None, batch_max_graphs=None,
+                 hbm_budget_bytes=None, **options):
+        self.lib = load_library()
+        self.opt = default_options(**options)
+        cfg = ServerConfig()
+        self.lib.louvain_server_default_config(ctypes.byref(cfg))
+        cfg.slots = slots
+        if batch_max_entries is not None:
+            cfg.batch_max_entries = batch_max_entries
+        if batch_max_graphs is not None:
+            cfg.batch_max_graphs = batch_max_graphs
+        if hbm_budget_bytes is not None:
+            cfg.hbm_budget_bytes = hbm_budget_bytes
+        h = ctypes.c_void_p()
+        rc = self.lib.louvain_server_create(ctypes.byref(h), ctypes.byref(self.opt), ctypes.byref(cfg), device)
+        if rc:
+            raise LouvainError(rc, "louvain_server_create failed")
+        self.h = h
+        self._n = {}
+
+    def submit(self, request_id: int, off, col, w):
+        off = np.ascontiguousarray(off, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        w = np.ascontiguousarray(w, dtype=np.int32)
+        rc = self.lib.louvain_server_submit(self.h, request_id, len(off) - 1, len(col), off.ctypes.data,
+                                            col.ctypes.data, w.ctypes.data)
+        if rc:
+            raise LouvainError(rc, f"submit of request {request_id} failed")
+        self._n[request_id] = len(off) - 1
+
+    def poll(self, wait_ms: int = 0, cap: int = 1024):
+        buf = (ServerResult * cap)()
+        cnt = ctypes.c_int64()
+        self.lib.louvain_server_poll(self.h, buf, cap, ctypes.byref(cnt), wait_ms)
+        out = []
+        for r in buf[:cnt.value]:
+            out.append({"id": r.request_id, "status": r.status, "batch_size": r.batch_size, "n": r.n,
+                        "communities": r.communities, "q": r.q, "num": _i128(r.num_hi, r.num_lo), "M": r.M,
+                        "submit_s": r.submit_s, "start_s": r.start_s, "done_s": r.done_s})
+        return out
+
+    def membership(self, request_id: int) -> np.ndarray:
+        n = self._n.pop(request_id)
+        out = np.empty(n, np.int32)
+        rc = self.lib.louvain_server_membership(self.h, request_id, out.ctypes.data, n)
+        if rc:
+            raise LouvainError(rc, f"no membership for request {request_id}")
+        return out
+
+    def stats(self):
+        out = np.zeros(8, np.int64)
+        self.lib.louvain_server_stats(self.h, out.ctypes.data)
+        keys = ["submitted", "finished", "runs", "queued", "reserved_bytes", "peak_reserved_bytes", "budget_bytes",
+                "slots"]
+        return dict(zip(keys, out.tolist()))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.louvain_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def arena_bytes(n: int, nnz: int) -> int:
+    b = ctypes.c_int64()
+    load_library().louvain_arena_bytes(n, nnz, ctypes.byref(b))
+    return b.value
