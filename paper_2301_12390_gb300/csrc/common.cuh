@@ -121,16 +121,20 @@ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
 // Open-addressing insert-or-add into a power-of-two table (shared or global
 // memory): keys int32 (kEmpty = free), values u64.  Returns false if the
 // table is full (the caller records kErrProbe).
-template <int CAP>
-__device__ __forceinline__ bool table_add_pow2(int32_t* keys, unsigned long long* vals, int32_t key,
-                                               unsigned long long w) {
+// Shared tables hold u32 sums when every sum fits (narrow arithmetic: M <
+// 2^31, so any K_{i->c} <= M fits), else u64.
+template <bool WIDE> struct TableVal { typedef unsigned long long T; };
+template <> struct TableVal<false> { typedef unsigned int T; };
+
+template <int CAP, typename V>
+__device__ __forceinline__ bool table_add_pow2(int32_t* keys, V* vals, int32_t key, unsigned long long w) {
   uint32_t h = hash32((uint32_t)key) & (CAP - 1);
 #pragma unroll 1
   for (int probe = 0; probe < CAP; ++probe) {
     int32_t k = keys[h];
     if (k == kEmpty) k = atomicCAS(&keys[h], kEmpty, key);
     if (k == kEmpty || k == key) {
-      atomicAdd(&vals[h], w);
+      atomicAdd(&vals[h], (V)w);
       return true;
     }
     h = (h + 1) & (CAP - 1);
@@ -140,9 +144,9 @@ __device__ __forceinline__ bool table_add_pow2(int32_t* keys, unsigned long long
 
 // Same, also reporting the slot and whether the key is new (for touched-slot
 // lists).  Returns -1 if the table is full.
-template <int CAP>
-__device__ __forceinline__ int table_add_pow2_slot(int32_t* keys, unsigned long long* vals, int32_t key,
-                                                   unsigned long long w, bool* fresh) {
+template <int CAP, typename V>
+__device__ __forceinline__ int table_add_pow2_slot(int32_t* keys, V* vals, int32_t key, unsigned long long w,
+                                                   bool* fresh) {
   uint32_t h = hash32((uint32_t)key) & (CAP - 1);
   *fresh = false;
 #pragma unroll 1
@@ -153,7 +157,7 @@ __device__ __forceinline__ int table_add_pow2_slot(int32_t* keys, unsigned long 
       if (k == kEmpty) *fresh = true;
     }
     if (k == kEmpty || k == key) {
-      atomicAdd(&vals[h], w);
+      atomicAdd(&vals[h], (V)w);
       return (int)h;
     }
     h = (h + 1) & (CAP - 1);
@@ -162,9 +166,8 @@ __device__ __forceinline__ int table_add_pow2_slot(int32_t* keys, unsigned long 
 }
 
 // Lookup in a power-of-two table; 0 if absent.
-template <int CAP>
-__device__ __forceinline__ unsigned long long table_get_pow2(const int32_t* keys, const unsigned long long* vals,
-                                                             int32_t key) {
+template <int CAP, typename V>
+__device__ __forceinline__ unsigned long long table_get_pow2(const int32_t* keys, const V* vals, int32_t key) {
   uint32_t h = hash32((uint32_t)key) & (CAP - 1);
 #pragma unroll 1
   for (int probe = 0; probe < CAP; ++probe) {

@@ -589,14 +589,14 @@ __global__ void __launch_bounds__(256) agg_warp_k(AggArgs a, const int32_t* __re
         int32_t D;
         unsigned long long w;
         staged_entry<W>(a, sp[wib], ss[wib], nm, t, &D, &w);
-        ok &= table_add_pow2<CAP>(keys, vals, D, w);
+        ok &= table_add_pow2<CAP, unsigned long long>(keys, vals, D, w);
       }
     } else {
       for (int64_t t = vs + lane; t < ve; t += kWarp) {
         int32_t D;
         unsigned long long w;
         virtual_entry<W>(a, cs, ce, t, &D, &w);
-        ok &= table_add_pow2<CAP>(keys, vals, D, w);
+        ok &= table_add_pow2<CAP, unsigned long long>(keys, vals, D, w);
       }
     }
     __syncwarp();
@@ -657,7 +657,7 @@ __global__ void __launch_bounds__(THREADS) agg_block_k(AggArgs a, const int32_t*
         unsigned long long w;
         if (nm <= TILE) staged_entry<W>(a, spre, sstart, nm, t, &D, &w);
         else virtual_entry<W>(a, cs, ce, t, &D, &w);
-        ok &= table_add_pow2<CAP>(keys, vals, D, w);
+        ok &= table_add_pow2<CAP, unsigned long long>(keys, vals, D, w);
       }
       __syncthreads();
     }
@@ -741,7 +741,7 @@ __global__ void __launch_bounds__(256) agg_global_insert_k(AggArgs a, const int3
     unsigned long long w;
     if (nm <= MAXM) staged_entry<W>(a, spre, sstart, nm, t, &D, &w);
     else virtual_entry<W>(a, cs, ce, t, &D, &w);
-    ok &= table_add_pow2<CAP>(skeys, svals, D, w);
+    ok &= table_add_pow2<CAP, unsigned long long>(skeys, svals, D, w);
   }
   __syncthreads();
   int32_t* keys = a.gkeys + base;

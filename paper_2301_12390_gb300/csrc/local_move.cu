@@ -215,13 +215,14 @@ template <typename W, bool WIDE, bool ASYNC, int CAP, int U>
 __global__ void __launch_bounds__(256, 4) lm_warp(LMArgs<W> a, const int32_t* __restrict__ verts, int nverts) {
   const IterView iv = iter_view(a);
   typedef typename Arith<WIDE>::S S;
+  typedef typename TableVal<WIDE>::T V;
   constexpr int WPB = 8;
   __shared__ int32_t skeys[WPB][CAP];
-  __shared__ unsigned long long svals[WPB][CAP];
+  __shared__ V svals[WPB][CAP];
   __shared__ BlockAcc acc;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   int32_t* keys = skeys[wib];
-  unsigned long long* vals = svals[wib];
+  V* vals = svals[wib];
   acc_init(acc);
   for (int t = lane; t < CAP; t += kWarp) { keys[t] = kEmpty; vals[t] = 0; }
   __syncthreads();
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(256, 4) lm_warp(LMArgs<W> a, const int32_t* __
       for (int u = 0; u < U; ++u) cc[u] = cc[u] != i ? ld_memb<ASYNC>(a.memb + cc[u]) : kEmpty;
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        if (cc[u] != kEmpty) ok &= table_add_pow2<CAP>(keys, vals, cc[u], ww[u]);
+        if (cc[u] != kEmpty) ok &= table_add_pow2<CAP, V>(keys, vals, cc[u], ww[u]);
     }
     __syncwarp();
     unsigned long long kid = 0;
@@ -308,30 +309,92 @@ __global__ void __launch_bounds__(256, 4) lm_warp(LMArgs<W> a, const int32_t* __
 
 // ----------------------------------------- buckets 3-4: block per vertex
 
+// A decided move waiting for the block to commit it.
+struct PendingMove {
+  int32_t i, c, d;
+};
+
+// Commit and mark the pending moves of a block (all threads take part).
+template <typename W, bool ASYNC>
+__device__ __forceinline__ void flush_moves(const LMArgs<W>& a, const IterView& iv, const PendingMove* q, int n,
+                                            int tid, int nthr) {
+  for (int t = tid; t < n; t += nthr) {
+    const PendingMove m = q[t];
+    if (ASYNC) {
+      const long long Ki = a.K[m.i];
+      a.memb[m.i] = m.c;
+      atomicAdd((unsigned long long*)(a.sig + m.d), (unsigned long long)(-Ki));
+      atomicAdd((unsigned long long*)(a.sig + m.c), (unsigned long long)Ki);
+      atomicSub(a.csize + m.d, 1);
+      atomicAdd(a.csize + m.c, 1);
+    } else {
+      unsigned long long pos = atomicAdd(&a.ctr->nmoves_list, 1ull);
+      a.moves[pos] = make_int2(m.i, m.c);
+    }
+  }
+  if (a.prune)
+    for (int t = 0; t < n; ++t) {
+      const int32_t i = q[t].i;
+      if (tid == 0) iv.sw[i] = iv.iter + 1;
+      for (int64_t x = a.off[i] + tid; x < a.off[i + 1]; x += nthr) iv.sw[a.col[x]] = iv.iter + 1;
+    }
+}
+
+// Decide (no commit yet): the exact gain of the best candidate against the
+// vertex's own community, the guard, and the S / move counts.
+template <typename W, bool WIDE, bool ASYNC>
+__device__ __forceinline__ bool decide_move(const LMArgs<W>& a, BlockAcc& acc, int32_t d, long long Ki,
+                                            typename Arith<WIDE>::S best, int32_t c, unsigned long long kid,
+                                            long long M, int graph) {
+  if (c < 0) return false;
+  typedef typename Arith<WIDE>::S S;
+  const S g = best - Arith<WIDE>::score(M, (long long)kid, Ki, ld_sig<ASYNC>(a.sig + d) - Ki);
+  if (!(g > 0)) return false;
+  if (a.guard && c > d && ld_size<ASYNC>(a.csize + d) == 1 && ld_size<ASYNC>(a.csize + c) == 1) return false;
+  const u128 gv = Arith<WIDE>::to_u128(g);
+  if (a.gid) {
+    atomicAdd(a.g_moves + graph, 1ull);
+    atomic_add_u128(a.g_s + 2 * graph, a.g_s + 2 * graph + 1, gv);
+  } else {
+    atomicAdd(&acc.moves, 1ull);
+    atomic_add_u128(&acc.s_lo, &acc.s_hi, gv);
+  }
+  return true;
+}
+
+// Two barriers per vertex: the small shared values alternate between two
+// copies by vertex parity, so the next vertex can start while warp 0 still
+// reduces and decides; moves queue in shared memory and are committed by the
+// whole block when the queue fills and at the end.
 template <typename W, bool WIDE, bool ASYNC, int CAP, int THREADS>
 __global__ void __launch_bounds__(THREADS) lm_block(LMArgs<W> a, const int32_t* __restrict__ verts, int nverts) {
   const IterView iv = iter_view(a);
   typedef typename Arith<WIDE>::S S;
+  typedef typename TableVal<WIDE>::T V;
   constexpr int NW = THREADS / kWarp;
   constexpr int U = 4;
-  // dynamic shared memory: values (CAP u64), keys (CAP i32), touched slots (CAP/2 i32)
+  constexpr int QCAP = 64;
+  // dynamic shared memory: values (CAP V), keys (CAP i32), touched slots (CAP/2 u16)
   extern __shared__ unsigned long long dyn[];
-  unsigned long long* vals = dyn;
-  int32_t* keys = (int32_t*)(dyn + CAP);
-  int32_t* touched = keys + CAP;
+  V* vals = (V*)dyn;
+  int32_t* keys = (int32_t*)(vals + CAP);
+  uint16_t* touched = (uint16_t*)(keys + CAP);
   __shared__ BlockAcc acc;
-  __shared__ S red_g[NW];
-  __shared__ int32_t red_c[NW];
-  __shared__ unsigned long long s_kid;
-  __shared__ int s_moved, s_nt;
+  __shared__ S red_g[2][NW];
+  __shared__ int32_t red_c[2][NW];
+  __shared__ unsigned long long s_kid[2];
+  __shared__ int s_nt[2];
+  __shared__ PendingMove queue[QCAP];
+  __shared__ int q_n;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   acc_init(acc);
-  if (threadIdx.x == 0) { s_nt = 0; s_kid = 0; }
+  if (threadIdx.x == 0) { s_nt[0] = s_nt[1] = 0; s_kid[0] = s_kid[1] = 0; q_n = 0; }
   for (int t = threadIdx.x; t < CAP; t += THREADS) { keys[t] = kEmpty; vals[t] = 0; }
   __syncthreads();
   bool ok = true;
+  int p = 0;
   for (int vi = blockIdx.x; vi < nverts; vi += gridDim.x) {
-    int32_t i = verts[vi];
+    const int32_t i = verts[vi];
     if (!is_active(a, iv, i)) continue;   // uniform across the block
     long long M;
     int graph;
@@ -356,19 +419,25 @@ __global__ void __launch_bounds__(THREADS) lm_block(LMArgs<W> a, const int32_t* 
         bool fresh = false;
         int h = -1;
         if (cc[u] != kEmpty) {
-          h = table_add_pow2_slot<CAP>(keys, vals, cc[u], ww[u], &fresh);
+          h = table_add_pow2_slot<CAP, V>(keys, vals, cc[u], ww[u], &fresh);
           if (h < 0) ok = false;
         }
         // one append per warp for the new keys of its lanes
         const unsigned m = __ballot_sync(0xffffffffu, fresh);
         int base = 0;
-        if (lane == 0 && m) base = atomicAdd(&s_nt, __popc(m));
+        if (lane == 0 && m) base = atomicAdd(&s_nt[p], __popc(m));
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (fresh) touched[base + __popc(m & lanemask_lt_lm())] = h;
+        if (fresh) touched[base + __popc(m & lanemask_lt_lm())] = (uint16_t)h;
       }
     }
-    __syncthreads();
-    const int nt = s_nt;
+    __syncthreads();   // B1: table complete; warp 0 has finished the previous vertex
+    if (q_n >= QCAP) {   // uniform: q_n was last written before this barrier
+      flush_moves<W, ASYNC>(a, iv, queue, q_n, threadIdx.x, THREADS);
+      __syncthreads();
+      if (threadIdx.x == 0) q_n = 0;
+    }
+    if (threadIdx.x == 0) { s_nt[p ^ 1] = 0; s_kid[p ^ 1] = 0; }   // the next vertex's copies
+    const int nt = s_nt[p];
     S bg = Arith<WIDE>::lowest();
     int32_t bc = -1;
     for (int t0 = 0; t0 < nt; t0 += U * THREADS) {
@@ -378,7 +447,7 @@ __global__ void __launch_bounds__(THREADS) lm_block(LMArgs<W> a, const int32_t* 
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int t = t0 + u * THREADS + threadIdx.x;
-        hs[u] = t < nt ? touched[t] : -1;
+        hs[u] = t < nt ? (int)touched[t] : -1;
         cs[u] = hs[u] >= 0 ? keys[hs[u]] : kEmpty;
       }
 #pragma unroll
@@ -390,33 +459,29 @@ __global__ void __launch_bounds__(THREADS) lm_block(LMArgs<W> a, const int32_t* 
           S g = Arith<WIDE>::score(M, (long long)vals[hs[u]], Ki, sg[u]);
           if (better(g, cs[u], bg, bc)) { bg = g; bc = cs[u]; }
         } else {
-          s_kid = vals[hs[u]];
+          s_kid[p] = vals[hs[u]];
         }
         keys[hs[u]] = kEmpty;
         vals[hs[u]] = 0;
       }
     }
     warp_argmax(bg, bc);
-    if (lane == 0) { red_g[wid] = bg; red_c[wid] = bc; }
-    __syncthreads();
+    if (lane == 0) { red_g[p][wid] = bg; red_c[p][wid] = bc; }
+    __syncthreads();   // B2: candidates evaluated, table clear
     if (wid == 0) {
-      bg = lane < NW ? red_g[lane] : Arith<WIDE>::lowest();
-      bc = lane < NW ? red_c[lane] : -1;
+      bg = lane < NW ? red_g[p][lane] : Arith<WIDE>::lowest();
+      bc = lane < NW ? red_c[p][lane] : -1;
       warp_argmax(bg, bc);
       if (lane == 0) {
         atomicAdd(&acc.edges, (unsigned long long)(e - b));
         atomicAdd(&acc.visited, 1ull);
-        s_moved = commit_choice<W, WIDE, ASYNC>(a, acc, i, d, Ki, bg, bc, s_kid, M, graph);
-        s_nt = 0;
-        s_kid = 0;
+        if (decide_move<W, WIDE, ASYNC>(a, acc, d, Ki, bg, bc, s_kid[p], M, graph)) queue[q_n++] = PendingMove{i, bc, d};
       }
     }
-    __syncthreads();
-    if (s_moved && a.prune) {
-      if (threadIdx.x == 0) iv.sw[i] = iv.iter + 1;
-      for (int64_t x = b + threadIdx.x; x < e; x += THREADS) iv.sw[a.col[x]] = iv.iter + 1;
-    }
+    p ^= 1;
   }
+  __syncthreads();
+  flush_moves<W, ASYNC>(a, iv, queue, q_n, threadIdx.x, THREADS);
   if (!ok) atomicOr(&acc.error, kErrProbe);
   __syncthreads();
   acc_flush(acc, a.ctr);
@@ -446,14 +511,15 @@ __device__ __forceinline__ int find_item(const int64_t* __restrict__ pre, int ni
   return lo;
 }
 
-template <typename W, bool ASYNC>
+template <typename W, bool WIDE, bool ASYNC>
 __global__ void __launch_bounds__(256) lm_hub_insert(LMArgs<W> a, const int32_t* __restrict__ hubs, int nhubs,
                                                      const int64_t* __restrict__ chunk_pre) {
+  typedef typename TableVal<WIDE>::T V;
   const IterView iv = iter_view(a);
   constexpr int CAP = 2 * kHubChunk;
   extern __shared__ unsigned long long hdyn[];
-  unsigned long long* svals = hdyn;
-  int32_t* skeys = (int32_t*)(hdyn + CAP);
+  V* svals = (V*)hdyn;
+  int32_t* skeys = (int32_t*)(svals + CAP);
   const int h = find_item(chunk_pre, nhubs, blockIdx.x);
   const int32_t i = hubs[h];
   if (!is_active(a, iv, i)) return;   // uniform across the block
@@ -485,7 +551,7 @@ __global__ void __launch_bounds__(256) lm_hub_insert(LMArgs<W> a, const int32_t*
     for (int u = 0; u < U; ++u) cc[u] = cc[u] != i ? ld_memb<ASYNC>(a.memb + cc[u]) : kEmpty;
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (cc[u] != kEmpty) ok &= table_add_pow2<CAP>(skeys, svals, cc[u], ww[u]);
+      if (cc[u] != kEmpty) ok &= table_add_pow2<CAP, V>(skeys, svals, cc[u], ww[u]);
   }
   __syncthreads();
   int32_t* keys = a.hkeys + base;
@@ -494,7 +560,7 @@ __global__ void __launch_bounds__(256) lm_hub_insert(LMArgs<W> a, const int32_t*
     int32_t c = skeys[t];
     if (c == kEmpty) continue;
     bool fresh;
-    ok &= gtable_add(keys, vals, cap, c, svals[t], &fresh);
+    ok &= gtable_add(keys, vals, cap, c, (unsigned long long)svals[t], &fresh);
   }
   if (!ok) atomicOr(&a.ctr->error, kErrProbe);
 }
@@ -670,14 +736,14 @@ void launch_bucket_t(const LMArgs<W>& a, int bucket, const int32_t* verts, int n
     }
     case 3: {
       constexpr int CAP = 2048;
-      size_t smem = (size_t)CAP * 14;
+      size_t smem = (size_t)CAP * (sizeof(typename TableVal<WIDE>::T) + 4 + 1);
       auto k = lm_block<W, WIDE, ASYNC, CAP, 128>;
       (count_launch(), k<<<grid_for(k, 128, smem, nverts), 128, smem, s>>>(a, verts, nverts));
       break;
     }
     case 4: {
       constexpr int CAP = 8192;
-      size_t smem = (size_t)CAP * 14;
+      size_t smem = (size_t)CAP * (sizeof(typename TableVal<WIDE>::T) + 4 + 1);
       auto k = lm_block<W, WIDE, ASYNC, CAP, 512>;
       static bool attr = false;
       if (!attr) {
@@ -710,9 +776,14 @@ void lm_launch_hubs(const LMArgs<W>& a, bool wide, bool async, const int32_t* hu
                     const int64_t* chunk_pre, int64_t nchunks, const int64_t* spre, int64_t nslotchunks,
                     cudaStream_t s) {
   if (nhubs <= 0 || nchunks <= 0) return;
-  const size_t smem = (size_t)(2 * kHubChunk) * 12;
-  if (async) (count_launch(), lm_hub_insert<W, true><<<(unsigned)nchunks, 256, smem, s>>>(a, hubs, nhubs, chunk_pre));
-  else (count_launch(), lm_hub_insert<W, false><<<(unsigned)nchunks, 256, smem, s>>>(a, hubs, nhubs, chunk_pre));
+  const size_t smem = (size_t)(2 * kHubChunk) * (wide ? 12 : 8);
+  if (wide) {
+    if (async) (count_launch(), lm_hub_insert<W, true, true><<<(unsigned)nchunks, 256, smem, s>>>(a, hubs, nhubs, chunk_pre));
+    else (count_launch(), lm_hub_insert<W, true, false><<<(unsigned)nchunks, 256, smem, s>>>(a, hubs, nhubs, chunk_pre));
+  } else {
+    if (async) (count_launch(), lm_hub_insert<W, false, true><<<(unsigned)nchunks, 256, smem, s>>>(a, hubs, nhubs, chunk_pre));
+    else (count_launch(), lm_hub_insert<W, false, false><<<(unsigned)nchunks, 256, smem, s>>>(a, hubs, nhubs, chunk_pre));
+  }
   const int g = nhubs < 4096 ? nhubs : 4096;
   if (wide) {
     if (async) {
