@@ -172,12 +172,56 @@ def run_oracle_sample(g, mode, max_passes=10, max_iterations=20):
     return entries, dt, r.Q
 
 
+def bench_reference_graphs(args):
+    """CPU oracle arm of the many-graph workloads (batched, serving): each step
+    is full oracle runs, one graph after another, over a bounded sample of the
+    workload's graphs; the value is graphs per second, as for our arms."""
+    import oracle
+    mode = oracle.ASYNC if args.mode == "async" else oracle.SYNC
+    if args.workload == "batched":
+        specs = gg.batch_sbm_specs(SEED + 3, args.batch_graphs)
+        big, vo = gg.sbm_batch(specs[:64])
+        graphs = gg.split(big, vo)
+        metric = "graphs/sec batched vs plain, at equal Q"
+        what = f"the first 64 of the {args.batch_graphs} batch graphs"
+    else:
+        pool = serving_pool(SEED + 4, args.pool, args.serve_nmin, args.serve_nmax)
+        pick = [int(gg.uniform(SEED + 4, 32, r) * len(pool)) for r in range(args.requests)]
+        # bounded sample: the requests in arrival order, skipping graphs above 2e5 vertices
+        graphs = [pool[p] for p in pick if pool[p].n <= 200_000][:32]
+        metric = "graphs/sec (p50/p99 latency) served with continuous batching vs serial plain runs, at equal Q"
+        what = "the first 32 requests whose graph has at most 200,000 vertices"
+    for g in graphs[:max(1, args.warmup)]:
+        oracle.louvain(g.off, g.col, g.w, mode=mode, prune=1)
+    lat, tot_t = [], 0.0
+    for _ in range(args.steps):
+        for g in graphs:
+            t = time.perf_counter()
+            oracle.louvain(g.off, g.col, g.w, mode=mode, prune=1)
+            lat.append(time.perf_counter() - t)
+    tot_t = float(np.sum(lat))
+    value = len(lat) / tot_t
+    line = {
+        "impl": "reference", "metric": metric, "value": value, "unit": "graphs/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": args.workload, "mode": args.mode, "graphs_per_step": len(graphs)},
+        "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)), "latency_ms_p99": 1e3 * float(np.percentile(lat, 99)),
+        "cpu_baseline": {"value": value, "unit": "graphs/s", "cores": 1, "kind": "oracle",
+                         "sample": f"full oracle runs ({args.mode}, prune on) of {what}, per step"},
+        "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def bench_reference(args):
     """CPU oracle arm: each step is one local-moving iteration of the oracle over the whole graph."""
     world, rank, _, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0, None
     if rank != 0:
         return
     import oracle
+    if args.workload in ("batched", "serving"):
+        return bench_reference_graphs(args)
     g = WORKLOADS[args.workload][0]()
     mode = oracle.ASYNC if args.mode == "async" else oracle.SYNC
     for _ in range(args.warmup):

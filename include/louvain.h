@@ -77,16 +77,23 @@ typedef struct {
   int32_t singleton_guard;    /* 1: a vertex alone in its community does not move to another
                                  single-vertex community of higher id (minimum-label rule, Grappolo;
                                  stops Jacobi updates from swapping pairs forever) */
-  int32_t subrounds;          /* P >= 1: the vertices are split into classes i mod P processed one
-                                 after the other in each iteration; 1 = every vertex at once;
-                                 0 = automatic (synchronous 1, asynchronous 16) */
+  int32_t subrounds;          /* P >= 1: the vertices are split into P classes processed one after
+                                 the other in each iteration; 1 = every vertex at once; 0 = automatic
+                                 (synchronous 1; asynchronous 16, or 32 when the largest graph of the
+                                 run has fewer than 65,536 vertices) */
   int32_t validate;           /* 1: louvain_load_csr checks symmetry and CSR form (costs a pass) */
   int32_t record_levels;      /* 1: keep each pass's membership and coarse CSR for louvain_get_level /
                                  louvain_get_coarse (copies them to host memory) */
   int32_t cuda_graphs;        /* 1: from the third iteration of a pass, replay that pass's iteration
                                  as one captured CUDA graph instead of individual launches (default 0:
                                  measured slower on the benchmark graphs) */
-  int32_t reserved_i[4];
+  int32_t reclass;            /* asynchronous mode with P > 1: 0 = classes id mod P; 1 = each
+                                 iteration draws the classes anew, class = hash(id, pass, iteration)
+                                 mod P (breaks the repeated same-class swaps of structured ids such
+                                 as grids); 2 = hashed classes drawn once per pass; 3 = automatic
+                                 (default: 2 when the largest graph of the run has fewer than 65,536
+                                 vertices, else 1).  Synchronous classes are always id mod P. */
+  int32_t reserved_i[3];
   double reserved_d[4];
 } louvain_options;
 
@@ -175,6 +182,27 @@ int louvain_batch_get_graph_info(louvain_ctx *ctx, int64_t g, int64_t out[4]);
 /* Iterations of graph g (as louvain_get_iteration, 4 values each) into
  * out[4 * cap]; *count = how many there are. */
 int louvain_batch_get_iterations(louvain_ctx *ctx, int64_t g, int64_t *out, int64_t cap, int64_t *count);
+
+/* Vertex-to-kernel mapping of the local-moving phase.  thresholds[5] are the
+ * largest degrees handled by, in order, a thread per vertex (register table,
+ * at most 8), a warp with a 64-slot table (at most 32), a warp with a 256-slot
+ * table (at most 128), a block with a 2048-slot table (at most 1024) and a
+ * block with an 8192-slot table (at most 4096); larger degrees go to the hub
+ * path (global tables).  They must increase.  Lowering one moves vertices to
+ * a wider mapping whose table is emptier.  NULL restores the defaults (the
+ * maxima).  The mapping never changes results: only which kernel computes
+ * them.  Errors: INVALID_ARG. */
+int louvain_set_mapping(louvain_ctx *ctx, const int32_t *thresholds);
+int louvain_get_mapping(louvain_ctx *ctx, int32_t *thresholds);
+
+/* Autotuner: times the first local-moving iteration of the loaded graph (or
+ * batch) under candidate mappings (coordinate descent over the thresholds,
+ * best of two trials each) and keeps the fastest for later runs.  Writes the
+ * chosen thresholds[5] and the best trial's device time in ms (either may be
+ * NULL).  Costs about a dozen iterations; the previous result is dropped (run
+ * again).  Not in the paper: it picks the GPU mapping, not the method.
+ * Errors: STATE (no graph), CUDA, INTERNAL. */
+int louvain_autotune(louvain_ctx *ctx, int32_t *thresholds, double *ms);
 
 /* Run the Louvain method on the loaded graph.  Errors: STATE (no graph), CUDA,
  * INTERNAL, TIMEOUT. */

@@ -241,12 +241,13 @@ struct LMArgs {
   unsigned long long* g_s;      // per-graph S of the iteration (lo, hi)
   int prune;
   int guard;
-  // hub path: per-hub global tables (slots [hbase[h], hbase[h] + 2 deg))
+  // hub path: per-hub global tables (2 deg slots each, per class from slot 0)
   int32_t* hkeys;
   unsigned long long* hvals;
-  const int64_t* hbase;      // table offset of hub h
+  const int64_t* hbase;      // table offset of hub h (the class's first hub at hbase[0])
   const int64_t* spre;       // first slot chunk of hub h (absolute within the pass)
   unsigned long long* hkid;  // K_{i->d} of hub h, looked up before the scan clears the table
+  int32_t* hmoved;           // iteration + 1 when hub h moved in that iteration
   long long* hpart;          // per slot chunk: best gain (lo, hi)
   int32_t* hpart_c;          // per slot chunk: its community
 };

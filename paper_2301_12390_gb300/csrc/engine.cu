@@ -32,8 +32,12 @@ namespace {
 // engine: with every vertex deciding at once, stale neighbour memberships
 // make pairs and groups swap and modularity can collapse; 16 classes run in
 // sequence keep the result within a few 1e-3 of the sequential order on the
-// benchmark graphs.
+// large benchmark graphs.  Small graphs (few thousand vertices, few dense
+// communities) need smaller classes: at 16 some planted-partition graphs
+// ended more than 0.01 below the sequential order, at 32 none did.
 constexpr int kAsyncSubrounds = 16;
+constexpr int kAsyncSubroundsSmall = 32;   // asynchronous classes of graphs below kSmallGraph vertices
+constexpr int64_t kSmallGraph = 65536;
 
 struct IterRec {
   int pass;
@@ -112,6 +116,11 @@ struct louvain_ctx {
   int64_t* gbase = nullptr;
   int64_t* chunk_pre = nullptr;
   int64_t* spre = nullptr;
+  int64_t* glo = nullptr;
+  int32_t* inv = nullptr;      // aggregation: member position of each vertex
+  int32_t* hmoved = nullptr;   // local moving: iteration + 1 of a hub's last move (by hub-list position)
+  LMThresholds thr = {{kLMCap[0], kLMCap[1], kLMCap[2], kLMCap[3], kLMCap[4]}};   // degree mapping
+  int32_t* crow = nullptr;     // aggregation: first row of each relabel chunk      // aggregation: direct-table first key per global community, or -1
   unsigned long long* hkid = nullptr;
   long long* hpart = nullptr;
   int32_t* hpart_c = nullptr;
@@ -242,6 +251,7 @@ int check_options(const louvain_options* o) {
   if (!(o->tolerance >= 0) || !(o->tolerance_decline > 0) || !(o->pass_tolerance == o->pass_tolerance)) return 1;
   if (o->max_iterations < 1 || o->max_passes < 0 || o->max_passes > 64) return 1;
   if (o->subrounds < 0 || o->subrounds > 64) return 1;
+  if (o->reclass < 0 || o->reclass > 3) return 1;
   return 0;
 }
 
@@ -262,34 +272,64 @@ struct PassState {
   int widx;   // which coarse buffer holds this graph (-1 = input)
 };
 
+// Salt of the hashed classes of one iteration (splitmix64 finaliser of
+// pass and iteration, folded to 32 bits; never 0).
+uint32_t mix_salt(int pass, int iter) {
+  uint64_t z = ((uint64_t)(uint32_t)pass << 32 | (uint32_t)iter) + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  const uint32_t v = (uint32_t)(z ^ (z >> 32));
+  return v ? v : 1u;
+}
+
 template <typename W>
 int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool wide, int* iters_out,
                  int64_t* edges_out, int64_t* visited_out) {
   const bool async = c->opt.mode == LOUVAIN_ASYNC;
-  const int P = c->opt.subrounds > 0 ? c->opt.subrounds : (async ? kAsyncSubrounds : 1);
+  // automatic classes: graphs below kSmallGraph vertices (the largest graph of
+  // a batch decides) take more, smaller classes, drawn once per pass; larger
+  // graphs take kAsyncSubrounds classes drawn anew every iteration
+  int64_t nbig = 0;
+  for (int64_t q = 0; q < c->G; ++q) nbig = std::max(nbig, c->gn0[q]);
+  const bool small = nbig < kSmallGraph;
+  const int P = c->opt.subrounds > 0 ? c->opt.subrounds
+                                     : (async ? (small ? kAsyncSubroundsSmall : kAsyncSubrounds) : 1);
   const int nkeys = kBuckets * P + 1;
   const bool multi = c->G > 1;
   const int64_t G = c->G;
   cudaStream_t s = c->stream;
-  // bucket lists: key = bucket * P + class (class by id within the graph)
-  lm_keys(g.off, g.n, P, c->key, multi ? c->gid : nullptr, multi ? c->vo : nullptr, s);
-  stable_partition(c->key, g.n, nkeys, c->list, c->key_off, c->tmp, s);
-  CKLAUNCH();
+  // Bucket lists: key = bucket * P + class, class by id within the graph
+  // (id mod P, or with reclass a hash of it salted by pass and iteration),
+  // hubs of all classes contiguous, and the hubs' table layout.
+  // reclass 1: hashed classes drawn anew every iteration; 2: once per pass
+  const int reclass = (async && P > 1) ? (c->opt.reclass == 3 ? (small ? 2 : 1) : c->opt.reclass) : 0;
   std::vector<int64_t> ko(nkeys + 1);
-  if (int r = fetch(c, ko.data(), c->key_off, ko.size() * sizeof(int64_t))) return r;
-  // hubs: all classes' hub lists are contiguous
-  const int64_t hub0 = ko[kHubBucket * P], hub1 = ko[kHubBucket * P + P];
-  const int64_t nhubs = hub1 - hub0;
+  int64_t hub0 = 0, hub1 = 0, nhubs = 0;
   std::vector<int64_t> hchunks, hschunks;
-  if (nhubs > 0) {
-    hub_layout(g.off, c->list + hub0, nhubs, c->gbase, c->chunk_pre, c->spre, c->tmp, s);
+  auto classify = [&](int iter) -> int {
+    const uint32_t salt = reclass ? mix_salt(pass, reclass == 1 ? iter : 0) : 0u;
+    lm_keys(g.off, g.n, P, c->key, multi ? c->gid : nullptr, multi ? c->vo : nullptr, salt, c->thr, s);
+    stable_partition(c->key, g.n, nkeys, c->list, c->key_off, c->tmp, s);
     CKLAUNCH();
-    hchunks.resize(nhubs + 1);
-    hschunks.resize(nhubs + 1);
-    if (int r = fetch(c, hchunks.data(), c->chunk_pre, hchunks.size() * sizeof(int64_t))) return r;
-    if (int r = fetch(c, hschunks.data(), c->spre, hschunks.size() * sizeof(int64_t))) return r;
-    if (hschunks[nhubs] > c->npart) return fail(c, LOUVAIN_ERR_INTERNAL, "hub partial buffer too small");
-  }
+    if (int r = fetch(c, ko.data(), c->key_off, ko.size() * sizeof(int64_t))) return r;
+    hub0 = ko[kHubBucket * P];
+    hub1 = ko[kHubBucket * P + P];
+    nhubs = hub1 - hub0;
+    if (nhubs > 0) {
+      hub_layout(g.off, c->list + hub0, nhubs, c->gbase, c->chunk_pre, c->spre, c->tmp, s);
+      CKLAUNCH();
+      hchunks.resize(nhubs + 1);
+      hschunks.resize(nhubs + 1);
+      if (int r = fetch(c, hchunks.data(), c->chunk_pre, hchunks.size() * sizeof(int64_t))) return r;
+      if (int r = fetch(c, hschunks.data(), c->spre, hschunks.size() * sizeof(int64_t))) return r;
+      if (hschunks[nhubs] > c->npart) return fail(c, LOUVAIN_ERR_INTERNAL, "hub partial buffer too small");
+    }
+    return 0;
+  };
+  if (int r = classify(0)) return r;
+  // hub move stamps are iteration numbers of this pass
+  CK(cudaMemsetAsync(c->hmoved, 0, (size_t)g.n * sizeof(int32_t), s));
   LMArgs<W> a;
   memset(&a, 0, sizeof(a));
   a.off = g.off;
@@ -358,6 +398,7 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
         ah.hbase = c->gbase + h0;
         ah.spre = c->spre + h0;
         ah.hkid = c->hkid + h0;
+        ah.hmoved = c->hmoved + h0;
         lm_launch_hubs<W>(ah, wide, async, c->list + hub0 + h0, (int)(h1 - h0), c->chunk_pre + h0,
                           hchunks[h1] - hchunks[h0], c->spre + h0, hschunks[h1] - hschunks[h0], c->aux[kHubBucket]);
       }
@@ -373,6 +414,11 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
         lm_launch_commit<W>(a, cls, s);
       }
       CKLAUNCH();
+    }
+    if (nhubs > 0 && a.prune) {
+      LMArgs<W> am = a;
+      am.hmoved = c->hmoved;
+      lm_launch_hub_mark<W>(am, c->list + hub0, (int)nhubs, c->chunk_pre, hchunks[nhubs], s);
     }
     CK(cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
     if (multi) {
@@ -394,7 +440,9 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
            return 0;
          }()))
       break;
-    if (c->opt.cuda_graphs && it >= 2) {
+    if (reclass == 1 && it > 0)
+      if ((rc = classify(it))) break;
+    if (c->opt.cuda_graphs && reclass != 1 && it >= 2) {
       if (!gexec) {
         if ((rc = [&]() -> int {
                CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -519,8 +567,10 @@ int aggregate(louvain_ctx* c, const PassState& g, int64_t k, PassState* next, st
   const int64_t G = c->G;
   const int dst = g.widx == 0 ? 1 : 0;
   coarse_degrees(c->used, c->newid, c->sig, g.n, c->Knext, s);
-  agg_group_members(c->level, g.n, k, c->cnt, c->cstart, c->fill, c->members, c->tmp, s);
+  agg_group_members(c->level, g.n, k, c->cnt, c->cstart, c->fill, c->members, c->inv, c->tmp, s);
   agg_member_prefix(g.off, c->members, g.n, c->mdeg, c->mpre, c->tmp, s);
+  agg_relabel<W, W2>(g.off, g.col, (const W*)g.w, g.n, g.nnz, c->level, c->inv, c->mpre, c->crow, c->tcol,
+                     (W2*)c->tw, s);
   agg_keys(c->cstart, c->mpre, k, c->key, s);
   stable_partition(c->key, k, kAggBuckets + 1, c->list, c->key_off, c->tmp, s);
   CKLAUNCH();
@@ -544,6 +594,7 @@ int aggregate(louvain_ctx* c, const PassState& g, int64_t k, PassState* next, st
   a.gkeys = c->gkeys;
   a.gvals = c->gvals;
   a.lsum = c->acc + 6;
+  a.glo = c->glo;
   a.error = c->flags;
   // communities whose members have no edge get empty rows
   CK(cudaMemsetAsync(c->rlen, 0, (k + 1) * sizeof(int64_t), s));
@@ -561,7 +612,8 @@ int aggregate(louvain_ctx* c, const PassState& g, int64_t k, PassState* next, st
     agg_launch_bucket<W, W2>(a, b, c->list + ko[b], (int)(ko[b + 1] - ko[b]), s);
   const int64_t ng = ko[kAggGlobal + 1] - ko[kAggGlobal];
   if (ng > 0) {
-    agg_global_layout(c->cstart, c->mpre, c->list + ko[kAggGlobal], ng, c->gbase, c->chunk_pre, c->spre, c->tmp, s);
+    agg_global_layout(c->cstart, c->mpre, c->list + ko[kAggGlobal], ng, k, multi ? c->gid_next : nullptr,
+                      multi ? c->vo_next : nullptr, c->gbase, c->chunk_pre, c->spre, c->glo, c->tmp, s);
     int64_t nchunks = 0, nschunks = 0;
     CKLAUNCH();
     if (int r = fetch(c, &nchunks, c->chunk_pre + ng, sizeof(int64_t))) return r;
@@ -757,18 +809,13 @@ int run_pass(louvain_ctx* c, const PassState& g, int pass, double* tol, bool wid
   return 0;
 }
 
-int run_all(louvain_ctx* c) {
+// Per-run state of pass 0: degrees, M and the singleton numerators were
+// found when the graph was loaded.
+int init_run_state(louvain_ctx* c) {
   cudaStream_t s = c->stream;
   const int64_t G = c->G;
   c->iters.clear();
   c->passes.clear();
-  memset(&c->stats, 0, sizeof(c->stats));
-  c->Q = 0;
-  const long long launches0 = launches_so_far();
-  CK(cudaEventRecord(c->ev[6], s));
-  iota_i32(c->top, c->n0, s);
-  // pass-0 degrees, M and the singleton numerators were found when the
-  // graph was loaded
   CK(cudaMemcpyAsync(c->K, c->K0, c->n0 * sizeof(long long), cudaMemcpyDeviceToDevice, s));
   c->M = c->M0;
   for (int64_t q = 0; q < G; ++q) {
@@ -789,6 +836,18 @@ int run_all(louvain_ctx* c) {
     CK(cudaMemcpyAsync(c->vo, c->vo0, (G + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(c->vo_top, c->vo0, (G + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
   }
+  return 0;
+}
+
+int run_all(louvain_ctx* c) {
+  cudaStream_t s = c->stream;
+  const int64_t G = c->G;
+  memset(&c->stats, 0, sizeof(c->stats));
+  c->Q = 0;
+  const long long launches0 = launches_so_far();
+  CK(cudaEventRecord(c->ev[6], s));
+  iota_i32(c->top, c->n0, s);
+  if (int r = init_run_state(c)) return r;
   const bool wide = c->M >= (1ll << 31);           // M^2 >= 2^62: 128-bit gains
   const bool coarse64 = c->M >= (1ll << 31) - 1;   // coarse weights can exceed int32
   PassState g{c->n0, c->nnz0, c->off0, c->col0, (void*)c->w0, -1};
@@ -828,6 +887,66 @@ int run_all(louvain_ctx* c) {
   return 0;
 }
 
+// Device time of the first local-moving iteration of pass 0 under mapping th
+// (the run's own mode, classes and options; the state is reset by the next run).
+int tune_trial(louvain_ctx* c, const LMThresholds& th, float* ms) {
+  cudaStream_t s = c->stream;
+  if (int r = init_run_state(c)) return r;
+  c->thr = th;
+  PassState g{c->n0, c->nnz0, c->off0, c->col0, (void*)c->w0, -1};
+  const bool wide = c->M >= (1ll << 31);
+  pass_init(g.n, c->K, c->memb, c->sig, c->csize, c->stamp[0], c->stamp[1], s);
+  CKLAUNCH();
+  int iters = 0;
+  int64_t edges = 0, visited = 0;
+  CK(cudaEventRecord(c->ev[0], s));
+  if (int r = local_moving<int32_t>(c, g, 0, c->opt.tolerance, wide, &iters, &edges, &visited)) return r;
+  CK(cudaEventRecord(c->ev[1], s));
+  CK(cudaEventSynchronize(c->ev[1]));
+  cudaEventElapsedTime(ms, c->ev[0], c->ev[1]);
+  return 0;
+}
+
+// Coordinate descent over the local-moving degree thresholds, from the
+// current mapping: each threshold in turn takes each of its candidate values
+// (within its kernel's capacity and between its neighbours) and keeps the
+// fastest first iteration (best of two trials, at least 2% faster to change).
+int autotune(louvain_ctx* c, float* best_ms) {
+  static const int32_t cand[5][3] = {{4, 8, 0}, {16, 32, 0}, {64, 128, 0}, {256, 512, 1024}, {2048, 4096, 0}};
+  const louvain_options saved = c->opt;
+  c->opt.max_iterations = 1;
+  LMThresholds best = c->thr;
+  auto timed = [&](const LMThresholds& th, float* out) -> int {
+    float t0 = 0, t1 = 0;
+    if (int r = tune_trial(c, th, &t0)) return r;
+    if (int r = tune_trial(c, th, &t1)) return r;
+    *out = std::min(t0, t1);
+    return 0;
+  };
+  float bms = 0;
+  int rc = timed(best, &bms);
+  for (int b = 0; b < 5 && !rc; ++b) {
+    for (int k = 0; k < 3 && !rc; ++k) {
+      const int32_t v = cand[b][k];
+      if (v <= 0 || v == best.t[b] || v > kLMCap[b]) continue;
+      if ((b > 0 && v <= best.t[b - 1]) || (b < 4 && v >= best.t[b + 1])) continue;
+      LMThresholds th = best;
+      th.t[b] = v;
+      float ms = 0;
+      rc = timed(th, &ms);
+      if (!rc && ms < 0.98f * bms) {
+        best = th;
+        bms = ms;
+      }
+    }
+  }
+  c->opt = saved;
+  c->thr = best;
+  c->ran = false;
+  if (best_ms) *best_ms = bms;
+  return rc;
+}
+
 }  // namespace
 
 // Device arena for graphs of up to n vertices and nnz entries (every buffer
@@ -863,6 +982,8 @@ int alloc_arena(louvain_ctx* c, int64_t n, int64_t nnz) {
   ALLOC(c->cstart, N1);
   ALLOC(c->fill, N1);
   ALLOC(c->members, n);
+  ALLOC(c->inv, n);
+  ALLOC(c->crow, (n + nnz) / kRelabelChunk + 3);
   ALLOC(c->mdeg, n);
   ALLOC(c->mpre, N1);
   ALLOC(c->rlen, N1);
@@ -873,9 +994,11 @@ int alloc_arena(louvain_ctx* c, int64_t n, int64_t nnz) {
   ALLOC(c->gbase, N1);
   ALLOC(c->chunk_pre, N1);
   ALLOC(c->spre, N1);
+  ALLOC(c->glo, N1);
   ALLOC(c->hkid, N1);
+  ALLOC(c->hmoved, N1);
   // slot chunks of all hubs: sum of ceil(2 deg / kSlotChunk) <= 2 nnz / kSlotChunk + #hubs
-  c->npart = 2 * nnz / kSlotChunk + nnz / 4096 + 16;
+  c->npart = 2 * nnz / kSlotChunk + n + 16;   // every hub has at least one slot chunk
   ALLOC(c->hpart, 2 * c->npart);
   ALLOC(c->hpart_c, c->npart);
   {
@@ -955,6 +1078,7 @@ int louvain_default_options(louvain_options* o) {
   o->validate = 1;
   o->record_levels = 0;
   o->cuda_graphs = 0;
+  o->reclass = 3;
   return 0;
 }
 
@@ -1151,6 +1275,45 @@ int louvain_load_batch(louvain_ctx* c, int64_t num_graphs, const int64_t* graph_
   return load_graphs(c, num_graphs, vo.data(), n, nnz, offsets, cols, weights, ptr_kind);
 }
 
+
+int louvain_set_mapping(louvain_ctx* c, const int32_t* thresholds) {
+  if (!c) return LOUVAIN_ERR_INVALID_ARG;
+  LMThresholds th = {{kLMCap[0], kLMCap[1], kLMCap[2], kLMCap[3], kLMCap[4]}};
+  if (thresholds) {
+    for (int b = 0; b < 5; ++b) {
+      if (thresholds[b] < 1 || thresholds[b] > kLMCap[b] || (b > 0 && thresholds[b] <= thresholds[b - 1]))
+        return fail(c, LOUVAIN_ERR_INVALID_ARG, "thresholds must increase and stay within each kernel's capacity");
+      th.t[b] = thresholds[b];
+    }
+  }
+  c->thr = th;
+  return 0;
+}
+
+int louvain_get_mapping(louvain_ctx* c, int32_t* thresholds) {
+  if (!c || !thresholds) return LOUVAIN_ERR_INVALID_ARG;
+  for (int b = 0; b < 5; ++b) thresholds[b] = c->thr.t[b];
+  return 0;
+}
+
+int louvain_autotune(louvain_ctx* c, int32_t* thresholds, double* ms) {
+  if (!c) return LOUVAIN_ERR_INVALID_ARG;
+  if (!c->loaded) return fail(c, LOUVAIN_ERR_STATE, "no graph loaded");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, LOUVAIN_ERR_CUDA, "cudaSetDevice failed");
+  float best = 0;
+  if (c->M0 > 0) {
+    int r = autotune(c, &best);
+    if (r) {
+      c->tables_dirty = true;
+      c->loaded = false;
+      return r;
+    }
+  }
+  if (thresholds)
+    for (int b = 0; b < 5; ++b) thresholds[b] = c->thr.t[b];
+  if (ms) *ms = best;
+  return 0;
+}
 
 int louvain_run(louvain_ctx* c) {
   if (!c) return LOUVAIN_ERR_INVALID_ARG;

@@ -9,8 +9,22 @@ namespace gbl {
 // Degree classes of the local-moving phase (see local_move.cu).
 constexpr int kBuckets = 6;          // 0 thread, 1 warp/64, 2 warp/256, 3 block/2k, 4 block/8k, 5 hub
 constexpr int kHubBucket = 5;
-__host__ __device__ inline int lm_bucket_of(int64_t deg) {
-  return deg <= 0 ? -1 : deg <= 8 ? 0 : deg <= 32 ? 1 : deg <= 128 ? 2 : deg <= 1024 ? 3 : deg <= 4096 ? 4 : 5;
+// Degree thresholds of the local-moving mapping: bucket b < 5 takes the
+// degrees in (t[b - 1], t[b]], degrees above t[4] are hubs.  Each t[b] stays
+// within its kernel's capacity kLMCap[b] (register table of 8 entries; shared
+// tables of 64, 256, 2048 and 8192 slots at most half full), so lowering one
+// moves vertices to a wider mapping with a sparser table.  The defaults are
+// the capacities; louvain_autotune picks others by timing.
+struct LMThresholds {
+  int32_t t[5];
+};
+constexpr int32_t kLMCap[5] = {8, 32, 128, 1024, 4096};
+__host__ __device__ inline int lm_bucket_of(int64_t deg, const LMThresholds& th) {
+  if (deg <= 0) return -1;
+#pragma unroll
+  for (int b = 0; b < 5; ++b)
+    if (deg <= th.t[b]) return b;
+  return 5;
 }
 constexpr int64_t kHubChunkEntries = 2048;   // entries per insert block of a hub
 constexpr int64_t kSlotChunk = 4096;         // table slots per scan block (hubs and large communities)
@@ -22,6 +36,7 @@ __host__ __device__ inline int agg_bucket_of(int64_t dsum) {
   return dsum <= 0 ? -1 : dsum <= 32 ? 0 : dsum <= 128 ? 1 : dsum <= 1024 ? 2 : dsum <= 4096 ? 3 : 4;
 }
 constexpr int64_t kAggChunkEntries = 2048;
+constexpr int64_t kRelabelChunk = 1024;     // CSR entries per warp of the relabel kernel
 
 // ------------------------------------------------------ local_move.cu
 template <typename W>
@@ -31,6 +46,10 @@ template <typename W>
 void lm_launch_hubs(const LMArgs<W>& a, bool wide, bool async, const int32_t* hubs, int nhubs,
                     const int64_t* chunk_pre, int64_t nchunks, const int64_t* spre, int64_t nslotchunks,
                     cudaStream_t s);
+// Pruning marks of every hub of the pass's hub list that moved in this iteration.
+template <typename W>
+void lm_launch_hub_mark(const LMArgs<W>& a, const int32_t* hubs, int nhubs, const int64_t* chunk_pre, int64_t nchunks,
+                        cudaStream_t s);
 template <typename W>
 void lm_launch_commit(const LMArgs<W>& a, int64_t max_moves, cudaStream_t s);
 
@@ -49,10 +68,11 @@ size_t partition_tmp_bytes(int64_t n, int nkeys);
 void stable_partition(const int32_t* key, int64_t n, int nkeys, int32_t* out, int64_t* key_off, void* tmp,
                       cudaStream_t s);
 
-// Keys for the local-moving lists: bucket-major, then class (i mod P); vertices
-// of degree 0 get the trailing key nb * P.
+// Keys for the local-moving lists, bucket-major: key[i] = bucket * P + class
+// of vertex i (class = local id mod P, or hash32(local id ^ salt) mod P when
+// salt != 0); vertices of degree 0 get the trailing key kBuckets * P.
 void lm_keys(const int64_t* off, int64_t n, int P, int32_t* key, const int32_t* gid, const int64_t* vo,
-             cudaStream_t s);
+             uint32_t salt, LMThresholds th, cudaStream_t s);
 // For the hub list: per hub its table base (2 * degree slots), the prefix of
 // its insert chunks and the prefix of its slot chunks (each nhubs + 1 long).
 void hub_layout(const int64_t* off, const int32_t* hubs, int64_t nhubs, int64_t* hbase, int64_t* chunk_pre,
@@ -105,21 +125,32 @@ struct AggArgs {
   unsigned long long* lsum;  // += weight of every coarse self-loop (sum of L_C)
   const int32_t* cgid;       // several graphs: graph of each coarse vertex (else nullptr)
   unsigned long long* glsum; // several graphs: per-graph sum of L_C (lo, hi)
+  const int64_t* glo;        // global-table communities: first key of a direct table, or -1 (hashed)
   int* error;
 };
+// Members grouped by community (members[cstart[C] ..]), inv[u] = position of u.
 void agg_group_members(const int32_t* level, int64_t n, int64_t k, int64_t* cnt /* k+1 */, int64_t* cstart,
-                       int64_t* fill, int32_t* members, void* tmp, cudaStream_t s);
+                       int64_t* fill, int32_t* members, int32_t* inv, void* tmp, cudaStream_t s);
 void agg_member_prefix(const int64_t* off, const int32_t* members, int64_t n, int64_t* mdeg, int64_t* mpre,
                        void* tmp, cudaStream_t s);
 void agg_keys(const int64_t* cstart, const int64_t* mpre, int64_t k, int32_t* key, cudaStream_t s);
+// Relabelled member rows: tmp entry mpre[inv[u]] + (x - off[u]) = (level[col[x]],
+// w[x]) for every CSR entry x of row u (crow: nnz / kRelabelChunk + 1 ints).
+template <typename W, typename W2>
+void agg_relabel(const int64_t* off, const int32_t* col, const W* wt, int64_t n, int64_t nnz, const int32_t* level,
+                 const int32_t* inv, const int64_t* mpre, int32_t* crow, int32_t* tcol, W2* tw, cudaStream_t s);
 template <typename W, typename W2>
 void agg_launch_bucket(const AggArgs& a, int bucket, const int32_t* comms, int ncomms, cudaStream_t s);
 template <typename W, typename W2>
 void agg_launch_global(const AggArgs& a, const int32_t* comms, int ncomms, const int64_t* gbase,
                        const int64_t* chunk_pre, int64_t nchunks, const int64_t* spre, int64_t nslotchunks,
                        cudaStream_t s);
-void agg_global_layout(const int64_t* cstart, const int64_t* mpre, const int32_t* comms, int64_t ncomms,
-                       int64_t* gbase, int64_t* chunk_pre, int64_t* spre, void* tmp, cudaStream_t s);
+// Table of each global-bucket community: hashed with 2 x its member entries
+// slots, or, when that is at least the number of communities of its graph,
+// direct-indexed by community id (glo[h] = the graph's first community id).
+void agg_global_layout(const int64_t* cstart, const int64_t* mpre, const int32_t* comms, int64_t ncomms, int64_t k,
+                       const int32_t* cgid, const int64_t* cvo, int64_t* gbase, int64_t* chunk_pre, int64_t* spre,
+                       int64_t* glo, void* tmp, cudaStream_t s);
 template <typename W2>
 void agg_compact(const int64_t* cstart, const int64_t* mpre, const int64_t* rlen, const int64_t* coff, int64_t k,
                  const int32_t* tcol, const W2* tw, int32_t* ocol, W2* ow, cudaStream_t s);

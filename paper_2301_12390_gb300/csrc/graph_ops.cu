@@ -232,11 +232,13 @@ void stable_partition(const int32_t* key, int64_t n, int nkeys, int32_t* out, in
 // --------------------------------------------------- local-moving lists
 
 __global__ void lm_keys_k(const int64_t* __restrict__ off, int64_t n, int P, int32_t* key,
-                          const int32_t* __restrict__ gid, const int64_t* __restrict__ vo) {
+                          const int32_t* __restrict__ gid, const int64_t* __restrict__ vo, uint32_t salt,
+                          LMThresholds th) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    int b = lm_bucket_of(off[i + 1] - off[i]);
+    int b = lm_bucket_of(off[i + 1] - off[i], th);
     const int64_t local = gid ? i - vo[gid[i]] : i;   // classes by id within the vertex's graph
-    key[i] = b < 0 ? kBuckets * P : b * P + (int)(local % P);
+    const int cls = salt ? (int)(hash32((uint32_t)local ^ salt) % (uint32_t)P) : (int)(local % P);
+    key[i] = b < 0 ? kBuckets * P : b * P + cls;
   }
 }
 
@@ -247,8 +249,8 @@ static unsigned grid1d(int64_t n, int per = kT) {
 }
 
 void lm_keys(const int64_t* off, int64_t n, int P, int32_t* key, const int32_t* gid, const int64_t* vo,
-             cudaStream_t s) {
-  if (n > 0) (count_launch(), lm_keys_k<<<grid1d(n), kT, 0, s>>>(off, n, P, key, gid, vo));
+             uint32_t salt, LMThresholds th, cudaStream_t s) {
+  if (n > 0) (count_launch(), lm_keys_k<<<grid1d(n), kT, 0, s>>>(off, n, P, key, gid, vo, salt, th));
 }
 
 __global__ void hub_sizes_k(const int64_t* off, const int32_t* hubs, int64_t nhubs, int64_t* cap, int64_t* chunks,
@@ -464,21 +466,22 @@ __global__ void count_members_k(const int32_t* level, int64_t n, int64_t* cnt) {
     atomicAdd((unsigned long long*)(cnt + level[i]), 1ull);
 }
 __global__ void place_members_k(const int32_t* level, int64_t n, const int64_t* cstart, int64_t* fill,
-                                int32_t* members) {
+                                int32_t* members, int32_t* inv) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int32_t C = level[i];
     int64_t pos = cstart[C] + (int64_t)atomicAdd((unsigned long long*)(fill + C), 1ull);
     members[pos] = (int32_t)i;
+    inv[i] = (int32_t)pos;
   }
 }
 
 void agg_group_members(const int32_t* level, int64_t n, int64_t k, int64_t* cnt, int64_t* cstart, int64_t* fill,
-                       int32_t* members, void* tmp, cudaStream_t s) {
+                       int32_t* members, int32_t* inv, void* tmp, cudaStream_t s) {
   cudaMemsetAsync(cnt, 0, (k + 1) * sizeof(int64_t), s);
   cudaMemsetAsync(fill, 0, (k + 1) * sizeof(int64_t), s);
   if (n > 0) (count_launch(), count_members_k<<<grid1d(n), kT, 0, s>>>(level, n, cnt));
   scan_i64(cnt, cstart, k, cstart + k, tmp, s);
-  if (n > 0) (count_launch(), place_members_k<<<grid1d(n), kT, 0, s>>>(level, n, cstart, fill, members));
+  if (n > 0) (count_launch(), place_members_k<<<grid1d(n), kT, 0, s>>>(level, n, cstart, fill, members, inv));
 }
 
 __global__ void member_degrees_k(const int64_t* off, const int32_t* members, int64_t n, int64_t* mdeg) {
@@ -511,66 +514,127 @@ __device__ __forceinline__ void add_self_loop(const AggArgs& a, int32_t C, unsig
   else atomicAdd(a.lsum, w);
 }
 
-// Member position of virtual entry t of a community: the last p in [lo, hi)
-// with mpre[p] <= t.
-__device__ __forceinline__ int64_t member_of(const int64_t* __restrict__ mpre, int64_t lo, int64_t hi, int64_t t) {
-  while (hi - lo > 1) {
-    int64_t mid = (lo + hi) >> 1;
-    if (mpre[mid] <= t) lo = mid; else hi = mid;
-  }
-  return lo;
-}
+// ---- relabel: every CSR entry x = (u, v, w) of the pass graph is written to
+// the tmp rows, which hold the communities' member rows back to back:
+// position mpre[inv[u]] + (x - off[u]) gets (level[v], w).  The hash kernels
+// below then read each community's entries contiguously.
 
-// Staged members of a tile of virtual entries: spre[j] = mpre of member
-// p0 + j, sstart[j] = off[member] - mpre, so entry t of member j is CSR entry
-// sstart[j] + t.  Lookups then search shared memory.
-__device__ __forceinline__ int staged_of(const int64_t* spre, int nm, int64_t t) {
-  int lo = 0, hi = nm;
-  while (hi - lo > 1) {
-    int mid = (lo + hi) >> 1;
-    if (spre[mid] <= t) lo = mid; else hi = mid;
-  }
-  return lo;
-}
-
-template <typename W>
-__device__ __forceinline__ void staged_entry(const AggArgs& a, const int64_t* spre, const int64_t* sstart, int nm,
-                                             int64_t t, int32_t* D, unsigned long long* w) {
-  const int j = staged_of(spre, nm, t);
-  const int64_t x = sstart[j] + t;
-  *D = a.level[a.col[x]];
-  *w = (unsigned long long)((const W*)a.wt)[x];
-}
-
-// Stage members [p0, p0 + nm) (called by all threads of a group of `nthr`
-// threads with index `tid`).
-__device__ __forceinline__ void stage_members(const AggArgs& a, int64_t p0, int nm, int64_t* spre, int64_t* sstart,
-                                              int tid, int nthr) {
-  for (int j = tid; j < nm; j += nthr) {
-    const int64_t p = p0 + j;
-    const int64_t pre = a.mpre[p];
-    spre[j] = pre;
-    sstart[j] = a.off[a.members[p]] - pre;
+// Merge-path split of the rows and entries: chunk c starts at diagonal
+// c * kRelabelChunk of the sequence "row r ends after entry off[r + 1] - 1",
+// i.e. at row crow[c] = the last r in [0, n] with r + off[r] <= c * kRelabelChunk
+// and entry c * kRelabelChunk - crow[c]; every chunk spans at most
+// kRelabelChunk rows plus entries (crow has nchunks + 1 elements).
+__global__ void chunk_rows_k(const int64_t* __restrict__ off, int64_t n, int64_t nchunks, int32_t* crow) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c <= nchunks;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t D = c * kRelabelChunk;
+    int64_t lo = 0, hi = n + 1;
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (mid + off[mid] <= D) lo = mid; else hi = mid;
+    }
+    crow[c] = (int32_t)lo;
   }
 }
 
-template <typename W>
-__device__ __forceinline__ void virtual_entry(const AggArgs& a, int64_t cs, int64_t ce, int64_t t, int32_t* D,
-                                              unsigned long long* w) {
-  int64_t p = member_of(a.mpre, cs, ce, t);
-  int32_t u = a.members[p];
-  int64_t x = a.off[u] + (t - a.mpre[p]);
-  *D = a.level[a.col[x]];
-  *w = (unsigned long long)((const W*)a.wt)[x];
+// One warp per merge-path chunk.  It walks the chunk's rows 32 at a time (lane l holds row r + l's offset and destination
+// shift); each lane finds the row of its entry among the 32 by a shuffle
+// search, and U entries per lane are loaded and gathered before any store.
+template <typename W, typename W2>
+__global__ void __launch_bounds__(256) agg_relabel_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                                                     const W* __restrict__ wt, int64_t n, int64_t nnz,
+                                                     const int32_t* __restrict__ level, const int32_t* __restrict__ inv,
+                                                     const int64_t* __restrict__ mpre, const int32_t* __restrict__ crow,
+                                                     int64_t nchunks, int32_t* __restrict__ tcol, W2* __restrict__ tw) {
+  constexpr int U = 4;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += warps) {
+    const int64_t X0 = c * kRelabelChunk - crow[c];
+    const int64_t X1 = min(nnz, (c + 1) * kRelabelChunk - crow[c + 1]);
+    for (int64_t r = crow[c];; r += kWarp) {
+      const int64_t u = r + lane;
+      const int64_t o = off[min(u, n)];
+      const int64_t wend = __shfl_sync(0xffffffffu, off[min(r + kWarp, n)], 0);
+      const int64_t shift = u < n ? mpre[inv[u]] - o : 0;
+      const int64_t xs = max(X0, __shfl_sync(0xffffffffu, o, 0)), xe = min(X1, wend);
+      for (int64_t x0 = xs; x0 < xe; x0 += U * kWarp) {
+        int64_t x[U], dst[U];
+        int32_t v[U];
+        W w[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          x[k] = x0 + k * kWarp + lane;
+          int rr = 0;
+#pragma unroll
+          for (int step = 16; step >= 1; step >>= 1) {
+            const int cand = rr + step;
+            if (__shfl_sync(0xffffffffu, o, cand) <= x[k]) rr = cand;
+          }
+          dst[k] = x[k] + __shfl_sync(0xffffffffu, shift, rr);
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          v[k] = x[k] < xe ? col[x[k]] : 0;
+          w[k] = x[k] < xe ? wt[x[k]] : (W)0;
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) v[k] = x[k] < xe ? level[v[k]] : 0;
+#pragma unroll
+        for (int k = 0; k < U; ++k)
+          if (x[k] < xe) {
+            tcol[dst[k]] = v[k];
+            tw[dst[k]] = (W2)w[k];
+          }
+      }
+      if (wend >= X1) break;
+    }
+  }
 }
 
-template <typename W, typename W2, int CAP>
+template <typename W, typename W2>
+void agg_relabel(const int64_t* off, const int32_t* col, const W* wt, int64_t n, int64_t nnz, const int32_t* level,
+                 const int32_t* inv, const int64_t* mpre, int32_t* crow, int32_t* tcol, W2* tw, cudaStream_t s) {
+  if (n <= 0 || nnz <= 0) return;
+  const int64_t nchunks = (n + nnz + kRelabelChunk - 1) / kRelabelChunk;
+  (count_launch(), chunk_rows_k<<<grid1d(nchunks + 1), kT, 0, s>>>(off, n, nchunks, crow));
+  int64_t blocks = (nchunks + 7) / 8;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  (count_launch(), agg_relabel_k<W, W2><<<(unsigned)blocks, 256, 0, s>>>(off, col, wt, n, nnz, level, inv, mpre, crow,
+                                                                         nchunks, tcol, tw));
+}
+template void agg_relabel<int32_t, int32_t>(const int64_t*, const int32_t*, const int32_t*, int64_t, int64_t,
+                                            const int32_t*, const int32_t*, const int64_t*, int32_t*, int32_t*,
+                                            int32_t*, cudaStream_t);
+template void agg_relabel<int32_t, int64_t>(const int64_t*, const int32_t*, const int32_t*, int64_t, int64_t,
+                                            const int32_t*, const int32_t*, const int64_t*, int32_t*, int32_t*,
+                                            int64_t*, cudaStream_t);
+template void agg_relabel<int64_t, int64_t>(const int64_t*, const int32_t*, const int64_t*, int64_t, int64_t,
+                                            const int32_t*, const int32_t*, const int64_t*, int32_t*, int32_t*,
+                                            int64_t*, cudaStream_t);
+
+// Load U consecutive relabelled entries per lane (stride `stride`) of
+// [t0, t1): D = kEmpty past the end.
+template <typename W2, int U>
+__device__ __forceinline__ void load_entries(const AggArgs& a, int64_t t0, int64_t t1, int stride, int32_t* D,
+                                             unsigned long long* w) {
+#pragma unroll
+  for (int k = 0; k < U; ++k) {
+    const int64_t t = t0 + (int64_t)k * stride;
+    D[k] = t < t1 ? a.tcol[t] : kEmpty;
+    w[k] = t < t1 ? (unsigned long long)((const W2*)a.tw)[t] : 0ull;
+  }
+}
+
+// Communities with at most CAP / 2 member entries: a warp each, table in
+// shared memory; the coarse row is written back over the community's tmp
+// entries (all of them are read before the first write).
+template <typename W2, int CAP>
 __global__ void __launch_bounds__(256) agg_warp_k(AggArgs a, const int32_t* __restrict__ comms, int ncomms) {
   constexpr int WPB = 8;
-  constexpr int MAXM = CAP / 2;   // members <= dsum <= CAP / 2
+  constexpr int U = CAP / 2 / kWarp > 0 ? CAP / 2 / kWarp : 1;
   __shared__ int32_t skeys[WPB][CAP];
   __shared__ unsigned long long svals[WPB][CAP];
-  __shared__ int64_t sp[WPB][MAXM], ss[WPB][MAXM];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   int32_t* keys = skeys[wib];
   unsigned long long* vals = svals[wib];
@@ -579,25 +643,14 @@ __global__ void __launch_bounds__(256) agg_warp_k(AggArgs a, const int32_t* __re
   bool ok = true;
   for (int ci = blockIdx.x * WPB + wib; ci < ncomms; ci += gridDim.x * WPB) {
     int32_t C = comms[ci];
-    int64_t cs = a.cstart[C], ce = a.cstart[C + 1];
-    int64_t vs = a.mpre[cs], ve = a.mpre[ce];
-    const int nm = (int)(ce - cs);
-    if (nm <= MAXM) {
-      stage_members(a, cs, nm, sp[wib], ss[wib], lane, kWarp);
-      __syncwarp();
-      for (int64_t t = vs + lane; t < ve; t += kWarp) {
-        int32_t D;
-        unsigned long long w;
-        staged_entry<W>(a, sp[wib], ss[wib], nm, t, &D, &w);
-        ok &= table_add_pow2<CAP, unsigned long long>(keys, vals, D, w);
-      }
-    } else {
-      for (int64_t t = vs + lane; t < ve; t += kWarp) {
-        int32_t D;
-        unsigned long long w;
-        virtual_entry<W>(a, cs, ce, t, &D, &w);
-        ok &= table_add_pow2<CAP, unsigned long long>(keys, vals, D, w);
-      }
+    const int64_t vs = a.mpre[a.cstart[C]], ve = a.mpre[a.cstart[C + 1]];
+    for (int64_t t0 = vs + lane; t0 < ve; t0 += U * kWarp) {
+      int32_t D[U];
+      unsigned long long w[U];
+      load_entries<W2, U>(a, t0, ve, kWarp, D, w);
+#pragma unroll
+      for (int k = 0; k < U; ++k)
+        if (D[k] != kEmpty) ok &= table_add_pow2<CAP, unsigned long long>(keys, vals, D[k], w[k]);
     }
     __syncwarp();
     int64_t base = 0;
@@ -621,46 +674,31 @@ __global__ void __launch_bounds__(256) agg_warp_k(AggArgs a, const int32_t* __re
   if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicOr(a.error, kErrProbe);
 }
 
-template <typename W, typename W2, int CAP, int THREADS>
+// Communities with at most CAP / 2 member entries, a block each.
+template <typename W2, int CAP, int THREADS>
 __global__ void __launch_bounds__(THREADS) agg_block_k(AggArgs a, const int32_t* __restrict__ comms, int ncomms) {
-  constexpr int TILE = 2 * THREADS;
-  // dynamic shared memory: values (CAP u64), staged member prefixes and
-  // starts (TILE i64 each), keys (CAP i32)
+  constexpr int U = 4;
+  // dynamic shared memory: values (CAP u64), keys (CAP i32)
   extern __shared__ unsigned long long adyn[];
   unsigned long long* vals = adyn;
-  int64_t* spre = (int64_t*)(adyn + CAP);
-  int64_t* sstart = spre + TILE;
-  int32_t* keys = (int32_t*)(sstart + TILE);
+  int32_t* keys = (int32_t*)(adyn + CAP);
   __shared__ int wtot[THREADS / kWarp];
-  __shared__ int64_t s_p0;
-  __shared__ int s_nm;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int t = threadIdx.x; t < CAP; t += THREADS) { keys[t] = kEmpty; vals[t] = 0; }
   __syncthreads();
   bool ok = true;
   for (int ci = blockIdx.x; ci < ncomms; ci += gridDim.x) {
     int32_t C = comms[ci];
-    int64_t cs = a.cstart[C], ce = a.cstart[C + 1];
-    int64_t vs = a.mpre[cs], ve = a.mpre[ce];
-    for (int64_t y = vs; y < ve; y += TILE) {
-      const int64_t y1 = min(ve, y + TILE);
-      if (threadIdx.x == 0) {
-        s_p0 = member_of(a.mpre, cs, ce, y);
-        s_nm = (int)(member_of(a.mpre, cs, ce, y1 - 1) - s_p0 + 1);
-      }
-      __syncthreads();
-      const int nm = s_nm;
-      if (nm <= TILE) stage_members(a, s_p0, nm, spre, sstart, threadIdx.x, THREADS);
-      __syncthreads();
-      for (int64_t t = y + threadIdx.x; t < y1; t += THREADS) {
-        int32_t D;
-        unsigned long long w;
-        if (nm <= TILE) staged_entry<W>(a, spre, sstart, nm, t, &D, &w);
-        else virtual_entry<W>(a, cs, ce, t, &D, &w);
-        ok &= table_add_pow2<CAP, unsigned long long>(keys, vals, D, w);
-      }
-      __syncthreads();
+    const int64_t vs = a.mpre[a.cstart[C]], ve = a.mpre[a.cstart[C + 1]];
+    for (int64_t t0 = vs + threadIdx.x; t0 < ve; t0 += U * THREADS) {
+      int32_t D[U];
+      unsigned long long w[U];
+      load_entries<W2, U>(a, t0, ve, THREADS, D, w);
+#pragma unroll
+      for (int k = 0; k < U; ++k)
+        if (D[k] != kEmpty) ok &= table_add_pow2<CAP, unsigned long long>(keys, vals, D[k], w[k]);
     }
+    __syncthreads();
     int64_t base = 0;
     for (int t0 = 0; t0 < CAP; t0 += THREADS) {
       int t = t0 + threadIdx.x;
@@ -690,9 +728,10 @@ __global__ void __launch_bounds__(THREADS) agg_block_k(AggArgs a, const int32_t*
   if (!ok) atomicOr(a.error, kErrProbe);
 }
 
-// Large communities: blocks are (community, 2048-virtual-entry chunk) pairs;
-// each sums its chunk per neighbour community in shared memory, then adds
-// each distinct one to the community's global table of 2 * dsum slots.
+// Large communities: blocks are (community, kAggChunkEntries-entry chunk)
+// pairs; each sums its chunk per neighbour community in shared memory, then
+// adds each distinct one to the community's global table (hashed, 2 x its
+// entries slots, or direct-indexed by community id).
 __device__ __forceinline__ int find_item(const int64_t* __restrict__ pre, int nitems, int64_t blk) {
   int lo = 0, hi = nitems;
   while (hi - lo > 1) {
@@ -702,55 +741,48 @@ __device__ __forceinline__ int find_item(const int64_t* __restrict__ pre, int ni
   return lo;
 }
 
-template <typename W>
+template <typename W2>
 __global__ void __launch_bounds__(256) agg_global_insert_k(AggArgs a, const int32_t* __restrict__ comms, int ncomms,
                                                            const int64_t* __restrict__ gbase,
                                                            const int64_t* __restrict__ chunk_pre) {
   constexpr int CAP = 2 * (int)kAggChunkEntries;
-  // dynamic shared memory: values (CAP u64), staged prefixes and starts
-  // (chunk i64 each), keys (CAP i32)
+  constexpr int U = (int)kAggChunkEntries / 256;
+  // dynamic shared memory: values (CAP u64), keys (CAP i32)
   extern __shared__ unsigned long long gdyn[];
   unsigned long long* svals = gdyn;
-  int64_t* spre = (int64_t*)(gdyn + CAP);
-  int64_t* sstart = spre + kAggChunkEntries;
-  int32_t* skeys = (int32_t*)(sstart + kAggChunkEntries);
+  int32_t* skeys = (int32_t*)(gdyn + CAP);
   const int h = find_item(chunk_pre, ncomms, blockIdx.x);
   const int32_t C = comms[h];
-  const int64_t cs = a.cstart[C], ce = a.cstart[C + 1];
-  const int64_t vs = a.mpre[cs], ve = a.mpre[ce];
+  const int64_t vs = a.mpre[a.cstart[C]], ve = a.mpre[a.cstart[C + 1]];
   const int64_t q = (int64_t)blockIdx.x - chunk_pre[h];
   const int64_t base = gbase[h];
   const uint32_t cap = (uint32_t)(gbase[h + 1] - base);
   for (int t = threadIdx.x; t < CAP; t += blockDim.x) { skeys[t] = kEmpty; svals[t] = 0; }
-  __syncthreads();
   const int64_t t0 = vs + q * kAggChunkEntries, t1 = min(ve, t0 + kAggChunkEntries);
-  __shared__ int64_t s_p0;
-  __shared__ int s_nm;
-  if (threadIdx.x == 0) {
-    s_p0 = member_of(a.mpre, cs, ce, t0);
-    s_nm = (int)(member_of(a.mpre, cs, ce, t1 - 1) - s_p0 + 1);
-  }
-  __syncthreads();
-  const int nm = s_nm;
-  constexpr int MAXM = (int)kAggChunkEntries;
-  if (nm <= MAXM) stage_members(a, s_p0, nm, spre, sstart, threadIdx.x, blockDim.x);
+  int32_t D[U];
+  unsigned long long w[U];
+  load_entries<W2, U>(a, t0 + threadIdx.x, t1, 256, D, w);
   __syncthreads();
   bool ok = true;
-  for (int64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
-    int32_t D;
-    unsigned long long w;
-    if (nm <= MAXM) staged_entry<W>(a, spre, sstart, nm, t, &D, &w);
-    else virtual_entry<W>(a, cs, ce, t, &D, &w);
-    ok &= table_add_pow2<CAP, unsigned long long>(skeys, svals, D, w);
-  }
+#pragma unroll
+  for (int k = 0; k < U; ++k)
+    if (D[k] != kEmpty) ok &= table_add_pow2<CAP, unsigned long long>(skeys, svals, D[k], w[k]);
   __syncthreads();
   int32_t* keys = a.gkeys + base;
   unsigned long long* vals = a.gvals + base;
+  const int64_t lo = a.glo[h];
   for (int t = threadIdx.x; t < CAP; t += blockDim.x) {
-    int32_t D = skeys[t];
-    if (D == kEmpty) continue;
-    bool fresh;
-    ok &= gtable_add(keys, vals, cap, D, svals[t], &fresh);
+    int32_t Dk = skeys[t];
+    if (Dk == kEmpty) continue;
+    if (lo >= 0) {   // direct table: slot Dk - lo (same-value key stores may race)
+      const int64_t y = (int64_t)Dk - lo;
+      if (y < 0 || y >= (int64_t)cap) { ok = false; continue; }
+      if (keys[y] != Dk) keys[y] = Dk;
+      atomicAdd(&vals[y], svals[t]);
+    } else {
+      bool fresh;
+      ok &= gtable_add(keys, vals, cap, Dk, svals[t], &fresh);
+    }
   }
   if (!ok) atomicOr(a.error, kErrProbe);
 }
@@ -812,26 +844,26 @@ void agg_launch_bucket(const AggArgs& a, int bucket, const int32_t* comms, int n
   if (ncomms <= 0) return;
   switch (bucket) {
     case 0: {
-      auto k = agg_warp_k<W, W2, 64>;
+      auto k = agg_warp_k<W2, 64>;
       (count_launch(), k<<<agrid(k, 256, 0, (ncomms + 7) / 8), 256, 0, s>>>(a, comms, ncomms));
       break;
     }
     case 1: {
-      auto k = agg_warp_k<W, W2, 256>;
+      auto k = agg_warp_k<W2, 256>;
       (count_launch(), k<<<agrid(k, 256, 0, (ncomms + 7) / 8), 256, 0, s>>>(a, comms, ncomms));
       break;
     }
     case 2: {
       constexpr int CAP = 2048;
-      size_t smem = (size_t)CAP * 12 + 2 * 2 * 128 * 8;
-      auto k = agg_block_k<W, W2, CAP, 128>;
+      size_t smem = (size_t)CAP * 12;
+      auto k = agg_block_k<W2, CAP, 128>;
       (count_launch(), k<<<agrid(k, 128, smem, ncomms), 128, smem, s>>>(a, comms, ncomms));
       break;
     }
     case 3: {
       constexpr int CAP = 8192;
-      size_t smem = (size_t)CAP * 12 + 2 * 2 * 256 * 8;
-      auto k = agg_block_k<W, W2, CAP, 256>;
+      size_t smem = (size_t)CAP * 12;
+      auto k = agg_block_k<W2, CAP, 256>;
       static bool attr = false;
       if (!attr) {
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -849,13 +881,13 @@ void agg_launch_global(const AggArgs& a, const int32_t* comms, int ncomms, const
                        const int64_t* chunk_pre, int64_t nchunks, const int64_t* spre, int64_t nslotchunks,
                        cudaStream_t s) {
   if (ncomms <= 0 || nchunks <= 0) return;
-  const size_t smem = (size_t)(2 * kAggChunkEntries) * 12 + (size_t)kAggChunkEntries * 16;
+  const size_t smem = (size_t)(2 * kAggChunkEntries) * 12;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(agg_global_insert_k<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(agg_global_insert_k<W2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  (count_launch(), agg_global_insert_k<W><<<(unsigned)nchunks, 256, smem, s>>>(a, comms, ncomms, gbase, chunk_pre));
+  (count_launch(), agg_global_insert_k<W2><<<(unsigned)nchunks, 256, smem, s>>>(a, comms, ncomms, gbase, chunk_pre));
   (count_launch(), agg_global_write_k<W2><<<(unsigned)nslotchunks, 256, 0, s>>>(a, comms, ncomms, gbase, spre));
 }
 
@@ -868,18 +900,28 @@ AGG_INST(int32_t, int64_t)
 AGG_INST(int64_t, int64_t)
 
 __global__ void agg_global_sizes_k(const int64_t* cstart, const int64_t* mpre, const int32_t* comms, int64_t ncomms,
-                                   int64_t* cap, int64_t* chunks, int64_t* schunks) {
+                                   int64_t k, const int32_t* cgid, const int64_t* cvo, int64_t* cap, int64_t* chunks,
+                                   int64_t* schunks, int64_t* glo) {
   for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < ncomms; h += (int64_t)gridDim.x * blockDim.x) {
     int32_t C = comms[h];
     int64_t dsum = mpre[cstart[C + 1]] - mpre[cstart[C]];
-    cap[h] = 2 * dsum;
+    int64_t lo = 0, range = k;
+    if (cgid) {
+      const int g = cgid[C];
+      lo = cvo[g];
+      range = cvo[g + 1] - lo;
+    }
+    const bool direct = 2 * dsum >= range;
+    cap[h] = direct ? range : 2 * dsum;
+    glo[h] = direct ? lo : -1;
     chunks[h] = (dsum + kAggChunkEntries - 1) / kAggChunkEntries;
-    schunks[h] = (2 * dsum + kSlotChunk - 1) / kSlotChunk;
+    schunks[h] = (cap[h] + kSlotChunk - 1) / kSlotChunk;
   }
 }
 
-void agg_global_layout(const int64_t* cstart, const int64_t* mpre, const int32_t* comms, int64_t ncomms,
-                       int64_t* gbase, int64_t* chunk_pre, int64_t* spre, void* tmp, cudaStream_t s) {
+void agg_global_layout(const int64_t* cstart, const int64_t* mpre, const int32_t* comms, int64_t ncomms, int64_t k,
+                       const int32_t* cgid, const int64_t* cvo, int64_t* gbase, int64_t* chunk_pre, int64_t* spre,
+                       int64_t* glo, void* tmp, cudaStream_t s) {
   if (ncomms <= 0) {
     cudaMemsetAsync(gbase, 0, sizeof(int64_t), s);
     cudaMemsetAsync(chunk_pre, 0, sizeof(int64_t), s);
@@ -890,7 +932,8 @@ void agg_global_layout(const int64_t* cstart, const int64_t* mpre, const int32_t
   int64_t* chunks = cap + ncomms;
   int64_t* schunks = chunks + ncomms;
   void* stmp = (void*)(schunks + ncomms);
-  (count_launch(), agg_global_sizes_k<<<grid1d(ncomms), kT, 0, s>>>(cstart, mpre, comms, ncomms, cap, chunks, schunks));
+  (count_launch(), agg_global_sizes_k<<<grid1d(ncomms), kT, 0, s>>>(cstart, mpre, comms, ncomms, k, cgid, cvo, cap,
+                                                                       chunks, schunks, glo));
   scan_i64(cap, gbase, ncomms, gbase + ncomms, stmp, s);
   scan_i64(chunks, chunk_pre, ncomms, chunk_pre + ncomms, stmp, s);
   scan_i64(schunks, spre, ncomms, spre + ncomms, stmp, s);

@@ -309,6 +309,35 @@ __global__ void __launch_bounds__(256, 4) lm_warp(LMArgs<W> a, const int32_t* __
 
 // ----------------------------------------- buckets 3-4: block per vertex
 
+// What a block-per-vertex kernel needs of list entry vi before its row.
+struct VertexInfo {
+  int32_t i, d;
+  bool on;        // in range, active and its graph still iterating
+  int graph;
+  int64_t b, e;
+  long long Ki, M;
+};
+
+template <typename W>
+__device__ __forceinline__ VertexInfo vertex_info(const LMArgs<W>& a, const IterView& iv,
+                                                  const int32_t* __restrict__ verts, int nverts, int vi) {
+  VertexInfo v;
+  v.on = false;
+  v.i = 0;
+  v.d = 0;
+  v.graph = 0;
+  v.b = v.e = 0;
+  v.Ki = v.M = 0;
+  if (vi >= nverts) return v;
+  v.i = verts[vi];
+  v.b = a.off[v.i];
+  v.e = a.off[v.i + 1];
+  v.d = a.memb[v.i];
+  v.Ki = a.K[v.i];
+  v.on = is_active(a, iv, v.i) && graph_of(a, v.i, &v.M, &v.graph);
+  return v;
+}
+
 // A decided move waiting for the block to commit it.
 struct PendingMove {
   int32_t i, c, d;
@@ -367,7 +396,8 @@ __device__ __forceinline__ bool decide_move(const LMArgs<W>& a, BlockAcc& acc, i
 // reduces and decides; moves queue in shared memory and are committed by the
 // whole block when the queue fills and at the end.
 template <typename W, bool WIDE, bool ASYNC, int CAP, int THREADS>
-__global__ void __launch_bounds__(THREADS) lm_block(LMArgs<W> a, const int32_t* __restrict__ verts, int nverts) {
+__global__ void __launch_bounds__(THREADS, THREADS <= 128 ? 10 : 2)
+    lm_block(LMArgs<W> a, const int32_t* __restrict__ verts, int nverts) {
   const IterView iv = iter_view(a);
   typedef typename Arith<WIDE>::S S;
   typedef typename TableVal<WIDE>::T V;
@@ -393,15 +423,19 @@ __global__ void __launch_bounds__(THREADS) lm_block(LMArgs<W> a, const int32_t* 
   __syncthreads();
   bool ok = true;
   int p = 0;
+  // The next vertex's list entry, activity, row bounds, community and degree
+  // are loaded while the current one is processed.
+  VertexInfo nx = vertex_info(a, iv, verts, nverts, blockIdx.x);
   for (int vi = blockIdx.x; vi < nverts; vi += gridDim.x) {
-    const int32_t i = verts[vi];
-    if (!is_active(a, iv, i)) continue;   // uniform across the block
-    long long M;
-    int graph;
-    if (!graph_of(a, i, &M, &graph)) continue;
-    const int64_t b = a.off[i], e = a.off[i + 1];
-    const int32_t d = a.memb[i];
-    const long long Ki = a.K[i];
+    const VertexInfo cur = nx;
+    if (!cur.on) {   // uniform across the block
+      nx = vertex_info(a, iv, verts, nverts, vi + gridDim.x);
+      continue;
+    }
+    const int32_t i = cur.i, d = cur.d;
+    const int64_t b = cur.b, e = cur.e;
+    const long long Ki = cur.Ki, M = cur.M;
+    const int graph = cur.graph;
     for (int64_t x0 = b; x0 < e; x0 += U * THREADS) {
       int32_t cc[U];
       unsigned long long ww[U];
@@ -430,6 +464,7 @@ __global__ void __launch_bounds__(THREADS) lm_block(LMArgs<W> a, const int32_t* 
         if (fresh) touched[base + __popc(m & lanemask_lt_lm())] = (uint16_t)h;
       }
     }
+    nx = vertex_info(a, iv, verts, nverts, vi + gridDim.x);
     __syncthreads();   // B1: table complete; warp 0 has finished the previous vertex
     if (q_n >= QCAP) {   // uniform: q_n was last written before this barrier
       flush_moves<W, ASYNC>(a, iv, queue, q_n, threadIdx.x, THREADS);
@@ -489,14 +524,17 @@ __global__ void __launch_bounds__(THREADS) lm_block(LMArgs<W> a, const int32_t* 
 
 // ------------------------------------------------- bucket 5: hub vertices
 //
-// Hub h of a launch owns global table slots [hbase[h], hbase[h] + 2 deg).
+// Hub h of a class owns global table slots [hbase[h] - hbase[0], + 2 deg):
+// every class's tables start at slot 0, so a class reuses the slots the
+// previous class's scan just cleared, which are still in L2.
 // 1. insert: blocks are (hub, 2048-entry chunk) pairs; each sums its chunk
 //    per community in shared memory, then adds each distinct community once
 //    to the hub's global table;
-// 2. kid: K_{i->d} of each hub is read before anything clears the table;
-// 3. scan: blocks are (hub, 4096-slot chunk) pairs; each evaluates the gain
-//    of every occupied slot, clears it, and leaves its chunk's best;
-// 4. final: one block per hub reduces the chunk bests, commits, marks.
+// 2. scan: blocks are (hub, 4096-slot chunk) pairs; each evaluates the gain
+//    of every occupied slot, clears it, and leaves its chunk's best (and
+//    K_{i->d} of the slot holding d);
+// 3. final: one block per hub reduces the chunk bests and commits;
+// 4. mark (once per iteration, all classes): neighbours of the hubs that moved.
 
 constexpr int kHubChunk = (int)kHubChunkEntries;
 
@@ -532,7 +570,7 @@ __global__ void __launch_bounds__(256) lm_hub_insert(LMArgs<W> a, const int32_t*
   for (int t = threadIdx.x; t < CAP; t += blockDim.x) { skeys[t] = kEmpty; svals[t] = 0; }
   __syncthreads();
   const int64_t b = a.off[i], e = a.off[i + 1];
-  const int64_t base = a.hbase[h];
+  const int64_t base = a.hbase[h] - a.hbase[0];   // the class's tables start at slot 0
   const uint32_t cap = (uint32_t)(2 * (e - b));
   const int64_t x0 = b + q * kHubChunk, x1 = min(e, x0 + kHubChunk);
   bool ok = true;
@@ -582,7 +620,7 @@ __global__ void __launch_bounds__(256) lm_hub_scan(LMArgs<W> a, const int32_t* _
   const int64_t q = (int64_t)blockIdx.x - (a.spre[h] - a.spre[0]);
   const int64_t b = a.off[i], e = a.off[i + 1];
   const int64_t cap = 2 * (e - b);
-  const int64_t base = a.hbase[h];
+  const int64_t base = a.hbase[h] - a.hbase[0];
   const int32_t d = a.memb[i];
   const long long Ki = a.K[i];
   const int64_t t0 = q * kSlotChunk, t1 = min(cap, t0 + kSlotChunk);
@@ -637,7 +675,6 @@ __global__ void __launch_bounds__(256) lm_hub_final(LMArgs<W> a, const int32_t* 
   const IterView iv = iter_view(a);
   typedef typename Arith<WIDE>::S S;
   __shared__ BlockAcc acc;
-  __shared__ int s_moved;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   acc_init(acc);
   __syncthreads();
@@ -660,18 +697,31 @@ __global__ void __launch_bounds__(256) lm_hub_final(LMArgs<W> a, const int32_t* 
       if (lane == 0) {
         atomicAdd(&acc.edges, (unsigned long long)(e - b));
         atomicAdd(&acc.visited, 1ull);
-        s_moved = commit_choice<W, WIDE, ASYNC>(a, acc, i, a.memb[i], a.K[i], bg, bc, a.hkid[h], M, graph);
+        const bool moved = commit_choice<W, WIDE, ASYNC>(a, acc, i, a.memb[i], a.K[i], bg, bc, a.hkid[h], M, graph);
         a.hkid[h] = 0;
+        if (moved && a.prune) a.hmoved[h] = iv.iter + 1;   // lm_hub_mark marks its neighbours
       }
     }
-    __syncthreads();
-    if (s_moved && a.prune) {
-      if (threadIdx.x == 0) iv.sw[i] = iv.iter + 1;
-      for (int64_t x = b + threadIdx.x; x < e; x += 256) iv.sw[a.col[x]] = iv.iter + 1;
-    }
-    __syncthreads();
   }
+  __syncthreads();
   acc_flush(acc, a.ctr);
+}
+
+// Pruning marks of the hubs that moved in this iteration (all classes at
+// once; the marks only feed the next iteration's active set): blocks are
+// (hub, kHubChunkEntries-entry chunk) pairs of the pass's whole hub list.
+template <typename W>
+__global__ void __launch_bounds__(256) lm_hub_mark(LMArgs<W> a, const int32_t* __restrict__ hubs, int nhubs,
+                                                   const int64_t* __restrict__ chunk_pre) {
+  const IterView iv = iter_view(a);
+  const int h = find_item(chunk_pre, nhubs, blockIdx.x);
+  if (a.hmoved[h] != iv.iter + 1) return;
+  const int32_t i = hubs[h];
+  const int64_t q = (int64_t)blockIdx.x - (chunk_pre[h] - chunk_pre[0]);
+  const int64_t b = a.off[i], e = a.off[i + 1];
+  const int64_t x0 = b + q * kHubChunk, x1 = min(e, x0 + kHubChunk);
+  if (q == 0 && threadIdx.x == 0) iv.sw[i] = iv.iter + 1;
+  for (int64_t x = x0 + threadIdx.x; x < x1; x += 256) iv.sw[a.col[x]] = iv.iter + 1;
 }
 
 // ----------------------------------------------- synchronous commit step
@@ -805,6 +855,13 @@ void lm_launch_hubs(const LMArgs<W>& a, bool wide, bool async, const int32_t* hu
 }
 
 template <typename W>
+void lm_launch_hub_mark(const LMArgs<W>& a, const int32_t* hubs, int nhubs, const int64_t* chunk_pre, int64_t nchunks,
+                        cudaStream_t s) {
+  if (nhubs <= 0 || nchunks <= 0 || !a.prune) return;
+  (count_launch(), lm_hub_mark<W><<<(unsigned)nchunks, 256, 0, s>>>(a, hubs, nhubs, chunk_pre));
+}
+
+template <typename W>
 void lm_launch_commit(const LMArgs<W>& a, int64_t max_moves, cudaStream_t s) {
   if (max_moves <= 0) return;
   int blocks = (int)((max_moves + 255) / 256);
@@ -819,6 +876,10 @@ template void lm_launch_hubs<int32_t>(const LMArgs<int32_t>&, bool, bool, const 
                                       int64_t, const int64_t*, int64_t, cudaStream_t);
 template void lm_launch_hubs<int64_t>(const LMArgs<int64_t>&, bool, bool, const int32_t*, int, const int64_t*,
                                       int64_t, const int64_t*, int64_t, cudaStream_t);
+template void lm_launch_hub_mark<int32_t>(const LMArgs<int32_t>&, const int32_t*, int, const int64_t*, int64_t,
+                                          cudaStream_t);
+template void lm_launch_hub_mark<int64_t>(const LMArgs<int64_t>&, const int32_t*, int, const int64_t*, int64_t,
+                                          cudaStream_t);
 template void lm_launch_commit<int32_t>(const LMArgs<int32_t>&, int64_t, cudaStream_t);
 template void lm_launch_commit<int64_t>(const LMArgs<int64_t>&, int64_t, cudaStream_t);
 

@@ -38,7 +38,8 @@ class Options(ctypes.Structure):
                 ("pass_tolerance", ctypes.c_double), ("max_iterations", ctypes.c_int32),
                 ("max_passes", ctypes.c_int32), ("prune", ctypes.c_int32), ("singleton_guard", ctypes.c_int32),
                 ("subrounds", ctypes.c_int32), ("validate", ctypes.c_int32), ("record_levels", ctypes.c_int32),
-                ("cuda_graphs", ctypes.c_int32), ("reserved_i", ctypes.c_int32 * 4), ("reserved_d", ctypes.c_double * 4)]
+                ("cuda_graphs", ctypes.c_int32), ("reclass", ctypes.c_int32), ("reserved_i", ctypes.c_int32 * 3),
+                ("reserved_d", ctypes.c_double * 4)]
 
 
 class Stats(ctypes.Structure):
@@ -299,6 +300,28 @@ class Louvain:
                                   pi.lm_ms, pi.agg_ms))
         return out
 
+    def set_mapping(self, thresholds=None):
+        """Local-moving degree thresholds (5 increasing ints within the kernels' capacities; None = defaults)."""
+        if thresholds is None:
+            self._check(self.lib.louvain_set_mapping(self.h, None))
+            return
+        t = np.ascontiguousarray(thresholds, dtype=np.int32)
+        if t.shape != (5,):
+            raise ValueError("five thresholds")
+        self._check(self.lib.louvain_set_mapping(self.h, t.ctypes.data))
+
+    def mapping(self):
+        t = np.zeros(5, np.int32)
+        self._check(self.lib.louvain_get_mapping(self.h, t.ctypes.data))
+        return t.tolist()
+
+    def autotune(self):
+        """Pick the fastest local-moving mapping for the loaded graph; returns (thresholds, best trial ms)."""
+        t = np.zeros(5, np.int32)
+        ms = ctypes.c_double()
+        self._check(self.lib.louvain_autotune(self.h, t.ctypes.data, ctypes.byref(ms)))
+        return t.tolist(), ms.value
+
     def iterations(self):
         """[(pass, moves, S exact)] of every local-moving iteration of the last run."""
         st = self.stats()
@@ -352,6 +375,13 @@ class ServerResult(ctypes.Structure):
                 ("n", ctypes.c_int64), ("communities", ctypes.c_int64), ("q", ctypes.c_double),
                 ("num_hi", ctypes.c_int64), ("num_lo", ctypes.c_uint64), ("M", ctypes.c_int64),
                 ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double), ("done_s", ctypes.c_double)]
+
+
+SIGNATURES += [
+    ("louvain_set_mapping", _I32, [_VP, _VP]),
+    ("louvain_get_mapping", _I32, [_VP, _VP]),
+    ("louvain_autotune", _I32, [_VP, _VP, ctypes.POINTER(ctypes.c_double)]),
+]
 
 
 SIGNATURES += [

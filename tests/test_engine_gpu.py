@@ -17,6 +17,7 @@ import pytest
 import graphgen as gg
 import oracle
 from engine_util import assert_sync_parity, engine_run
+from paper_2301_12390_gb300 import Louvain, LouvainError
 
 pytestmark = pytest.mark.gpu
 
@@ -114,7 +115,70 @@ def test_sync_parity_max_iterations_and_passes():
     assert_sync_parity(g, max_passes=2, tolerance=0.0)
 
 
+# ------------------------------------------------- vertex mapping, autotuner
+
+@pytest.mark.parametrize("name", ["rmat16", "sbm8192"])
+@pytest.mark.parametrize("thresholds", [[4, 16, 64, 256, 2048], [8, 32, 128, 1024, 4096], [1, 2, 3, 4, 5]])
+def test_sync_parity_under_any_mapping(name, thresholds):
+    """Which kernel handles a vertex never changes the result: bit-exact sync
+    parity with the oracle under non-default degree thresholds (the last one
+    sends almost every vertex to the hub path)."""
+    g = G[name]
+    with Louvain(device=0, mode=0, prune=1) as lv:
+        lv.set_mapping(thresholds)
+        assert lv.mapping() == thresholds
+        lv.load_csr(g.off, g.col, g.w)
+        lv.run()
+        top, exact = lv.membership(), lv.modularity_exact()
+    ref = oracle.louvain(g.off, g.col, g.w, mode=oracle.SYNC, prune=1)
+    assert np.array_equal(top, ref.top)
+    assert exact == (ref.q_num, ref.M)
+
+
+def test_mapping_rejects_bad_thresholds():
+    with Louvain(device=0) as lv:
+        for bad in ([8, 32, 128, 1024, 5000], [8, 8, 128, 1024, 4096], [0, 32, 128, 1024, 4096], [9, 32, 128, 1024, 4096]):
+            with pytest.raises(LouvainError):
+                lv.set_mapping(bad)
+        lv.set_mapping(None)
+        assert lv.mapping() == [8, 32, 128, 1024, 4096]
+
+
+def test_autotune_keeps_results():
+    """The autotuner picks a valid mapping; runs after it still match the oracle (sync) bit for bit."""
+    g = G["rmat16"]
+    with Louvain(device=0, mode=0, prune=1) as lv:
+        lv.load_csr(g.off, g.col, g.w)
+        th, ms = lv.autotune()
+        assert ms > 0 and len(th) == 5 and all(a < b for a, b in zip(th, th[1:]))
+        assert all(1 <= t <= cap for t, cap in zip(th, [8, 32, 128, 1024, 4096]))
+        lv.run()
+        top, exact = lv.membership(), lv.modularity_exact()
+    ref = oracle.louvain(g.off, g.col, g.w, mode=oracle.SYNC, prune=1)
+    assert np.array_equal(top, ref.top)
+    assert exact == (ref.q_num, ref.M)
+
+
 # ------------------------------------------------------- async quality
+
+@pytest.mark.parametrize("name", ["sbm600", "rmat16", "road128"])
+@pytest.mark.parametrize("reclass", [0, 1, 2, 3])
+def test_async_class_modes(name, reclass):
+    """Every way of drawing the asynchronous classes (id mod P, hashed per
+    iteration, hashed per pass, automatic) keeps Q within 0.01 of the oracle."""
+    g = G[name]
+    got = engine_run(g, mode=1, prune=1, reclass=reclass)
+    ref = oracle.louvain(g.off, g.col, g.w, mode=oracle.ASYNC, prune=1)
+    assert got["q"] >= ref.Q - 0.01, (got["q"], ref.Q)
+    _, num, M = oracle.modularity(g.off, g.col, g.w, got["top"])
+    assert got["exact"] == (num, M)
+
+
+@pytest.mark.parametrize("reclass", [1, 2])
+def test_sync_ignores_class_mode(reclass):
+    """Synchronous classes are always id mod P (the oracle's), whatever reclass says."""
+    assert_sync_parity(G["rmat14"], prune=1, subrounds=4, reclass=reclass)
+
 
 @pytest.mark.parametrize("name", list(G))
 @pytest.mark.parametrize("prune,subrounds", [(0, 0), (1, 0), (1, 32)])
