@@ -79,8 +79,8 @@ typedef struct {
                                  stops Jacobi updates from swapping pairs forever) */
   int32_t subrounds;          /* P >= 1: the vertices are split into P classes processed one after
                                  the other in each iteration; 1 = every vertex at once; 0 = automatic
-                                 (synchronous 1; asynchronous 16, or 32 when the largest graph of the
-                                 run has fewer than 65,536 vertices) */
+                                 (synchronous 1; asynchronous, per graph: 32 for a graph of fewer than
+                                 65,536 vertices, else 16) */
   int32_t validate;           /* 1: louvain_load_csr checks symmetry and CSR form (costs a pass) */
   int32_t record_levels;      /* 1: keep each pass's membership and coarse CSR for louvain_get_level /
                                  louvain_get_coarse (copies them to host memory) */
@@ -91,8 +91,9 @@ typedef struct {
                                  iteration draws the classes anew, class = hash(id, pass, iteration)
                                  mod P (breaks the repeated same-class swaps of structured ids such
                                  as grids); 2 = hashed classes drawn once per pass; 3 = automatic
-                                 (default: 2 when the largest graph of the run has fewer than 65,536
-                                 vertices, else 1).  Synchronous classes are always id mod P. */
+                                 (default; per graph: 2 for a graph of fewer than 65,536 vertices,
+                                 else 1).  Synchronous classes are always id mod P.  Every graph of
+                                 a batch gets the schedule it gets alone. */
   int32_t reserved_i[3];
   double reserved_d[4];
 } louvain_options;

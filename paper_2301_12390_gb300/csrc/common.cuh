@@ -201,6 +201,41 @@ __device__ __forceinline__ bool gtable_add(int32_t* keys, unsigned long long* va
   return false;
 }
 
+// gtable_add for J entries of one thread at once (k[j] = kEmpty: none): each
+// round issues the compare-and-swaps of every pending entry before looking at
+// any result, so J probes are in flight together instead of one.
+template <int J>
+__device__ __forceinline__ bool gtable_add_many(int32_t* keys, unsigned long long* vals, uint32_t cap,
+                                                const int32_t* k, const unsigned long long* v) {
+  uint32_t h[J];
+  bool pend[J];
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    pend[j] = k[j] != kEmpty;
+    h[j] = pend[j] ? __umulhi(hash32((uint32_t)k[j]), cap) : 0u;
+  }
+#pragma unroll 1
+  for (uint32_t probe = 0; probe < cap; ++probe) {
+    int32_t old[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) old[j] = pend[j] ? atomicCAS(&keys[h[j]], kEmpty, k[j]) : kEmpty;
+    bool any = false;
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      if (!pend[j]) continue;
+      if (old[j] == kEmpty || old[j] == k[j]) {
+        atomicAdd(&vals[h[j]], v[j]);
+        pend[j] = false;
+      } else {
+        h[j] = h[j] + 1 == cap ? 0u : h[j] + 1;
+        any = true;
+      }
+    }
+    if (!any) return true;
+  }
+  return false;
+}
+
 __device__ __forceinline__ unsigned long long gtable_get(const int32_t* keys, const unsigned long long* vals,
                                                          uint32_t cap, int32_t key) {
   uint32_t h = __umulhi(hash32((uint32_t)key), cap);

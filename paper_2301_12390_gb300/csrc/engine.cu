@@ -119,6 +119,7 @@ struct louvain_ctx {
   int64_t* glo = nullptr;
   int32_t* inv = nullptr;      // aggregation: member position of each vertex
   int32_t* hmoved = nullptr;   // local moving: iteration + 1 of a hub's last move (by hub-list position)
+  int32_t* d_gsmall = nullptr; // per graph: fewer than kSmallGraph vertices (its class schedule)
   LMThresholds thr = {{kLMCap[0], kLMCap[1], kLMCap[2], kLMCap[3], kLMCap[4]}};   // degree mapping
   int32_t* crow = nullptr;     // aggregation: first row of each relabel chunk      // aggregation: direct-table first key per global community, or -1
   unsigned long long* hkid = nullptr;
@@ -287,29 +288,34 @@ template <typename W>
 int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool wide, int* iters_out,
                  int64_t* edges_out, int64_t* visited_out) {
   const bool async = c->opt.mode == LOUVAIN_ASYNC;
-  // automatic classes: graphs below kSmallGraph vertices (the largest graph of
-  // a batch decides) take more, smaller classes, drawn once per pass; larger
-  // graphs take kAsyncSubrounds classes drawn anew every iteration
-  int64_t nbig = 0;
-  for (int64_t q = 0; q < c->G; ++q) nbig = std::max(nbig, c->gn0[q]);
-  const bool small = nbig < kSmallGraph;
-  const int P = c->opt.subrounds > 0 ? c->opt.subrounds
-                                     : (async ? (small ? kAsyncSubroundsSmall : kAsyncSubrounds) : 1);
+  // Classes, per graph: a graph below kSmallGraph vertices takes
+  // kAsyncSubroundsSmall classes drawn once per pass, a larger one
+  // kAsyncSubrounds classes drawn anew every iteration (automatic settings),
+  // so a graph gets the same schedule alone and in a batch.  Synchronous
+  // classes are id mod P.
+  bool any_small = false, any_big = false;
+  for (int64_t q = 0; q < c->G; ++q) (c->gn0[q] < kSmallGraph ? any_small : any_big) = true;
+  ClassSpec cs{1, 1, 0u, 0u, c->G == 1 && c->gn0[0] < kSmallGraph ? 1 : 0};
+  if (c->opt.subrounds > 0) cs.Ps = cs.Pb = c->opt.subrounds;
+  else if (async) { cs.Ps = kAsyncSubroundsSmall; cs.Pb = kAsyncSubrounds; }
+  const int P = std::max(any_small ? cs.Ps : 1, any_big ? cs.Pb : 1);
   const int nkeys = kBuckets * P + 1;
   const bool multi = c->G > 1;
   const int64_t G = c->G;
   cudaStream_t s = c->stream;
-  // Bucket lists: key = bucket * P + class, class by id within the graph
-  // (id mod P, or with reclass a hash of it salted by pass and iteration),
-  // hubs of all classes contiguous, and the hubs' table layout.
-  // reclass 1: hashed classes drawn anew every iteration; 2: once per pass
-  const int reclass = (async && P > 1) ? (c->opt.reclass == 3 ? (small ? 2 : 1) : c->opt.reclass) : 0;
+  // reclass: 1 = hashed classes drawn anew every iteration, 2 = once per pass
+  const int mode_s = (async && cs.Ps > 1) ? (c->opt.reclass == 3 ? 2 : c->opt.reclass) : 0;
+  const int mode_b = (async && cs.Pb > 1) ? (c->opt.reclass == 3 ? 1 : c->opt.reclass) : 0;
+  const bool reclass = (any_small && mode_s == 1) || (any_big && mode_b == 1);   // every iteration
+  // Bucket lists: key = bucket * P + class, hubs of all classes contiguous,
+  // and the hubs' table layout.
   std::vector<int64_t> ko(nkeys + 1);
   int64_t hub0 = 0, hub1 = 0, nhubs = 0;
   std::vector<int64_t> hchunks, hschunks;
   auto classify = [&](int iter) -> int {
-    const uint32_t salt = reclass ? mix_salt(pass, reclass == 1 ? iter : 0) : 0u;
-    lm_keys(g.off, g.n, P, c->key, multi ? c->gid : nullptr, multi ? c->vo : nullptr, salt, c->thr, s);
+    cs.salt_s = mode_s ? mix_salt(pass, mode_s == 1 ? iter : 0) : 0u;
+    cs.salt_b = mode_b ? mix_salt(pass, mode_b == 1 ? iter : 0) : 0u;
+    lm_keys(g.off, g.n, P, c->key, multi ? c->gid : nullptr, multi ? c->vo : nullptr, c->d_gsmall, cs, c->thr, s);
     stable_partition(c->key, g.n, nkeys, c->list, c->key_off, c->tmp, s);
     CKLAUNCH();
     if (int r = fetch(c, ko.data(), c->key_off, ko.size() * sizeof(int64_t))) return r;
@@ -379,7 +385,17 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
       CK(cudaMemsetAsync(c->d_gmoves, 0, G * sizeof(unsigned long long), s));
       CK(cudaMemsetAsync(c->d_gs, 0, 2 * G * sizeof(unsigned long long), s));
     }
-    for (int ch = 0; ch < P; ++ch) {
+    // a small pass graph without vertices above degree 128: one launch per
+    // class on the main stream
+    const bool small_pass = g.nnz <= kSmallPassEntries && ko[3 * P] == ko[kBuckets * P];
+    for (int ch = 0; ch < P && small_pass; ++ch) {
+      int64_t cls = 0;
+      for (int b = 0; b < 3; ++b) cls += ko[b * P + ch + 1] - ko[b * P + ch];
+      lm_launch_class<W>(a, wide, async, c->list, c->key_off, P, ch, cls, s);
+      if (!async) lm_launch_commit<W>(a, cls, s);
+      CKLAUNCH();
+    }
+    for (int ch = 0; ch < P && !small_pass; ++ch) {
       // fork: every non-empty bucket of the class on its own stream
       bool used[kBuckets] = {};
       CK(cudaEventRecord(c->ev_fork, s));
@@ -440,9 +456,9 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
            return 0;
          }()))
       break;
-    if (reclass == 1 && it > 0)
+    if (reclass && it > 0)
       if ((rc = classify(it))) break;
-    if (c->opt.cuda_graphs && reclass != 1 && it >= 2) {
+    if (c->opt.cuda_graphs && !reclass && it >= 2) {
       if (!gexec) {
         if ((rc = [&]() -> int {
                CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -1023,6 +1039,7 @@ int alloc_arena(louvain_ctx* c, int64_t n, int64_t nnz) {
   ALLOC(c->kcount, N1 + 1);
   ALLOC(c->d_Mg, N1);
   ALLOC(c->d_gon, N1);
+  ALLOC(c->d_gsmall, N1);
   ALLOC(c->d_gmoves, N1);
   ALLOC(c->d_gs, 2 * N1);
   ALLOC(c->d_gL, 2 * N1);
@@ -1209,6 +1226,12 @@ int load_graphs(louvain_ctx* c, int64_t G, const int64_t* vo, int64_t n, int64_t
   c->gqnum0.assign(G, 0);
   for (int64_t q = 0; q < G; ++q) c->gn0[q] = vo[q + 1] - vo[q];
   CK(cudaMemcpyAsync(c->vo0, vo, (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  {
+    std::vector<int32_t> small(G);
+    for (int64_t q = 0; q < G; ++q) small[q] = c->gn0[q] < kSmallGraph ? 1 : 0;
+    CK(cudaMemcpyAsync(c->d_gsmall, small.data(), G * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));   // the host vector goes out of scope
+  }
   if (G == 1) {
     c->gM0[0] = c->M0;
     c->gqnum0[0] = c->qnum0;

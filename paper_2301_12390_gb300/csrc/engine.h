@@ -46,6 +46,12 @@ template <typename W>
 void lm_launch_hubs(const LMArgs<W>& a, bool wide, bool async, const int32_t* hubs, int nhubs,
                     const int64_t* chunk_pre, int64_t nchunks, const int64_t* spre, int64_t nslotchunks,
                     cudaStream_t s);
+// Class ch of a small pass graph with no vertex above degree 128 in one
+// launch (buckets 0-2, nverts vertices); ko = the bucket offsets (device).
+template <typename W>
+void lm_launch_class(const LMArgs<W>& a, bool wide, bool async, const int32_t* list, const int64_t* ko, int P,
+                     int ch, int64_t nverts, cudaStream_t s);
+constexpr int64_t kSmallPassEntries = 1 << 21;   // CSR entries up to which a pass takes one launch per class
 // Pruning marks of every hub of the pass's hub list that moved in this iteration.
 template <typename W>
 void lm_launch_hub_mark(const LMArgs<W>& a, const int32_t* hubs, int nhubs, const int64_t* chunk_pre, int64_t nchunks,
@@ -68,11 +74,20 @@ size_t partition_tmp_bytes(int64_t n, int nkeys);
 void stable_partition(const int32_t* key, int64_t n, int nkeys, int32_t* out, int64_t* key_off, void* tmp,
                       cudaStream_t s);
 
+// Vertex classes of one iteration: a vertex of a small graph (per-graph flag
+// gsmall, or single_small with one graph) takes class (local id mod Ps, or
+// hash32(local id ^ salt_s) mod Ps when salt_s != 0); of a large graph the
+// same with Pb and salt_b.
+struct ClassSpec {
+  int32_t Ps, Pb;
+  uint32_t salt_s, salt_b;
+  int32_t single_small;
+};
 // Keys for the local-moving lists, bucket-major: key[i] = bucket * P + class
-// of vertex i (class = local id mod P, or hash32(local id ^ salt) mod P when
-// salt != 0); vertices of degree 0 get the trailing key kBuckets * P.
+// of vertex i (P >= Ps, Pb); vertices of degree 0 get the trailing key
+// kBuckets * P.
 void lm_keys(const int64_t* off, int64_t n, int P, int32_t* key, const int32_t* gid, const int64_t* vo,
-             uint32_t salt, LMThresholds th, cudaStream_t s);
+             const int32_t* gsmall, ClassSpec cs, LMThresholds th, cudaStream_t s);
 // For the hub list: per hub its table base (2 * degree slots), the prefix of
 // its insert chunks and the prefix of its slot chunks (each nhubs + 1 long).
 void hub_layout(const int64_t* off, const int32_t* hubs, int64_t nhubs, int64_t* hbase, int64_t* chunk_pre,

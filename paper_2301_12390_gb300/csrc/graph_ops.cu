@@ -232,12 +232,20 @@ void stable_partition(const int32_t* key, int64_t n, int nkeys, int32_t* out, in
 // --------------------------------------------------- local-moving lists
 
 __global__ void lm_keys_k(const int64_t* __restrict__ off, int64_t n, int P, int32_t* key,
-                          const int32_t* __restrict__ gid, const int64_t* __restrict__ vo, uint32_t salt,
-                          LMThresholds th) {
+                          const int32_t* __restrict__ gid, const int64_t* __restrict__ vo,
+                          const int32_t* __restrict__ gsmall, ClassSpec cs, LMThresholds th) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int b = lm_bucket_of(off[i + 1] - off[i], th);
-    const int64_t local = gid ? i - vo[gid[i]] : i;   // classes by id within the vertex's graph
-    const int cls = salt ? (int)(hash32((uint32_t)local ^ salt) % (uint32_t)P) : (int)(local % P);
+    int64_t local = i;   // classes by id within the vertex's graph
+    bool small = cs.single_small != 0;
+    if (gid) {
+      const int g = gid[i];
+      local = i - vo[g];
+      small = gsmall[g] != 0;
+    }
+    const uint32_t Pg = (uint32_t)(small ? cs.Ps : cs.Pb);
+    const uint32_t salt = small ? cs.salt_s : cs.salt_b;
+    const int cls = salt ? (int)(hash32((uint32_t)local ^ salt) % Pg) : (int)(local % Pg);
     key[i] = b < 0 ? kBuckets * P : b * P + cls;
   }
 }
@@ -249,8 +257,8 @@ static unsigned grid1d(int64_t n, int per = kT) {
 }
 
 void lm_keys(const int64_t* off, int64_t n, int P, int32_t* key, const int32_t* gid, const int64_t* vo,
-             uint32_t salt, LMThresholds th, cudaStream_t s) {
-  if (n > 0) (count_launch(), lm_keys_k<<<grid1d(n), kT, 0, s>>>(off, n, P, key, gid, vo, salt, th));
+             const int32_t* gsmall, ClassSpec cs, LMThresholds th, cudaStream_t s) {
+  if (n > 0) (count_launch(), lm_keys_k<<<grid1d(n), kT, 0, s>>>(off, n, P, key, gid, vo, gsmall, cs, th));
 }
 
 __global__ void hub_sizes_k(const int64_t* off, const int32_t* hubs, int64_t nhubs, int64_t* cap, int64_t* chunks,
@@ -771,17 +779,26 @@ __global__ void __launch_bounds__(256) agg_global_insert_k(AggArgs a, const int3
   int32_t* keys = a.gkeys + base;
   unsigned long long* vals = a.gvals + base;
   const int64_t lo = a.glo[h];
-  for (int t = threadIdx.x; t < CAP; t += blockDim.x) {
-    int32_t Dk = skeys[t];
-    if (Dk == kEmpty) continue;
-    if (lo >= 0) {   // direct table: slot Dk - lo (same-value key stores may race)
+  if (lo >= 0) {   // direct table: slot Dk - lo (same-value key stores may race)
+    for (int t = threadIdx.x; t < CAP; t += blockDim.x) {
+      const int32_t Dk = skeys[t];
+      if (Dk == kEmpty) continue;
       const int64_t y = (int64_t)Dk - lo;
       if (y < 0 || y >= (int64_t)cap) { ok = false; continue; }
       if (keys[y] != Dk) keys[y] = Dk;
       atomicAdd(&vals[y], svals[t]);
-    } else {
-      bool fresh;
-      ok &= gtable_add(keys, vals, cap, Dk, svals[t], &fresh);
+    }
+  } else {
+    constexpr int J = 8;
+    for (int t0 = 0; t0 < CAP; t0 += J * 256) {
+      int32_t kk[J];
+      unsigned long long vv[J];
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        kk[j] = skeys[t0 + j * 256 + threadIdx.x];
+        vv[j] = svals[t0 + j * 256 + threadIdx.x];
+      }
+      ok &= gtable_add_many<J>(keys, vals, cap, kk, vv);
     }
   }
   if (!ok) atomicOr(a.error, kErrProbe);

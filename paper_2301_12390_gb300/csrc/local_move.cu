@@ -37,20 +37,27 @@ __device__ __forceinline__ unsigned lanemask_lt_lm() {
 // read them through the read-only path; asynchronous launches use plain
 // loads, which may return a value that another vertex has since changed —
 // exactly the staleness the asynchronous variant allows.
+// Loads of memberships, community totals and sizes.  LD 0: read-only path
+// (nothing writes them while the kernel runs: a synchronous class); 1: plain
+// (asynchronous in-place updates, any recent value will do); 2: L2 only (the
+// kernel itself updates them between its classes and must see the result).
+template <int LD, typename T>
+__device__ __forceinline__ T ld_state(const T* p) {
+  if (LD == 0) return __ldg(p);
+  if (LD == 2) return __ldcg(p);
+  return *p;
+}
 template <bool ASYNC>
 __device__ __forceinline__ int32_t ld_memb(const int32_t* p) {
-  if (ASYNC) return *p;
-  return __ldg(p);
+  return ld_state<ASYNC ? 1 : 0>(p);
 }
 template <bool ASYNC>
 __device__ __forceinline__ long long ld_sig(const long long* p) {
-  if (ASYNC) return *p;
-  return __ldg(p);
+  return ld_state<ASYNC ? 1 : 0>(p);
 }
 template <bool ASYNC>
 __device__ __forceinline__ int32_t ld_size(const int32_t* p) {
-  if (ASYNC) return *p;
-  return __ldg(p);
+  return ld_state<ASYNC ? 1 : 0>(p);
 }
 
 // Block-level accumulators, flushed once per block.
@@ -78,15 +85,18 @@ __device__ __forceinline__ void acc_flush(BlockAcc& b, DevCounters* ctr) {
 // Returns whether the vertex moves.
 // `best` is the best candidate's score, `score_d` the vertex's own; the move
 // needs gain = best - score_d > 0.
-template <typename W, bool WIDE, bool ASYNC>
+// sd, szd: Sigma_d and the size of d, loaded with the vertex's row (constant
+// within a synchronous class; an asynchronous decision may use any recent
+// value).
+template <typename W, bool WIDE, bool ASYNC, int LD = (ASYNC ? 1 : 0)>
 __device__ __forceinline__ bool commit_choice(const LMArgs<W>& a, BlockAcc& acc, int32_t i, int32_t d, long long Ki,
-                                              typename Arith<WIDE>::S best, int32_t c, unsigned long long kid,
-                                              long long M, int graph) {
+                                              long long sd, int32_t szd, typename Arith<WIDE>::S best, int32_t c,
+                                              unsigned long long kid, long long M, int graph) {
   if (c < 0) return false;
   typedef typename Arith<WIDE>::S S;
-  const S g = best - Arith<WIDE>::score(M, (long long)kid, Ki, ld_sig<ASYNC>(a.sig + d) - Ki);
+  const S g = best - Arith<WIDE>::score(M, (long long)kid, Ki, sd - Ki);
   if (!(g > 0)) return false;
-  if (a.guard && c > d && ld_size<ASYNC>(a.csize + d) == 1 && ld_size<ASYNC>(a.csize + c) == 1) return false;
+  if (a.guard && c > d && szd == 1 && ld_state<LD>(a.csize + c) == 1) return false;
   if (ASYNC) {
     a.memb[i] = c;
     atomicAdd((unsigned long long*)(a.sig + d), (unsigned long long)(-Ki));
@@ -142,12 +152,45 @@ __device__ __forceinline__ bool is_active(const LMArgs<W>& a, const IterView& iv
   return !a.prune || iv.iter == 0 || iv.sr[i] == iv.iter;
 }
 
+// What a per-vertex kernel needs of list entry vi before its row: loaded one
+// vertex ahead so that these loads overlap the previous vertex.
+struct VertexInfo {
+  int32_t i, d, szd;
+  bool on;        // in range, active and its graph still iterating
+  int graph;
+  int64_t b, e;
+  long long Ki, M, sd;
+};
+
+template <typename W, bool ASYNC, int LD = (ASYNC ? 1 : 0)>
+__device__ __forceinline__ VertexInfo vertex_info(const LMArgs<W>& a, const IterView& iv,
+                                                  const int32_t* __restrict__ verts, int nverts, int vi) {
+  VertexInfo v;
+  v.on = false;
+  v.i = 0;
+  v.d = 0;
+  v.szd = 0;
+  v.graph = 0;
+  v.b = v.e = 0;
+  v.Ki = v.M = v.sd = 0;
+  if (vi >= nverts) return v;
+  v.i = verts[vi];
+  v.b = a.off[v.i];
+  v.e = a.off[v.i + 1];
+  v.d = ld_state<LD == 2 ? 2 : 1>(a.memb + v.i);
+  v.Ki = a.K[v.i];
+  v.sd = ld_state<LD>(a.sig + v.d);
+  v.szd = ld_state<LD>(a.csize + v.d);
+  v.on = is_active(a, iv, v.i) && graph_of(a, v.i, &v.M, &v.graph);
+  return v;
+}
+
 // --------------------------------------------- bucket 0: thread per vertex
 
 // The row (<= 8 entries) is loaded first and its neighbours' communities
 // gathered with all loads in flight; duplicates are then merged in registers.
 template <typename W, bool WIDE, bool ASYNC>
-__global__ void __launch_bounds__(256, 4) lm_thread(LMArgs<W> a, const int32_t* __restrict__ verts, int nverts) {
+__global__ void __launch_bounds__(256, 3) lm_thread(LMArgs<W> a, const int32_t* __restrict__ verts, int nverts) {
   const IterView iv = iter_view(a);
   typedef typename Arith<WIDE>::S S;
   __shared__ BlockAcc acc;
@@ -162,6 +205,8 @@ __global__ void __launch_bounds__(256, 4) lm_thread(LMArgs<W> a, const int32_t* 
     const int64_t b = a.off[i], e = a.off[i + 1];
     const int32_t d = a.memb[i];
     const long long Ki = a.K[i];
+    const long long sd = ld_sig<ASYNC>(a.sig + d);
+    const int32_t szd = ld_size<ASYNC>(a.csize + d);
     int32_t cc[8];
     unsigned long long ww[8];
 #pragma unroll
@@ -198,7 +243,7 @@ __global__ void __launch_bounds__(256, 4) lm_thread(LMArgs<W> a, const int32_t* 
     }
     atomicAdd(&acc.edges, (unsigned long long)(e - b));
         atomicAdd(&acc.visited, 1ull);
-    if (commit_choice<W, WIDE, ASYNC>(a, acc, i, d, Ki, bg, bc, kid, M, graph) && a.prune) {
+    if (commit_choice<W, WIDE, ASYNC>(a, acc, i, d, Ki, sd, szd, bg, bc, kid, M, graph) && a.prune) {
       iv.sw[i] = iv.iter + 1;
       for (int64_t x = b; x < e; ++x) iv.sw[a.col[x]] = iv.iter + 1;
     }
@@ -209,10 +254,89 @@ __global__ void __launch_bounds__(256, 4) lm_thread(LMArgs<W> a, const int32_t* 
 
 // ------------------------------------------ buckets 1-2: warp per vertex
 
+// One vertex of degree <= U * 32 by one warp: its neighbour communities summed
+// in the warp's shared table (CAP slots, left empty again), the best score
+// against its own community's, the move committed and its neighbours marked.
+template <typename W, bool WIDE, bool ASYNC, int CAP, int U, int LD>
+__device__ __forceinline__ void warp_vertex(const LMArgs<W>& a, const IterView& iv, BlockAcc& acc, int32_t* keys,
+                                            typename TableVal<WIDE>::T* vals, const VertexInfo& cur, int lane,
+                                            bool& ok) {
+  typedef typename Arith<WIDE>::S S;
+  typedef typename TableVal<WIDE>::T V;
+  const int32_t i = cur.i, d = cur.d;
+  const int64_t b = cur.b, e = cur.e;
+  const long long Ki = cur.Ki, M = cur.M;
+  const int graph = cur.graph;
+  for (int64_t x0 = b; x0 < e; x0 += U * kWarp) {
+    int32_t cc[U];
+    unsigned long long ww[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t x = x0 + u * kWarp + lane;
+      const bool v = x < e;
+      cc[u] = v ? a.col[x] : i;
+      ww[u] = v ? (unsigned long long)a.wt[x] : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) cc[u] = cc[u] != i ? ld_state<LD>(a.memb + cc[u]) : kEmpty;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (cc[u] != kEmpty) ok &= table_add_pow2<CAP, V>(keys, vals, cc[u], ww[u]);
+  }
+  __syncwarp();
+  unsigned long long kid = 0;
+  S bg = Arith<WIDE>::lowest();
+  int32_t bc = -1;
+#pragma unroll
+  for (int t0 = 0; t0 < CAP; t0 += kWarp * 4) {
+    int32_t cs[4];
+    long long sg[4];
+    unsigned long long vs[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int t = t0 + u * kWarp + lane;
+      cs[u] = t < CAP ? keys[t] : kEmpty;
+      vs[u] = t < CAP ? vals[t] : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) sg[u] = (cs[u] != kEmpty && cs[u] != d) ? ld_state<LD>(a.sig + cs[u]) : 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int t = t0 + u * kWarp + lane;
+      if (cs[u] != kEmpty) {
+        if (cs[u] != d) {
+          S g = Arith<WIDE>::score(M, (long long)vs[u], Ki, sg[u]);
+          if (better(g, cs[u], bg, bc)) { bg = g; bc = cs[u]; }
+        } else {
+          kid = vs[u];
+        }
+        keys[t] = kEmpty;
+        vals[t] = 0;
+      }
+    }
+  }
+  warp_argmax(bg, bc);
+  {
+    const unsigned has = __ballot_sync(0xffffffffu, kid != 0);
+    kid = has ? __shfl_sync(0xffffffffu, kid, __ffs(has) - 1) : 0ull;
+  }
+  bool moved = false;
+  if (lane == 0) {
+    atomicAdd(&acc.edges, (unsigned long long)(e - b));
+    atomicAdd(&acc.visited, 1ull);
+    moved = commit_choice<W, WIDE, ASYNC, LD>(a, acc, i, d, Ki, cur.sd, cur.szd, bg, bc, kid, M, graph);
+  }
+  moved = __shfl_sync(0xffffffffu, moved, 0);
+  if (moved && a.prune) {
+    if (lane == 0) iv.sw[i] = iv.iter + 1;
+    for (int64_t x = b + lane; x < e; x += kWarp) iv.sw[a.col[x]] = iv.iter + 1;
+  }
+}
+
 // U entries per lane are loaded and gathered before any insert (U * 32 covers
 // the bucket's largest degree), so their memory latencies overlap.
 template <typename W, bool WIDE, bool ASYNC, int CAP, int U>
-__global__ void __launch_bounds__(256, 4) lm_warp(LMArgs<W> a, const int32_t* __restrict__ verts, int nverts) {
+__global__ void __launch_bounds__(256, 3) lm_warp(LMArgs<W> a, const int32_t* __restrict__ verts, int nverts) {
   const IterView iv = iter_view(a);
   typedef typename Arith<WIDE>::S S;
   typedef typename TableVal<WIDE>::T V;
@@ -227,79 +351,52 @@ __global__ void __launch_bounds__(256, 4) lm_warp(LMArgs<W> a, const int32_t* __
   for (int t = lane; t < CAP; t += kWarp) { keys[t] = kEmpty; vals[t] = 0; }
   __syncthreads();
   bool ok = true;
-  for (int vi = blockIdx.x * WPB + wib; vi < nverts; vi += gridDim.x * WPB) {
-    int32_t i = verts[vi];
-    if (!is_active(a, iv, i)) continue;
-    long long M;
-    int graph;
-    if (!graph_of(a, i, &M, &graph)) continue;
-    const int64_t b = a.off[i], e = a.off[i + 1];
-    const int32_t d = a.memb[i];
-    const long long Ki = a.K[i];
-    for (int64_t x0 = b; x0 < e; x0 += U * kWarp) {
-      int32_t cc[U];
-      unsigned long long ww[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int64_t x = x0 + u * kWarp + lane;
-        const bool v = x < e;
-        cc[u] = v ? a.col[x] : i;
-        ww[u] = v ? (unsigned long long)a.wt[x] : 0ull;
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) cc[u] = cc[u] != i ? ld_memb<ASYNC>(a.memb + cc[u]) : kEmpty;
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (cc[u] != kEmpty) ok &= table_add_pow2<CAP, V>(keys, vals, cc[u], ww[u]);
-    }
+  const int stride = gridDim.x * WPB;
+  VertexInfo nx = vertex_info<W, ASYNC>(a, iv, verts, nverts, blockIdx.x * WPB + wib);
+  for (int vi = blockIdx.x * WPB + wib; vi < nverts; vi += stride) {
+    const VertexInfo cur = nx;
+    nx = vertex_info<W, ASYNC>(a, iv, verts, nverts, vi + stride);
+    if (!cur.on) continue;
+    warp_vertex<W, WIDE, ASYNC, CAP, U, (ASYNC ? 1 : 0)>(a, iv, acc, keys, vals, cur, lane, ok);
     __syncwarp();
-    unsigned long long kid = 0;
-    S bg = Arith<WIDE>::lowest();
-    int32_t bc = -1;
-#pragma unroll
-    for (int t0 = 0; t0 < CAP; t0 += kWarp * 4) {
-      int32_t cs[4];
-      long long sg[4];
-      unsigned long long vs[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int t = t0 + u * kWarp + lane;
-        cs[u] = t < CAP ? keys[t] : kEmpty;
-        vs[u] = t < CAP ? vals[t] : 0ull;
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) sg[u] = (cs[u] != kEmpty && cs[u] != d) ? ld_sig<ASYNC>(a.sig + cs[u]) : 0;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int t = t0 + u * kWarp + lane;
-        if (cs[u] != kEmpty) {
-          if (cs[u] != d) {
-            S g = Arith<WIDE>::score(M, (long long)vs[u], Ki, sg[u]);
-            if (better(g, cs[u], bg, bc)) { bg = g; bc = cs[u]; }
-          } else {
-            kid = vs[u];
-          }
-          keys[t] = kEmpty;
-          vals[t] = 0;
-        }
-      }
-    }
-    warp_argmax(bg, bc);
-    {
-      const unsigned has = __ballot_sync(0xffffffffu, kid != 0);
-      kid = has ? __shfl_sync(0xffffffffu, kid, __ffs(has) - 1) : 0ull;
-    }
-    bool moved = false;
-    if (lane == 0) {
-      atomicAdd(&acc.edges, (unsigned long long)(e - b));
-        atomicAdd(&acc.visited, 1ull);
-      moved = commit_choice<W, WIDE, ASYNC>(a, acc, i, d, Ki, bg, bc, kid, M, graph);
-    }
-    moved = __shfl_sync(0xffffffffu, moved, 0);
-    if (moved && a.prune) {
-      if (lane == 0) iv.sw[i] = iv.iter + 1;
-      for (int64_t x = b + lane; x < e; x += kWarp) iv.sw[a.col[x]] = iv.iter + 1;
-    }
+  }
+  if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicOr(&acc.error, kErrProbe);
+  __syncthreads();
+  acc_flush(acc, a.ctr);
+}
+
+// ----------------------------- small pass graphs: one launch per class
+//
+// When no vertex of the pass graph has degree above 128 and the graph is
+// small, the launches of a class are few microseconds of work each: one
+// kernel then takes the whole class, a warp per vertex of buckets 0-2 (as
+// lm_warp, 256-slot tables), instead of one kernel per bucket on forked
+// streams.  ko = the bucket offsets of the class lists (device).
+template <typename W, bool WIDE, bool ASYNC>
+__global__ void __launch_bounds__(256, 4) lm_class(LMArgs<W> a, const int32_t* __restrict__ list,
+                                                   const int64_t* __restrict__ ko, int P, int ch) {
+  const IterView iv = iter_view(a);
+  typedef typename TableVal<WIDE>::T V;
+  constexpr int WPB = 8, CAP = 256, U = 4;
+  __shared__ int32_t skeys[WPB][CAP];
+  __shared__ V svals[WPB][CAP];
+  __shared__ BlockAcc acc;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  int32_t* keys = skeys[wib];
+  V* vals = svals[wib];
+  acc_init(acc);
+  for (int t = lane; t < CAP; t += kWarp) { keys[t] = kEmpty; vals[t] = 0; }
+  __syncthreads();
+  bool ok = true;
+  const int64_t r0 = ko[ch], n0 = ko[ch + 1] - r0;
+  const int64_t r1 = ko[P + ch], n1 = ko[P + ch + 1] - r1;
+  const int64_t r2 = ko[2 * P + ch], n2 = ko[2 * P + ch + 1] - r2;
+  const int64_t tot = n0 + n1 + n2;
+  for (int64_t t = (int64_t)blockIdx.x * WPB + wib; t < tot; t += (int64_t)gridDim.x * WPB) {
+    const int64_t idx = t < n0 ? r0 + t : (t < n0 + n1 ? r1 + (t - n0) : r2 + (t - n0 - n1));
+    const VertexInfo cur = vertex_info<W, ASYNC>(a, iv, list + idx, 1, 0);
+    if (!cur.on) continue;
+    warp_vertex<W, WIDE, ASYNC, CAP, U, (ASYNC ? 1 : 0)>(a, iv, acc, keys, vals, cur, lane, ok);
     __syncwarp();
   }
   if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicOr(&acc.error, kErrProbe);
@@ -308,35 +405,6 @@ __global__ void __launch_bounds__(256, 4) lm_warp(LMArgs<W> a, const int32_t* __
 }
 
 // ----------------------------------------- buckets 3-4: block per vertex
-
-// What a block-per-vertex kernel needs of list entry vi before its row.
-struct VertexInfo {
-  int32_t i, d;
-  bool on;        // in range, active and its graph still iterating
-  int graph;
-  int64_t b, e;
-  long long Ki, M;
-};
-
-template <typename W>
-__device__ __forceinline__ VertexInfo vertex_info(const LMArgs<W>& a, const IterView& iv,
-                                                  const int32_t* __restrict__ verts, int nverts, int vi) {
-  VertexInfo v;
-  v.on = false;
-  v.i = 0;
-  v.d = 0;
-  v.graph = 0;
-  v.b = v.e = 0;
-  v.Ki = v.M = 0;
-  if (vi >= nverts) return v;
-  v.i = verts[vi];
-  v.b = a.off[v.i];
-  v.e = a.off[v.i + 1];
-  v.d = a.memb[v.i];
-  v.Ki = a.K[v.i];
-  v.on = is_active(a, iv, v.i) && graph_of(a, v.i, &v.M, &v.graph);
-  return v;
-}
 
 // A decided move waiting for the block to commit it.
 struct PendingMove {
@@ -371,15 +439,18 @@ __device__ __forceinline__ void flush_moves(const LMArgs<W>& a, const IterView& 
 
 // Decide (no commit yet): the exact gain of the best candidate against the
 // vertex's own community, the guard, and the S / move counts.
+// sd, szd: Sigma_d and the size of d, read when the vertex's row was
+// (constant within a synchronous class; an asynchronous decision may use any
+// recent value).
 template <typename W, bool WIDE, bool ASYNC>
-__device__ __forceinline__ bool decide_move(const LMArgs<W>& a, BlockAcc& acc, int32_t d, long long Ki,
-                                            typename Arith<WIDE>::S best, int32_t c, unsigned long long kid,
-                                            long long M, int graph) {
+__device__ __forceinline__ bool decide_move(const LMArgs<W>& a, BlockAcc& acc, int32_t d, long long Ki, long long sd,
+                                            int32_t szd, typename Arith<WIDE>::S best, int32_t c,
+                                            unsigned long long kid, long long M, int graph) {
   if (c < 0) return false;
   typedef typename Arith<WIDE>::S S;
-  const S g = best - Arith<WIDE>::score(M, (long long)kid, Ki, ld_sig<ASYNC>(a.sig + d) - Ki);
+  const S g = best - Arith<WIDE>::score(M, (long long)kid, Ki, sd - Ki);
   if (!(g > 0)) return false;
-  if (a.guard && c > d && ld_size<ASYNC>(a.csize + d) == 1 && ld_size<ASYNC>(a.csize + c) == 1) return false;
+  if (a.guard && c > d && szd == 1 && ld_size<ASYNC>(a.csize + c) == 1) return false;
   const u128 gv = Arith<WIDE>::to_u128(g);
   if (a.gid) {
     atomicAdd(a.g_moves + graph, 1ull);
@@ -396,7 +467,7 @@ __device__ __forceinline__ bool decide_move(const LMArgs<W>& a, BlockAcc& acc, i
 // reduces and decides; moves queue in shared memory and are committed by the
 // whole block when the queue fills and at the end.
 template <typename W, bool WIDE, bool ASYNC, int CAP, int THREADS>
-__global__ void __launch_bounds__(THREADS, THREADS <= 128 ? 10 : 2)
+__global__ void __launch_bounds__(THREADS, THREADS <= 128 ? 8 : 2)
     lm_block(LMArgs<W> a, const int32_t* __restrict__ verts, int nverts) {
   const IterView iv = iter_view(a);
   typedef typename Arith<WIDE>::S S;
@@ -425,11 +496,11 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 128 ? 10 : 2)
   int p = 0;
   // The next vertex's list entry, activity, row bounds, community and degree
   // are loaded while the current one is processed.
-  VertexInfo nx = vertex_info(a, iv, verts, nverts, blockIdx.x);
+  VertexInfo nx = vertex_info<W, ASYNC>(a, iv, verts, nverts, blockIdx.x);
   for (int vi = blockIdx.x; vi < nverts; vi += gridDim.x) {
     const VertexInfo cur = nx;
     if (!cur.on) {   // uniform across the block
-      nx = vertex_info(a, iv, verts, nverts, vi + gridDim.x);
+      nx = vertex_info<W, ASYNC>(a, iv, verts, nverts, vi + gridDim.x);
       continue;
     }
     const int32_t i = cur.i, d = cur.d;
@@ -464,7 +535,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 128 ? 10 : 2)
         if (fresh) touched[base + __popc(m & lanemask_lt_lm())] = (uint16_t)h;
       }
     }
-    nx = vertex_info(a, iv, verts, nverts, vi + gridDim.x);
+    nx = vertex_info<W, ASYNC>(a, iv, verts, nverts, vi + gridDim.x);
     __syncthreads();   // B1: table complete; warp 0 has finished the previous vertex
     if (q_n >= QCAP) {   // uniform: q_n was last written before this barrier
       flush_moves<W, ASYNC>(a, iv, queue, q_n, threadIdx.x, THREADS);
@@ -510,7 +581,8 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 128 ? 10 : 2)
       if (lane == 0) {
         atomicAdd(&acc.edges, (unsigned long long)(e - b));
         atomicAdd(&acc.visited, 1ull);
-        if (decide_move<W, WIDE, ASYNC>(a, acc, d, Ki, bg, bc, s_kid[p], M, graph)) queue[q_n++] = PendingMove{i, bc, d};
+        if (decide_move<W, WIDE, ASYNC>(a, acc, d, Ki, cur.sd, cur.szd, bg, bc, s_kid[p], M, graph))
+          queue[q_n++] = PendingMove{i, bc, d};
       }
     }
     p ^= 1;
@@ -574,7 +646,7 @@ __global__ void __launch_bounds__(256) lm_hub_insert(LMArgs<W> a, const int32_t*
   const uint32_t cap = (uint32_t)(2 * (e - b));
   const int64_t x0 = b + q * kHubChunk, x1 = min(e, x0 + kHubChunk);
   bool ok = true;
-  constexpr int U = 4;
+  constexpr int U = kHubChunk / 256;
   for (int64_t y = x0; y < x1; y += U * 256) {
     int32_t cc[U];
     unsigned long long ww[U];
@@ -594,11 +666,16 @@ __global__ void __launch_bounds__(256) lm_hub_insert(LMArgs<W> a, const int32_t*
   __syncthreads();
   int32_t* keys = a.hkeys + base;
   unsigned long long* vals = a.hvals + base;
-  for (int t = threadIdx.x; t < CAP; t += blockDim.x) {
-    int32_t c = skeys[t];
-    if (c == kEmpty) continue;
-    bool fresh;
-    ok &= gtable_add(keys, vals, cap, c, (unsigned long long)svals[t], &fresh);
+  constexpr int J = 8;
+  for (int t0 = 0; t0 < CAP; t0 += J * 256) {
+    int32_t kk[J];
+    unsigned long long vv[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      kk[j] = skeys[t0 + j * 256 + threadIdx.x];
+      vv[j] = (unsigned long long)svals[t0 + j * 256 + threadIdx.x];
+    }
+    ok &= gtable_add_many<J>(keys, vals, cap, kk, vv);
   }
   if (!ok) atomicOr(&a.ctr->error, kErrProbe);
 }
@@ -697,7 +774,9 @@ __global__ void __launch_bounds__(256) lm_hub_final(LMArgs<W> a, const int32_t* 
       if (lane == 0) {
         atomicAdd(&acc.edges, (unsigned long long)(e - b));
         atomicAdd(&acc.visited, 1ull);
-        const bool moved = commit_choice<W, WIDE, ASYNC>(a, acc, i, a.memb[i], a.K[i], bg, bc, a.hkid[h], M, graph);
+        const int32_t d = a.memb[i];
+        const bool moved = commit_choice<W, WIDE, ASYNC>(a, acc, i, d, a.K[i], ld_sig<ASYNC>(a.sig + d),
+                                                         ld_size<ASYNC>(a.csize + d), bg, bc, a.hkid[h], M, graph);
         a.hkid[h] = 0;
         if (moved && a.prune) a.hmoved[h] = iv.iter + 1;   // lm_hub_mark marks its neighbours
       }
@@ -855,6 +934,22 @@ void lm_launch_hubs(const LMArgs<W>& a, bool wide, bool async, const int32_t* hu
 }
 
 template <typename W>
+void lm_launch_class(const LMArgs<W>& a, bool wide, bool async, const int32_t* list, const int64_t* ko, int P,
+                     int ch, int64_t nverts, cudaStream_t s) {
+  if (nverts <= 0) return;
+  int64_t blocks = (nverts + 7) / 8;
+  if (blocks > 152 * 4) blocks = 152 * 4;
+  const unsigned g = (unsigned)blocks;
+  if (wide) {
+    if (async) (count_launch(), lm_class<W, true, true><<<g, 256, 0, s>>>(a, list, ko, P, ch));
+    else (count_launch(), lm_class<W, true, false><<<g, 256, 0, s>>>(a, list, ko, P, ch));
+  } else {
+    if (async) (count_launch(), lm_class<W, false, true><<<g, 256, 0, s>>>(a, list, ko, P, ch));
+    else (count_launch(), lm_class<W, false, false><<<g, 256, 0, s>>>(a, list, ko, P, ch));
+  }
+}
+
+template <typename W>
 void lm_launch_hub_mark(const LMArgs<W>& a, const int32_t* hubs, int nhubs, const int64_t* chunk_pre, int64_t nchunks,
                         cudaStream_t s) {
   if (nhubs <= 0 || nchunks <= 0 || !a.prune) return;
@@ -876,6 +971,10 @@ template void lm_launch_hubs<int32_t>(const LMArgs<int32_t>&, bool, bool, const 
                                       int64_t, const int64_t*, int64_t, cudaStream_t);
 template void lm_launch_hubs<int64_t>(const LMArgs<int64_t>&, bool, bool, const int32_t*, int, const int64_t*,
                                       int64_t, const int64_t*, int64_t, cudaStream_t);
+template void lm_launch_class<int32_t>(const LMArgs<int32_t>&, bool, bool, const int32_t*, const int64_t*, int,
+                                       int, int64_t, cudaStream_t);
+template void lm_launch_class<int64_t>(const LMArgs<int64_t>&, bool, bool, const int32_t*, const int64_t*, int,
+                                       int, int64_t, cudaStream_t);
 template void lm_launch_hub_mark<int32_t>(const LMArgs<int32_t>&, const int32_t*, int, const int64_t*, int64_t,
                                           cudaStream_t);
 template void lm_launch_hub_mark<int64_t>(const LMArgs<int64_t>&, const int32_t*, int, const int64_t*, int64_t,
