@@ -379,7 +379,7 @@ def bench_batched(args):
         parts.append((d_off[v0:v1 + 1] - e0, d_col[e0:e1] - v0, d_w[e0:e1]))
     torch.cuda.synchronize()
     stream = torch.cuda.Stream(device=device)
-    opts = dict(mode=mode, prune=1, validate=1)
+    opts = dict(mode=mode, prune=1, validate=1, cuda_graphs=1 if args.cuda_graphs else 0)
     # one at a time
     lv = Louvain(device=device, stream=stream.cuda_stream, **opts)
     biggest = int(np.argmax(np.diff(big.off[vo])))
@@ -444,6 +444,7 @@ def bench_batched(args):
                         "latency_ms_p99": 1e3 * float(np.percentile(blat, 99)), "mean_q": float(q_batch.mean()),
                         "lm_edges_per_s": lm_edges / (lm_ms / 1e3) if lm_ms else None},
             "mapping": {"thresholds": mapping, "autotuned": not args.no_autotune, "best_trial_ms": tune_ms},
+            "cuda_graphs": bool(args.cuda_graphs),
             "speedup_vs_plain": value / (G / plain_s),
             "q_batched_minus_plain": {"mean": float((q_batch - q_plain).mean()),
                                       "min": float((q_batch - q_plain).min())},
@@ -571,6 +572,7 @@ def main():
     ap.add_argument("--mode", default="async", choices=["async", "sync"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="batched workload: keep the default vertex mapping")
+    ap.add_argument("--cuda-graphs", action="store_true", help="batched workload: replay iterations as CUDA graphs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -209,6 +209,17 @@ int louvain_autotune(louvain_ctx *ctx, int32_t *thresholds, double *ms);
  * INTERNAL, TIMEOUT. */
 int louvain_run(louvain_ctx *ctx);
 
+/* Incremental re-run (the dynamic-graph setting the paper gives as motivation,
+ * Section 1): run as louvain_run, but pass 0 starts from memb[n] (kind
+ * `ptr_kind`, n = the loaded n) instead of singletons: community totals and
+ * sizes are summed over its communities, the pass's "before" modularity is
+ * memb's, and pass 0's level is kept even when no vertex moves.  With several
+ * graphs loaded, memb holds global ids and each vertex's id must lie in its
+ * own graph's vertex range.  Singletons give exactly louvain_run's result.
+ * Errors: INVALID_ARG (wrong n, an id out of range: the graph stays loaded),
+ * STATE, CUDA, INTERNAL. */
+int louvain_run_from(louvain_ctx *ctx, const int32_t *memb, int64_t n, int ptr_kind);
+
 /* Top-level community of every input vertex into out[n] (kind `ptr_kind`);
  * community ids are dense in [0, k) by the renumbering rule (ascending old id
  * at every pass); with several graphs loaded, dense per graph.  n must equal

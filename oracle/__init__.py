@@ -64,6 +64,8 @@ def _load():
         lib.or_vertex_gains.restype = i64
         lib.or_louvain.argtypes = [i64, vp, vp, vp, ctypes.POINTER(Options), i32]
         lib.or_louvain.restype = vp
+        lib.or_louvain_from.argtypes = [i64, vp, vp, vp, ctypes.POINTER(Options), i32, vp]
+        lib.or_louvain_from.restype = vp
         lib.or_free.argtypes = [vp]
         lib.or_result_summary.argtypes = [vp, vp, vp]
         lib.or_result_top.argtypes = [vp, vp]
@@ -115,16 +117,24 @@ class Result:
 
 def louvain(off, col, w, mode=SYNC, tolerance=0.01, tolerance_decline=10.0, pass_tolerance=0.0,
             max_iterations=20, max_passes=10, prune=0, singleton_guard=1, subrounds=1,
-            record_levels=False) -> Result:
+            record_levels=False, initial=None) -> Result:
     """Run the oracle Louvain; exact integers for every recorded quantity.
 
-    singleton_guard and subrounds apply to the synchronous mode only."""
+    singleton_guard and subrounds apply to the synchronous mode only.
+    initial: a membership of the input (values in [0, n)) that pass 0 starts
+    from instead of singletons (an incremental re-run)."""
     lib = _load()
     off, col, w = _arrs(off, col, w)
     n = len(off) - 1
     opt = Options.make(mode, tolerance, tolerance_decline, pass_tolerance, max_iterations, max_passes, prune,
                        singleton_guard, subrounds)
-    h = lib.or_louvain(n, off.ctypes.data, col.ctypes.data, w.ctypes.data, ctypes.byref(opt), int(record_levels))
+    init = None
+    if initial is not None:
+        init = np.ascontiguousarray(initial, dtype=np.int32)
+        if init.shape != (n,):
+            raise ValueError("initial membership must have n entries")
+    h = lib.or_louvain_from(n, off.ctypes.data, col.ctypes.data, w.ctypes.data, ctypes.byref(opt),
+                            int(record_levels), None if init is None else init.ctypes.data)
     if not h:
         raise ValueError("oracle: invalid options")
     try:

@@ -302,9 +302,17 @@ void or_free(or_result *r) {
   free(r);
 }
 
-or_result *or_louvain(int64_t n, const int64_t *off, const int32_t *col, const int64_t *w, const or_options *opt,
-                      int record_levels) {
+/* Louvain from an initial membership of the input (init, values in [0, n);
+   NULL = singletons, the method as the paper states it).  With init, pass 0
+   starts from init's communities (totals and sizes summed over their members),
+   its "before" numerator is init's, and its level is kept even when no vertex
+   moves, so the result is never coarser than init's renumbering requires. */
+or_result *or_louvain_from(int64_t n, const int64_t *off, const int32_t *col, const int64_t *w,
+                           const or_options *opt, int record_levels, const int32_t *init) {
   if (opt->max_passes > 64 || opt->max_passes < 0 || opt->max_iterations < 0) return NULL;
+  if (init)
+    for (int64_t v = 0; v < n; ++v)
+      if (init[v] < 0 || init[v] >= n) return NULL;
   or_result *r = (or_result *)calloc(1, sizeof(or_result));
   r->n0 = n;
   r->top = (int32_t *)malloc((size_t)(n ? n : 1) * 4);
@@ -328,9 +336,9 @@ or_result *or_louvain(int64_t n, const int64_t *off, const int32_t *col, const i
   double tol = opt->tolerance;
   i128 Qnum = 0;
   {
-    /* singleton partition of the input */
+    /* the partition pass 0 starts from: singletons, or init */
     int32_t *id = (int32_t *)malloc((size_t)(n ? n : 1) * 4);
-    for (int64_t v = 0; v < n; ++v) id[v] = (int32_t)v;
+    for (int64_t v = 0; v < n; ++v) id[v] = init ? init[v] : (int32_t)v;
     int64_t Mx;
     Qnum = q_numerator(n, g.off, g.col, g.w, id, &Mx);
     free(id);
@@ -346,12 +354,15 @@ or_result *or_louvain(int64_t n, const int64_t *off, const int32_t *col, const i
     int32_t *mv_i = (int32_t *)malloc((size_t)(np ? np : 1) * 4), *mv_c = (int32_t *)malloc((size_t)(np ? np : 1) * 4);
     uint8_t *active = (uint8_t *)malloc((size_t)(np ? np : 1));
     uint8_t *moved = (uint8_t *)calloc((size_t)(np ? np : 1), 1);
+    const int warm = p == 0 && init != NULL;
     for (int64_t i = 0; i < np; ++i) {
       for (int64_t e = g.off[i]; e < g.off[i + 1]; ++e) K[i] += g.w[e];
-      sig[i] = K[i];
-      size[i] = 1;
-      memb[i] = (int32_t)i;
+      memb[i] = warm ? init[i] : (int32_t)i;
       active[i] = 1;
+    }
+    for (int64_t i = 0; i < np; ++i) {
+      sig[memb[i]] += K[i];
+      size[memb[i]] += 1;
     }
     i128 Nbefore = Qnum;
     scratch s;
@@ -419,7 +430,7 @@ or_result *or_louvain(int64_t n, const int64_t *off, const int32_t *col, const i
     r->pass_Nbefore[p] = Nbefore;
     r->npasses = p + 1;
     free(s.acc); free(s.seen); free(mv_i); free(mv_c); free(active); free(moved); free(size);
-    if (pass_moves == 0) {
+    if (pass_moves == 0 && !warm) {
       r->pass_Nafter[p] = Nbefore;
       r->pass_k[p] = np;
       free(K); free(sig); free(memb);
@@ -469,6 +480,11 @@ or_result *or_louvain(int64_t n, const int64_t *off, const int32_t *col, const i
   r->Qnum = Qnum;
   r->Q = (M == 0) ? 0.0 : dbl_ratio(Qnum, M2);
   return r;
+}
+
+or_result *or_louvain(int64_t n, const int64_t *off, const int32_t *col, const int64_t *w, const or_options *opt,
+                      int record_levels) {
+  return or_louvain_from(n, off, col, w, opt, record_levels, NULL);
 }
 
 /* ------------------------------------------------------------ accessors */

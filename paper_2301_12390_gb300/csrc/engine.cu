@@ -121,6 +121,7 @@ struct louvain_ctx {
   int32_t* hmoved = nullptr;   // local moving: iteration + 1 of a hub's last move (by hub-list position)
   int32_t* d_gsmall = nullptr; // per graph: fewer than kSmallGraph vertices (its class schedule)
   LMThresholds thr = {{kLMCap[0], kLMCap[1], kLMCap[2], kLMCap[3], kLMCap[4]}};   // degree mapping
+  bool warm = false;           // this run's pass 0 starts from the membership in memb
   int32_t* crow = nullptr;     // aggregation: first row of each relabel chunk      // aggregation: direct-table first key per global community, or -1
   unsigned long long* hkid = nullptr;
   long long* hpart = nullptr;
@@ -702,7 +703,22 @@ int run_pass(louvain_ctx* c, const PassState& g, int pass, double* tol, bool wid
   pr.info.n = g.n;
   pr.info.nnz = g.nnz;
   CK(cudaEventRecord(c->ev[0], s));
-  pass_init(g.n, c->K, c->memb, c->sig, c->csize, c->stamp[0], c->stamp[1], s);
+  // pass 0 of louvain_run_from starts from the caller's membership (in memb)
+  const bool warm = pass == 0 && c->warm;
+  if (warm) {
+    CK(cudaMemsetAsync(c->flags, 0, sizeof(int), s));
+    pass_init_from(g.n, c->K, c->memb, c->sig, c->csize, c->stamp[0], c->stamp[1], multi ? c->gid : nullptr,
+                   multi ? c->vo : nullptr, c->flags, s);
+    CKLAUNCH();
+    int flag = 0;
+    if (int r = fetch(c, &flag, c->flags, sizeof(int))) return r;
+    if (flag) return fail(c, LOUVAIN_ERR_INVALID_ARG, "initial membership: an id outside its graph's vertex range");
+    std::vector<i128> n0(G, 0);
+    if (int r = q_numerators<W>(c, g, n0)) return r;
+    for (int64_t q = 0; q < G; ++q) c->gst[q].qnum = n0[q];
+  } else {
+    pass_init(g.n, c->K, c->memb, c->sig, c->csize, c->stamp[0], c->stamp[1], s);
+  }
   CKLAUNCH();
   const i128 nbefore = c->gst[0].qnum;
   int64_t edges = 0, visited = 0;
@@ -728,7 +744,7 @@ int run_pass(louvain_ctx* c, const PassState& g, int pass, double* tol, bool wid
   for (int64_t q = 0; q < G; ++q)
     if (!c->gst[q].stopped) c->gst[q].passes++;
   float ms_init = 0, ms_lm = 0;
-  if (pmoves == 0) {
+  if (pmoves == 0 && !warm) {
     // no graph moved: every graph stops, nothing to renumber
     CK(cudaEventSynchronize(c->ev[2]));
     cudaEventElapsedTime(&ms_init, c->ev[0], c->ev[1]);
@@ -780,7 +796,7 @@ int run_pass(louvain_ctx* c, const PassState& g, int pass, double* tol, bool wid
   for (int64_t q = 0; q < G; ++q) {
     GraphState& st = c->gst[q];
     if (st.stopped) continue;
-    if (st.pass_moves == 0) {
+    if (st.pass_moves == 0 && !warm) {
       st.stopped = true;   // its level is the identity: nothing changes
     } else {
       const i128 gain = nafter[q] - st.qnum;
@@ -1335,6 +1351,36 @@ int louvain_autotune(louvain_ctx* c, int32_t* thresholds, double* ms) {
   if (thresholds)
     for (int b = 0; b < 5; ++b) thresholds[b] = c->thr.t[b];
   if (ms) *ms = best;
+  return 0;
+}
+
+int louvain_run_from(louvain_ctx* c, const int32_t* memb, int64_t n, int ptr_kind) {
+  if (!c) return LOUVAIN_ERR_INVALID_ARG;
+  if (!c->loaded) return fail(c, LOUVAIN_ERR_STATE, "no graph loaded");
+  if (n != c->n0 || (!memb && n > 0) || (ptr_kind != LOUVAIN_PTR_HOST && ptr_kind != LOUVAIN_PTR_DEVICE))
+    return fail(c, LOUVAIN_ERR_INVALID_ARG, "the initial membership must have the loaded n entries");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, LOUVAIN_ERR_CUDA, "cudaSetDevice failed");
+  c->ran = false;
+  if (n > 0) {
+    const cudaMemcpyKind kind = ptr_kind == LOUVAIN_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (cudaMemcpyAsync(c->memb, memb, n * sizeof(int32_t), kind, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream) != cudaSuccess)
+      return fail(c, LOUVAIN_ERR_CUDA, "copy of the initial membership failed");
+    check_membership(n, c->memb, c->G > 1 ? c->gid0 : nullptr, c->G > 1 ? c->vo0 : nullptr, c->flags, c->stream);
+    int flag = 0;
+    if (cudaGetLastError() != cudaSuccess || fetch(c, &flag, c->flags, sizeof(int)))
+      return fail(c, LOUVAIN_ERR_CUDA, "membership check failed");
+    if (flag) return fail(c, LOUVAIN_ERR_INVALID_ARG, "initial membership: an id outside its graph's vertex range");
+  }
+  c->warm = true;
+  int r = run_all(c);
+  c->warm = false;
+  if (r) {
+    c->tables_dirty = true;
+    c->loaded = false;   // load again before the next run
+    return r;
+  }
+  c->ran = true;
   return 0;
 }
 

@@ -26,7 +26,7 @@ __host__ __device__ inline int lm_bucket_of(int64_t deg, const LMThresholds& th)
     if (deg <= th.t[b]) return b;
   return 5;
 }
-constexpr int64_t kHubChunkEntries = 2048;   // entries per insert block of a hub
+constexpr int64_t kHubChunkEntries = 1024;   // entries per insert block of a hub
 constexpr int64_t kSlotChunk = 4096;         // table slots per scan block (hubs and large communities)
 
 // Community classes of the aggregation phase by total member degree.
@@ -101,6 +101,14 @@ void row_sums(const int64_t* off, const int32_t* col, const W* wt, int64_t n, lo
 // Pass set-up: memb = identity, Sigma = K, sizes 1, stamps -1.
 void pass_init(int64_t n, const long long* K, int32_t* memb, long long* sig, int32_t* csize, int32_t* stampA,
                int32_t* stampB, cudaStream_t s);
+// *flag |= 1 if some memb[i] lies outside vertex i's graph's range (gid and
+// vo null: outside [0, n)).
+void check_membership(int64_t n, const int32_t* memb, const int32_t* gid, const int64_t* vo, int* flag,
+                      cudaStream_t s);
+// Pass 0 from the membership already in memb (validated per graph; *flag set
+// on a bad id): Sigma and sizes summed over the communities' members.
+void pass_init_from(int64_t n, const long long* K, int32_t* memb, long long* sig, int32_t* csize, int32_t* stampA,
+                    int32_t* stampB, const int32_t* gid, const int64_t* vo, int* flag, cudaStream_t s);
 
 // Modularity numerator parts: sumL (u64) += weights inside communities,
 // ss (u128 lo/hi) += sum over c < n of sig[c]^2.

@@ -376,6 +376,52 @@ void pass_init(int64_t n, const long long* K, int32_t* memb, long long* sig, int
   if (n > 0) (count_launch(), pass_init_k<<<grid1d(n), kT, 0, s>>>(n, K, memb, sig, csize, stampA, stampB));
 }
 
+// Pass 0 from a given membership (already in memb): ids must lie in the
+// vertex's graph's range [vo[g], vo[g + 1]) (one graph: [0, n)); a bad id
+// sets *flag and is replaced by the vertex itself.  Then Sigma and sizes.
+__global__ void pass_init_from_k(int64_t n, int32_t* memb, int32_t* sa, int32_t* sb, const int32_t* __restrict__ gid,
+                                 const int64_t* __restrict__ vo, int* flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t lo = gid ? vo[gid[i]] : 0, hi = gid ? vo[gid[i] + 1] : n;
+    const int32_t c = memb[i];
+    if (c < lo || c >= hi) {
+      atomicOr(flag, 1);
+      memb[i] = (int32_t)i;
+    }
+    sa[i] = -1;
+    sb[i] = -1;
+  }
+}
+__global__ void community_sizes_k(const long long* K, const int32_t* memb, int64_t n, long long* sig, int32_t* csize) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = memb[i];
+    atomicAdd((unsigned long long*)(sig + c), (unsigned long long)K[i]);
+    atomicAdd(csize + c, 1);
+  }
+}
+
+__global__ void check_membership_k(int64_t n, const int32_t* __restrict__ memb, const int32_t* __restrict__ gid,
+                                   const int64_t* __restrict__ vo, int* flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t lo = gid ? vo[gid[i]] : 0, hi = gid ? vo[gid[i] + 1] : n;
+    if (memb[i] < lo || memb[i] >= hi) atomicOr(flag, 1);
+  }
+}
+
+void check_membership(int64_t n, const int32_t* memb, const int32_t* gid, const int64_t* vo, int* flag,
+                      cudaStream_t s) {
+  if (n > 0) (count_launch(), check_membership_k<<<grid1d(n), kT, 0, s>>>(n, memb, gid, vo, flag));
+}
+
+void pass_init_from(int64_t n, const long long* K, int32_t* memb, long long* sig, int32_t* csize, int32_t* stampA,
+                    int32_t* stampB, const int32_t* gid, const int64_t* vo, int* flag, cudaStream_t s) {
+  if (n <= 0) return;
+  cudaMemsetAsync(sig, 0, n * sizeof(long long), s);
+  cudaMemsetAsync(csize, 0, n * sizeof(int32_t), s);
+  (count_launch(), pass_init_from_k<<<grid1d(n), kT, 0, s>>>(n, memb, stampA, stampB, gid, vo, flag));
+  (count_launch(), community_sizes_k<<<grid1d(n), kT, 0, s>>>(K, memb, n, sig, csize));
+}
+
 template <typename W>
 __global__ void __launch_bounds__(kT) intra_weight_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
                                                      const W* __restrict__ wt, int64_t n,

@@ -336,7 +336,7 @@ __device__ __forceinline__ void warp_vertex(const LMArgs<W>& a, const IterView& 
 // U entries per lane are loaded and gathered before any insert (U * 32 covers
 // the bucket's largest degree), so their memory latencies overlap.
 template <typename W, bool WIDE, bool ASYNC, int CAP, int U>
-__global__ void __launch_bounds__(256, 3) lm_warp(LMArgs<W> a, const int32_t* __restrict__ verts, int nverts) {
+__global__ void __launch_bounds__(256, 4) lm_warp(LMArgs<W> a, const int32_t* __restrict__ verts, int nverts) {
   const IterView iv = iter_view(a);
   typedef typename Arith<WIDE>::S S;
   typedef typename TableVal<WIDE>::T V;

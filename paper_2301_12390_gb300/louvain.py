@@ -257,6 +257,13 @@ class Louvain:
     def run(self):
         self._check(self.lib.louvain_run(self.h))
 
+    def run_from(self, memb):
+        """Incremental re-run: pass 0 starts from membership memb (host array or device tensor, n entries)."""
+        if not _is_device(memb):
+            memb = np.ascontiguousarray(memb, dtype=np.int32)
+        self._check(self.lib.louvain_run_from(self.h, _ptr(memb), self.n,
+                                              PTR_DEVICE if _is_device(memb) else PTR_HOST))
+
     def membership(self, out=None) -> np.ndarray:
         if out is None:
             out = np.empty(self.n, np.int32)
@@ -381,6 +388,7 @@ SIGNATURES += [
     ("louvain_set_mapping", _I32, [_VP, _VP]),
     ("louvain_get_mapping", _I32, [_VP, _VP]),
     ("louvain_autotune", _I32, [_VP, _VP, ctypes.POINTER(ctypes.c_double)]),
+    ("louvain_run_from", _I32, [_VP, _VP, _I64, _I32]),
 ]
 
 

@@ -159,6 +159,66 @@ def test_autotune_keeps_results():
     assert exact == (ref.q_num, ref.M)
 
 
+# ------------------------------------------ incremental re-runs (warm start)
+
+@pytest.mark.parametrize("name", ["sbm600", "rmat16", "road128"])
+def test_sync_run_from_matches_oracle(name):
+    """Pass 0 from a given membership: bit-exact sync parity with the oracle
+    started from the same membership (a random one, the identity, and the
+    graph's own previous result)."""
+    g = G[name]
+    rng = np.random.default_rng(5)
+    inits = [rng.integers(0, g.n, g.n).astype(np.int32), np.arange(g.n, dtype=np.int32)]
+    with Louvain(device=0, mode=0, prune=1) as lv:
+        lv.load_csr(g.off, g.col, g.w)
+        lv.run()
+        inits.append(lv.membership())
+        for init in inits:
+            lv.run_from(init)
+            top, exact = lv.membership(), lv.modularity_exact()
+            its = lv.iterations()
+            ref = oracle.louvain(g.off, g.col, g.w, mode=oracle.SYNC, prune=1, initial=init)
+            assert np.array_equal(top, ref.top)
+            assert exact == (ref.q_num, ref.M)
+            assert its == list(ref.iterations)
+
+
+def test_async_run_from_keeps_quality_and_rejects_bad_ids():
+    g = G["sbm8192"]
+    with Louvain(device=0, mode=1, prune=1) as lv:
+        lv.load_csr(g.off, g.col, g.w)
+        lv.run()
+        prev = lv.membership()
+        q_prev = lv.modularity()
+        lv.run_from(prev)
+        assert lv.modularity() >= q_prev - 0.01
+        bad = prev.copy()
+        bad[3] = g.n
+        with pytest.raises(LouvainError):
+            lv.run_from(bad)
+        lv.run()   # the graph stays loaded after a rejected membership
+        assert lv.modularity() > 0.5
+
+
+def test_batch_run_from_equals_each_graph_alone():
+    """Several graphs: a run from per-graph memberships (global ids) gives,
+    in sync mode, each graph's result from its own membership alone."""
+    gs = [G["sbm600"], G["road128"], gg.sbm(3, 300, 6, 0.2, 0.02)]
+    big, vo = gg.concat(gs)
+    rng = np.random.default_rng(9)
+    init = np.concatenate([vo[k] + rng.integers(0, g.n, g.n) for k, g in enumerate(gs)]).astype(np.int32)
+    with Louvain(device=0, mode=0, prune=1) as lv:
+        lv.load_batch(vo, big.off, big.col, big.w)
+        lv.run_from(init)
+        memb = lv.membership()
+        q, nums, Ms = lv.batch_modularity()
+    for k, g in enumerate(gs):
+        ref = oracle.louvain(g.off, g.col, g.w, mode=oracle.SYNC, prune=1,
+                             initial=init[vo[k]:vo[k + 1]] - vo[k])
+        assert np.array_equal(memb[vo[k]:vo[k + 1]], ref.top), k
+        assert nums[k] == ref.q_num, k
+
+
 # ------------------------------------------------------- async quality
 
 @pytest.mark.parametrize("name", ["sbm600", "rmat16", "road128"])

@@ -347,3 +347,58 @@ def test_empty_and_edgeless_graphs():
     g = gg.from_weighted_edges(3, [(1, 1, 4)])   # a lone self-loop: nothing to move to
     r = run(g)
     assert list(r.top) == [0, 1, 2] and r.passes[0].moves == 0
+
+
+# ------------------------------------------ incremental re-runs (warm start)
+
+@pytest.mark.parametrize("mode", [oracle.SYNC, oracle.ASYNC])
+@pytest.mark.parametrize("prune", [0, 1])
+def test_warm_start_from_singletons_is_the_cold_run(mode, prune):
+    """Starting from the singleton partition is the method as stated: the
+    same iterations, passes, levels and result."""
+    rng = random.Random(7)
+    for trial in range(4):
+        g = gg.sbm(100 + trial, 120, 4, 0.3, 0.03, wmin=1, wmax=4)
+        cold = run(g, mode=mode, prune=prune, record_levels=True)
+        warm = run(g, mode=mode, prune=prune, record_levels=True, initial=np.arange(g.n))
+        assert np.array_equal(cold.top, warm.top) and cold.q_num == warm.q_num
+        assert cold.iterations == warm.iterations
+        for a, b in zip(cold.passes, warm.passes):
+            assert (a.n, a.nnz, a.k, a.moves, a.n_before, a.n_after) == (b.n, b.nnz, b.k, b.moves, b.n_before, b.n_after)
+
+
+def test_warm_start_async_never_lowers_the_initial_modularity():
+    """Sequential moves only take positive gains and aggregation keeps Q, so
+    an asynchronous re-run ends at least at the initial partition's Q."""
+    rng = random.Random(11)
+    for trial in range(12):
+        g = gg.sbm(200 + trial, 90, 3, 0.3, 0.05, wmin=1, wmax=5)
+        init = np.array([rng.randrange(g.n) for _ in range(g.n)], np.int32)
+        q0, _, _ = oracle.modularity(g.off, g.col, g.w, init)
+        r = run(g, mode=oracle.ASYNC, initial=init)
+        assert r.passes[0].n_before == oracle.modularity(g.off, g.col, g.w, init)[1]
+        assert r.Q >= q0 - 1e-12, (r.Q, q0)
+
+
+def test_warm_start_where_nothing_can_move_keeps_the_initial_partition():
+    """No vertex has a neighbour outside its community (one community per
+    connected piece): nothing moves, and the result is the initial partition,
+    renumbered, with its own modularity; from the clique partition of
+    disjoint cliques likewise (Q = 1 - 1/k)."""
+    g = cliques(3, 4)
+    one = np.zeros(g.n, np.int32)
+    for mode in (oracle.SYNC, oracle.ASYNC):
+        r = run(g, mode=mode, initial=one)
+        assert len(r.passes) == 1 and r.passes[0].moves == 0
+        assert np.array_equal(r.top, one) and r.q_num == oracle.modularity(g.off, g.col, g.w, one)[1]
+        blocks = (np.arange(g.n) // 4).astype(np.int32) * 4   # ids 0, 4, 8: renumbered to 0, 1, 2
+        r = run(g, mode=mode, initial=blocks)
+        assert np.array_equal(r.top, np.arange(g.n) // 4)
+        assert Fraction(int(r.q_num), r.M * r.M) == 1 - Fraction(1, 3)
+
+
+def test_warm_start_rejects_out_of_range_memberships():
+    g = cliques(2, 3)
+    for bad in ([0, 1, 2, 3, 4, 6], [-1, 0, 0, 0, 0, 0]):
+        with pytest.raises(ValueError):
+            run(g, initial=np.array(bad, np.int32))
