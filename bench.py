@@ -516,6 +516,7 @@ def bench_serving(args):
                 for x in srv.poll(wait_ms=100):
                     results[x["id"]] = x
             st = srv.stats()
+            tm = srv.timings()
         lat = np.array([results[r]["done_s"] - results[r]["submit_s"] for r in range(R)])
         span = max(results[r]["done_s"] for r in range(R)) - min(results[r]["submit_s"] for r in range(R))
         q = np.array([results[r]["q"] for r in range(R)])
@@ -524,7 +525,7 @@ def bench_serving(args):
         return {"graphs_per_s": R / span, "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
                 "latency_ms_p99": 1e3 * float(np.percentile(lat, 99)), "makespan_s": span, "runs": st["runs"],
                 "mean_q": float(q.mean()), "all_ok": ok, "peak_reserved_gb": st["peak_reserved_bytes"] / 1e9,
-                "mean_batch": float(bsz.mean())}, q
+                "mean_batch": float(bsz.mean()), "slot_seconds": {k: round(v, 3) for k, v in tm.items()}}, q
 
     clocks = Clocks(0)
     plain, q_plain = run_arm(slots=1, batch_max_entries=0)

@@ -172,6 +172,14 @@ int louvain_load_batch(louvain_ctx *ctx, int64_t num_graphs, const int64_t *grap
 /* Number of graphs loaded (1 after louvain_load_csr). */
 int louvain_get_num_graphs(louvain_ctx *ctx, int64_t *num_graphs);
 
+/* Load num_graphs graphs given as separate host CSRs (graph g: ns[g] vertices,
+ * nnzs[g] entries, offsets[g], cols[g], weights[g] as in louvain_load_csr, ids
+ * local to the graph): the same as louvain_load_batch of their block-diagonal
+ * concatenation, without building it on the host (each graph is copied to its
+ * place on the device, ids rebased there).  Errors as louvain_load_batch. */
+int louvain_load_parts(louvain_ctx *ctx, int64_t num_graphs, const int64_t *ns, const int64_t *nnzs,
+                       const int64_t *const *offsets, const int32_t *const *cols, const int32_t *const *weights);
+
 /* Per graph g < num_graphs: modularity q[g]; exact numerator and M
  * (num_hi, num_lo, M may be NULL), host arrays of num_graphs entries. */
 int louvain_batch_get_modularity(louvain_ctx *ctx, double *q, int64_t *num_hi, uint64_t *num_lo, int64_t *M);
@@ -219,6 +227,19 @@ int louvain_run(louvain_ctx *ctx);
  * Errors: INVALID_ARG (wrong n, an id out of range: the graph stays loaded),
  * STATE, CUDA, INTERNAL. */
 int louvain_run_from(louvain_ctx *ctx, const int32_t *memb, int64_t n, int ptr_kind);
+
+/* Partition, then merge (one graph loaded): vertex u goes to part
+ * floor(u * parts / n); every part's induced subgraph (the entries whose ends
+ * share a part) runs on its own, all parts together as one batch in a second
+ * context on the same device and stream; then the whole graph runs from the
+ * parts' communities (louvain_run_from), whose pass 0 moves vertices across
+ * part boundaries and whose later passes merge communities.  parts = 1 is
+ * louvain_run.  *parts_ms (may be NULL) gets the parts' run time; statistics
+ * and results are those of the whole-graph run.  Not in the paper (Section 2
+ * reviews partition-based methods): the single-graph basis for spreading one
+ * graph over several GPUs.  Errors: INVALID_ARG, STATE (no graph, or several
+ * loaded), OOM, CUDA, INTERNAL. */
+int louvain_run_partitioned(louvain_ctx *ctx, int64_t parts, double *parts_ms);
 
 /* Top-level community of every input vertex into out[n] (kind `ptr_kind`);
  * community ids are dense in [0, k) by the renumbering rule (ascending old id
@@ -331,6 +352,10 @@ int louvain_server_poll(louvain_server *srv, louvain_server_result *out, int64_t
 int louvain_server_membership(louvain_server *srv, int64_t request_id, int32_t *out, int64_t n);
 /* out: submitted, finished, runs, queued, reserved bytes, peak reserved, budget, slots. */
 int louvain_server_stats(louvain_server *srv, int64_t out[8]);
+/* Seconds spent, summed over all runs of all slots, in: assembling batches on
+ * the host, loading them (copy to the device, validation), running them, and
+ * fetching results (memberships, modularities). */
+int louvain_server_timings(louvain_server *srv, double out[4]);
 /* Finishes every queued request, then frees everything. */
 void louvain_server_destroy(louvain_server *srv);
 

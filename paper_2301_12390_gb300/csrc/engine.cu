@@ -122,6 +122,7 @@ struct louvain_ctx {
   int32_t* d_gsmall = nullptr; // per graph: fewer than kSmallGraph vertices (its class schedule)
   LMThresholds thr = {{kLMCap[0], kLMCap[1], kLMCap[2], kLMCap[3], kLMCap[4]}};   // degree mapping
   bool warm = false;           // this run's pass 0 starts from the membership in memb
+  louvain_ctx* sub = nullptr;  // louvain_run_partitioned: the parts' context (same device and stream)
   int32_t* crow = nullptr;     // aggregation: first row of each relabel chunk      // aggregation: direct-table first key per global community, or -1
   unsigned long long* hkid = nullptr;
   long long* hpart = nullptr;
@@ -1169,15 +1170,24 @@ namespace {
 
 // Load one graph (G = 1) or G graphs whose vertices are the contiguous ranges
 // [vo[g], vo[g + 1]) of one CSR with no entry between ranges (vo: host).
+// Graphs given as separate host CSRs (louvain_load_parts).
+struct PartsIn {
+  const int64_t* nnz;
+  const int64_t* const* off;
+  const int32_t* const* col;
+  const int32_t* const* w;
+};
+
 int load_graphs(louvain_ctx* c, int64_t G, const int64_t* vo, int64_t n, int64_t nnz, const int64_t* offsets,
-                const int32_t* cols, const int32_t* weights, int ptr_kind) {
+                const int32_t* cols, const int32_t* weights, int ptr_kind, const PartsIn* parts = nullptr) {
   if (!c) return LOUVAIN_ERR_INVALID_ARG;
   if (n < 0 || nnz < 0 || (ptr_kind != LOUVAIN_PTR_HOST && ptr_kind != LOUVAIN_PTR_DEVICE))
     return fail(c, LOUVAIN_ERR_INVALID_ARG, "negative size or bad pointer kind");
-  if (!offsets || (nnz > 0 && (!cols || !weights))) return fail(c, LOUVAIN_ERR_INVALID_ARG, "null pointer");
+  if (!parts && (!offsets || (nnz > 0 && (!cols || !weights))))
+    return fail(c, LOUVAIN_ERR_INVALID_ARG, "null pointer");
   if (n >= (1ll << 31) - 1) return fail(c, LOUVAIN_ERR_OVERFLOW, "n must be below 2^31 - 1");
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, LOUVAIN_ERR_CUDA, "cudaSetDevice failed");
-  if (ptr_kind == LOUVAIN_PTR_HOST) {
+  if (ptr_kind == LOUVAIN_PTR_HOST && !parts) {
     // cheap host checks first
     if (offsets[0] != 0 || offsets[n] != nnz) return fail(c, LOUVAIN_ERR_BAD_CSR, "offsets[0] != 0 or offsets[n] != nnz");
   }
@@ -1191,10 +1201,28 @@ int load_graphs(louvain_ctx* c, int64_t G, const int64_t* vo, int64_t n, int64_t
   const int64_t N1 = n + 1;
   cudaStream_t s = c->stream;
   cudaMemcpyKind kind = ptr_kind == LOUVAIN_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-  CK(cudaMemcpyAsync(c->off0, offsets, N1 * sizeof(int64_t), kind, s));
-  if (nnz) {
-    CK(cudaMemcpyAsync(c->col0, cols, nnz * sizeof(int32_t), kind, s));
-    CK(cudaMemcpyAsync(c->w0, weights, nnz * sizeof(int32_t), kind, s));
+  if (parts) {
+    // each graph straight to its place; offsets and columns rebased on the device
+    std::vector<int64_t> eo(G + 1, 0);
+    for (int64_t q = 0; q < G; ++q) eo[q + 1] = eo[q] + parts->nnz[q];
+    for (int64_t q = 0; q < G; ++q) {
+      const int64_t nq = vo[q + 1] - vo[q], eq = parts->nnz[q];
+      if (nq) CK(cudaMemcpyAsync(c->off0 + vo[q], parts->off[q], nq * sizeof(int64_t), kind, s));
+      if (eq) {
+        CK(cudaMemcpyAsync(c->col0 + eo[q], parts->col[q], eq * sizeof(int32_t), kind, s));
+        CK(cudaMemcpyAsync(c->w0 + eo[q], parts->w[q], eq * sizeof(int32_t), kind, s));
+      }
+    }
+    CK(cudaMemcpyAsync(c->vo0, vo, (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->vo_a, eo.data(), (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    rebase_parts(c->off0, c->col0, n, nnz, c->vo0, c->vo_a, (int)G, s);
+    CK(cudaStreamSynchronize(s));   // eo goes out of scope
+  } else {
+    CK(cudaMemcpyAsync(c->off0, offsets, N1 * sizeof(int64_t), kind, s));
+    if (nnz) {
+      CK(cudaMemcpyAsync(c->col0, cols, nnz * sizeof(int32_t), kind, s));
+      CK(cudaMemcpyAsync(c->w0, weights, nnz * sizeof(int32_t), kind, s));
+    }
   }
   if (c->tables_dirty) {
     // global tables start empty; every later use clears what it touched
@@ -1315,6 +1343,27 @@ int louvain_load_batch(louvain_ctx* c, int64_t num_graphs, const int64_t* graph_
 }
 
 
+int louvain_load_parts(louvain_ctx* c, int64_t num_graphs, const int64_t* ns, const int64_t* nnzs,
+                       const int64_t* const* offsets, const int32_t* const* cols, const int32_t* const* weights) {
+  if (!c) return LOUVAIN_ERR_INVALID_ARG;
+  if (num_graphs < 1 || !ns || !nnzs || !offsets || !cols || !weights)
+    return fail(c, LOUVAIN_ERR_INVALID_ARG, "num_graphs >= 1 and every array given");
+  std::vector<int64_t> vo(num_graphs + 1, 0);
+  int64_t nnz = 0;
+  for (int64_t q = 0; q < num_graphs; ++q) {
+    if (ns[q] < 0 || nnzs[q] < 0 || !offsets[q] || (nnzs[q] > 0 && (!cols[q] || !weights[q])))
+      return fail(c, LOUVAIN_ERR_INVALID_ARG, "negative size or null pointer in a graph");
+    if (offsets[q][0] != 0 || offsets[q][ns[q]] != nnzs[q])
+      return fail(c, LOUVAIN_ERR_BAD_CSR, "offsets[0] != 0 or offsets[n] != nnz in a graph");
+    vo[q + 1] = vo[q] + ns[q];
+    nnz += nnzs[q];
+  }
+  const int64_t n = vo[num_graphs];
+  if (num_graphs > n + 1) return fail(c, LOUVAIN_ERR_INVALID_ARG, "more graphs than vertices + 1");
+  PartsIn parts{nnzs, offsets, cols, weights};
+  return load_graphs(c, num_graphs, vo.data(), n, nnz, nullptr, nullptr, nullptr, LOUVAIN_PTR_HOST, &parts);
+}
+
 int louvain_set_mapping(louvain_ctx* c, const int32_t* thresholds) {
   if (!c) return LOUVAIN_ERR_INVALID_ARG;
   LMThresholds th = {{kLMCap[0], kLMCap[1], kLMCap[2], kLMCap[3], kLMCap[4]}};
@@ -1382,6 +1431,55 @@ int louvain_run_from(louvain_ctx* c, const int32_t* memb, int64_t n, int ptr_kin
   }
   c->ran = true;
   return 0;
+}
+
+int louvain_run_partitioned(louvain_ctx* c, int64_t parts, double* parts_ms) {
+  if (!c) return LOUVAIN_ERR_INVALID_ARG;
+  if (!c->loaded) return fail(c, LOUVAIN_ERR_STATE, "no graph loaded");
+  if (c->G != 1) return fail(c, LOUVAIN_ERR_STATE, "partition-then-merge takes one loaded graph");
+  if (parts < 1) return fail(c, LOUVAIN_ERR_INVALID_ARG, "parts must be >= 1");
+  const int64_t n = c->n0, nnz = c->nnz0;
+  if (parts > n) parts = n > 0 ? n : 1;
+  if (parts_ms) *parts_ms = 0;
+  if (parts == 1 || n == 0) return louvain_run(c);
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, LOUVAIN_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t s = c->stream;
+  c->ran = false;
+  // 1. the parts' induced subgraphs, as one block-diagonal CSR in the coarse
+  //    buffers (free before a run)
+  int64_t* flags = (int64_t*)c->tw;
+  int64_t* pos = (int64_t*)c->wX[1];
+  induced_parts(c->off0, c->col0, c->w0, n, nnz, parts, flags, pos, c->scal, c->offX[0], c->colX[0],
+                (int32_t*)c->wX[0], c->tmp, s);
+  CKLAUNCH();
+  int64_t nnz_sub = 0;
+  if (int r = fetch(c, &nnz_sub, c->scal, sizeof(int64_t))) return r;
+  std::vector<int64_t> vo(parts + 1);
+  for (int64_t p = 0; p <= parts; ++p) vo[p] = (p * n + parts - 1) / parts;
+  // 2. every part on its own, in one batched run of a second context
+  if (!c->sub) {
+    louvain_options o = c->opt;
+    o.validate = 0;        // an induced subgraph of a valid graph is valid
+    o.record_levels = 0;
+    if (louvain_create(&c->sub, &o, c->device, (void*)s)) return fail(c, LOUVAIN_ERR_CUDA, "parts context");
+  } else {
+    louvain_options o = c->opt;
+    o.validate = 0;
+    o.record_levels = 0;
+    louvain_set_options(c->sub, &o);
+  }
+  c->sub->thr = c->thr;
+  int r = louvain_load_batch(c->sub, parts, vo.data(), n, nnz_sub, c->offX[0], c->colX[0], (int32_t*)c->wX[0],
+                             LOUVAIN_PTR_DEVICE);
+  if (!r) r = louvain_run(c->sub);
+  if (r) return fail(c, r, std::string("parts run: ") + louvain_last_error(c->sub));
+  if (parts_ms) *parts_ms = c->sub->stats.total_ms;
+  // 3. merge: the whole graph from the parts' communities (global ids)
+  if ((r = louvain_get_membership(c->sub, c->level, n, LOUVAIN_PTR_DEVICE)))
+    return fail(c, r, std::string("parts membership: ") + louvain_last_error(c->sub));
+  part_base(c->level, n, parts, s);
+  CKLAUNCH();
+  return louvain_run_from(c, c->level, n, LOUVAIN_PTR_DEVICE);
 }
 
 int louvain_run(louvain_ctx* c) {
@@ -1584,6 +1682,7 @@ int louvain_get_device_bytes(louvain_ctx* c, int64_t* bytes) {
 
 void louvain_destroy(louvain_ctx* c) {
   if (!c) return;
+  if (c->sub) louvain_destroy(c->sub);
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   free_all(c);

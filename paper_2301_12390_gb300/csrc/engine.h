@@ -101,6 +101,17 @@ void row_sums(const int64_t* off, const int32_t* col, const W* wt, int64_t n, lo
 // Pass set-up: memb = identity, Sigma = K, sizes 1, stamps -1.
 void pass_init(int64_t n, const long long* K, int32_t* memb, long long* sig, int32_t* csize, int32_t* stampA,
                int32_t* stampB, cudaStream_t s);
+// Partition, then merge: vertex u in part floor(u * parts / n) (part p's
+// first vertex ceil(p * n / parts)); induced_parts writes the induced
+// subgraphs' block-diagonal CSR (flags, pos: nnz scratch; total: 1 device
+// int64); part_base turns part-local community ids into global ones.
+void induced_parts(const int64_t* off, const int32_t* col, const int32_t* w, int64_t n, int64_t nnz, int64_t parts,
+                   int64_t* flags, int64_t* pos, int64_t* total, int64_t* off_sub, int32_t* col_sub, int32_t* w_sub,
+                   void* tmp, cudaStream_t s);
+void part_base(int32_t* memb, int64_t n, int64_t parts, cudaStream_t s);
+// Shift the offsets and columns of graphs copied side by side (see louvain_load_parts).
+void rebase_parts(int64_t* off, int32_t* col, int64_t n, int64_t nnz, const int64_t* vo, const int64_t* eo, int G,
+                  cudaStream_t s);
 // *flag |= 1 if some memb[i] lies outside vertex i's graph's range (gid and
 // vo null: outside [0, n)).
 void check_membership(int64_t n, const int32_t* memb, const int32_t* gid, const int64_t* vo, int* flag,

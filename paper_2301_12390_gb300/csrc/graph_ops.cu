@@ -376,6 +376,94 @@ void pass_init(int64_t n, const long long* K, int32_t* memb, long long* sig, int
   if (n > 0) (count_launch(), pass_init_k<<<grid1d(n), kT, 0, s>>>(n, K, memb, sig, csize, stampA, stampB));
 }
 
+// ------------------------------------------------ partition, then merge
+//
+// Vertex u belongs to part floor(u * parts / n); the induced subgraphs keep
+// the entries whose ends share a part, in order (a stable compaction).
+
+__device__ __forceinline__ int64_t part_of(int64_t u, int64_t n, int64_t parts) { return (u * parts) / n; }
+
+__global__ void induced_flags_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col, int64_t n,
+                                int64_t parts, int64_t* flags) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+    const int64_t pu = part_of(u, n, parts);
+    for (int64_t x = off[u] + lane; x < off[u + 1]; x += 32) flags[x] = part_of(col[x], n, parts) == pu ? 1 : 0;
+  }
+}
+
+__global__ void induced_scatter_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                                  const int32_t* __restrict__ w, int64_t n, int64_t nnz, int64_t parts,
+                                  const int64_t* __restrict__ pos, const int64_t* __restrict__ total, int64_t* off_sub,
+                                  int32_t* col_sub, int32_t* w_sub) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+    const int64_t pu = part_of(u, n, parts);
+    if (lane == 0) off_sub[u] = off[u] < nnz ? pos[off[u]] : *total;
+    for (int64_t x = off[u] + lane; x < off[u + 1]; x += 32)
+      if (part_of(col[x], n, parts) == pu) {
+        col_sub[pos[x]] = col[x];
+        w_sub[pos[x]] = w[x];
+      }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) off_sub[n] = *total;
+}
+
+void induced_parts(const int64_t* off, const int32_t* col, const int32_t* w, int64_t n, int64_t nnz, int64_t parts,
+                   int64_t* flags, int64_t* pos, int64_t* total, int64_t* off_sub, int32_t* col_sub, int32_t* w_sub,
+                   void* tmp, cudaStream_t s) {
+  if (n <= 0) return;
+  int64_t blocks = (n + 7) / 8;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (nnz > 0) {
+    (count_launch(), induced_flags_k<<<(unsigned)blocks, 256, 0, s>>>(off, col, n, parts, flags));
+    scan_i64(flags, pos, nnz, total, tmp, s);
+  } else {
+    cudaMemsetAsync(total, 0, sizeof(int64_t), s);
+  }
+  (count_launch(), induced_scatter_k<<<(unsigned)blocks, 256, 0, s>>>(off, col, w, n, nnz, parts, pos, total, off_sub,
+                                                                       col_sub, w_sub));
+}
+
+// memb[u] += first vertex of u's part (part-local community ids to global).
+__global__ void part_base_k(int32_t* memb, int64_t n, int64_t parts) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = part_of(u, n, parts);
+    memb[u] += (int32_t)((p * n + parts - 1) / parts);
+  }
+}
+void part_base(int32_t* memb, int64_t n, int64_t parts, cudaStream_t s) {
+  if (n > 0) (count_launch(), part_base_k<<<grid1d(n), kT, 0, s>>>(memb, n, parts));
+}
+
+// Several graphs copied side by side from separate CSRs: part g's offsets
+// are shifted by its first entry eo[g] and its columns by its first vertex
+// vo[g] (vo, eo: G + 1 prefixes); off[n] = nnz.
+__global__ void rebase_parts_k(int64_t* off, int32_t* col, int64_t n, int64_t nnz, const int64_t* __restrict__ vo,
+                               const int64_t* __restrict__ eo, int G) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n + nnz; t += stride) {
+    const bool vertex = t < n;
+    const int64_t x = vertex ? t : t - n;
+    const int64_t* pre = vertex ? vo : eo;
+    int lo = 0, hi = G;   // the last g with pre[g] <= x
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (pre[mid] <= x) lo = mid; else hi = mid;
+    }
+    if (vertex) off[x] += eo[lo];
+    else col[x] += (int32_t)vo[lo];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) off[n] = nnz;
+}
+
+void rebase_parts(int64_t* off, int32_t* col, int64_t n, int64_t nnz, const int64_t* vo, const int64_t* eo, int G,
+                  cudaStream_t s) {
+  (count_launch(), rebase_parts_k<<<grid1d(n + nnz), kT, 0, s>>>(off, col, n, nnz, vo, eo, G));
+}
+
 // Pass 0 from a given membership (already in memb): ids must lie in the
 // vertex's graph's range [vo[g], vo[g + 1]) (one graph: [0, n)); a bad id
 // sets *flag and is replaced by the vertex itself.  Then Sigma and sizes.

@@ -59,6 +59,7 @@ struct louvain_server {
   std::vector<std::thread> threads;
   int64_t reserved_total = 0, peak_reserved = 0;
   int64_t submitted = 0, finished = 0, runs = 0;
+  double t_assemble = 0, t_load = 0, t_run = 0, t_fetch = 0;   // seconds summed over runs (all slots)
   bool stopping = false;
   std::string err;
 };
@@ -86,24 +87,27 @@ int run_batch(louvain_server* S, Slot& slot, std::vector<Request>& batch, double
   const int64_t G = (int64_t)batch.size();
   int64_t N = 0, E = 0;
   for (auto& r : batch) { N += r.n; E += r.nnz; }
-  std::vector<int64_t> vo(G + 1, 0), off(N + 1, 0);
-  std::vector<int32_t> col(E), w(E);
-  int64_t v0 = 0, e0 = 0;
+  const double t0 = now_s(S->t0);
+  // no host-side concatenation: one request loads from its own arrays, a
+  // batch is copied graph by graph to its place on the device
+  std::vector<int64_t> vo(G + 1, 0), ns(G), nnzs(G);
+  std::vector<const int64_t*> offs(G);
+  std::vector<const int32_t*> cols(G), ws(G);
   for (int64_t g = 0; g < G; ++g) {
     const Request& r = batch[g];
-    for (int64_t i = 0; i < r.n; ++i) off[v0 + i + 1] = r.off[i + 1] + e0;
-    for (int64_t x = 0; x < r.nnz; ++x) {
-      col[e0 + x] = r.col[x] + (int32_t)v0;
-      w[e0 + x] = r.w[x];
-    }
-    v0 += r.n;
-    e0 += r.nnz;
-    vo[g + 1] = v0;
+    vo[g + 1] = vo[g] + r.n;
+    ns[g] = r.n;
+    nnzs[g] = r.nnz;
+    offs[g] = r.off.data();
+    cols[g] = r.col.data();
+    ws[g] = r.w.data();
   }
-  int rc = G == 1 ? louvain_load_csr(slot.ctx, N, E, off.data(), col.data(), w.data(), LOUVAIN_PTR_HOST)
-                  : louvain_load_batch(slot.ctx, G, vo.data(), N, E, off.data(), col.data(), w.data(),
-                                       LOUVAIN_PTR_HOST);
+  const double t1 = now_s(S->t0);
+  int rc = G == 1 ? louvain_load_csr(slot.ctx, N, E, offs[0], cols[0], ws[0], LOUVAIN_PTR_HOST)
+                  : louvain_load_parts(slot.ctx, G, ns.data(), nnzs.data(), offs.data(), cols.data(), ws.data());
+  const double t2 = now_s(S->t0);
   if (!rc) rc = louvain_run(slot.ctx);
+  const double t3 = now_s(S->t0);
   std::vector<int32_t> memb(N);
   std::vector<double> q(G, 0.0);
   std::vector<int64_t> hi(G, 0), M(G, 0);
@@ -111,6 +115,13 @@ int run_batch(louvain_server* S, Slot& slot, std::vector<Request>& batch, double
   if (!rc) rc = louvain_get_membership(slot.ctx, memb.data(), N, LOUVAIN_PTR_HOST);
   if (!rc) rc = louvain_batch_get_modularity(slot.ctx, q.data(), hi.data(), lo.data(), M.data());
   const double done_s = now_s(S->t0);
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->t_assemble += t1 - t0;
+    S->t_load += t2 - t1;
+    S->t_run += t3 - t2;
+    S->t_fetch += done_s - t3;
+  }
   for (int64_t g = 0; g < G; ++g) {
     louvain_server_result x = make_result(batch[g], rc, batch[g].submit_s, start_s, done_s, (int)G);
     if (!rc) {
@@ -328,6 +339,16 @@ int louvain_server_stats(louvain_server* S, int64_t out[8]) {
   out[5] = S->peak_reserved;
   out[6] = S->cfg.hbm_budget_bytes;
   out[7] = S->cfg.slots;
+  return 0;
+}
+
+int louvain_server_timings(louvain_server* S, double out[4]) {
+  if (!S || !out) return LOUVAIN_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  out[0] = S->t_assemble;
+  out[1] = S->t_load;
+  out[2] = S->t_run;
+  out[3] = S->t_fetch;
   return 0;
 }
 

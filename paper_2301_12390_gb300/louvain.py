@@ -231,6 +231,21 @@ class Louvain:
         self._check(self.lib.louvain_get_num_graphs(self.h, ctypes.byref(g)))
         return g.value
 
+    def load_parts(self, graphs):
+        """Load graphs [(off, col, w), ...] (host arrays, ids local to each graph) as one batch, copied graph by
+        graph to the device (no host-side concatenation)."""
+        G = len(graphs)
+        arrs = [(np.ascontiguousarray(o, np.int64), np.ascontiguousarray(c, np.int32), np.ascontiguousarray(w, np.int32))
+                for o, c, w in graphs]
+        ns = np.array([len(o) - 1 for o, _, _ in arrs], np.int64)
+        nnzs = np.array([len(c) for _, c, _ in arrs], np.int64)
+        P = ctypes.c_void_p * G
+        offs = P(*[o.ctypes.data for o, _, _ in arrs])
+        cols = P(*[c.ctypes.data for _, c, _ in arrs])
+        ws = P(*[w.ctypes.data for _, _, w in arrs])
+        self._check(self.lib.louvain_load_parts(self.h, G, ns.ctypes.data, nnzs.ctypes.data, offs, cols, ws))
+        self.n = int(ns.sum())
+
     def batch_modularity(self):
         """(q[G] float64, exact numerators [G] python ints, M[G])."""
         G = self.num_graphs()
@@ -256,6 +271,13 @@ class Louvain:
 
     def run(self):
         self._check(self.lib.louvain_run(self.h))
+
+    def run_partitioned(self, parts: int) -> float:
+        """Partition, then merge: parts' induced subgraphs run as one batch, then the whole graph from their
+        communities. Returns the parts' run time in ms."""
+        ms = ctypes.c_double()
+        self._check(self.lib.louvain_run_partitioned(self.h, parts, ctypes.byref(ms)))
+        return ms.value
 
     def run_from(self, memb):
         """Incremental re-run: pass 0 starts from membership memb (host array or device tensor, n entries)."""
@@ -389,6 +411,8 @@ SIGNATURES += [
     ("louvain_get_mapping", _I32, [_VP, _VP]),
     ("louvain_autotune", _I32, [_VP, _VP, ctypes.POINTER(ctypes.c_double)]),
     ("louvain_run_from", _I32, [_VP, _VP, _I64, _I32]),
+    ("louvain_load_parts", _I32, [_VP, _I64, _VP, _VP, _VP, _VP, _VP]),
+    ("louvain_run_partitioned", _I32, [_VP, _I64, ctypes.POINTER(ctypes.c_double)]),
 ]
 
 
@@ -401,6 +425,7 @@ SIGNATURES += [
     ("louvain_server_membership", _I32, [_VP, _I64, _VP, _I64]),
     ("louvain_server_stats", _I32, [_VP, _VP]),
     ("louvain_server_destroy", None, [_VP]),
+    ("louvain_server_timings", _I32, [_VP, _VP]),
 ]
 
 
@@ -463,6 +488,12 @@ class Server:
         keys = ["submitted", "finished", "runs", "queued", "reserved_bytes", "peak_reserved_bytes", "budget_bytes",
                 "slots"]
         return dict(zip(keys, out.tolist()))
+
+    def timings(self):
+        """Seconds summed over all runs: host batch assembly, load, run, result fetch."""
+        out = np.zeros(4, np.float64)
+        self.lib.louvain_server_timings(self.h, out.ctypes.data)
+        return dict(zip(["assemble_s", "load_s", "run_s", "fetch_s"], out.tolist()))
 
     def close(self):
         if getattr(self, "h", None):

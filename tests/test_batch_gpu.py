@@ -86,3 +86,18 @@ def test_batch_rejects_entries_between_graphs():
         lv.load_batch(vo, big.off, big.col, big.w)
         lv.run()
         assert lv.num_graphs() == 2
+
+
+def test_load_parts_equals_load_batch():
+    """Graphs loaded from separate host CSRs (copied side by side on the
+    device) run exactly as their block-diagonal concatenation."""
+    membs, q, nums, Ms, iters = run_batch(GS, mode=0, prune=1)
+    with Louvain(device=0, mode=0, prune=1) as lv:
+        lv.load_parts([(g.off, g.col, g.w) for g in GS])
+        lv.run()
+        memb = lv.membership()
+        q2, nums2, Ms2 = lv.batch_modularity()
+    big, vo = gg.concat(GS)
+    for g in range(len(GS)):
+        assert np.array_equal(memb[vo[g]:vo[g + 1]], membs[g]), g
+    assert list(nums2) == list(nums) and list(Ms2) == list(Ms)
