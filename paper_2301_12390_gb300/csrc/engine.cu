@@ -314,11 +314,22 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
   std::vector<int64_t> ko(nkeys + 1);
   int64_t hub0 = 0, hub1 = 0, nhubs = 0;
   std::vector<int64_t> hchunks, hschunks;
+  // sub_m > 0: the classes are drawn anew over the sub_m vertices with edges
+  // kept in c->level (a small pass; its other vertices are isolated)
+  int64_t sub_m = 0;
   auto classify = [&](int iter) -> int {
     cs.salt_s = mode_s ? mix_salt(pass, mode_s == 1 ? iter : 0) : 0u;
     cs.salt_b = mode_b ? mix_salt(pass, mode_b == 1 ? iter : 0) : 0u;
-    lm_keys(g.off, g.n, P, c->key, multi ? c->gid : nullptr, multi ? c->vo : nullptr, c->d_gsmall, cs, c->thr, s);
-    stable_partition(c->key, g.n, nkeys, c->list, c->key_off, c->tmp, s);
+    if (sub_m > 0) {
+      int32_t* idx = (int32_t*)c->moves;   // free until a synchronous commit
+      lm_keys_sub(g.off, c->level, sub_m, P, c->key, multi ? c->gid : nullptr, multi ? c->vo : nullptr, c->d_gsmall,
+                  cs, c->thr, s);
+      stable_partition(c->key, sub_m, nkeys, idx, c->key_off, c->tmp, s);
+      gather_ids(idx, c->level, sub_m, c->list, s);
+    } else {
+      lm_keys(g.off, g.n, P, c->key, multi ? c->gid : nullptr, multi ? c->vo : nullptr, c->d_gsmall, cs, c->thr, s);
+      stable_partition(c->key, g.n, nkeys, c->list, c->key_off, c->tmp, s);
+    }
     CKLAUNCH();
     if (int r = fetch(c, ko.data(), c->key_off, ko.size() * sizeof(int64_t))) return r;
     hub0 = ko[kHubBucket * P];
@@ -336,6 +347,16 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
     return 0;
   };
   if (int r = classify(0)) return r;
+  // A small pass graph without vertices above degree 128 takes one launch per
+  // class; when its classes are drawn anew every iteration, only its vertices
+  // with edges are partitioned again (on R-MAT most vertices of the late
+  // passes are isolated).
+  const bool small_pass = g.nnz <= kSmallPassEntries && ko[3 * P] == ko[kBuckets * P];
+  if (small_pass && reclass && ko[3 * P] < g.n) {
+    // later classifications partition only the vertices with edges
+    sub_m = ko[3 * P];
+    CK(cudaMemcpyAsync(c->level, c->list, sub_m * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  }
   // hub move stamps are iteration numbers of this pass
   CK(cudaMemsetAsync(c->hmoved, 0, (size_t)g.n * sizeof(int32_t), s));
   LMArgs<W> a;
@@ -389,7 +410,6 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
     }
     // a small pass graph without vertices above degree 128: one launch per
     // class on the main stream
-    const bool small_pass = g.nnz <= kSmallPassEntries && ko[3 * P] == ko[kBuckets * P];
     for (int ch = 0; ch < P && small_pass; ++ch) {
       int64_t cls = 0;
       for (int b = 0; b < 3; ++b) cls += ko[b * P + ch + 1] - ko[b * P + ch];
@@ -648,7 +668,7 @@ int aggregate(louvain_ctx* c, const PassState& g, int64_t k, PassState* next, st
   int flag = 0;
   if (int r = fetch(c, &flag, c->flags, sizeof(int))) return r;
   if (flag) return fail(c, LOUVAIN_ERR_INTERNAL, "aggregation: hash table overflow");
-  agg_compact<W2>(c->cstart, c->mpre, c->rlen, c->offX[dst], k, c->tcol, (const W2*)c->tw, c->colX[dst],
+  agg_compact<W2>(c->cstart, c->mpre, c->offX[dst], k, nnz2, c->crow, c->tcol, (const W2*)c->tw, c->colX[dst],
                   (W2*)c->wX[dst], s);
   CKLAUNCH();
   // Q numerator after the pass: M * sum_C L_C (coarse self-loops) - sum_c Sigma_c^2

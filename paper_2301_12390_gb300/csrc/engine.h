@@ -38,6 +38,29 @@ __host__ __device__ inline int agg_bucket_of(int64_t dsum) {
 constexpr int64_t kAggChunkEntries = 2048;
 constexpr int64_t kRelabelChunk = 1024;     // CSR entries per warp of the relabel kernel
 
+// Vertex classes of one iteration: a vertex of a small graph (per-graph flag
+// gsmall, or single_small with one graph) takes class (local id mod Ps, or
+// hash32(local id ^ salt_s) mod Ps when salt_s != 0); of a large graph the
+// same with Pb and salt_b.
+struct ClassSpec {
+  int32_t Ps, Pb;
+  uint32_t salt_s, salt_b;
+  int32_t single_small;
+};
+// The class of vertex i (gid, vo, gsmall null: one graph).
+__device__ __forceinline__ int vertex_class(int64_t i, const int32_t* gid, const int64_t* vo, const int32_t* gsmall,
+                                            const ClassSpec& cs) {
+  int64_t local = i;
+  bool small = cs.single_small != 0;
+  if (gid) {
+    const int g = gid[i];
+    local = i - vo[g];
+    small = gsmall[g] != 0;
+  }
+  const uint32_t Pg = (uint32_t)(small ? cs.Ps : cs.Pb);
+  const uint32_t salt = small ? cs.salt_s : cs.salt_b;
+  return salt ? (int)(hash32((uint32_t)local ^ salt) % Pg) : (int)(local % Pg);
+}
 // ------------------------------------------------------ local_move.cu
 template <typename W>
 void lm_launch_bucket(const LMArgs<W>& a, bool wide, bool async, int bucket, const int32_t* verts, int nverts,
@@ -74,20 +97,15 @@ size_t partition_tmp_bytes(int64_t n, int nkeys);
 void stable_partition(const int32_t* key, int64_t n, int nkeys, int32_t* out, int64_t* key_off, void* tmp,
                       cudaStream_t s);
 
-// Vertex classes of one iteration: a vertex of a small graph (per-graph flag
-// gsmall, or single_small with one graph) takes class (local id mod Ps, or
-// hash32(local id ^ salt_s) mod Ps when salt_s != 0); of a large graph the
-// same with Pb and salt_b.
-struct ClassSpec {
-  int32_t Ps, Pb;
-  uint32_t salt_s, salt_b;
-  int32_t single_small;
-};
 // Keys for the local-moving lists, bucket-major: key[i] = bucket * P + class
 // of vertex i (P >= Ps, Pb); vertices of degree 0 get the trailing key
 // kBuckets * P.
 void lm_keys(const int64_t* off, int64_t n, int P, int32_t* key, const int32_t* gid, const int64_t* vo,
              const int32_t* gsmall, ClassSpec cs, LMThresholds th, cudaStream_t s);
+// lm_keys for the m vertices sub[0..m); gather_ids: out[j] = sub[idx[j]].
+void lm_keys_sub(const int64_t* off, const int32_t* sub, int64_t m, int P, int32_t* key, const int32_t* gid,
+                 const int64_t* vo, const int32_t* gsmall, ClassSpec cs, LMThresholds th, cudaStream_t s);
+void gather_ids(const int32_t* idx, const int32_t* sub, int64_t m, int32_t* out, cudaStream_t s);
 // For the hub list: per hub its table base (2 * degree slots), the prefix of
 // its insert chunks and the prefix of its slot chunks (each nhubs + 1 long).
 void hub_layout(const int64_t* off, const int32_t* hubs, int64_t nhubs, int64_t* hbase, int64_t* chunk_pre,
@@ -185,9 +203,12 @@ void agg_launch_global(const AggArgs& a, const int32_t* comms, int ncomms, const
 void agg_global_layout(const int64_t* cstart, const int64_t* mpre, const int32_t* comms, int64_t ncomms, int64_t k,
                        const int32_t* cgid, const int64_t* cvo, int64_t* gbase, int64_t* chunk_pre, int64_t* spre,
                        int64_t* glo, void* tmp, cudaStream_t s);
+// Coarse rows from their tmp positions to the coarse CSR (coff = its
+// offsets, k rows, nnz2 entries; crow: merge-path scratch of
+// (k + nnz2) / kRelabelChunk + 2 ints).
 template <typename W2>
-void agg_compact(const int64_t* cstart, const int64_t* mpre, const int64_t* rlen, const int64_t* coff, int64_t k,
-                 const int32_t* tcol, const W2* tw, int32_t* ocol, W2* ow, cudaStream_t s);
+void agg_compact(const int64_t* cstart, const int64_t* mpre, const int64_t* coff, int64_t k, int64_t nnz2,
+                 int32_t* crow, const int32_t* tcol, const W2* tw, int32_t* ocol, W2* ow, cudaStream_t s);
 
 // Several graphs in one CSR (contiguous vertex ranges per graph).
 void graph_totals(const long long* K, const int32_t* gid, int64_t n, unsigned long long* Mg, cudaStream_t s);

@@ -3,6 +3,7 @@
 // paper: each community becomes a super-vertex, edges between communities
 // are merged with summed weights, edges inside one become a summed
 // self-loop).  No library primitives: scan and partition are our own.
+#include <type_traits>
 #include "common.cuh"
 #include "engine.h"
 
@@ -236,18 +237,25 @@ __global__ void lm_keys_k(const int64_t* __restrict__ off, int64_t n, int P, int
                           const int32_t* __restrict__ gsmall, ClassSpec cs, LMThresholds th) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int b = lm_bucket_of(off[i + 1] - off[i], th);
-    int64_t local = i;   // classes by id within the vertex's graph
-    bool small = cs.single_small != 0;
-    if (gid) {
-      const int g = gid[i];
-      local = i - vo[g];
-      small = gsmall[g] != 0;
-    }
-    const uint32_t Pg = (uint32_t)(small ? cs.Ps : cs.Pb);
-    const uint32_t salt = small ? cs.salt_s : cs.salt_b;
-    const int cls = salt ? (int)(hash32((uint32_t)local ^ salt) % Pg) : (int)(local % Pg);
-    key[i] = b < 0 ? kBuckets * P : b * P + cls;
+    key[i] = b < 0 ? kBuckets * P : b * P + (P > 1 ? vertex_class(i, gid, vo, gsmall, cs) : 0);
   }
+}
+
+// The same keys for the vertices of a subset (key[j] for vertex sub[j]).
+__global__ void lm_keys_sub_k(const int64_t* __restrict__ off, const int32_t* __restrict__ sub, int64_t m, int P,
+                              int32_t* key, const int32_t* __restrict__ gid, const int64_t* __restrict__ vo,
+                              const int32_t* __restrict__ gsmall, ClassSpec cs, LMThresholds th) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t i = sub[j];
+    int b = lm_bucket_of(off[i + 1] - off[i], th);
+    key[j] = b < 0 ? kBuckets * P : b * P + (P > 1 ? vertex_class(i, gid, vo, gsmall, cs) : 0);
+  }
+}
+
+__global__ void gather_ids_k(const int32_t* __restrict__ idx, const int32_t* __restrict__ sub, int64_t m,
+                             int32_t* out) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
+    out[j] = sub[idx[j]];
 }
 
 static unsigned grid1d(int64_t n, int per = kT) {
@@ -380,6 +388,14 @@ void pass_init(int64_t n, const long long* K, int32_t* memb, long long* sig, int
 //
 // Vertex u belongs to part floor(u * parts / n); the induced subgraphs keep
 // the entries whose ends share a part, in order (a stable compaction).
+
+void lm_keys_sub(const int64_t* off, const int32_t* sub, int64_t m, int P, int32_t* key, const int32_t* gid,
+                 const int64_t* vo, const int32_t* gsmall, ClassSpec cs, LMThresholds th, cudaStream_t s) {
+  if (m > 0) (count_launch(), lm_keys_sub_k<<<grid1d(m), kT, 0, s>>>(off, sub, m, P, key, gid, vo, gsmall, cs, th));
+}
+void gather_ids(const int32_t* idx, const int32_t* sub, int64_t m, int32_t* out, cudaStream_t s) {
+  if (m > 0) (count_launch(), gather_ids_k<<<grid1d(m), kT, 0, s>>>(idx, sub, m, out));
+}
 
 __device__ __forceinline__ int64_t part_of(int64_t u, int64_t n, int64_t parts) { return (u * parts) / n; }
 
@@ -755,6 +771,11 @@ template void agg_relabel<int64_t, int64_t>(const int64_t*, const int32_t*, cons
                                             const int32_t*, const int32_t*, const int64_t*, int32_t*, int32_t*,
                                             int64_t*, cudaStream_t);
 
+// Shared-table values of the aggregation: coarse weights of 32 bits (total
+// weight below 2^31) fit 32-bit sums.
+template <typename W2>
+using AggVal = typename std::conditional<sizeof(W2) == 4, unsigned int, unsigned long long>::type;
+
 // Load U consecutive relabelled entries per lane (stride `stride`) of
 // [t0, t1): D = kEmpty past the end.
 template <typename W2, int U>
@@ -773,13 +794,14 @@ __device__ __forceinline__ void load_entries(const AggArgs& a, int64_t t0, int64
 // entries (all of them are read before the first write).
 template <typename W2, int CAP>
 __global__ void __launch_bounds__(256) agg_warp_k(AggArgs a, const int32_t* __restrict__ comms, int ncomms) {
+  typedef AggVal<W2> V;
   constexpr int WPB = 8;
   constexpr int U = CAP / 2 / kWarp > 0 ? CAP / 2 / kWarp : 1;
   __shared__ int32_t skeys[WPB][CAP];
-  __shared__ unsigned long long svals[WPB][CAP];
+  __shared__ V svals[WPB][CAP];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   int32_t* keys = skeys[wib];
-  unsigned long long* vals = svals[wib];
+  V* vals = svals[wib];
   for (int t = lane; t < CAP; t += kWarp) { keys[t] = kEmpty; vals[t] = 0; }
   __syncwarp();
   bool ok = true;
@@ -792,7 +814,7 @@ __global__ void __launch_bounds__(256) agg_warp_k(AggArgs a, const int32_t* __re
       load_entries<W2, U>(a, t0, ve, kWarp, D, w);
 #pragma unroll
       for (int k = 0; k < U; ++k)
-        if (D[k] != kEmpty) ok &= table_add_pow2<CAP, unsigned long long>(keys, vals, D[k], w[k]);
+        if (D[k] != kEmpty) ok &= table_add_pow2<CAP, V>(keys, vals, D[k], w[k]);
     }
     __syncwarp();
     int64_t base = 0;
@@ -819,11 +841,12 @@ __global__ void __launch_bounds__(256) agg_warp_k(AggArgs a, const int32_t* __re
 // Communities with at most CAP / 2 member entries, a block each.
 template <typename W2, int CAP, int THREADS>
 __global__ void __launch_bounds__(THREADS) agg_block_k(AggArgs a, const int32_t* __restrict__ comms, int ncomms) {
+  typedef AggVal<W2> V;
   constexpr int U = 4;
-  // dynamic shared memory: values (CAP u64), keys (CAP i32)
+  // dynamic shared memory: values (CAP V), keys (CAP i32)
   extern __shared__ unsigned long long adyn[];
-  unsigned long long* vals = adyn;
-  int32_t* keys = (int32_t*)(adyn + CAP);
+  V* vals = (V*)adyn;
+  int32_t* keys = (int32_t*)(vals + CAP);
   __shared__ int wtot[THREADS / kWarp];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int t = threadIdx.x; t < CAP; t += THREADS) { keys[t] = kEmpty; vals[t] = 0; }
@@ -838,7 +861,7 @@ __global__ void __launch_bounds__(THREADS) agg_block_k(AggArgs a, const int32_t*
       load_entries<W2, U>(a, t0, ve, THREADS, D, w);
 #pragma unroll
       for (int k = 0; k < U; ++k)
-        if (D[k] != kEmpty) ok &= table_add_pow2<CAP, unsigned long long>(keys, vals, D[k], w[k]);
+        if (D[k] != kEmpty) ok &= table_add_pow2<CAP, V>(keys, vals, D[k], w[k]);
     }
     __syncthreads();
     int64_t base = 0;
@@ -887,12 +910,13 @@ template <typename W2>
 __global__ void __launch_bounds__(256) agg_global_insert_k(AggArgs a, const int32_t* __restrict__ comms, int ncomms,
                                                            const int64_t* __restrict__ gbase,
                                                            const int64_t* __restrict__ chunk_pre) {
+  typedef AggVal<W2> V;
   constexpr int CAP = 2 * (int)kAggChunkEntries;
   constexpr int U = (int)kAggChunkEntries / 256;
-  // dynamic shared memory: values (CAP u64), keys (CAP i32)
+  // dynamic shared memory: values (CAP V), keys (CAP i32)
   extern __shared__ unsigned long long gdyn[];
-  unsigned long long* svals = gdyn;
-  int32_t* skeys = (int32_t*)(gdyn + CAP);
+  V* svals = (V*)gdyn;
+  int32_t* skeys = (int32_t*)(svals + CAP);
   const int h = find_item(chunk_pre, ncomms, blockIdx.x);
   const int32_t C = comms[h];
   const int64_t vs = a.mpre[a.cstart[C]], ve = a.mpre[a.cstart[C + 1]];
@@ -908,7 +932,7 @@ __global__ void __launch_bounds__(256) agg_global_insert_k(AggArgs a, const int3
   bool ok = true;
 #pragma unroll
   for (int k = 0; k < U; ++k)
-    if (D[k] != kEmpty) ok &= table_add_pow2<CAP, unsigned long long>(skeys, svals, D[k], w[k]);
+    if (D[k] != kEmpty) ok &= table_add_pow2<CAP, V>(skeys, svals, D[k], w[k]);
   __syncthreads();
   int32_t* keys = a.gkeys + base;
   unsigned long long* vals = a.gvals + base;
@@ -920,7 +944,7 @@ __global__ void __launch_bounds__(256) agg_global_insert_k(AggArgs a, const int3
       const int64_t y = (int64_t)Dk - lo;
       if (y < 0 || y >= (int64_t)cap) { ok = false; continue; }
       if (keys[y] != Dk) keys[y] = Dk;
-      atomicAdd(&vals[y], svals[t]);
+      atomicAdd(&vals[y], (unsigned long long)svals[t]);
     }
   } else {
     constexpr int J = 8;
@@ -930,7 +954,7 @@ __global__ void __launch_bounds__(256) agg_global_insert_k(AggArgs a, const int3
 #pragma unroll
       for (int j = 0; j < J; ++j) {
         kk[j] = skeys[t0 + j * 256 + threadIdx.x];
-        vv[j] = svals[t0 + j * 256 + threadIdx.x];
+        vv[j] = (unsigned long long)svals[t0 + j * 256 + threadIdx.x];
       }
       ok &= gtable_add_many<J>(keys, vals, cap, kk, vv);
     }
@@ -1006,14 +1030,14 @@ void agg_launch_bucket(const AggArgs& a, int bucket, const int32_t* comms, int n
     }
     case 2: {
       constexpr int CAP = 2048;
-      size_t smem = (size_t)CAP * 12;
+      size_t smem = (size_t)CAP * (4 + sizeof(AggVal<W2>));
       auto k = agg_block_k<W2, CAP, 128>;
       (count_launch(), k<<<agrid(k, 128, smem, ncomms), 128, smem, s>>>(a, comms, ncomms));
       break;
     }
     case 3: {
       constexpr int CAP = 8192;
-      size_t smem = (size_t)CAP * 12;
+      size_t smem = (size_t)CAP * (4 + sizeof(AggVal<W2>));
       auto k = agg_block_k<W2, CAP, 256>;
       static bool attr = false;
       if (!attr) {
@@ -1032,7 +1056,7 @@ void agg_launch_global(const AggArgs& a, const int32_t* comms, int ncomms, const
                        const int64_t* chunk_pre, int64_t nchunks, const int64_t* spre, int64_t nslotchunks,
                        cudaStream_t s) {
   if (ncomms <= 0 || nchunks <= 0) return;
-  const size_t smem = (size_t)(2 * kAggChunkEntries) * 12;
+  const size_t smem = (size_t)(2 * kAggChunkEntries) * (4 + sizeof(AggVal<W2>));
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(agg_global_insert_k<W2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1090,38 +1114,77 @@ void agg_global_layout(const int64_t* cstart, const int64_t* mpre, const int32_t
   scan_i64(schunks, spre, ncomms, spre + ncomms, stmp, s);
 }
 
-// Copy each community's tmp row (at mpre[cstart[C]], rlen[C] long) to its
-// coarse position coff[C]; blocks take kT communities each.
+// Copy each community's coarse row from its tmp position mpre[cstart[C]] to
+// coff[C] (coff: k + 1 offsets).  Merge-path chunks of the rows and output
+// entries (chunk_rows_k over coff) give every warp the same amount of work
+// however skewed the rows are; within a chunk a warp walks the rows 32 at a
+// time and each lane finds its entry's row by a shuffle search, as in the
+// relabel kernel.
 template <typename W2>
-__global__ void __launch_bounds__(kT) agg_compact_k(const int64_t* __restrict__ cstart,
-                                                    const int64_t* __restrict__ mpre, const int64_t* __restrict__ coff,
-                                                    int64_t k, const int32_t* __restrict__ tcol,
-                                                    const W2* __restrict__ tw, int32_t* ocol, W2* ow) {
-  __shared__ int64_t soff[kT + 1];
-  __shared__ int64_t ssrc[kT];
-  const int64_t C0 = (int64_t)blockIdx.x * kT;
-  const int nr = (int)min((int64_t)kT, k - C0);
-  for (int t = threadIdx.x; t <= nr; t += kT) soff[t] = coff[C0 + t];
-  if (threadIdx.x < nr) ssrc[threadIdx.x] = mpre[cstart[C0 + threadIdx.x]];
-  __syncthreads();
-  for (int64_t o = soff[0] + threadIdx.x; o < soff[nr]; o += kT) {
-    int r = row_of(soff, nr, o);
-    int64_t src = ssrc[r] + (o - soff[r]);
-    ocol[o] = tcol[src];
-    ow[o] = tw[src];
+__global__ void __launch_bounds__(256) agg_compact_k(const int64_t* __restrict__ coff, int64_t k, int64_t nnz2,
+                                                     const int64_t* __restrict__ cstart,
+                                                     const int64_t* __restrict__ mpre, const int32_t* __restrict__ crow,
+                                                     int64_t nchunks, const int32_t* __restrict__ tcol,
+                                                     const W2* __restrict__ tw, int32_t* __restrict__ ocol,
+                                                     W2* __restrict__ ow) {
+  constexpr int U = 4;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += warps) {
+    const int64_t X0 = c * kRelabelChunk - crow[c];
+    const int64_t X1 = min(nnz2, (c + 1) * kRelabelChunk - crow[c + 1]);
+    for (int64_t r = crow[c];; r += kWarp) {
+      const int64_t C = r + lane;
+      const int64_t o = coff[min(C, k)];
+      const int64_t wend = __shfl_sync(0xffffffffu, coff[min(r + kWarp, k)], 0);
+      const int64_t shift = C < k ? mpre[cstart[C]] - o : 0;
+      const int64_t xs = max(X0, __shfl_sync(0xffffffffu, o, 0)), xe = min(X1, wend);
+      for (int64_t x0 = xs; x0 < xe; x0 += U * kWarp) {
+        int64_t x[U], src[U];
+        int32_t cv[U];
+        W2 wv[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+          x[q] = x0 + q * kWarp + lane;
+          int rr = 0;
+#pragma unroll
+          for (int step = 16; step >= 1; step >>= 1) {
+            const int cand = rr + step;
+            if (__shfl_sync(0xffffffffu, o, cand) <= x[q]) rr = cand;
+          }
+          src[q] = x[q] + __shfl_sync(0xffffffffu, shift, rr);
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+          cv[q] = x[q] < xe ? tcol[src[q]] : 0;
+          wv[q] = x[q] < xe ? tw[src[q]] : (W2)0;
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+          if (x[q] < xe) {
+            ocol[x[q]] = cv[q];
+            ow[x[q]] = wv[q];
+          }
+      }
+      if (wend >= X1) break;
+    }
   }
 }
 
 template <typename W2>
-void agg_compact(const int64_t* cstart, const int64_t* mpre, const int64_t* rlen, const int64_t* coff, int64_t k,
-                 const int32_t* tcol, const W2* tw, int32_t* ocol, W2* ow, cudaStream_t s) {
-  (void)rlen;
-  if (k <= 0) return;
-  (count_launch(), agg_compact_k<W2><<<(unsigned)((k + kT - 1) / kT), kT, 0, s>>>(cstart, mpre, coff, k, tcol, tw, ocol, ow));
+void agg_compact(const int64_t* cstart, const int64_t* mpre, const int64_t* coff, int64_t k, int64_t nnz2,
+                 int32_t* crow, const int32_t* tcol, const W2* tw, int32_t* ocol, W2* ow, cudaStream_t s) {
+  if (k <= 0 || nnz2 <= 0) return;
+  const int64_t nchunks = (k + nnz2 + kRelabelChunk - 1) / kRelabelChunk;
+  (count_launch(), chunk_rows_k<<<grid1d(nchunks + 1), kT, 0, s>>>(coff, k, nchunks, crow));
+  int64_t blocks = (nchunks + 7) / 8;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  (count_launch(), agg_compact_k<W2><<<(unsigned)blocks, 256, 0, s>>>(coff, k, nnz2, cstart, mpre, crow, nchunks, tcol,
+                                                                       tw, ocol, ow));
 }
-template void agg_compact<int32_t>(const int64_t*, const int64_t*, const int64_t*, const int64_t*, int64_t,
+template void agg_compact<int32_t>(const int64_t*, const int64_t*, const int64_t*, int64_t, int64_t, int32_t*,
                                    const int32_t*, const int32_t*, int32_t*, int32_t*, cudaStream_t);
-template void agg_compact<int64_t>(const int64_t*, const int64_t*, const int64_t*, const int64_t*, int64_t,
+template void agg_compact<int64_t>(const int64_t*, const int64_t*, const int64_t*, int64_t, int64_t, int32_t*,
                                    const int32_t*, const int64_t*, int32_t*, int64_t*, cudaStream_t);
 
 // ----------------------------------------------------------- several graphs
