@@ -275,16 +275,6 @@ struct PassState {
   int widx;   // which coarse buffer holds this graph (-1 = input)
 };
 
-// Salt of the hashed classes of one iteration (splitmix64 finaliser of
-// pass and iteration, folded to 32 bits; never 0).
-uint32_t mix_salt(int pass, int iter) {
-  uint64_t z = ((uint64_t)(uint32_t)pass << 32 | (uint32_t)iter) + 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  z ^= z >> 31;
-  const uint32_t v = (uint32_t)(z ^ (z >> 32));
-  return v ? v : 1u;
-}
 
 template <typename W>
 int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool wide, int* iters_out,
@@ -297,7 +287,7 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
   // classes are id mod P.
   bool any_small = false, any_big = false;
   for (int64_t q = 0; q < c->G; ++q) (c->gn0[q] < kSmallGraph ? any_small : any_big) = true;
-  ClassSpec cs{1, 1, 0u, 0u, c->G == 1 && c->gn0[0] < kSmallGraph ? 1 : 0};
+  ClassSpec cs{1, 1, 0, 0, pass, c->G == 1 && c->gn0[0] < kSmallGraph ? 1 : 0};
   if (c->opt.subrounds > 0) cs.Ps = cs.Pb = c->opt.subrounds;
   else if (async) { cs.Ps = kAsyncSubroundsSmall; cs.Pb = kAsyncSubrounds; }
   const int P = std::max(any_small ? cs.Ps : 1, any_big ? cs.Pb : 1);
@@ -309,6 +299,8 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
   const int mode_s = (async && cs.Ps > 1) ? (c->opt.reclass == 3 ? 2 : c->opt.reclass) : 0;
   const int mode_b = (async && cs.Pb > 1) ? (c->opt.reclass == 3 ? 1 : c->opt.reclass) : 0;
   const bool reclass = (any_small && mode_s == 1) || (any_big && mode_b == 1);   // every iteration
+  cs.mode_s = mode_s;
+  cs.mode_b = mode_b;
   // Bucket lists: key = bucket * P + class, hubs of all classes contiguous,
   // and the hubs' table layout.
   std::vector<int64_t> ko(nkeys + 1);
@@ -317,19 +309,20 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
   // sub_m > 0: the classes are drawn anew over the sub_m vertices with edges
   // kept in c->level (a small pass; its other vertices are isolated)
   int64_t sub_m = 0;
+  // the class lists of the vertices with edges only, all on the device (a
+  // small pass whose classes are drawn anew: part of its iteration)
+  auto reclassify_small = [&]() {
+    int32_t* idx = (int32_t*)c->moves;   // free in asynchronous mode
+    lm_keys_sub(g.off, c->level, sub_m, P, c->key, multi ? c->gid : nullptr, multi ? c->vo : nullptr, c->d_gsmall,
+                cs, c->d_iter, c->thr, s);
+    stable_partition(c->key, sub_m, nkeys, idx, c->key_off, c->tmp, s);
+    gather_ids(idx, c->level, sub_m, c->list, s);
+  };
   auto classify = [&](int iter) -> int {
-    cs.salt_s = mode_s ? mix_salt(pass, mode_s == 1 ? iter : 0) : 0u;
-    cs.salt_b = mode_b ? mix_salt(pass, mode_b == 1 ? iter : 0) : 0u;
-    if (sub_m > 0) {
-      int32_t* idx = (int32_t*)c->moves;   // free until a synchronous commit
-      lm_keys_sub(g.off, c->level, sub_m, P, c->key, multi ? c->gid : nullptr, multi ? c->vo : nullptr, c->d_gsmall,
-                  cs, c->thr, s);
-      stable_partition(c->key, sub_m, nkeys, idx, c->key_off, c->tmp, s);
-      gather_ids(idx, c->level, sub_m, c->list, s);
-    } else {
-      lm_keys(g.off, g.n, P, c->key, multi ? c->gid : nullptr, multi ? c->vo : nullptr, c->d_gsmall, cs, c->thr, s);
-      stable_partition(c->key, g.n, nkeys, c->list, c->key_off, c->tmp, s);
-    }
+    (void)iter;   // the kernels read the iteration on the device
+    lm_keys(g.off, g.n, P, c->key, multi ? c->gid : nullptr, multi ? c->vo : nullptr, c->d_gsmall, cs, c->d_iter,
+            c->thr, s);
+    stable_partition(c->key, g.n, nkeys, c->list, c->key_off, c->tmp, s);
     CKLAUNCH();
     if (int r = fetch(c, ko.data(), c->key_off, ko.size() * sizeof(int64_t))) return r;
     hub0 = ko[kHubBucket * P];
@@ -352,11 +345,14 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
   // with edges are partitioned again (on R-MAT most vertices of the late
   // passes are isolated).
   const bool small_pass = g.nnz <= kSmallPassEntries && ko[3 * P] == ko[kBuckets * P];
-  if (small_pass && reclass && ko[3 * P] < g.n) {
+  if (small_pass && reclass) {
     // later classifications partition only the vertices with edges
     sub_m = ko[3 * P];
     CK(cudaMemcpyAsync(c->level, c->list, sub_m * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   }
+  // a class kernel of a small pass loops over its class, however large: one
+  // grid for the pass, so its iteration's launches do not depend on the draw
+  const int64_t class_grid_verts = (ko[3 * P] + P - 1) / P + 1;
   // hub move stamps are iteration numbers of this pass
   CK(cudaMemsetAsync(c->hmoved, 0, (size_t)g.n * sizeof(int32_t), s));
   LMArgs<W> a;
@@ -409,12 +405,11 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
       CK(cudaMemsetAsync(c->d_gs, 0, 2 * G * sizeof(unsigned long long), s));
     }
     // a small pass graph without vertices above degree 128: one launch per
-    // class on the main stream
+    // class on the main stream (and the new draw of its classes first)
+    if (small_pass && sub_m > 0) reclassify_small();
     for (int ch = 0; ch < P && small_pass; ++ch) {
-      int64_t cls = 0;
-      for (int b = 0; b < 3; ++b) cls += ko[b * P + ch + 1] - ko[b * P + ch];
-      lm_launch_class<W>(a, wide, async, c->list, c->key_off, P, ch, cls, s);
-      if (!async) lm_launch_commit<W>(a, cls, s);
+      lm_launch_class<W>(a, wide, async, c->list, c->key_off, P, ch, class_grid_verts, s);
+      if (!async) lm_launch_commit<W>(a, ko[3 * P], s);
       CKLAUNCH();
     }
     for (int ch = 0; ch < P && !small_pass; ++ch) {
@@ -478,9 +473,12 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
            return 0;
          }()))
       break;
-    if (reclass && it > 0)
+    if (reclass && it > 0 && !small_pass)
       if ((rc = classify(it))) break;
-    if (c->opt.cuda_graphs && !reclass && it >= 2) {
+    // A small pass replays its iteration as a captured CUDA graph from the
+    // second iteration on (all its launches are fixed for the pass); others
+    // only with the cuda_graphs option and fixed classes.
+    if ((small_pass && it >= 1) || (c->opt.cuda_graphs && !reclass && it >= 2)) {
       if (!gexec) {
         if ((rc = [&]() -> int {
                CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));

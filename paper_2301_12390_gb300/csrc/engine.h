@@ -40,16 +40,28 @@ constexpr int64_t kRelabelChunk = 1024;     // CSR entries per warp of the relab
 
 // Vertex classes of one iteration: a vertex of a small graph (per-graph flag
 // gsmall, or single_small with one graph) takes class (local id mod Ps, or
-// hash32(local id ^ salt_s) mod Ps when salt_s != 0); of a large graph the
-// same with Pb and salt_b.
+// with mode_s != 0 hash32(local id ^ salt) mod Ps); of a large graph the same
+// with Pb and mode_b.  Mode 1 salts by (pass, iteration), mode 2 by pass only;
+// the iteration is read on the device, so an iteration's launches do not
+// depend on it.
 struct ClassSpec {
   int32_t Ps, Pb;
-  uint32_t salt_s, salt_b;
+  int32_t mode_s, mode_b;
+  int32_t pass;
   int32_t single_small;
 };
-// The class of vertex i (gid, vo, gsmall null: one graph).
+// splitmix64 finaliser of (pass, iteration), folded to 32 bits, never 0.
+__host__ __device__ inline uint32_t class_salt(int pass, int iter) {
+  uint64_t z = ((uint64_t)(uint32_t)pass << 32 | (uint32_t)iter) + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  const uint32_t v = (uint32_t)(z ^ (z >> 32));
+  return v ? v : 1u;
+}
+// The class of vertex i in iteration iter (gid, vo, gsmall null: one graph).
 __device__ __forceinline__ int vertex_class(int64_t i, const int32_t* gid, const int64_t* vo, const int32_t* gsmall,
-                                            const ClassSpec& cs) {
+                                            const ClassSpec& cs, int iter) {
   int64_t local = i;
   bool small = cs.single_small != 0;
   if (gid) {
@@ -58,9 +70,11 @@ __device__ __forceinline__ int vertex_class(int64_t i, const int32_t* gid, const
     small = gsmall[g] != 0;
   }
   const uint32_t Pg = (uint32_t)(small ? cs.Ps : cs.Pb);
-  const uint32_t salt = small ? cs.salt_s : cs.salt_b;
-  return salt ? (int)(hash32((uint32_t)local ^ salt) % Pg) : (int)(local % Pg);
+  const int mode = small ? cs.mode_s : cs.mode_b;
+  if (!mode) return (int)(local % Pg);
+  return (int)(hash32((uint32_t)local ^ class_salt(cs.pass, mode == 1 ? iter : 0)) % Pg);
 }
+
 // ------------------------------------------------------ local_move.cu
 template <typename W>
 void lm_launch_bucket(const LMArgs<W>& a, bool wide, bool async, int bucket, const int32_t* verts, int nverts,
@@ -101,10 +115,11 @@ void stable_partition(const int32_t* key, int64_t n, int nkeys, int32_t* out, in
 // of vertex i (P >= Ps, Pb); vertices of degree 0 get the trailing key
 // kBuckets * P.
 void lm_keys(const int64_t* off, int64_t n, int P, int32_t* key, const int32_t* gid, const int64_t* vo,
-             const int32_t* gsmall, ClassSpec cs, LMThresholds th, cudaStream_t s);
+             const int32_t* gsmall, ClassSpec cs, const int* d_iter, LMThresholds th, cudaStream_t s);
 // lm_keys for the m vertices sub[0..m); gather_ids: out[j] = sub[idx[j]].
 void lm_keys_sub(const int64_t* off, const int32_t* sub, int64_t m, int P, int32_t* key, const int32_t* gid,
-                 const int64_t* vo, const int32_t* gsmall, ClassSpec cs, LMThresholds th, cudaStream_t s);
+                 const int64_t* vo, const int32_t* gsmall, ClassSpec cs, const int* d_iter, LMThresholds th,
+                 cudaStream_t s);
 void gather_ids(const int32_t* idx, const int32_t* sub, int64_t m, int32_t* out, cudaStream_t s);
 // For the hub list: per hub its table base (2 * degree slots), the prefix of
 // its insert chunks and the prefix of its slot chunks (each nhubs + 1 long).

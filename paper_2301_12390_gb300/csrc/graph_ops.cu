@@ -234,21 +234,25 @@ void stable_partition(const int32_t* key, int64_t n, int nkeys, int32_t* out, in
 
 __global__ void lm_keys_k(const int64_t* __restrict__ off, int64_t n, int P, int32_t* key,
                           const int32_t* __restrict__ gid, const int64_t* __restrict__ vo,
-                          const int32_t* __restrict__ gsmall, ClassSpec cs, LMThresholds th) {
+                          const int32_t* __restrict__ gsmall, ClassSpec cs, const int* __restrict__ d_iter,
+                          LMThresholds th) {
+  const int iter = *d_iter;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int b = lm_bucket_of(off[i + 1] - off[i], th);
-    key[i] = b < 0 ? kBuckets * P : b * P + (P > 1 ? vertex_class(i, gid, vo, gsmall, cs) : 0);
+    key[i] = b < 0 ? kBuckets * P : b * P + (P > 1 ? vertex_class(i, gid, vo, gsmall, cs, iter) : 0);
   }
 }
 
 // The same keys for the vertices of a subset (key[j] for vertex sub[j]).
 __global__ void lm_keys_sub_k(const int64_t* __restrict__ off, const int32_t* __restrict__ sub, int64_t m, int P,
                               int32_t* key, const int32_t* __restrict__ gid, const int64_t* __restrict__ vo,
-                              const int32_t* __restrict__ gsmall, ClassSpec cs, LMThresholds th) {
+                              const int32_t* __restrict__ gsmall, ClassSpec cs, const int* __restrict__ d_iter,
+                              LMThresholds th) {
+  const int iter = *d_iter;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
     const int32_t i = sub[j];
     int b = lm_bucket_of(off[i + 1] - off[i], th);
-    key[j] = b < 0 ? kBuckets * P : b * P + (P > 1 ? vertex_class(i, gid, vo, gsmall, cs) : 0);
+    key[j] = b < 0 ? kBuckets * P : b * P + (P > 1 ? vertex_class(i, gid, vo, gsmall, cs, iter) : 0);
   }
 }
 
@@ -265,8 +269,8 @@ static unsigned grid1d(int64_t n, int per = kT) {
 }
 
 void lm_keys(const int64_t* off, int64_t n, int P, int32_t* key, const int32_t* gid, const int64_t* vo,
-             const int32_t* gsmall, ClassSpec cs, LMThresholds th, cudaStream_t s) {
-  if (n > 0) (count_launch(), lm_keys_k<<<grid1d(n), kT, 0, s>>>(off, n, P, key, gid, vo, gsmall, cs, th));
+             const int32_t* gsmall, ClassSpec cs, const int* d_iter, LMThresholds th, cudaStream_t s) {
+  if (n > 0) (count_launch(), lm_keys_k<<<grid1d(n), kT, 0, s>>>(off, n, P, key, gid, vo, gsmall, cs, d_iter, th));
 }
 
 __global__ void hub_sizes_k(const int64_t* off, const int32_t* hubs, int64_t nhubs, int64_t* cap, int64_t* chunks,
@@ -390,8 +394,10 @@ void pass_init(int64_t n, const long long* K, int32_t* memb, long long* sig, int
 // the entries whose ends share a part, in order (a stable compaction).
 
 void lm_keys_sub(const int64_t* off, const int32_t* sub, int64_t m, int P, int32_t* key, const int32_t* gid,
-                 const int64_t* vo, const int32_t* gsmall, ClassSpec cs, LMThresholds th, cudaStream_t s) {
-  if (m > 0) (count_launch(), lm_keys_sub_k<<<grid1d(m), kT, 0, s>>>(off, sub, m, P, key, gid, vo, gsmall, cs, th));
+                 const int64_t* vo, const int32_t* gsmall, ClassSpec cs, const int* d_iter, LMThresholds th,
+                 cudaStream_t s) {
+  if (m > 0)
+    (count_launch(), lm_keys_sub_k<<<grid1d(m), kT, 0, s>>>(off, sub, m, P, key, gid, vo, gsmall, cs, d_iter, th));
 }
 void gather_ids(const int32_t* idx, const int32_t* sub, int64_t m, int32_t* out, cudaStream_t s) {
   if (m > 0) (count_launch(), gather_ids_k<<<grid1d(m), kT, 0, s>>>(idx, sub, m, out));
