@@ -94,7 +94,12 @@ typedef struct {
                                  (default; per graph: 2 for a graph of fewer than 65,536 vertices,
                                  else 1).  Synchronous classes are always id mod P.  Every graph of
                                  a batch gets the schedule it gets alone. */
-  int32_t reserved_i[3];
+  int32_t bucket_streams;     /* asynchronous mode: 1 (default) = every degree bucket (thread, warp,
+                                 block and hub kernels) runs the iteration's classes in order on its
+                                 own stream, without waiting for the other buckets' previous class;
+                                 0 = a class starts when every bucket has finished the previous one.
+                                 Synchronous classes always wait (Jacobi per class). */
+  int32_t reserved_i[2];
   double reserved_d[4];
 } louvain_options;
 

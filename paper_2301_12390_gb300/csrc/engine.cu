@@ -255,6 +255,7 @@ int check_options(const louvain_options* o) {
   if (o->max_iterations < 1 || o->max_passes < 0 || o->max_passes > 64) return 1;
   if (o->subrounds < 0 || o->subrounds > 64) return 1;
   if (o->reclass < 0 || o->reclass > 3) return 1;
+  if (o->bucket_streams < 0 || o->bucket_streams > 1) return 1;
   return 0;
 }
 
@@ -412,7 +413,41 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
       if (!async) lm_launch_commit<W>(a, ko[3 * P], s);
       CKLAUNCH();
     }
-    for (int ch = 0; ch < P && !small_pass; ++ch) {
+    // Asynchronous, with bucket_streams: every degree bucket runs the classes
+    // in order on its own stream without waiting for the other buckets'
+    // previous class; the streams join at the end of the iteration.
+    const bool streams = async && c->opt.bucket_streams && !small_pass;
+    bool sused[kBuckets] = {};
+    if (streams) {
+      CK(cudaEventRecord(c->ev_fork, s));
+      for (int b = 0; b < kBuckets; ++b) CK(cudaStreamWaitEvent(c->aux[b], c->ev_fork, 0));
+      for (int ch = 0; ch < P; ++ch) {
+        for (int b = 0; b < kHubBucket; ++b) {
+          int64_t s0 = ko[b * P + ch], s1 = ko[b * P + ch + 1];
+          if (s1 <= s0) continue;
+          sused[b] = true;
+          lm_launch_bucket<W>(a, wide, async, b, c->list + s0, (int)(s1 - s0), c->aux[b]);
+        }
+        int64_t h0 = ko[kHubBucket * P + ch] - hub0, h1 = ko[kHubBucket * P + ch + 1] - hub0;
+        if (h1 > h0) {
+          sused[kHubBucket] = true;
+          LMArgs<W> ah = a;
+          ah.hbase = c->gbase + h0;
+          ah.spre = c->spre + h0;
+          ah.hkid = c->hkid + h0;
+          ah.hmoved = c->hmoved + h0;
+          lm_launch_hubs<W>(ah, wide, async, c->list + hub0 + h0, (int)(h1 - h0), c->chunk_pre + h0,
+                            hchunks[h1] - hchunks[h0], c->spre + h0, hschunks[h1] - hschunks[h0], c->aux[kHubBucket]);
+        }
+        CKLAUNCH();
+      }
+      for (int b = 0; b < kBuckets; ++b) {
+        if (!sused[b]) continue;
+        CK(cudaEventRecord(c->ev_join[b], c->aux[b]));
+        CK(cudaStreamWaitEvent(s, c->ev_join[b], 0));
+      }
+    }
+    for (int ch = 0; ch < P && !small_pass && !streams; ++ch) {
       // fork: every non-empty bucket of the class on its own stream
       bool used[kBuckets] = {};
       CK(cudaEventRecord(c->ev_fork, s));
@@ -1131,6 +1166,7 @@ int louvain_default_options(louvain_options* o) {
   o->record_levels = 0;
   o->cuda_graphs = 0;
   o->reclass = 3;
+  o->bucket_streams = 1;
   return 0;
 }
 

@@ -38,7 +38,8 @@ class Options(ctypes.Structure):
                 ("pass_tolerance", ctypes.c_double), ("max_iterations", ctypes.c_int32),
                 ("max_passes", ctypes.c_int32), ("prune", ctypes.c_int32), ("singleton_guard", ctypes.c_int32),
                 ("subrounds", ctypes.c_int32), ("validate", ctypes.c_int32), ("record_levels", ctypes.c_int32),
-                ("cuda_graphs", ctypes.c_int32), ("reclass", ctypes.c_int32), ("reserved_i", ctypes.c_int32 * 3),
+                ("cuda_graphs", ctypes.c_int32), ("reclass", ctypes.c_int32), ("bucket_streams", ctypes.c_int32),
+                ("reserved_i", ctypes.c_int32 * 2),
                 ("reserved_d", ctypes.c_double * 4)]
 
 
