@@ -36,7 +36,10 @@ namespace {
 // communities) need smaller classes: at 16 some planted-partition graphs
 // ended more than 0.01 below the sequential order, at 32 none did.
 constexpr int kAsyncSubrounds = 16;
-constexpr int kAsyncSubroundsSmall = 32;   // asynchronous classes of graphs below kSmallGraph vertices
+constexpr int kAsyncSubroundsSmall = 32;
+// Asynchronous bucket streams: the hubs of an iteration run in this many
+// groups of consecutive classes (hub groups = classes: one per class).
+constexpr int kHubGroups = 16;   // asynchronous classes of graphs below kSmallGraph vertices
 constexpr int64_t kSmallGraph = 65536;
 
 struct IterRec {
@@ -428,7 +431,11 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
           sused[b] = true;
           lm_launch_bucket<W>(a, wide, async, b, c->list + s0, (int)(s1 - s0), c->aux[b]);
         }
-        int64_t h0 = ko[kHubBucket * P + ch] - hub0, h1 = ko[kHubBucket * P + ch + 1] - hub0;
+        // hubs go in groups of consecutive classes (one launch sequence each)
+        const int hstep = P / kHubGroups > 1 ? P / kHubGroups : 1;
+        if (ch % hstep != 0) continue;
+        const int chend = ch + hstep < P ? ch + hstep : P;
+        int64_t h0 = ko[kHubBucket * P + ch] - hub0, h1 = ko[kHubBucket * P + chend] - hub0;
         if (h1 > h0) {
           sused[kHubBucket] = true;
           LMArgs<W> ah = a;

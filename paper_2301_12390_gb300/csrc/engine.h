@@ -1,6 +1,9 @@
 // engine.h — host-side declarations shared by the engine's translation units.
 #pragma once
 #include <cstdint>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cuda_runtime.h>
 #include "common.cuh"
 
@@ -248,5 +251,26 @@ void validate_csr(const int64_t* off, const int32_t* col, const int32_t* wt, int
 void widen_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
 void fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t s);
 void iota_i32(int32_t* p, int64_t n, cudaStream_t s);
+
+// Resident blocks per SM of a kernel at a block size and dynamic shared
+// memory size, asked of the runtime once per combination (the query costs
+// several microseconds of host time, and launches are on the host's critical
+// path when kernels are short).
+template <typename K>
+int blocks_per_sm(K kernel, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, size_t>, int> cache;
+  const auto key = std::make_tuple((const void*)kernel, threads, smem);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess || per < 1) {
+    cudaGetLastError();
+    per = 1;
+  }
+  cache.emplace(key, per);
+  return per;
+}
 
 }  // namespace gbl

@@ -1013,7 +1013,7 @@ int agrid(K kernel, int threads, size_t smem, int work) {
     if (sms <= 0) sms = 1;
   }
   int per = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess || per < 1) per = 1;
+  per = blocks_per_sm(kernel, threads, smem);
   int g = sms * per;
   if (work < g) g = work;
   return g < 1 ? 1 : g;

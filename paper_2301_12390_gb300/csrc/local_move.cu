@@ -836,9 +836,7 @@ int grid_for(K kernel, int threads, size_t smem, int work_blocks) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
   }
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
-    per_sm = 1;
+  const int per_sm = blocks_per_sm(kernel, threads, smem);
   int g = sms * per_sm;
   if (work_blocks < g) g = work_blocks;
   return g < 1 ? 1 : g;
