@@ -13,8 +13,11 @@
 // cannot fit even alone is answered with LOUVAIN_ERR_OOM.
 #include <chrono>
 #include <condition_variable>
+#include <cstdint>
 #include <cstring>
 #include <deque>
+#include <map>
+#include <iterator>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -25,11 +28,87 @@
 
 namespace {
 
+// Pinned host memory for request graphs, reused from request to request
+// (block sizes recur): a request's device load is then a DMA instead of a
+// copy staged through the driver's buffers.  At most cap bytes are pinned;
+// past that a request keeps pageable memory.
+class PinnedPool {
+ public:
+  explicit PinnedPool(size_t cap) : cap_(cap) {}
+  ~PinnedPool() {
+    for (auto& kv : free_) cudaFreeHost(kv.second);
+  }
+  void* get(size_t bytes, size_t* got) {
+    std::lock_guard<std::mutex> lk(mu_);
+    auto it = free_.lower_bound(bytes);
+    if (it != free_.end() && it->first <= 2 * bytes + (1u << 20)) {
+      void* p = it->second;
+      *got = it->first;
+      free_.erase(it);
+      return p;
+    }
+    const size_t sz = (bytes + (1u << 20) - 1) & ~(size_t)((1u << 20) - 1);
+    while (held_ + sz > cap_ && !free_.empty()) {   // give back free blocks, largest first
+      auto e = std::prev(free_.end());
+      cudaFreeHost(e->second);
+      held_ -= e->first;
+      free_.erase(e);
+    }
+    if (held_ + sz > cap_) return nullptr;
+    void* p = nullptr;
+    if (cudaMallocHost(&p, sz) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    held_ += sz;
+    *got = sz;
+    return p;
+  }
+  void put(void* p, size_t bytes) {
+    std::lock_guard<std::mutex> lk(mu_);
+    free_.emplace(bytes, p);
+  }
+
+ private:
+  std::mutex mu_;
+  std::multimap<size_t, void*> free_;
+  size_t held_ = 0, cap_;
+};
+
+// A block of the pool, returned to it when its owner goes away.
+struct PinnedBlock {
+  PinnedPool* pool = nullptr;
+  void* p = nullptr;
+  size_t bytes = 0;
+  PinnedBlock() = default;
+  PinnedBlock(const PinnedBlock&) = delete;
+  PinnedBlock& operator=(const PinnedBlock&) = delete;
+  PinnedBlock(PinnedBlock&& o) noexcept : pool(o.pool), p(o.p), bytes(o.bytes) { o.p = nullptr; }
+  PinnedBlock& operator=(PinnedBlock&& o) noexcept {
+    if (this != &o) {
+      release();
+      pool = o.pool;
+      p = o.p;
+      bytes = o.bytes;
+      o.p = nullptr;
+    }
+    return *this;
+  }
+  ~PinnedBlock() { release(); }
+  void release() {
+    if (p && pool) pool->put(p, bytes);
+    p = nullptr;
+  }
+};
+
 struct Request {
   int64_t id = 0;
   int64_t n = 0, nnz = 0;
-  std::vector<int64_t> off;
-  std::vector<int32_t> col, w;
+  PinnedBlock pin;              // the graph's arrays, pinned
+  std::vector<char> heap;       // or pageable, when the pool is full
+  const int64_t* off = nullptr;
+  const int32_t* col = nullptr;
+  const int32_t* w = nullptr;
   double submit_s = 0;
 };
 
@@ -46,6 +125,7 @@ double now_s(std::chrono::steady_clock::time_point t0) {
 }  // namespace
 
 struct louvain_server {
+  PinnedPool pinned{(size_t)8 << 30};   // destroyed last: queued requests return their blocks first
   louvain_options opt;
   louvain_server_config cfg;
   int device = 0;
@@ -98,9 +178,9 @@ int run_batch(louvain_server* S, Slot& slot, std::vector<Request>& batch, double
     vo[g + 1] = vo[g] + r.n;
     ns[g] = r.n;
     nnzs[g] = r.nnz;
-    offs[g] = r.off.data();
-    cols[g] = r.col.data();
-    ws[g] = r.w.data();
+    offs[g] = r.off;
+    cols[g] = r.col;
+    ws[g] = r.w;
   }
   const double t1 = now_s(S->t0);
   int rc = G == 1 ? louvain_load_csr(slot.ctx, N, E, offs[0], cols[0], ws[0], LOUVAIN_PTR_HOST)
@@ -288,9 +368,29 @@ int louvain_server_submit(louvain_server* S, int64_t request_id, int64_t n, int6
   r.id = request_id;
   r.n = n;
   r.nnz = nnz;
-  r.off.assign(offsets, offsets + n + 1);
-  r.col.assign(cols, cols + nnz);
-  r.w.assign(weights, weights + nnz);
+  // one block: offsets, then columns and weights (16-byte aligned)
+  const size_t b_off = (size_t)(n + 1) * sizeof(int64_t);
+  const size_t at_col = (b_off + 15) & ~(size_t)15;
+  const size_t at_w = at_col + (((size_t)nnz * sizeof(int32_t) + 15) & ~(size_t)15);
+  const size_t total = at_w + (size_t)nnz * sizeof(int32_t);
+  size_t got = 0;
+  char* base = (char*)S->pinned.get(total, &got);
+  if (base) {
+    r.pin.pool = &S->pinned;
+    r.pin.p = base;
+    r.pin.bytes = got;
+  } else {
+    r.heap.resize(total + 16);
+    base = (char*)(((uintptr_t)r.heap.data() + 15) & ~(uintptr_t)15);
+  }
+  memcpy(base, offsets, b_off);
+  if (nnz) {
+    memcpy(base + at_col, cols, (size_t)nnz * sizeof(int32_t));
+    memcpy(base + at_w, weights, (size_t)nnz * sizeof(int32_t));
+  }
+  r.off = (const int64_t*)base;
+  r.col = (const int32_t*)(base + at_col);
+  r.w = (const int32_t*)(base + at_w);
   {
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->stopping) return LOUVAIN_ERR_STATE;
