@@ -117,9 +117,11 @@ typedef struct {
   double total_ms;            /* device time of louvain_run */
   int64_t lm_vertices;        /* vertices visited by local-moving */
   int64_t lm_bytes;           /* algorithmic bytes of local-moving: 8 + sizeof(weight) per scanned entry
-                                 (column, weight, neighbour membership) + 32 per visited vertex */
+                                 (column, weight, neighbour membership), 32 per visited vertex, 8 per
+                                 distinct candidate community (its total) and 16 per move (two totals) */
   int64_t kernel_launches;    /* kernels the run launched */
-  int64_t reserved[5];
+  int64_t lm_candidates;      /* distinct candidate communities evaluated by local-moving */
+  int64_t reserved[4];
 } louvain_stats;
 
 /* Per-pass record. */

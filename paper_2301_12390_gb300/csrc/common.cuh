@@ -36,6 +36,7 @@ struct DevCounters {
   unsigned long long edges;        // CSR entries scanned
   unsigned long long visited;      // vertices visited
   unsigned long long nmoves_list;  // entries in the synchronous move list
+  unsigned long long cands;        // distinct candidate communities evaluated (other than the own)
   int error;
   int pad;
 };

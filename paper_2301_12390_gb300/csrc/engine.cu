@@ -125,6 +125,7 @@ struct louvain_ctx {
   int32_t* d_gsmall = nullptr; // per graph: fewer than kSmallGraph vertices (its class schedule)
   LMThresholds thr = {{kLMCap[0], kLMCap[1], kLMCap[2], kLMCap[3], kLMCap[4]}};   // degree mapping
   bool warm = false;           // this run's pass 0 starts from the membership in memb
+  int64_t lm_cands = 0;        // candidate communities evaluated by this run's local moving
   louvain_ctx* sub = nullptr;  // louvain_run_partitioned: the parts' context (same device and stream)
   int32_t* crow = nullptr;     // aggregation: first row of each relabel chunk      // aggregation: direct-table first key per global community, or -1
   unsigned long long* hkid = nullptr;
@@ -394,7 +395,7 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
     c->h_gon[q] = c->gst[q].stopped ? 0 : 1;
   }
   if (multi) CK(cudaMemcpyAsync(c->d_gon, c->h_gon, G * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-  int64_t edges_total = 0, visited_total = 0;
+  int64_t edges_total = 0, visited_total = 0, cands_total = 0;
 
   // One iteration's launch sequence: counters cleared, every class's buckets
   // forked onto their streams and joined (synchronous: then committed), and
@@ -563,6 +564,7 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
     }
     edges_total += (int64_t)c->h_ctr->edges;
     visited_total += (int64_t)c->h_ctr->visited;
+    cands_total += (int64_t)c->h_ctr->cands;
     bool any_on = false;
     if (!multi) {
       const u128 S = ((u128)c->h_ctr->s_hi << 64) | (u128)c->h_ctr->s_lo;
@@ -606,6 +608,7 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
   *iters_out = it;
   *edges_out = edges_total;
   *visited_out = visited_total;
+  c->lm_cands += cands_total;
   return 0;
 }
 
@@ -798,7 +801,11 @@ int run_pass(louvain_ctx* c, const PassState& g, int pass, double* tol, bool wid
   // and neighbour membership; per visited vertex two offsets, its membership,
   // degree, own community total and activity stamp (32 B)
   c->stats.lm_vertices += visited;
-  c->stats.lm_bytes += edges * (int64_t)(4 + sizeof(W) + 4) + visited * 32;
+  // + per distinct candidate community its total Sigma_c (8), per move the two
+  // totals it updates (16)
+  const int64_t cands = c->lm_cands - c->stats.lm_candidates;
+  c->stats.lm_candidates = c->lm_cands;
+  c->stats.lm_bytes += edges * (int64_t)(4 + sizeof(W) + 4) + visited * 32 + cands * 8 + pmoves * 16;
   c->stats.moves += pmoves;
   c->stats.iterations += iters;
   c->stats.passes = pass + 1;
@@ -936,6 +943,7 @@ int run_all(louvain_ctx* c) {
   cudaStream_t s = c->stream;
   const int64_t G = c->G;
   memset(&c->stats, 0, sizeof(c->stats));
+  c->lm_cands = 0;
   c->Q = 0;
   const long long launches0 = launches_so_far();
   CK(cudaEventRecord(c->ev[6], s));

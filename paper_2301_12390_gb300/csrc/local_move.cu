@@ -62,18 +62,19 @@ __device__ __forceinline__ int32_t ld_size(const int32_t* p) {
 
 // Block-level accumulators, flushed once per block.
 struct BlockAcc {
-  unsigned long long moves, edges, visited, s_lo, s_hi;
+  unsigned long long moves, edges, visited, s_lo, s_hi, cands;
   int error;
 };
 
 __device__ __forceinline__ void acc_init(BlockAcc& b) {
-  if (threadIdx.x == 0) { b.moves = 0; b.edges = 0; b.visited = 0; b.s_lo = 0; b.s_hi = 0; b.error = 0; }
+  if (threadIdx.x == 0) { b.moves = 0; b.edges = 0; b.visited = 0; b.s_lo = 0; b.s_hi = 0; b.cands = 0; b.error = 0; }
 }
 __device__ __forceinline__ void acc_flush(BlockAcc& b, DevCounters* ctr) {
   if (threadIdx.x == 0) {
     if (b.moves) atomicAdd(&ctr->moves, b.moves);
     if (b.edges) atomicAdd(&ctr->edges, b.edges);
     if (b.visited) atomicAdd(&ctr->visited, b.visited);
+    if (b.cands) atomicAdd(&ctr->cands, b.cands);
     u128 s = ((u128)b.s_hi << 64) | (u128)b.s_lo;
     if (s) atomic_add_u128(&ctr->s_lo, &ctr->s_hi, s);
     if (b.error) atomicOr(&ctr->error, b.error);
@@ -234,13 +235,16 @@ __global__ void __launch_bounds__(256, 3) lm_thread(LMArgs<W> a, const int32_t* 
     for (int k = 0; k < 8; ++k) sg[k] = (cc[k] != kEmpty && cc[k] != d) ? ld_sig<ASYNC>(a.sig + cc[k]) : 0;
     S bg = Arith<WIDE>::lowest();
     int32_t bc = -1;
+    unsigned ncand = 0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       if (cc[k] != kEmpty && cc[k] != d) {
+        ++ncand;
         S g = Arith<WIDE>::score(M, (long long)ww[k], Ki, sg[k]);
         if (better(g, cc[k], bg, bc)) { bg = g; bc = cc[k]; }
       }
     }
+    atomicAdd(&acc.cands, (unsigned long long)ncand);
     atomicAdd(&acc.edges, (unsigned long long)(e - b));
         atomicAdd(&acc.visited, 1ull);
     if (commit_choice<W, WIDE, ASYNC>(a, acc, i, d, Ki, sd, szd, bg, bc, kid, M, graph) && a.prune) {
@@ -287,6 +291,7 @@ __device__ __forceinline__ void warp_vertex(const LMArgs<W>& a, const IterView& 
   unsigned long long kid = 0;
   S bg = Arith<WIDE>::lowest();
   int32_t bc = -1;
+  unsigned ncand = 0;
 #pragma unroll
   for (int t0 = 0; t0 < CAP; t0 += kWarp * 4) {
     int32_t cs[4];
@@ -305,6 +310,7 @@ __device__ __forceinline__ void warp_vertex(const LMArgs<W>& a, const IterView& 
       const int t = t0 + u * kWarp + lane;
       if (cs[u] != kEmpty) {
         if (cs[u] != d) {
+          ++ncand;
           S g = Arith<WIDE>::score(M, (long long)vs[u], Ki, sg[u]);
           if (better(g, cs[u], bg, bc)) { bg = g; bc = cs[u]; }
         } else {
@@ -316,12 +322,14 @@ __device__ __forceinline__ void warp_vertex(const LMArgs<W>& a, const IterView& 
     }
   }
   warp_argmax(bg, bc);
+  ncand = __reduce_add_sync(0xffffffffu, ncand);
   {
     const unsigned has = __ballot_sync(0xffffffffu, kid != 0);
     kid = has ? __shfl_sync(0xffffffffu, kid, __ffs(has) - 1) : 0ull;
   }
   bool moved = false;
   if (lane == 0) {
+    atomicAdd(&acc.cands, (unsigned long long)ncand);
     atomicAdd(&acc.edges, (unsigned long long)(e - b));
     atomicAdd(&acc.visited, 1ull);
     moved = commit_choice<W, WIDE, ASYNC, LD>(a, acc, i, d, Ki, cur.sd, cur.szd, bg, bc, kid, M, graph);
@@ -581,6 +589,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 128 ? 8 : 2)
       if (lane == 0) {
         atomicAdd(&acc.edges, (unsigned long long)(e - b));
         atomicAdd(&acc.visited, 1ull);
+        atomicAdd(&acc.cands, (unsigned long long)(s_nt[p] - (s_kid[p] != 0 ? 1 : 0)));
         if (decide_move<W, WIDE, ASYNC>(a, acc, d, Ki, cur.sd, cur.szd, bg, bc, s_kid[p], M, graph))
           queue[q_n++] = PendingMove{i, bc, d};
       }
@@ -703,6 +712,7 @@ __global__ void __launch_bounds__(256) lm_hub_scan(LMArgs<W> a, const int32_t* _
   const int64_t t0 = q * kSlotChunk, t1 = min(cap, t0 + kSlotChunk);
   S bg = Arith<WIDE>::lowest();
   int32_t bc = -1;
+  unsigned ncand = 0;
   constexpr int U = 4;
   for (int64_t y = t0; y < t1; y += U * 256) {
     int32_t cs[U];
@@ -721,6 +731,7 @@ __global__ void __launch_bounds__(256) lm_hub_scan(LMArgs<W> a, const int32_t* _
       if (cs[u] == kEmpty) continue;
       const int64_t t = y + u * 256 + threadIdx.x;
       if (cs[u] != d) {
+        ++ncand;
         S g = Arith<WIDE>::score(M, (long long)vs[u], Ki, sg[u]);
         if (better(g, cs[u], bg, bc)) { bg = g; bc = cs[u]; }
       } else {
@@ -730,6 +741,8 @@ __global__ void __launch_bounds__(256) lm_hub_scan(LMArgs<W> a, const int32_t* _
       a.hvals[base + t] = 0;
     }
   }
+  ncand = __reduce_add_sync(0xffffffffu, ncand);
+  if (lane == 0 && ncand) atomicAdd(&a.ctr->cands, (unsigned long long)ncand);
   warp_argmax(bg, bc);
   if (lane == 0) { red_g[wid] = bg; red_c[wid] = bc; }
   __syncthreads();

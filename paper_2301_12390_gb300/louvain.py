@@ -48,7 +48,8 @@ class Stats(ctypes.Structure):
                 ("lm_edges", ctypes.c_int64), ("communities", ctypes.c_int64), ("q", ctypes.c_double),
                 ("lm_ms", ctypes.c_double), ("agg_ms", ctypes.c_double), ("other_ms", ctypes.c_double),
                 ("total_ms", ctypes.c_double), ("lm_vertices", ctypes.c_int64), ("lm_bytes", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64), ("reserved", ctypes.c_int64 * 5)]
+                ("kernel_launches", ctypes.c_int64), ("lm_candidates", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 4)]
 
 
 class PassInfo(ctypes.Structure):

@@ -396,3 +396,17 @@ def test_device_pointers_match_host():
         out = torch.empty(g.n, dtype=torch.int32, device="cuda")
         lv.membership(out)
         assert np.array_equal(out.cpu().numpy(), host["top"])
+
+
+def test_local_moving_byte_model():
+    """lm_bytes follows the algorithmic model: 12 per scanned entry (32-bit
+    weights), 32 per visited vertex, 8 per candidate community, 16 per move;
+    every visited vertex with a neighbour outside its community has at least
+    one candidate, and there are never more candidates than scanned entries."""
+    g = G["rmat14"]
+    with Louvain(device=0, mode=0, prune=1) as lv:
+        lv.load_csr(g.off, g.col, g.w)
+        lv.run()
+        st = lv.stats()
+    assert 0 < st.lm_candidates <= st.lm_edges
+    assert st.lm_bytes == 12 * st.lm_edges + 32 * st.lm_vertices + 8 * st.lm_candidates + 16 * st.moves
