@@ -117,8 +117,11 @@ void stable_partition(const int32_t* key, int64_t n, int nkeys, int32_t* out, in
 // Keys for the local-moving lists, bucket-major: key[i] = bucket * P + class
 // of vertex i (P >= Ps, Pb); vertices of degree 0 get the trailing key
 // kBuckets * P.
+// active (may be null): the stamps of this iteration; with it, vertices not
+// active in it, or of a stopped graph (g_on), get the trailing key.
 void lm_keys(const int64_t* off, int64_t n, int P, int32_t* key, const int32_t* gid, const int64_t* vo,
-             const int32_t* gsmall, ClassSpec cs, const int* d_iter, LMThresholds th, cudaStream_t s);
+             const int32_t* gsmall, ClassSpec cs, const int* d_iter, LMThresholds th, const int32_t* active,
+             const int32_t* g_on, cudaStream_t s);
 // lm_keys for the m vertices sub[0..m); gather_ids: out[j] = sub[idx[j]].
 void lm_keys_sub(const int64_t* off, const int32_t* sub, int64_t m, int P, int32_t* key, const int32_t* gid,
                  const int64_t* vo, const int32_t* gsmall, ClassSpec cs, const int* d_iter, LMThresholds th,

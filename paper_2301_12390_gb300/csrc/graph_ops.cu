@@ -232,13 +232,17 @@ void stable_partition(const int32_t* key, int64_t n, int nkeys, int32_t* out, in
 
 // --------------------------------------------------- local-moving lists
 
+// With `active` (the stamps read in this iteration), vertices that are not
+// active, or whose graph has stopped (g_on), get the trailing key too, so the
+// lists hold only the vertices the iteration visits.
 __global__ void lm_keys_k(const int64_t* __restrict__ off, int64_t n, int P, int32_t* key,
                           const int32_t* __restrict__ gid, const int64_t* __restrict__ vo,
                           const int32_t* __restrict__ gsmall, ClassSpec cs, const int* __restrict__ d_iter,
-                          LMThresholds th) {
+                          LMThresholds th, const int32_t* __restrict__ active, const int32_t* __restrict__ g_on) {
   const int iter = *d_iter;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int b = lm_bucket_of(off[i + 1] - off[i], th);
+    if (active && (active[i] != iter || (gid && !g_on[gid[i]]))) b = -1;
     key[i] = b < 0 ? kBuckets * P : b * P + (P > 1 ? vertex_class(i, gid, vo, gsmall, cs, iter) : 0);
   }
 }
@@ -269,8 +273,10 @@ static unsigned grid1d(int64_t n, int per = kT) {
 }
 
 void lm_keys(const int64_t* off, int64_t n, int P, int32_t* key, const int32_t* gid, const int64_t* vo,
-             const int32_t* gsmall, ClassSpec cs, const int* d_iter, LMThresholds th, cudaStream_t s) {
-  if (n > 0) (count_launch(), lm_keys_k<<<grid1d(n), kT, 0, s>>>(off, n, P, key, gid, vo, gsmall, cs, d_iter, th));
+             const int32_t* gsmall, ClassSpec cs, const int* d_iter, LMThresholds th, const int32_t* active,
+             const int32_t* g_on, cudaStream_t s) {
+  if (n > 0)
+    (count_launch(), lm_keys_k<<<grid1d(n), kT, 0, s>>>(off, n, P, key, gid, vo, gsmall, cs, d_iter, th, active, g_on));
 }
 
 __global__ void hub_sizes_k(const int64_t* off, const int32_t* hubs, int64_t nhubs, int64_t* cap, int64_t* chunks,

@@ -180,9 +180,11 @@ __device__ __forceinline__ VertexInfo vertex_info(const LMArgs<W>& a, const Iter
   v.e = a.off[v.i + 1];
   v.d = ld_state<LD == 2 ? 2 : 1>(a.memb + v.i);
   v.Ki = a.K[v.i];
-  v.sd = ld_state<LD>(a.sig + v.d);
-  v.szd = ld_state<LD>(a.csize + v.d);
   v.on = is_active(a, iv, v.i) && graph_of(a, v.i, &v.M, &v.graph);
+  if (v.on) {   // the loads that depend on d, only for a vertex that is visited
+    v.sd = ld_state<LD>(a.sig + v.d);
+    v.szd = ld_state<LD>(a.csize + v.d);
+  }
   return v;
 }
 
