@@ -270,13 +270,14 @@ def bench_ours(args):
     clocks.start()
     time.sleep(0.3)   # let the sampler start before the load
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    lm_edges = lm_bytes = launches = 0
+    lm_edges = lm_bytes = launches = iters = 0
     lm_ms = agg_ms = 0.0
     qs = []
     start.record(stream)
     for _ in range(args.steps):
         lv.run()
         st = lv.stats()
+        iters += sum(p.iterations for p in lv.passes()[:1])
         lm_edges += st.lm_edges
         lm_bytes += st.lm_bytes
         lm_ms += st.lm_ms
@@ -344,7 +345,11 @@ def bench_ours(args):
             "gpu_launches": launches,
             "breakdown": {"lm_ms_per_step": lm_ms / args.steps, "agg_ms_per_step": agg_ms / args.steps,
                           "lm_edges_per_step": lm_edges / args.steps,
-                          "lm_only_edges_per_s": lm_edges / (lm_ms / 1e3)},
+                          "lm_only_edges_per_s": lm_edges / (lm_ms / 1e3),
+                          # time to solution: input entries per second of the whole run
+                          "input_edges_per_s": world * g.nnz / (ms / args.steps / 1e3),
+                          # pass 0 (the input graph): its iterations times nnz per second of its local moving
+                          "pass0_iterations_per_step": iters / args.steps},
         }
         print(json.dumps(line), flush=True)
     lv.close()
