@@ -81,6 +81,43 @@ __device__ __forceinline__ void acc_flush(BlockAcc& b, DevCounters* ctr) {
   }
 }
 
+__device__ __forceinline__ u128 warp_sum_u128(u128 v) {
+  unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo, o), h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const unsigned long long nl = lo + l2;
+    hi = hi + h2 + (nl < lo ? 1ull : 0ull);
+    lo = nl;
+  }
+  return ((u128)hi << 64) | (u128)lo;
+}
+
+// All 32 lanes of a warp: the moves and gains of the lanes that moved (gv of
+// a lane that did not is ignored), summed per graph of a batch and added
+// with one atomic per distinct graph, or to the block's accumulator.
+template <typename W>
+__device__ __forceinline__ void warp_move_totals(const LMArgs<W>& a, BlockAcc& acc, bool moved, int graph, u128 gv) {
+  unsigned pend = __ballot_sync(0xffffffffu, moved);
+  while (pend) {
+    const int leader = __ffs(pend) - 1;
+    const int gl = __shfl_sync(0xffffffffu, graph, leader);
+    const bool in = moved && (!a.gid || graph == gl);
+    const unsigned inm = __ballot_sync(0xffffffffu, in);
+    const u128 sum = warp_sum_u128(in ? gv : (u128)0);
+    if ((int)(threadIdx.x & 31) == leader) {
+      if (a.gid) {
+        atomicAdd(a.g_moves + gl, (unsigned long long)__popc(inm));
+        atomic_add_u128(a.g_s + 2 * gl, a.g_s + 2 * gl + 1, sum);
+      } else {
+        atomicAdd(&acc.moves, (unsigned long long)__popc(inm));
+        atomic_add_u128(&acc.s_lo, &acc.s_hi, sum);
+      }
+    }
+    pend &= ~inm;
+  }
+}
+
 // Decide-and-apply for vertex i (called by one thread): guard, then either
 // an in-place move (asynchronous) or an entry in the move list (synchronous).
 // Returns whether the vertex moves.
@@ -92,7 +129,8 @@ __device__ __forceinline__ void acc_flush(BlockAcc& b, DevCounters* ctr) {
 template <typename W, bool WIDE, bool ASYNC, int LD = (ASYNC ? 1 : 0)>
 __device__ __forceinline__ bool commit_choice(const LMArgs<W>& a, BlockAcc& acc, int32_t i, int32_t d, long long Ki,
                                               long long sd, int32_t szd, typename Arith<WIDE>::S best, int32_t c,
-                                              unsigned long long kid, long long M, int graph) {
+                                              unsigned long long kid, long long M, int graph,
+                                              u128* defer_gain = nullptr) {
   if (c < 0) return false;
   typedef typename Arith<WIDE>::S S;
   const S g = best - Arith<WIDE>::score(M, (long long)kid, Ki, sd - Ki);
@@ -109,6 +147,10 @@ __device__ __forceinline__ bool commit_choice(const LMArgs<W>& a, BlockAcc& acc,
     a.moves[pos] = make_int2(i, c);
   }
   u128 gv = Arith<WIDE>::to_u128(g);   // g > 0 here
+  if (defer_gain) {   // the caller adds the move and its gain
+    *defer_gain = gv;
+    return true;
+  }
   if (a.gid) {
     atomicAdd(a.g_moves + graph, 1ull);
     atomic_add_u128(a.g_s + 2 * graph, a.g_s + 2 * graph + 1, gv);
@@ -199,60 +241,80 @@ __global__ void __launch_bounds__(256, 3) lm_thread(LMArgs<W> a, const int32_t* 
   __shared__ BlockAcc acc;
   acc_init(acc);
   __syncthreads();
-  for (int vi = blockIdx.x * blockDim.x + threadIdx.x; vi < nverts; vi += gridDim.x * blockDim.x) {
-    int32_t i = verts[vi];
-    if (!is_active(a, iv, i)) continue;
-    long long M;
-    int graph;
-    if (!graph_of(a, i, &M, &graph)) continue;
-    const int64_t b = a.off[i], e = a.off[i + 1];
-    const int32_t d = a.memb[i];
-    const long long Ki = a.K[i];
-    const long long sd = ld_sig<ASYNC>(a.sig + d);
-    const int32_t szd = ld_size<ASYNC>(a.csize + d);
-    int32_t cc[8];
-    unsigned long long ww[8];
+  // Whole warps iterate together and sum their counters, moves and gains
+  // over the warp: per-lane atomics on the block's counters serialise
+  // (measured: a third of this kernel's time).
+  for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < nverts; base += gridDim.x * blockDim.x) {
+    const int vi = base + (int)(threadIdx.x & 31);
+    bool moved = false;
+    u128 gv = 0;
+    int graph = 0;
+    unsigned n_edges = 0, n_visited = 0, n_cand = 0;
+    do {
+      if (vi >= nverts) break;
+      int32_t i = verts[vi];
+      if (!is_active(a, iv, i)) break;
+      long long M;
+      if (!graph_of(a, i, &M, &graph)) break;
+      const int64_t b = a.off[i], e = a.off[i + 1];
+      const int32_t d = a.memb[i];
+      const long long Ki = a.K[i];
+      const long long sd = ld_sig<ASYNC>(a.sig + d);
+      const int32_t szd = ld_size<ASYNC>(a.csize + d);
+      int32_t cc[8];
+      unsigned long long ww[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const bool v = b + k < e;
-      cc[k] = v ? a.col[b + k] : i;
-      ww[k] = v ? (unsigned long long)a.wt[b + k] : 0ull;
-    }
-#pragma unroll
-    for (int k = 0; k < 8; ++k) cc[k] = cc[k] != i ? ld_memb<ASYNC>(a.memb + cc[k]) : kEmpty;
-#pragma unroll
-    for (int k = 1; k < 8; ++k) {
-      bool merged = false;
-#pragma unroll
-      for (int l = 0; l < k; ++l)
-        if (!merged && cc[k] != kEmpty && cc[l] == cc[k]) { ww[l] += ww[k]; merged = true; }
-      if (merged) cc[k] = kEmpty;
-    }
-    unsigned long long kid = 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-      if (cc[k] == d) kid = ww[k];
-    long long sg[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) sg[k] = (cc[k] != kEmpty && cc[k] != d) ? ld_sig<ASYNC>(a.sig + cc[k]) : 0;
-    S bg = Arith<WIDE>::lowest();
-    int32_t bc = -1;
-    unsigned ncand = 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      if (cc[k] != kEmpty && cc[k] != d) {
-        ++ncand;
-        S g = Arith<WIDE>::score(M, (long long)ww[k], Ki, sg[k]);
-        if (better(g, cc[k], bg, bc)) { bg = g; bc = cc[k]; }
+      for (int k = 0; k < 8; ++k) {
+        const bool v = b + k < e;
+        cc[k] = v ? a.col[b + k] : i;
+        ww[k] = v ? (unsigned long long)a.wt[b + k] : 0ull;
       }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) cc[k] = cc[k] != i ? ld_memb<ASYNC>(a.memb + cc[k]) : kEmpty;
+#pragma unroll
+      for (int k = 1; k < 8; ++k) {
+        bool merged = false;
+#pragma unroll
+        for (int l = 0; l < k; ++l)
+          if (!merged && cc[k] != kEmpty && cc[l] == cc[k]) { ww[l] += ww[k]; merged = true; }
+        if (merged) cc[k] = kEmpty;
+      }
+      unsigned long long kid = 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (cc[k] == d) kid = ww[k];
+      long long sg[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) sg[k] = (cc[k] != kEmpty && cc[k] != d) ? ld_sig<ASYNC>(a.sig + cc[k]) : 0;
+      S bg = Arith<WIDE>::lowest();
+      int32_t bc = -1;
+      unsigned ncand = 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (cc[k] != kEmpty && cc[k] != d) {
+          ++ncand;
+          S g = Arith<WIDE>::score(M, (long long)ww[k], Ki, sg[k]);
+          if (better(g, cc[k], bg, bc)) { bg = g; bc = cc[k]; }
+        }
+      }
+      n_cand = ncand;
+      n_edges = (unsigned)(e - b);
+      n_visited = 1;
+      moved = commit_choice<W, WIDE, ASYNC>(a, acc, i, d, Ki, sd, szd, bg, bc, kid, M, graph, &gv);
+      if (moved && a.prune) {
+        iv.sw[i] = iv.iter + 1;
+        for (int64_t x = b; x < e; ++x) iv.sw[a.col[x]] = iv.iter + 1;
+      }
+    } while (false);
+    n_edges = __reduce_add_sync(0xffffffffu, n_edges);
+    n_visited = __reduce_add_sync(0xffffffffu, n_visited);
+    n_cand = __reduce_add_sync(0xffffffffu, n_cand);
+    if ((threadIdx.x & 31) == 0 && n_visited) {
+      atomicAdd(&acc.edges, (unsigned long long)n_edges);
+      atomicAdd(&acc.visited, (unsigned long long)n_visited);
+      atomicAdd(&acc.cands, (unsigned long long)n_cand);
     }
-    atomicAdd(&acc.cands, (unsigned long long)ncand);
-    atomicAdd(&acc.edges, (unsigned long long)(e - b));
-        atomicAdd(&acc.visited, 1ull);
-    if (commit_choice<W, WIDE, ASYNC>(a, acc, i, d, Ki, sd, szd, bg, bc, kid, M, graph) && a.prune) {
-      iv.sw[i] = iv.iter + 1;
-      for (int64_t x = b; x < e; ++x) iv.sw[a.col[x]] = iv.iter + 1;
-    }
+    warp_move_totals(a, acc, moved, graph, gv);
   }
   __syncthreads();
   acc_flush(acc, a.ctr);
@@ -698,6 +760,7 @@ __global__ void __launch_bounds__(256) lm_hub_scan(LMArgs<W> a, const int32_t* _
   constexpr int NW = 256 / kWarp;
   __shared__ S red_g[NW];
   __shared__ int32_t red_c[NW];
+  __shared__ unsigned red_n[NW];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int h = find_item(a.spre, nhubs, blockIdx.x);
   const int32_t i = hubs[h];
@@ -744,14 +807,15 @@ __global__ void __launch_bounds__(256) lm_hub_scan(LMArgs<W> a, const int32_t* _
     }
   }
   ncand = __reduce_add_sync(0xffffffffu, ncand);
-  if (lane == 0 && ncand) atomicAdd(&a.ctr->cands, (unsigned long long)ncand);
   warp_argmax(bg, bc);
-  if (lane == 0) { red_g[wid] = bg; red_c[wid] = bc; }
+  if (lane == 0) { red_g[wid] = bg; red_c[wid] = bc; red_n[wid] = ncand; }
   __syncthreads();
   if (wid == 0) {
     bg = lane < NW ? red_g[lane] : Arith<WIDE>::lowest();
     bc = lane < NW ? red_c[lane] : -1;
     warp_argmax(bg, bc);
+    ncand = __reduce_add_sync(0xffffffffu, lane < NW ? red_n[lane] : 0u);
+    if (lane == 0 && ncand) atomicAdd(&a.ctr->cands, (unsigned long long)ncand);
     if (lane == 0) {
       const int64_t slot = a.spre[h] + q;
       u128 gu = (u128)(i128)bg;
