@@ -80,7 +80,8 @@ typedef struct {
   int32_t subrounds;          /* P >= 1: the vertices are split into P classes processed one after
                                  the other in each iteration; 1 = every vertex at once; 0 = automatic
                                  (synchronous 1; asynchronous, per graph: 32 for a graph of fewer than
-                                 65,536 vertices, else 16) */
+                                 65,536 vertices, else 8 for a graph of fewer than 8 entries per vertex,
+                                 else 16) */
   int32_t validate;           /* 1: louvain_load_csr checks symmetry and CSR form (costs a pass) */
   int32_t record_levels;      /* 1: keep each pass's membership and coarse CSR for louvain_get_level /
                                  louvain_get_coarse (copies them to host memory) */

@@ -9,6 +9,7 @@
 // once: the iteration test is (2.0 * dbl(S)) / dbl(M^2) <= tolerance and the
 // pass test dbl(N_after - N_before) / dbl(M^2) <= pass_tolerance, dbl() the
 // correctly rounded int128 -> double conversion.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -29,17 +30,23 @@ long long launches_so_far() { return g_launches.load(std::memory_order_relaxed);
 namespace {
 
 // Vertex classes per asynchronous iteration when the options leave it to the
-// engine: with every vertex deciding at once, stale neighbour memberships
-// make pairs and groups swap and modularity can collapse; 16 classes run in
-// sequence keep the result within a few 1e-3 of the sequential order on the
-// large benchmark graphs.  Small graphs (few thousand vertices, few dense
-// communities) need smaller classes: at 16 some planted-partition graphs
-// ended more than 0.01 below the sequential order, at 32 none did.
-constexpr int kAsyncSubrounds = 16;
+// engine, per graph: with every vertex deciding at once, stale neighbour
+// memberships make pairs and groups swap and modularity can collapse; classes
+// run in sequence keep the result near the sequential order's.  Small graphs
+// (few thousand vertices, few dense communities) need small classes: at 16
+// some planted-partition graphs ended more than 0.01 below the sequential
+// order, at 32 none did.  A large graph of fewer than kSparseEntries entries
+// per vertex (a vertex rarely shares its class with a neighbour) takes 8: the
+// road grid ran 13% faster than at 16 with the same Q.  A denser one takes
+// 16: 24 raised R-MAT s22's Q from 0.076 to 0.077 (the sequential order's is
+// 0.075) but took the serving pool's large graphs 9% more run time.
+constexpr int kAsyncSubroundsLarge = 16;
+constexpr int kAsyncSubroundsSparse = 8;
 constexpr int kAsyncSubroundsSmall = 32;
+constexpr int64_t kSparseEntries = 8;
 // Asynchronous bucket streams: the hubs of an iteration run in this many
-// groups of consecutive classes (hub groups = classes: one per class).
-constexpr int kHubGroups = 16;   // asynchronous classes of graphs below kSmallGraph vertices
+// groups of consecutive classes (one class per group up to this many classes).
+constexpr int kHubGroups = 16;
 constexpr int64_t kSmallGraph = 65536;
 // Active-list filtering (local_moving): measured on the 4,096-graph SBM batch
 // (pass 0, most graphs stopped after a few iterations: 150 -> 96 ms) and the
@@ -127,7 +134,8 @@ struct louvain_ctx {
   int64_t* glo = nullptr;
   int32_t* inv = nullptr;      // aggregation: member position of each vertex
   int32_t* hmoved = nullptr;   // local moving: iteration + 1 of a hub's last move (by hub-list position)
-  int32_t* d_gsmall = nullptr; // per graph: fewer than kSmallGraph vertices (its class schedule)
+  int32_t* d_gcat = nullptr;   // per graph: its class-schedule category (kCatSmall, kCatLarge, kCatSparse)
+  std::vector<int32_t> hgcat;   // the same on the host
   LMThresholds thr = {{kLMCap[0], kLMCap[1], kLMCap[2], kLMCap[3], kLMCap[4]}};   // degree mapping
   bool warm = false;           // this run's pass 0 starts from the membership in memb
   int64_t lm_cands = 0;        // candidate communities evaluated by this run's local moving
@@ -290,24 +298,30 @@ template <typename W>
 int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool wide, int* iters_out,
                  int64_t* edges_out, int64_t* visited_out) {
   const bool async = c->opt.mode == LOUVAIN_ASYNC;
-  // Classes, per graph: a graph below kSmallGraph vertices takes
-  // kAsyncSubroundsSmall classes drawn once per pass, a larger one
-  // kAsyncSubrounds classes drawn anew every iteration (automatic settings),
-  // so a graph gets the same schedule alone and in a batch.  Synchronous
-  // classes are id mod P.
-  bool any_small = false, any_big = false;
-  for (int64_t q = 0; q < c->G; ++q) (c->gn0[q] < kSmallGraph ? any_small : any_big) = true;
-  ClassSpec cs{1, 1, 0, 0, pass, c->G == 1 && c->gn0[0] < kSmallGraph ? 1 : 0};
-  if (c->opt.subrounds > 0) cs.Ps = cs.Pb = c->opt.subrounds;
-  else if (async) { cs.Ps = kAsyncSubroundsSmall; cs.Pb = kAsyncSubrounds; }
-  const int P = std::max(any_small ? cs.Ps : 1, any_big ? cs.Pb : 1);
+  // Classes, per graph (its category, set at load): a graph below
+  // kSmallGraph vertices takes kAsyncSubroundsSmall classes drawn once per
+  // pass, a larger one kAsyncSubroundsLarge (or, sparse, kAsyncSubroundsSparse)
+  // classes drawn anew every iteration (automatic settings), so a graph gets
+  // the same schedule alone and in a batch.  Synchronous classes are id mod P.
+  bool any_cat[3] = {false, false, false};
+  for (int64_t q = 0; q < c->G; ++q) any_cat[c->hgcat[q]] = true;
+  const bool any_small = any_cat[kCatSmall], any_big = any_cat[kCatLarge] || any_cat[kCatSparse];
+  ClassSpec cs{1, 1, 1, 0, 0, pass, c->G == 1 ? c->hgcat[0] : kCatLarge};
+  if (c->opt.subrounds > 0) {
+    cs.Ps = cs.Pb = cs.Pl = c->opt.subrounds;
+  } else if (async) {
+    cs.Ps = kAsyncSubroundsSmall;
+    cs.Pb = kAsyncSubroundsLarge;
+    cs.Pl = kAsyncSubroundsSparse;
+  }
+  const int P = std::max({any_small ? cs.Ps : 1, any_cat[kCatLarge] ? cs.Pb : 1, any_cat[kCatSparse] ? cs.Pl : 1});
   const int nkeys = kBuckets * P + 1;
   const bool multi = c->G > 1;
   const int64_t G = c->G;
   cudaStream_t s = c->stream;
   // reclass: 1 = hashed classes drawn anew every iteration, 2 = once per pass
   const int mode_s = (async && cs.Ps > 1) ? (c->opt.reclass == 3 ? 2 : c->opt.reclass) : 0;
-  const int mode_b = (async && cs.Pb > 1) ? (c->opt.reclass == 3 ? 1 : c->opt.reclass) : 0;
+  const int mode_b = (async && (cs.Pb > 1 || cs.Pl > 1)) ? (c->opt.reclass == 3 ? 1 : c->opt.reclass) : 0;
   const bool reclass = (any_small && mode_s == 1) || (any_big && mode_b == 1);   // every iteration
   cs.mode_s = mode_s;
   cs.mode_b = mode_b;
@@ -323,7 +337,7 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
   // small pass whose classes are drawn anew: part of its iteration)
   auto reclassify_small = [&]() {
     int32_t* idx = (int32_t*)c->moves;   // free in asynchronous mode
-    lm_keys_sub(g.off, c->level, sub_m, P, c->key, multi ? c->gid : nullptr, multi ? c->vo : nullptr, c->d_gsmall,
+    lm_keys_sub(g.off, c->level, sub_m, P, c->key, multi ? c->gid : nullptr, multi ? c->vo : nullptr, c->d_gcat,
                 cs, c->d_iter, c->thr, s);
     stable_partition(c->key, sub_m, nkeys, idx, c->key_off, c->tmp, s);
     gather_ids(idx, c->level, sub_m, c->list, s);
@@ -336,7 +350,7 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
   // iterating): the late iterations of a pass, and batches whose graphs have
   // mostly stopped, launch over those alone.  A filtered list is never reused.
   auto classify = [&](int iter, bool filter) -> int {
-    lm_keys(g.off, g.n, P, c->key, multi ? c->gid : nullptr, multi ? c->vo : nullptr, c->d_gsmall, cs, c->d_iter,
+    lm_keys(g.off, g.n, P, c->key, multi ? c->gid : nullptr, multi ? c->vo : nullptr, c->d_gcat, cs, c->d_iter,
             c->thr, filter ? c->stamp[iter & 1] : nullptr, multi ? c->d_gon : nullptr, s);
     stable_partition(c->key, g.n, nkeys, c->list, c->key_off, c->tmp, s);
     CKLAUNCH();
@@ -1146,7 +1160,7 @@ int alloc_arena(louvain_ctx* c, int64_t n, int64_t nnz) {
   ALLOC(c->kcount, N1 + 1);
   ALLOC(c->d_Mg, N1);
   ALLOC(c->d_gon, N1);
-  ALLOC(c->d_gsmall, N1);
+  ALLOC(c->d_gcat, N1);
   ALLOC(c->d_gmoves, N1);
   ALLOC(c->d_gs, 2 * N1);
   ALLOC(c->d_gL, 2 * N1);
@@ -1376,10 +1390,22 @@ int load_graphs(louvain_ctx* c, int64_t G, const int64_t* vo, int64_t n, int64_t
   for (int64_t q = 0; q < G; ++q) c->gn0[q] = vo[q + 1] - vo[q];
   CK(cudaMemcpyAsync(c->vo0, vo, (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   {
-    std::vector<int32_t> small(G);
-    for (int64_t q = 0; q < G; ++q) small[q] = c->gn0[q] < kSmallGraph ? 1 : 0;
-    CK(cudaMemcpyAsync(c->d_gsmall, small.data(), G * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    CK(cudaStreamSynchronize(s));   // the host vector goes out of scope
+    // class-schedule category per graph: small below kSmallGraph vertices,
+    // else sparse below kSparseEntries entries per vertex
+    std::vector<int64_t> ge(G);
+    if (G == 1) {
+      ge[0] = nnz;
+    } else {
+      graph_entries(c->off0, c->vo0, G, (int64_t*)c->d_gs, s);   // d_gs: scratch until the totals below
+      CKLAUNCH();
+      if (int r = fetch(c, ge.data(), c->d_gs, G * sizeof(int64_t))) return r;
+    }
+    c->hgcat.assign(G, kCatLarge);
+    for (int64_t q = 0; q < G; ++q)
+      c->hgcat[q] = c->gn0[q] < kSmallGraph ? kCatSmall
+                    : (ge[q] < kSparseEntries * c->gn0[q] ? kCatSparse : kCatLarge);
+    CK(cudaMemcpyAsync(c->d_gcat, c->hgcat.data(), G * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
   }
   if (G == 1) {
     c->gM0[0] = c->M0;

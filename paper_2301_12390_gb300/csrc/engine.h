@@ -41,17 +41,18 @@ __host__ __device__ inline int agg_bucket_of(int64_t dsum) {
 constexpr int64_t kAggChunkEntries = 2048;
 constexpr int64_t kRelabelChunk = 1024;     // CSR entries per warp of the relabel kernel
 
-// Vertex classes of one iteration: a vertex of a small graph (per-graph flag
-// gsmall, or single_small with one graph) takes class (local id mod Ps, or
-// with mode_s != 0 hash32(local id ^ salt) mod Ps); of a large graph the same
-// with Pb and mode_b.  Mode 1 salts by (pass, iteration), mode 2 by pass only;
-// the iteration is read on the device, so an iteration's launches do not
-// depend on it.
+// Vertex classes of one iteration.  Every graph has a schedule category
+// (per-graph gcat, or single_cat with one graph): kCatSmall takes class
+// (local id mod Ps, or with mode_s != 0 hash32(local id ^ salt) mod Ps),
+// kCatLarge the same with Pb and mode_b, kCatSparse with Pl and mode_b.
+// Mode 1 salts by (pass, iteration), mode 2 by pass only; the iteration is
+// read on the device, so an iteration's launches do not depend on it.
+constexpr int32_t kCatLarge = 0, kCatSmall = 1, kCatSparse = 2;
 struct ClassSpec {
-  int32_t Ps, Pb;
+  int32_t Ps, Pb, Pl;
   int32_t mode_s, mode_b;
   int32_t pass;
-  int32_t single_small;
+  int32_t single_cat;
 };
 // splitmix64 finaliser of (pass, iteration), folded to 32 bits, never 0.
 __host__ __device__ inline uint32_t class_salt(int pass, int iter) {
@@ -62,18 +63,18 @@ __host__ __device__ inline uint32_t class_salt(int pass, int iter) {
   const uint32_t v = (uint32_t)(z ^ (z >> 32));
   return v ? v : 1u;
 }
-// The class of vertex i in iteration iter (gid, vo, gsmall null: one graph).
-__device__ __forceinline__ int vertex_class(int64_t i, const int32_t* gid, const int64_t* vo, const int32_t* gsmall,
+// The class of vertex i in iteration iter (gid, vo, gcat null: one graph).
+__device__ __forceinline__ int vertex_class(int64_t i, const int32_t* gid, const int64_t* vo, const int32_t* gcat,
                                             const ClassSpec& cs, int iter) {
   int64_t local = i;
-  bool small = cs.single_small != 0;
+  int cat = cs.single_cat;
   if (gid) {
     const int g = gid[i];
     local = i - vo[g];
-    small = gsmall[g] != 0;
+    cat = gcat[g];
   }
-  const uint32_t Pg = (uint32_t)(small ? cs.Ps : cs.Pb);
-  const int mode = small ? cs.mode_s : cs.mode_b;
+  const uint32_t Pg = (uint32_t)(cat == kCatSmall ? cs.Ps : (cat == kCatSparse ? cs.Pl : cs.Pb));
+  const int mode = cat == kCatSmall ? cs.mode_s : cs.mode_b;
   if (!mode) return (int)(local % Pg);
   return (int)(hash32((uint32_t)local ^ class_salt(cs.pass, mode == 1 ? iter : 0)) % Pg);
 }
@@ -120,11 +121,11 @@ void stable_partition(const int32_t* key, int64_t n, int nkeys, int32_t* out, in
 // active (may be null): the stamps of this iteration; with it, vertices not
 // active in it, or of a stopped graph (g_on), get the trailing key.
 void lm_keys(const int64_t* off, int64_t n, int P, int32_t* key, const int32_t* gid, const int64_t* vo,
-             const int32_t* gsmall, ClassSpec cs, const int* d_iter, LMThresholds th, const int32_t* active,
+             const int32_t* gcat, ClassSpec cs, const int* d_iter, LMThresholds th, const int32_t* active,
              const int32_t* g_on, cudaStream_t s);
 // lm_keys for the m vertices sub[0..m); gather_ids: out[j] = sub[idx[j]].
 void lm_keys_sub(const int64_t* off, const int32_t* sub, int64_t m, int P, int32_t* key, const int32_t* gid,
-                 const int64_t* vo, const int32_t* gsmall, ClassSpec cs, const int* d_iter, LMThresholds th,
+                 const int64_t* vo, const int32_t* gcat, ClassSpec cs, const int* d_iter, LMThresholds th,
                  cudaStream_t s);
 void gather_ids(const int32_t* idx, const int32_t* sub, int64_t m, int32_t* out, cudaStream_t s);
 // For the hub list: per hub its table base (2 * degree slots), the prefix of
@@ -242,6 +243,7 @@ void graph_renumber(const int32_t* used, const int32_t* newid, const int32_t* gi
                     int32_t* gid_next, cudaStream_t s);
 void localize_membership(const int32_t* top, const int32_t* gid0, const int64_t* vo, int64_t n0, int32_t* out,
                          cudaStream_t s);
+void graph_entries(const int64_t* off, const int64_t* vo, int64_t G, int64_t* out, cudaStream_t s);
 void graph_ids(const int64_t* vo, int G, int64_t n, int32_t* gid, const int64_t* off, const int32_t* col, int* flags,
                cudaStream_t s);
 

@@ -237,26 +237,26 @@ void stable_partition(const int32_t* key, int64_t n, int nkeys, int32_t* out, in
 // lists hold only the vertices the iteration visits.
 __global__ void lm_keys_k(const int64_t* __restrict__ off, int64_t n, int P, int32_t* key,
                           const int32_t* __restrict__ gid, const int64_t* __restrict__ vo,
-                          const int32_t* __restrict__ gsmall, ClassSpec cs, const int* __restrict__ d_iter,
+                          const int32_t* __restrict__ gcat, ClassSpec cs, const int* __restrict__ d_iter,
                           LMThresholds th, const int32_t* __restrict__ active, const int32_t* __restrict__ g_on) {
   const int iter = *d_iter;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int b = lm_bucket_of(off[i + 1] - off[i], th);
     if (active && (active[i] != iter || (gid && !g_on[gid[i]]))) b = -1;
-    key[i] = b < 0 ? kBuckets * P : b * P + (P > 1 ? vertex_class(i, gid, vo, gsmall, cs, iter) : 0);
+    key[i] = b < 0 ? kBuckets * P : b * P + (P > 1 ? vertex_class(i, gid, vo, gcat, cs, iter) : 0);
   }
 }
 
 // The same keys for the vertices of a subset (key[j] for vertex sub[j]).
 __global__ void lm_keys_sub_k(const int64_t* __restrict__ off, const int32_t* __restrict__ sub, int64_t m, int P,
                               int32_t* key, const int32_t* __restrict__ gid, const int64_t* __restrict__ vo,
-                              const int32_t* __restrict__ gsmall, ClassSpec cs, const int* __restrict__ d_iter,
+                              const int32_t* __restrict__ gcat, ClassSpec cs, const int* __restrict__ d_iter,
                               LMThresholds th) {
   const int iter = *d_iter;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
     const int32_t i = sub[j];
     int b = lm_bucket_of(off[i + 1] - off[i], th);
-    key[j] = b < 0 ? kBuckets * P : b * P + (P > 1 ? vertex_class(i, gid, vo, gsmall, cs, iter) : 0);
+    key[j] = b < 0 ? kBuckets * P : b * P + (P > 1 ? vertex_class(i, gid, vo, gcat, cs, iter) : 0);
   }
 }
 
@@ -273,10 +273,10 @@ static unsigned grid1d(int64_t n, int per = kT) {
 }
 
 void lm_keys(const int64_t* off, int64_t n, int P, int32_t* key, const int32_t* gid, const int64_t* vo,
-             const int32_t* gsmall, ClassSpec cs, const int* d_iter, LMThresholds th, const int32_t* active,
+             const int32_t* gcat, ClassSpec cs, const int* d_iter, LMThresholds th, const int32_t* active,
              const int32_t* g_on, cudaStream_t s) {
   if (n > 0)
-    (count_launch(), lm_keys_k<<<grid1d(n), kT, 0, s>>>(off, n, P, key, gid, vo, gsmall, cs, d_iter, th, active, g_on));
+    (count_launch(), lm_keys_k<<<grid1d(n), kT, 0, s>>>(off, n, P, key, gid, vo, gcat, cs, d_iter, th, active, g_on));
 }
 
 __global__ void hub_sizes_k(const int64_t* off, const int32_t* hubs, int64_t nhubs, int64_t* cap, int64_t* chunks,
@@ -400,10 +400,10 @@ void pass_init(int64_t n, const long long* K, int32_t* memb, long long* sig, int
 // the entries whose ends share a part, in order (a stable compaction).
 
 void lm_keys_sub(const int64_t* off, const int32_t* sub, int64_t m, int P, int32_t* key, const int32_t* gid,
-                 const int64_t* vo, const int32_t* gsmall, ClassSpec cs, const int* d_iter, LMThresholds th,
+                 const int64_t* vo, const int32_t* gcat, ClassSpec cs, const int* d_iter, LMThresholds th,
                  cudaStream_t s) {
   if (m > 0)
-    (count_launch(), lm_keys_sub_k<<<grid1d(m), kT, 0, s>>>(off, sub, m, P, key, gid, vo, gsmall, cs, d_iter, th));
+    (count_launch(), lm_keys_sub_k<<<grid1d(m), kT, 0, s>>>(off, sub, m, P, key, gid, vo, gcat, cs, d_iter, th));
 }
 void gather_ids(const int32_t* idx, const int32_t* sub, int64_t m, int32_t* out, cudaStream_t s) {
   if (m > 0) (count_launch(), gather_ids_k<<<grid1d(m), kT, 0, s>>>(idx, sub, m, out));
@@ -1352,6 +1352,16 @@ void graph_ids(const int64_t* vo, int G, int64_t n, int32_t* gid, const int64_t*
   if (G <= 0 || n <= 0) return;
   (count_launch(), graph_ids_k<<<G < 65535 ? G : 65535, 256, 0, s>>>(vo, G, n, gid));
   (count_launch(), graph_check_k<<<(unsigned)((n + kT - 1) / kT), kT, 0, s>>>(off, col, gid, n, flags));
+}
+
+// Entries of every graph of a batch: off[vo[q + 1]] - off[vo[q]].
+__global__ void graph_entries_k(const int64_t* __restrict__ off, const int64_t* __restrict__ vo, int64_t G,
+                                int64_t* __restrict__ out) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < G) out[q] = off[vo[q + 1]] - off[vo[q]];
+}
+void graph_entries(const int64_t* off, const int64_t* vo, int64_t G, int64_t* out, cudaStream_t s) {
+  if (G > 0) (count_launch(), graph_entries_k<<<(unsigned)((G + kT - 1) / kT), kT, 0, s>>>(off, vo, G, out));
 }
 
 // -------------------------------------------------------------- validation
