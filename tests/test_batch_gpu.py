@@ -75,6 +75,22 @@ def test_async_batch_quality_per_graph():
         assert (num, M) == (nums[g], Ms[g]), g
 
 
+def test_async_batch_of_large_graphs_quality_per_graph():
+    """A batch holding graphs of every class-schedule category: a large sparse
+    road grid (fewer than 8 entries per vertex), a large dense R-MAT and small
+    SBMs; each graph keeps its own schedule and ends within 0.01 of the oracle."""
+    gs = [gg.sbm(5, 900, 6, 0.2, 0.01, wmin=1, wmax=5),
+          gg.grid_road(79, 320, 0.1, 0.001, wmin=1, wmax=100),   # 102,400 vertices, ~3.6 entries each
+          gg.rmat(80, 17, 8, wmin=1, wmax=8),                     # 131,072 vertices, hubs
+          gg.sbm(6, 2500, 12, 0.1, 0.005, wmin=1, wmax=5)]
+    membs, q, nums, Ms, iters = run_batch(gs, mode=1, prune=1)
+    for g, graph in enumerate(gs):
+        ref = oracle.louvain(graph.off, graph.col, graph.w, mode=oracle.ASYNC, prune=1)
+        assert q[g] >= ref.Q - 0.01, (g, q[g], ref.Q)
+        _, num, M = oracle.modularity(graph.off, graph.col, graph.w, membs[g])
+        assert (num, M) == (nums[g], Ms[g]), g
+
+
 def test_batch_rejects_entries_between_graphs():
     from paper_2301_12390_gb300 import LouvainError
     a, b = gg.sbm(1, 50, 2, 0.3, 0.05), gg.sbm(2, 60, 2, 0.3, 0.05)

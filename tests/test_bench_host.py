@@ -1,0 +1,31 @@
+"""Host-side choices of bench.py (no GPU): the bounded CPU-baseline sample."""
+import sys
+import os
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+import graphgen as gg  # noqa: E402
+import oracle  # noqa: E402
+
+
+class _Sized:
+    def __init__(self, nnz):
+        self.nnz = nnz
+
+
+def test_oracle_sample_is_bounded():
+    # small graphs: a full run; large ones: pass 0, iterations capped so that
+    # the scanned entries stay within the sample's budget
+    assert bench.oracle_sample_plan(_Sized(137_000))[:2] == (10, 20)
+    for nnz in (60_000_000, 128_307_544, 900_000_000, 5_000_000_000):
+        passes, iters, what = bench.oracle_sample_plan(_Sized(nnz))
+        assert passes == 1 and 1 <= iters <= 20 and "pass 0" in what
+        assert iters == 1 or iters * nnz <= bench.ORACLE_SAMPLE_ENTRIES
+
+
+def test_oracle_sample_counts_scanned_entries():
+    # prune off: every iteration of a pass scans every entry of that pass's graph
+    g = gg.sbm(7, 400, 4, 0.2, 0.01)
+    e, dt, q = bench.run_oracle_sample(g, oracle.SYNC, max_passes=1, max_iterations=3)
+    r = oracle.louvain(g.off, g.col, g.w, mode=oracle.SYNC, prune=0, max_passes=1, max_iterations=3)
+    assert e == g.nnz * r.passes[0].iterations and dt >= 0 and q == r.Q
