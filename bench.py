@@ -45,6 +45,12 @@ WORKLOADS = {
 }
 METRIC = "edges/sec in local-moving"
 L2_BYTES = 126 << 20   # GB300 L2 (about 126 MB)
+# DRAM bytes the local-moving phase moves per algorithmic byte, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of every local-moving
+# launch of an asynchronous R-MAT s22 run with L2 kept between launches:
+# 13.85 GB for 8.86 GB of algorithmic bytes.  Taken on the current kernels;
+# None where no capture was taken.
+LM_TRAFFIC_PER_BYTE = {("rmat22", "async"): 1.56}
 UNIT = "edges/s"
 
 
@@ -378,7 +384,12 @@ def bench_ours(args):
                              "inputs larger than L2 (col+w %.0f MB)" % ((g.col.nbytes + g.w.nbytes) / 1e6),
                        "modularity": qs[-1]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                         "traffic": None, "kernel": "local-moving phase (all its kernels, CUDA events)",
+                         "traffic": (LM_TRAFFIC_PER_BYTE[(args.workload, args.mode)] * lm_bytes / args.steps
+                                     if (args.workload, args.mode) in LM_TRAFFIC_PER_BYTE else None),
+                         "traffic_unit": "bytes per step (local-moving phase)",
+                         "traffic_source": "ncu DRAM bytes of every local-moving launch of one run, L2 kept between "
+                                           "launches, scaled to this step by its algorithmic bytes",
+                         "kernel": "local-moving phase (all its kernels, CUDA events)",
                          "peak_source": peak_src},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
