@@ -174,7 +174,7 @@ def sum_over_ranks(pg, x: float, device) -> float:
 # that, else pass 0 with its iterations capped.  Runs shorter than
 # ORACLE_SAMPLE_MIN_S repeat until that much time is measured.
 ORACLE_SAMPLE_ENTRIES = 1.0e9
-ORACLE_SAMPLE_MIN_S = 5.0
+ORACLE_SAMPLE_MIN_S = 10.0
 
 
 def oracle_sample_plan(g):
