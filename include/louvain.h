@@ -97,8 +97,10 @@ typedef struct {
                                  a batch gets the schedule it gets alone. */
   int32_t bucket_streams;     /* asynchronous mode: 1 (default) = every degree bucket (thread, warp,
                                  block and hub kernels) runs the iteration's classes in order on its
-                                 own stream, without waiting for the other buckets' previous class;
-                                 0 = a class starts when every bucket has finished the previous one.
+                                 own stream, without waiting for the other buckets' previous class
+                                 (the streams' priorities rise with the bucket's degree range, so the
+                                 blocks of high-degree vertices are scheduled first); 0 = a class
+                                 starts when every bucket has finished the previous one.
                                  Synchronous classes always wait (Jacobi per class). */
   int32_t reserved_i[2];
   double reserved_d[4];
