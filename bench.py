@@ -245,6 +245,9 @@ def bench_reference(args):
     import oracle
     if args.workload in ("batched", "serving"):
         return bench_reference_graphs(args)
+    if args.workload == "tolerance":
+        print(json.dumps({"impl": "reference", "unavailable": "the tolerance sweep has no reference arm"}), flush=True)
+        return
     g = WORKLOADS[args.workload][0]()
     mode = oracle.ASYNC if args.mode == "async" else oracle.SYNC
     for _ in range(args.warmup):
@@ -619,13 +622,58 @@ def bench_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_tolerance(args):
+    """The paper's sweep of the initial tolerance and its decline factor
+    (Section 3.1: tolerances 1 to 1e-12 in factors of 10, decline factors 10 to
+    1e4) re-run on the synthetic single graphs: for every (graph, tolerance,
+    decline) the median device time per run, Q, passes and iterations over a
+    few runs, the graph resident in HBM.  One JSON line; `value` is R-MAT s22's
+    time per run at the default schedule (0.01, 10)."""
+    import torch
+    from paper_2301_12390_gb300 import Louvain, SYNC, ASYNC
+    torch.cuda.set_device(0)
+    mode = ASYNC if args.mode == "async" else SYNC
+    tols = [1.0, 1e-1, 1e-2, 1e-3, 1e-4, 1e-6, 1e-9, 1e-12]
+    declines = [1.0, 10.0, 100.0, 1e3, 1e4]
+    runs = max(3, min(args.steps, 5))
+    table = []
+    for wl in ("sbm8192", "rmat22", "road4096"):
+        g = WORKLOADS[wl][0]()
+        with Louvain(device=0, mode=mode, prune=1, validate=0) as lv:
+            lv.load_csr(g.off, g.col, g.w)
+            for _ in range(args.warmup):
+                lv.run()
+            for tol in tols:
+                for dec in declines:
+                    lv.set_options(tolerance=tol, tolerance_decline=dec)
+                    ms, qs, ps, its = [], [], [], []
+                    for _ in range(runs):
+                        lv.run()
+                        st = lv.stats()
+                        ms.append(st.total_ms)
+                        qs.append(st.q)
+                        ps.append(st.passes)
+                        its.append(st.iterations)
+                    table.append({"workload": wl, "tolerance": tol, "decline": dec,
+                                  "ms_per_run": float(np.median(ms)), "q": float(np.median(qs)),
+                                  "passes": int(np.median(ps)), "iterations": int(np.median(its))})
+    default = [r for r in table if r["workload"] == "rmat22" and r["tolerance"] == 1e-2 and r["decline"] == 10.0][0]
+    line = {"metric": "time per run and Q by initial tolerance and decline factor", "value": default["ms_per_run"],
+            "unit": "ms", "n_gpus": 1, "steps": runs, "warmup": args.warmup, "ms_per_step": default["ms_per_run"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "tolerance", "mode": args.mode, "graphs": ["sbm8192", "rmat22", "road4096"],
+                       "tolerances": tols, "declines": declines, "prune": 1},
+            "table": table}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS) + ["batched", "serving"])
+    ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS) + ["batched", "serving", "tolerance"])
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--requests", type=int, default=1000)
     ap.add_argument("--pool", type=int, default=64)
@@ -646,6 +694,8 @@ def main():
         bench_batched(args)
     elif args.workload == "serving":
         bench_serving(args)
+    elif args.workload == "tolerance":
+        bench_tolerance(args)
     else:
         bench_ours(args)
 
