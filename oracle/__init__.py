@@ -43,13 +43,13 @@ class Options(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("tolerance", ctypes.c_double), ("tolerance_decline", ctypes.c_double),
                 ("pass_tolerance", ctypes.c_double), ("max_iterations", ctypes.c_int),
                 ("max_passes", ctypes.c_int), ("prune", ctypes.c_int), ("singleton_guard", ctypes.c_int),
-                ("subrounds", ctypes.c_int)]
+                ("subrounds", ctypes.c_int), ("colour_classes", ctypes.c_int)]
 
     @classmethod
     def make(cls, mode=SYNC, tolerance=0.01, tolerance_decline=10.0, pass_tolerance=0.0, max_iterations=20,
-             max_passes=10, prune=0, singleton_guard=1, subrounds=1):
+             max_passes=10, prune=0, singleton_guard=1, subrounds=1, colour_classes=0):
         return cls(mode, tolerance, tolerance_decline, pass_tolerance, max_iterations, max_passes, prune,
-                   singleton_guard, subrounds)
+                   singleton_guard, subrounds, colour_classes)
 
 
 def _load():
@@ -77,6 +77,8 @@ def _load():
         lib.or_aggregate.restype = i32
         lib.or_brute_best.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp]
         lib.or_brute_best.restype = i32
+        lib.or_colour_classes.argtypes = [i64, vp, vp, i32, vp]
+        lib.or_colour_classes.restype = i32
         _lib = lib
     return _lib
 
@@ -117,17 +119,19 @@ class Result:
 
 def louvain(off, col, w, mode=SYNC, tolerance=0.01, tolerance_decline=10.0, pass_tolerance=0.0,
             max_iterations=20, max_passes=10, prune=0, singleton_guard=1, subrounds=1,
-            record_levels=False, initial=None) -> Result:
+            record_levels=False, initial=None, colour_classes=0) -> Result:
     """Run the oracle Louvain; exact integers for every recorded quantity.
 
-    singleton_guard and subrounds apply to the synchronous mode only.
+    singleton_guard, subrounds and colour_classes apply to the synchronous
+    mode only (colour_classes: the classes are colour_classes() of every pass
+    graph instead of i mod subrounds).
     initial: a membership of the input (values in [0, n)) that pass 0 starts
     from instead of singletons (an incremental re-run)."""
     lib = _load()
     off, col, w = _arrs(off, col, w)
     n = len(off) - 1
     opt = Options.make(mode, tolerance, tolerance_decline, pass_tolerance, max_iterations, max_passes, prune,
-                       singleton_guard, subrounds)
+                       singleton_guard, subrounds, int(colour_classes))
     init = None
     if initial is not None:
         init = np.ascontiguousarray(initial, dtype=np.int32)
@@ -167,6 +171,20 @@ def louvain(off, col, w, mode=SYNC, tolerance=0.01, tolerance_decline=10.0, pass
         return res
     finally:
         lib.or_free(h)
+
+
+def colour_classes(off, col, pass_index=0):
+    """(classes, count): the capped greedy colouring of a graph that the
+    colour-class mode uses in pass `pass_index` (see or_colour_classes)."""
+    lib = _load()
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    n = len(off) - 1
+    cls = np.empty(max(n, 1), np.int32)
+    k = lib.or_colour_classes(n, off.ctypes.data, col.ctypes.data, int(pass_index), cls.ctypes.data)
+    if k < 0:
+        raise ValueError("oracle: bad graph")
+    return cls[:n], int(k)
 
 
 def modularity(off, col, w, memb):

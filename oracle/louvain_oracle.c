@@ -62,7 +62,12 @@
  *   - singleton guard (synchronous only): a vertex alone in its community
  *     does not move to another single-vertex community with a higher id
  *     (the minimum-label rule of Grappolo, which the paper cites): without
- *     it, Jacobi updates swap pairs of singletons forever.
+ *     it, Jacobi updates swap pairs of singletons forever;
+ *   - colour classes (synchronous, optional): the classes are a greedy
+ *     colouring of the pass graph instead of i mod P, so that no two
+ *     neighbours decide in the same class (Section 2's coarse-grained form,
+ *     a set of vertices processed in parallel, as in the Grappolo heuristics
+ *     it cites); see colour_classes().
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -77,6 +82,7 @@ typedef struct {
   int max_iterations, max_passes, prune;
   int singleton_guard; /* synchronous only: see decide() */
   int subrounds;       /* synchronous only: vertex classes i mod P run in sequence */
+  int colour_classes;  /* synchronous only: vertex classes from colour_classes() instead of i mod P */
 } or_options;
 
 /* ------------------------------------------------------------ helpers */
@@ -187,6 +193,68 @@ int64_t or_vertex_gains(int64_t n, const int64_t *off, const int32_t *col, const
   }
   free(K); free(sig); free(acc);
   return cnt;
+}
+
+/* ------------------------------------------------------ colour classes */
+
+/* The lowbias32 integer hash (C. Wellons, "Prospecting for hash functions"). */
+static uint32_t lowbias32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+
+typedef struct {
+  uint32_t h;
+  int32_t v;
+} pri_item;
+
+/* descending hash, then ascending id */
+static int pri_cmp(const void *a, const void *b) {
+  const pri_item *x = (const pri_item *)a, *y = (const pri_item *)b;
+  if (x->h != y->h) return x->h > y->h ? -1 : 1;
+  return (x->v > y->v) - (x->v < y->v);
+}
+
+/* Vertex classes of pass `pass` on an n-vertex graph: a greedy colouring
+ * capped at 64 classes.  Vertex v's priority is lowbias32(v XOR s) with
+ * s = 0x9E3779B9 * (pass + 1) (mod 2^32); the vertices take their class one
+ * at a time in descending priority (ties: lower id first), each the smallest
+ * class in 0..62 that none of its already-classed neighbours holds, else 63.
+ * Classes below 63 hold no two neighbours.  Returns the number of classes
+ * (largest class + 1; 1 for an empty graph). */
+static int colour_classes(int64_t n, const int64_t *off, const int32_t *col, int pass, int32_t *cls) {
+  const uint32_t salt = 0x9E3779B9u * (uint32_t)(pass + 1);
+  pri_item *order = (pri_item *)malloc((size_t)(n ? n : 1) * sizeof(pri_item));
+  for (int64_t v = 0; v < n; ++v) {
+    order[v].h = lowbias32((uint32_t)v ^ salt);
+    order[v].v = (int32_t)v;
+    cls[v] = -1;
+  }
+  qsort(order, (size_t)n, sizeof(pri_item), pri_cmp);
+  int top = 0;
+  for (int64_t t = 0; t < n; ++t) {
+    const int32_t v = order[t].v;
+    uint64_t used = 0;
+    for (int64_t e = off[v]; e < off[v + 1]; ++e) {
+      const int32_t u = col[e];
+      if (u != v && cls[u] >= 0) used |= (uint64_t)1 << cls[u];
+    }
+    int c = 0;
+    while (c < 63 && ((used >> c) & 1)) ++c;
+    cls[v] = c;
+    if (c > top) top = c;
+  }
+  free(order);
+  return top + 1;
+}
+
+int or_colour_classes(int64_t n, const int64_t *off, const int32_t *col, int pass, int32_t *cls) {
+  if (n < 0 || !off || !cls) return -1;
+  return colour_classes(n, off, col, pass, cls);
 }
 
 /* ------------------------------------------------------- result record */
@@ -372,6 +440,11 @@ or_result *or_louvain_from(int64_t n, const int64_t *off, const int32_t *col, co
     int64_t pass_moves = 0;
     int iters = 0;
     int P = opt->subrounds > 1 ? opt->subrounds : 1;
+    int32_t *cls = NULL;   /* colour classes of this pass */
+    if (opt->mode == 0 && opt->colour_classes) {
+      cls = (int32_t *)malloc((size_t)(np ? np : 1) * 4);
+      P = colour_classes(np, g.off, g.col, p, cls);
+    }
     /* local-moving phase (a2-a5) */
     for (int it = 0; it < opt->max_iterations; ++it) {
       i128 S = 0;
@@ -382,8 +455,8 @@ or_result *or_louvain_from(int64_t n, const int64_t *off, const int32_t *col, co
            the previous classes; the class's moves are applied together */
         for (int ch = 0; ch < P; ++ch) {
           int64_t nm = 0;
-          for (int64_t i = ch; i < np; i += P) {
-            if (!active[i]) continue;
+          for (int64_t i = cls ? 0 : ch; i < np; i += cls ? 1 : P) {
+            if (!active[i] || (cls && cls[i] != ch)) continue;
             i128 gain;
             int32_t c = decide(&s, i, g.off, g.col, g.w, memb, K, sig, size, opt->singleton_guard, M, &gain);
             if (c >= 0) { mv_i[nm] = (int32_t)i; mv_c[nm] = c; ++nm; S += gain; }
@@ -429,7 +502,7 @@ or_result *or_louvain_from(int64_t n, const int64_t *off, const int32_t *col, co
     r->pass_iters[p] = iters;
     r->pass_Nbefore[p] = Nbefore;
     r->npasses = p + 1;
-    free(s.acc); free(s.seen); free(mv_i); free(mv_c); free(active); free(moved); free(size);
+    free(s.acc); free(s.seen); free(mv_i); free(mv_c); free(active); free(moved); free(size); free(cls);
     if (pass_moves == 0 && !warm) {
       r->pass_Nafter[p] = Nbefore;
       r->pass_k[p] = np;

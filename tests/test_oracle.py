@@ -402,3 +402,86 @@ def test_warm_start_rejects_out_of_range_memberships():
     for bad in ([0, 1, 2, 3, 4, 6], [-1, 0, 0, 0, 0, 0]):
         with pytest.raises(ValueError):
             run(g, initial=np.array(bad, np.int32))
+
+
+# ------------------------------------------------ colour classes (option f1)
+
+def _check_greedy_classes(g, cls, k):
+    """Pins of a capped greedy colouring that do not depend on the priority
+    order: classes below 63 hold no two neighbours; a vertex in class c < 63
+    has a neighbour in every class below c (it took the smallest free one);
+    one in class 63 has neighbours in all of 0..62; the count is max + 1."""
+    assert k == (int(cls.max()) + 1 if g.n else 1)
+    assert cls.min(initial=0) >= 0 and cls.max(initial=0) <= 63
+    for v in range(g.n):
+        nb = {int(cls[u]) for u in g.col[g.off[v]:g.off[v + 1]] if u != v}
+        c = int(cls[v])
+        if c < 63:
+            assert c not in nb, (v, c)
+            assert set(range(c)) <= nb, (v, c)
+        else:
+            assert set(range(63)) <= nb, v
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_colour_classes_are_a_greedy_colouring(seed):
+    rng = random.Random(seed)
+    g = random_graph(rng, 60, 0.15 + 0.1 * seed)
+    for p in range(3):
+        cls, k = oracle.colour_classes(g.off, g.col, p)
+        _check_greedy_classes(g, cls, k)
+    big = gg.rmat(seed, 11, 8, wmin=1, wmax=4)
+    cls, k = oracle.colour_classes(big.off, big.col, 0)
+    _check_greedy_classes(big, cls, k)
+
+
+def test_colour_classes_special_cases():
+    # a clique of 70: classes 0..62 once each, the last 7 vertices share 63
+    c70 = cliques(1, 70)
+    cls, k = oracle.colour_classes(c70.off, c70.col, 0)
+    assert k == 64 and sorted(cls.tolist()) == list(range(63)) + [63] * 7
+    # a star takes two classes, whichever vertex comes first; isolated vertices take 0
+    star = gg.from_weighted_edges(9, [(0, v, 1) for v in range(1, 8)])
+    cls, k = oracle.colour_classes(star.off, star.col, 0)
+    assert k == 2 and cls[8] == 0 and all(cls[v] != cls[0] for v in range(1, 8))
+    empty = gg.from_weighted_edges(0, [])
+    assert oracle.colour_classes(empty.off, empty.col, 0)[1] == 1
+    # deterministic, and drawn anew for every pass
+    g = gg.sbm(3, 500, 5, 0.1, 0.01)
+    a0, _ = oracle.colour_classes(g.off, g.col, 0)
+    assert np.array_equal(a0, oracle.colour_classes(g.off, g.col, 0)[0])
+    assert not np.array_equal(a0, oracle.colour_classes(g.off, g.col, 1)[0])
+
+
+def test_colour_class_runs_reach_closed_forms_and_exact_q():
+    for k, s in [(3, 4), (5, 6), (8, 3)]:
+        r = run(cliques(k, s), mode=oracle.SYNC, colour_classes=1)
+        assert Fraction(r.q_num, r.M * r.M) == 1 - Fraction(1, k)
+    g = gg.sbm(11, 600, 12, 0.15, 0.01, wmin=1, wmax=9)
+    for prune in (0, 1):
+        r = run(g, mode=oracle.SYNC, colour_classes=1, prune=prune)
+        _, num, _ = oracle.modularity(g.off, g.col, g.w, r.top)
+        assert num == r.q_num and r.Q > 0.3
+
+
+def test_colour_classes_on_a_clique_are_the_sequential_order():
+    """On a clique every vertex has a class of its own, so the colour-class
+    run (Jacobi per class, no guard) is the sequential run in class order:
+    the oracle's asynchronous run on the vertices renumbered by class."""
+    rng = random.Random(5)
+    n = 40
+    # weights from a wide range: no two candidate gains tie, so the lowest-id
+    # tie rule (which the renumbering would change) never decides
+    edges = [(u, v, rng.randint(1, 1_000_000)) for u in range(n) for v in range(u + 1, n)]
+    g = gg.from_weighted_edges(n, edges)
+    cls, k = oracle.colour_classes(g.off, g.col, 0)
+    assert k == n and sorted(cls.tolist()) == list(range(n))
+    # renumber: new id = class
+    edges2 = [(int(cls[u]), int(cls[v]), w) for (u, v, w) in edges]
+    g2 = gg.from_weighted_edges(n, edges2)
+    a = run(g, mode=oracle.SYNC, colour_classes=1, singleton_guard=0, max_passes=1)
+    b = run(g2, mode=oracle.ASYNC, max_passes=1)
+    assert a.q_num == b.q_num
+    assert a.iterations == b.iterations                  # every iteration's moves and gain sum
+    pairs = {(int(a.top[v]), int(b.top[cls[v]])) for v in range(n)}
+    assert len(pairs) == len({x for x, _ in pairs}) == len({y for _, y in pairs})   # the same partition
