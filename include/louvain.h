@@ -102,7 +102,16 @@ typedef struct {
                                  blocks of high-degree vertices are scheduled first); 0 = a class
                                  starts when every bucket has finished the previous one.
                                  Synchronous classes always wait (Jacobi per class). */
-  int32_t reserved_i[2];
+  int32_t colour_classes;     /* 1: the classes of every pass are a greedy colouring of the pass graph
+                                 instead of subrounds / reclass (Section 2's coarse-grained form: a set
+                                 of vertices processed in parallel, as in the Grappolo heuristics the
+                                 paper cites; here no two neighbours share a class).  Vertex priority
+                                 lowbias32(local id XOR 0x9E3779B9 * (pass + 1)), higher first, ties to
+                                 the lower id; in priority order each vertex takes the smallest class in
+                                 0..62 that no preceding neighbour holds, else 63.  The pass has (largest
+                                 class + 1) classes.  Synchronous: deterministic, equal to the oracle's
+                                 colour-class mode.  0 (default): subrounds / reclass */
+  int32_t reserved_i[1];
   double reserved_d[4];
 } louvain_options;
 

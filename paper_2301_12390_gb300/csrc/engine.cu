@@ -273,6 +273,7 @@ int check_options(const louvain_options* o) {
   if (o->subrounds < 0 || o->subrounds > 64) return 1;
   if (o->reclass < 0 || o->reclass > 3) return 1;
   if (o->bucket_streams < 0 || o->bucket_streams > 1) return 1;
+  if (o->colour_classes < 0 || o->colour_classes > 1) return 1;
   return 0;
 }
 
@@ -294,10 +295,66 @@ struct PassState {
 };
 
 
+// Colour classes of the pass graph (option colour_classes) into c->members,
+// the aggregation's member list, which is free until the pass aggregates;
+// c->inv (predecessor counts) and c->mdeg / c->fill (the two frontiers) are
+// free too.  Rounds run kColourRoundsPerCheck at a time between host checks
+// of the frontier (a round with an empty frontier does nothing).  *ncls =
+// the number of classes (largest class + 1).
+constexpr int kColourRoundsPerCheck = 8;
+int colour_pass(louvain_ctx* c, const PassState& g, int pass, int* ncls) {
+  cudaStream_t s = c->stream;
+  const bool multi = c->G > 1;
+  const int32_t* gid = multi ? c->gid : nullptr;
+  const int64_t* vo = multi ? c->vo : nullptr;
+  const uint32_t salt = 0x9E3779B9u * (uint32_t)(pass + 1);
+  int32_t* cls = c->members;
+  int32_t* cnt = c->inv;
+  int32_t* front[2] = {(int32_t*)c->mdeg, (int32_t*)c->fill};
+  unsigned long long* sz = (unsigned long long*)(c->scal + 4);   // [0], [1]: frontier sizes; [2]: coloured
+  int* cmax = (int*)(c->scal + 7);
+  CK(cudaMemsetAsync(sz, 0, 3 * sizeof(unsigned long long), s));
+  CK(cudaMemsetAsync(c->flags, 0, sizeof(int), s));
+  colour_init(g.off, g.col, g.n, gid, vo, salt, cnt, cls, front[0], sz, s);
+  int64_t r = 0;
+  for (;;) {
+    for (int k = 0; k < kColourRoundsPerCheck; ++k, ++r) {
+      const int a = (int)(r & 1), b = a ^ 1;
+      CK(cudaMemsetAsync(sz + b, 0, sizeof(unsigned long long), s));
+      colour_round(g.off, g.col, g.n, gid, vo, salt, front[a], sz + a, cnt, cls, front[b], sz + b, sz + 2, c->flags,
+                   s);
+    }
+    CKLAUNCH();
+    unsigned long long left = 0;
+    if (int e = fetch(c, &left, sz + (r & 1), sizeof(left))) return e;
+    if (left == 0) break;
+    if (r > g.n + kColourRoundsPerCheck) return fail(c, LOUVAIN_ERR_INTERNAL, "colouring did not end");
+  }
+  unsigned long long coloured = 0;
+  int flags = 0;
+  if (int e = fetch(c, &coloured, sz + 2, sizeof(coloured))) return e;
+  if (int e = fetch(c, &flags, c->flags, sizeof(flags))) return e;
+  if ((int64_t)coloured != g.n || (flags & 2))
+    return fail(c, LOUVAIN_ERR_INTERNAL, "colouring left a vertex without a class (asymmetric CSR?)");
+  CK(cudaMemsetAsync(cmax, 0, sizeof(int), s));
+  class_max(cls, g.n, cmax, s);
+  CKLAUNCH();
+  int m = 0;
+  if (int e = fetch(c, &m, cmax, sizeof(m))) return e;
+  *ncls = m + 1;
+  return 0;
+}
+
 template <typename W>
 int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool wide, int* iters_out,
                  int64_t* edges_out, int64_t* visited_out) {
   const bool async = c->opt.mode == LOUVAIN_ASYNC;
+  // Colour classes (option): the classes are a greedy colouring of the pass
+  // graph, the same for every iteration of the pass.
+  const bool colour = c->opt.colour_classes != 0;
+  int ncls = 1;
+  if (colour)
+    if (int r = colour_pass(c, g, pass, &ncls)) return r;
   // Classes, per graph (its category, set at load): a graph below
   // kSmallGraph vertices takes kAsyncSubroundsSmall classes drawn once per
   // pass, a larger one kAsyncSubroundsLarge (or, sparse, kAsyncSubroundsSparse)
@@ -306,22 +363,26 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
   bool any_cat[3] = {false, false, false};
   for (int64_t q = 0; q < c->G; ++q) any_cat[c->hgcat[q]] = true;
   const bool any_small = any_cat[kCatSmall], any_big = any_cat[kCatLarge] || any_cat[kCatSparse];
-  ClassSpec cs{1, 1, 1, 0, 0, pass, c->G == 1 ? c->hgcat[0] : kCatLarge};
-  if (c->opt.subrounds > 0) {
+  ClassSpec cs{1, 1, 1, 0, 0, pass, c->G == 1 ? c->hgcat[0] : kCatLarge, nullptr};
+  if (colour) {
+    cs.Ps = cs.Pb = cs.Pl = ncls;
+    cs.colour = c->members;
+  } else if (c->opt.subrounds > 0) {
     cs.Ps = cs.Pb = cs.Pl = c->opt.subrounds;
   } else if (async) {
     cs.Ps = kAsyncSubroundsSmall;
     cs.Pb = kAsyncSubroundsLarge;
     cs.Pl = kAsyncSubroundsSparse;
   }
-  const int P = std::max({any_small ? cs.Ps : 1, any_cat[kCatLarge] ? cs.Pb : 1, any_cat[kCatSparse] ? cs.Pl : 1});
+  const int P = colour ? ncls
+                       : std::max({any_small ? cs.Ps : 1, any_cat[kCatLarge] ? cs.Pb : 1, any_cat[kCatSparse] ? cs.Pl : 1});
   const int nkeys = kBuckets * P + 1;
   const bool multi = c->G > 1;
   const int64_t G = c->G;
   cudaStream_t s = c->stream;
   // reclass: 1 = hashed classes drawn anew every iteration, 2 = once per pass
-  const int mode_s = (async && cs.Ps > 1) ? (c->opt.reclass == 3 ? 2 : c->opt.reclass) : 0;
-  const int mode_b = (async && (cs.Pb > 1 || cs.Pl > 1)) ? (c->opt.reclass == 3 ? 1 : c->opt.reclass) : 0;
+  const int mode_s = (!colour && async && cs.Ps > 1) ? (c->opt.reclass == 3 ? 2 : c->opt.reclass) : 0;
+  const int mode_b = (!colour && async && (cs.Pb > 1 || cs.Pl > 1)) ? (c->opt.reclass == 3 ? 1 : c->opt.reclass) : 0;
   const bool reclass = (any_small && mode_s == 1) || (any_big && mode_b == 1);   // every iteration
   cs.mode_s = mode_s;
   cs.mode_b = mode_b;

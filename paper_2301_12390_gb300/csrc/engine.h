@@ -53,6 +53,7 @@ struct ClassSpec {
   int32_t mode_s, mode_b;
   int32_t pass;
   int32_t single_cat;
+  const int32_t* colour;   // colour classes of the pass graph's vertices, or null
 };
 // splitmix64 finaliser of (pass, iteration), folded to 32 bits, never 0.
 __host__ __device__ inline uint32_t class_salt(int pass, int iter) {
@@ -66,6 +67,7 @@ __host__ __device__ inline uint32_t class_salt(int pass, int iter) {
 // The class of vertex i in iteration iter (gid, vo, gcat null: one graph).
 __device__ __forceinline__ int vertex_class(int64_t i, const int32_t* gid, const int64_t* vo, const int32_t* gcat,
                                             const ClassSpec& cs, int iter) {
+  if (cs.colour) return cs.colour[i];
   int64_t local = i;
   int cat = cs.single_cat;
   if (gid) {
@@ -244,6 +246,14 @@ void graph_renumber(const int32_t* used, const int32_t* newid, const int32_t* gi
 void localize_membership(const int32_t* top, const int32_t* gid0, const int64_t* vo, int64_t n0, int32_t* out,
                          cudaStream_t s);
 void graph_entries(const int64_t* off, const int64_t* vo, int64_t G, int64_t* out, cudaStream_t s);
+// Colour classes: capped greedy colouring of a pass graph (graph_ops.cu).
+void colour_init(const int64_t* off, const int32_t* col, int64_t n, const int32_t* gid, const int64_t* vo,
+                 uint32_t salt, int32_t* cnt, int32_t* cls, int32_t* front, unsigned long long* nfront,
+                 cudaStream_t s);
+void colour_round(const int64_t* off, const int32_t* col, int64_t n, const int32_t* gid, const int64_t* vo,
+                  uint32_t salt, const int32_t* front, const unsigned long long* nfront, int32_t* cnt, int32_t* cls,
+                  int32_t* next, unsigned long long* nnext, unsigned long long* total, int* flags, cudaStream_t s);
+void class_max(const int32_t* cls, int64_t n, int* out, cudaStream_t s);
 void graph_ids(const int64_t* vo, int G, int64_t n, int32_t* gid, const int64_t* off, const int32_t* col, int* flags,
                cudaStream_t s);
 

@@ -1364,6 +1364,124 @@ void graph_entries(const int64_t* off, const int64_t* vo, int64_t G, int64_t* ou
   if (G > 0) (count_launch(), graph_entries_k<<<(unsigned)((G + kT - 1) / kT), kT, 0, s>>>(off, vo, G, out));
 }
 
+// ------------------------------------------------------ colour classes
+//
+// A capped greedy colouring of the pass graph (the class schedule of the
+// colour_classes option): a vertex's priority is hash32(local id ^ salt)
+// (lowbias32), salt = 0x9E3779B9 * (pass + 1); a vertex precedes its
+// neighbour when its priority is higher (ties: the lower id).  In priority
+// order each vertex takes the smallest class in 0..62 that no preceding
+// neighbour holds, else 63 - computed in rounds: a vertex whose preceding
+// neighbours all have their class takes its own (Jones-Plassmann order), then
+// counts itself off its succeeding neighbours.  Every edge is read twice.
+// Edges never join two graphs of a batch, so global ids order ties as local
+// ones do.
+
+__device__ __forceinline__ uint32_t colour_pri(int64_t v, const int32_t* gid, const int64_t* vo, uint32_t salt) {
+  const int64_t local = gid ? v - vo[gid[v]] : v;
+  return hash32((uint32_t)local ^ salt);
+}
+
+// Warp per vertex: cnt[v] = its preceding neighbours; those with none start.
+__global__ void colour_init_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col, int64_t n,
+                              const int32_t* __restrict__ gid, const int64_t* __restrict__ vo, uint32_t salt,
+                              int32_t* __restrict__ cnt, int32_t* __restrict__ cls, int32_t* __restrict__ front,
+                              unsigned long long* __restrict__ nfront) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t ws = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = w0; v < n; v += ws) {   // uniform across the warp
+    const uint32_t pv = colour_pri(v, gid, vo, salt);
+    unsigned c = 0;
+    for (int64_t x = off[v] + lane; x < off[v + 1]; x += kWarp) {
+      const int32_t u = col[x];
+      if (u == v) continue;
+      const uint32_t pu = colour_pri(u, gid, vo, salt);
+      if (pu > pv || (pu == pv && u < v)) ++c;
+    }
+    c = __reduce_add_sync(0xffffffffu, c);
+    if (lane == 0) {
+      cnt[v] = (int32_t)c;
+      cls[v] = -1;
+      if (c == 0) front[atomicAdd(nfront, 1ull)] = (int32_t)v;
+    }
+  }
+}
+
+// Warp per frontier vertex: its class from its preceding neighbours' classes,
+// then one predecessor fewer for each succeeding neighbour; those left with
+// none form the next frontier.  A class outside 0..63 (a preceding neighbour
+// without one) sets flags bit 1 and is not used.
+__global__ void colour_round_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                               const int32_t* __restrict__ gid, const int64_t* __restrict__ vo, uint32_t salt,
+                               const int32_t* __restrict__ front, const unsigned long long* __restrict__ nfront,
+                               int32_t* __restrict__ cnt, int32_t* __restrict__ cls, int32_t* __restrict__ next,
+                               unsigned long long* __restrict__ nnext, unsigned long long* __restrict__ total,
+                               int* __restrict__ flags) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nf = (int64_t)*nfront;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *total += (unsigned long long)nf;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t ws = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = w0; t < nf; t += ws) {   // uniform across the warp
+    const int32_t v = front[t];
+    const uint32_t pv = colour_pri(v, gid, vo, salt);
+    unsigned long long used = 0;
+    bool bad = false;
+    for (int64_t x = off[v] + lane; x < off[v + 1]; x += kWarp) {
+      const int32_t u = col[x];
+      if (u == v) continue;
+      const uint32_t pu = colour_pri(u, gid, vo, salt);
+      if (pu > pv || (pu == pv && u < v)) {
+        const int32_t cu = cls[u];
+        if (cu >= 0 && cu < 64) used |= 1ull << cu;
+        else bad = true;
+      }
+    }
+    const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)used);
+    const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(used >> 32));
+    const unsigned long long free_cls = ~(((unsigned long long)hi << 32) | lo) & 0x7fffffffffffffffull;
+    if (lane == 0) cls[v] = free_cls ? __ffsll((long long)free_cls) - 1 : 63;
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flags, 2);
+    for (int64_t x = off[v] + lane; x < off[v + 1]; x += kWarp) {
+      const int32_t u = col[x];
+      if (u == v) continue;
+      const uint32_t pu = colour_pri(u, gid, vo, salt);
+      if (pv > pu || (pv == pu && v < u))
+        if (atomicSub(cnt + u, 1) == 1) next[atomicAdd(nnext, 1ull)] = u;
+    }
+  }
+}
+
+__global__ void class_max_k(const int32_t* __restrict__ cls, int64_t n, int* __restrict__ out) {
+  int m = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, cls[i]);
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+static unsigned warp_grid(int64_t items) {
+  const int64_t b = (items + 7) / 8;   // 8 warps per block of 256
+  return (unsigned)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
+}
+
+void colour_init(const int64_t* off, const int32_t* col, int64_t n, const int32_t* gid, const int64_t* vo,
+                 uint32_t salt, int32_t* cnt, int32_t* cls, int32_t* front, unsigned long long* nfront,
+                 cudaStream_t s) {
+  if (n > 0) (count_launch(), colour_init_k<<<warp_grid(n), 256, 0, s>>>(off, col, n, gid, vo, salt, cnt, cls, front,
+                                                                         nfront));
+}
+void colour_round(const int64_t* off, const int32_t* col, int64_t n, const int32_t* gid, const int64_t* vo,
+                  uint32_t salt, const int32_t* front, const unsigned long long* nfront, int32_t* cnt, int32_t* cls,
+                  int32_t* next, unsigned long long* nnext, unsigned long long* total, int* flags, cudaStream_t s) {
+  (count_launch(), colour_round_k<<<warp_grid(n), 256, 0, s>>>(off, col, gid, vo, salt, front, nfront, cnt, cls,
+                                                                next, nnext, total, flags));
+}
+void class_max(const int32_t* cls, int64_t n, int* out, cudaStream_t s) {
+  if (n > 0) (count_launch(), class_max_k<<<grid1d(n), kT, 0, s>>>(cls, n, out));
+}
+
 // -------------------------------------------------------------- validation
 
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {

@@ -39,7 +39,7 @@ class Options(ctypes.Structure):
                 ("max_passes", ctypes.c_int32), ("prune", ctypes.c_int32), ("singleton_guard", ctypes.c_int32),
                 ("subrounds", ctypes.c_int32), ("validate", ctypes.c_int32), ("record_levels", ctypes.c_int32),
                 ("cuda_graphs", ctypes.c_int32), ("reclass", ctypes.c_int32), ("bucket_streams", ctypes.c_int32),
-                ("reserved_i", ctypes.c_int32 * 2),
+                ("colour_classes", ctypes.c_int32), ("reserved_i", ctypes.c_int32 * 1),
                 ("reserved_d", ctypes.c_double * 4)]
 
 

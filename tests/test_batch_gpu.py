@@ -66,6 +66,18 @@ def test_sync_batch_equals_each_graph_alone(prune, subrounds):
         assert np.array_equal(membs[g], ref.top) and nums[g] == ref.q_num, g
 
 
+def test_sync_batch_with_colour_classes_equals_each_graph_alone():
+    """Colour classes are drawn from local ids, so a graph gets the same
+    classes, and the same synchronous result, alone and in a batch."""
+    membs, q, nums, Ms, iters = run_batch(GS, mode=0, prune=1, colour_classes=1)
+    for g, graph in enumerate(GS):
+        m1, q1, (num1, M1), it1 = run_alone(graph, mode=0, prune=1, colour_classes=1)
+        assert np.array_equal(membs[g], m1), g
+        assert (nums[g], Ms[g]) == (num1, M1) and iters[g] == it1, g
+        ref = oracle.louvain(graph.off, graph.col, graph.w, mode=oracle.SYNC, prune=1, colour_classes=1)
+        assert np.array_equal(membs[g], ref.top) and nums[g] == ref.q_num, g
+
+
 def test_async_batch_quality_per_graph():
     membs, q, nums, Ms, iters = run_batch(GS, mode=1, prune=1)
     for g, graph in enumerate(GS):

@@ -305,6 +305,24 @@ def test_async_quality(name, prune, subrounds):
     assert got["exact"] == (num, M)
 
 
+@pytest.mark.parametrize("name", ["sbm600", "rmat16", "road128", "sbm8192"])
+@pytest.mark.parametrize("prune", [0, 1])
+def test_sync_parity_colour_classes(name, prune):
+    """Colour classes (a greedy colouring of every pass graph) in synchronous
+    mode: bit-exact with the oracle's colour-class mode at every pass."""
+    assert_sync_parity(G[name], prune=prune, colour_classes=1)
+
+
+@pytest.mark.parametrize("name", ["rmat16", "road128"])
+def test_async_quality_colour_classes(name):
+    g = G[name]
+    got = engine_run(g, mode=1, prune=1, colour_classes=1)
+    ref = oracle.louvain(g.off, g.col, g.w, mode=oracle.ASYNC, prune=1)
+    assert got["q"] >= ref.Q - 0.01, (got["q"], ref.Q)
+    _, num, M = oracle.modularity(g.off, g.col, g.w, got["top"])
+    assert got["exact"] == (num, M)
+
+
 # ---------------------------------------------------------- edge cases
 
 @pytest.mark.parametrize("mode", [0, 1])
