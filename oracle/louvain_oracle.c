@@ -57,8 +57,8 @@
  *     community totals and community sizes as they were when the iteration
  *     began (Jacobi); with `subrounds` P > 1 the vertices are split into the
  *     classes i mod P, run one class after the other, each class Jacobi on
- *     the state left by the classes before it (the partially asynchronous
- *     ordering the paper points to as the likely best parallel form);
+ *     the state left by the classes before it (the coarse-grained form of
+ *     Section 2: a set of vertices processed in parallel);
  *   - singleton guard (synchronous only): a vertex alone in its community
  *     does not move to another single-vertex community with a higher id
  *     (the minimum-label rule of Grappolo, which the paper cites): without
