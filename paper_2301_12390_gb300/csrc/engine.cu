@@ -1279,6 +1279,7 @@ int louvain_default_options(louvain_options* o) {
   o->cuda_graphs = 0;
   o->reclass = 3;
   o->bucket_streams = 1;
+  o->colour_classes = 0;
   return 0;
 }
 
