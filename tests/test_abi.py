@@ -48,3 +48,33 @@ def test_default_options_are_the_papers(lib_path):
     o = default_options()
     assert (o.tolerance, o.tolerance_decline, o.pass_tolerance) == (0.01, 10.0, 0.0)
     assert (o.max_iterations, o.max_passes, o.mode) == (20, 10, 0)
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every ctypes structure of the binding has the header struct's size and
+    each field at the header's offset (a C program built against
+    include/louvain.h prints them)."""
+    import shutil
+    import subprocess
+    from paper_2301_12390_gb300 import louvain as L
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"louvain_options": L.Options, "louvain_stats": L.Stats, "louvain_pass_info": L.PassInfo,
+               "louvain_server_config": L.ServerConfig, "louvain_server_result": L.ServerResult}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "louvain.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for field in cls._fields_:
+            lines.append(f'  printf("{cname} {field[0]} %zu\\n", offsetof({cname}, {field[0]}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {(a, b): int(c) for a, b, c in (ln.split() for ln in out if ln)}
+    for cname, cls in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for field in cls._fields_:
+            assert got[(cname, field[0])] == getattr(cls, field[0]).offset, (cname, field[0])
