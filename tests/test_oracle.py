@@ -260,13 +260,13 @@ def test_louvain_ring_of_cliques_reaches_clique_partition(mode):
         assert Fraction(r.q_num, r.M * r.M) >= clique_q
 
 
-@pytest.mark.parametrize("mode", [oracle.SYNC, oracle.ASYNC])
+@pytest.mark.parametrize("mode,colour", [(oracle.SYNC, 0), (oracle.ASYNC, 0), (oracle.SYNC, 1)])
 @pytest.mark.parametrize("prune", [0, 1])
 @pytest.mark.parametrize("subrounds", [1, 4])
-def test_pass_invariants(mode, prune, subrounds):
+def test_pass_invariants(mode, colour, prune, subrounds):
     """Aggregation keeps M and Q; levels compose to the top membership; k shrinks."""
     g = gg.sbm(11, 600, 12, 0.15, 0.01, wmin=1, wmax=9)
-    r = run(g, mode=mode, prune=prune, subrounds=subrounds, record_levels=True)
+    r = run(g, mode=mode, prune=prune, subrounds=subrounds, record_levels=True, colour_classes=colour)
     assert r.Q > 0.3
     off, col, w = g.off, g.col, g.w.astype(np.int64)
     top = np.arange(g.n)
