@@ -230,32 +230,32 @@ def test_hand_worked_runs():
             assert [list(t) for t in r.iterations] == ex["iterations"], case["name"]
 
 
-@pytest.mark.parametrize("mode", [oracle.SYNC, oracle.ASYNC])
-def test_louvain_never_beats_brute_force_and_finds_clique_optimum(mode):
+@pytest.mark.parametrize("mode,colour", [(oracle.SYNC, 0), (oracle.ASYNC, 0), (oracle.SYNC, 1)])
+def test_louvain_never_beats_brute_force_and_finds_clique_optimum(mode, colour):
     rng = random.Random(6)
     for _ in range(25):
         n = rng.randint(2, 10)
         g = random_graph(rng, n, 0.4)
         if g.nnz == 0:
             continue
-        r = run(g, mode=mode)
+        r = run(g, mode=mode, colour_classes=colour)
         best, _, _ = oracle.brute_best(g.off, g.col, g.w)
         assert r.q_num <= best
         _, num, _ = oracle.modularity(g.off, g.col, g.w, r.top)
         assert num == r.q_num
     for k, s in [(2, 4), (3, 3), (5, 5)]:
         g = cliques(k, s)
-        r = run(g, mode=mode)
+        r = run(g, mode=mode, colour_classes=colour)
         assert Fraction(r.q_num, r.M * r.M) == 1 - Fraction(1, k)
         best, _, _ = oracle.brute_best(g.off, g.col, g.w) if k * s <= 10 else (r.q_num, None, None)
         assert r.q_num == best
 
 
-@pytest.mark.parametrize("mode", [oracle.SYNC, oracle.ASYNC])
-def test_louvain_ring_of_cliques_reaches_clique_partition(mode):
+@pytest.mark.parametrize("mode,colour", [(oracle.SYNC, 0), (oracle.ASYNC, 0), (oracle.SYNC, 1)])
+def test_louvain_ring_of_cliques_reaches_clique_partition(mode, colour):
     for k, s in [(6, 5), (12, 4)]:
         g = cliques(k, s, ring=True)
-        r = run(g, mode=mode)
+        r = run(g, mode=mode, colour_classes=colour)
         clique_q = Fraction(s * (s - 1), s * (s - 1) + 2) - Fraction(1, k)
         assert Fraction(r.q_num, r.M * r.M) >= clique_q
 
