@@ -29,3 +29,24 @@ def test_oracle_sample_counts_scanned_entries():
     e, dt, q = bench.run_oracle_sample(g, oracle.SYNC, max_passes=1, max_iterations=3)
     r = oracle.louvain(g.off, g.col, g.w, mode=oracle.SYNC, prune=0, max_passes=1, max_iterations=3)
     assert e == g.nnz * r.passes[0].iterations and dt >= 0 and q == r.Q
+
+
+def test_serving_pool_is_seeded_and_in_range():
+    a = bench.serving_pool(bench.SEED + 4, 6, 1000, 20000)
+    b = bench.serving_pool(bench.SEED + 4, 6, 1000, 20000)
+    assert len(a) == 6
+    for g, h in zip(a, b):
+        assert g.n == h.n and (g.off == h.off).all() and (g.col == h.col).all() and (g.w == h.w).all()
+        assert 1000 <= g.n <= 20000 and g.nnz > 0
+        assert g.w.min() >= 1 and g.w.max() <= 8
+        # symmetric: the multiset of (u, v, w) equals that of (v, u, w)
+        rows = (g.off[1:] - g.off[:-1])
+        u = gg_rows(rows)
+        fwd = sorted(zip(u.tolist(), g.col.tolist(), g.w.tolist()))
+        bwd = sorted(zip(g.col.tolist(), u.tolist(), g.w.tolist()))
+        assert fwd == bwd
+
+
+def gg_rows(rows):
+    import numpy as np
+    return np.repeat(np.arange(len(rows), dtype=np.int64), rows)
