@@ -78,3 +78,17 @@ def test_binding_structs_match_the_header(tmp_path):
         assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
         for field in cls._fields_:
             assert got[(cname, field[0])] == getattr(cls, field[0]).offset, (cname, field[0])
+
+
+def test_arena_sizing_without_a_device(lib_path):
+    """louvain_arena_bytes sizes a context's device arena by a dry run (no GPU
+    needed): 68 bytes per CSR entry (input, two coarse copies, relabelled rows,
+    global tables) and a few hundred per vertex, growing with both."""
+    from paper_2301_12390_gb300.louvain import arena_bytes
+    n, e = 1_000_000, 10_000_000
+    b = arena_bytes(n, e)
+    per_entry = (arena_bytes(n, 2 * e) - b) / e
+    per_vertex = (arena_bytes(2 * n, e) - b) / n
+    assert abs(per_entry - 68) < 0.5, per_entry
+    assert 300 < per_vertex < 450, per_vertex
+    assert arena_bytes(0, 0) < arena_bytes(10, 0) < arena_bytes(10, 10)
