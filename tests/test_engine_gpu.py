@@ -58,7 +58,7 @@ def test_hand_worked_runs_on_gpu():
         o = dict(case["options"])
         mode = 0 if o.pop("mode") == "sync" else 1
         ex = case["expect"]
-        for prune in (0, 1):
+        for prune in ([o.pop("prune")] if "prune" in o else (0, 1)):
             got = engine_run(g, mode=mode, prune=prune, **o)
             if mode == 0:
                 assert list(got["top"]) == ex["top"], case["name"]

@@ -221,7 +221,7 @@ def test_hand_worked_runs():
         g = gg.from_weighted_edges(case["n"], [tuple(e) for e in case["edges"]])
         o = dict(case["options"])
         mode = oracle.SYNC if o.pop("mode") == "sync" else oracle.ASYNC
-        for prune in (0, 1):
+        for prune in ([o.pop("prune")] if "prune" in o else (0, 1)):
             r = run(g, mode=mode, prune=prune, **o)
             ex = case["expect"]
             assert list(r.top) == ex["top"], case["name"]
