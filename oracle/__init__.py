@@ -43,13 +43,13 @@ class Options(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("tolerance", ctypes.c_double), ("tolerance_decline", ctypes.c_double),
                 ("pass_tolerance", ctypes.c_double), ("max_iterations", ctypes.c_int),
                 ("max_passes", ctypes.c_int), ("prune", ctypes.c_int), ("singleton_guard", ctypes.c_int),
-                ("subrounds", ctypes.c_int), ("colour_classes", ctypes.c_int)]
+                ("subrounds", ctypes.c_int), ("colour_classes", ctypes.c_int), ("stop_rule", ctypes.c_int)]
 
     @classmethod
     def make(cls, mode=SYNC, tolerance=0.01, tolerance_decline=10.0, pass_tolerance=0.0, max_iterations=20,
-             max_passes=10, prune=0, singleton_guard=1, subrounds=1, colour_classes=0):
+             max_passes=10, prune=0, singleton_guard=1, subrounds=1, colour_classes=0, stop_rule=0):
         return cls(mode, tolerance, tolerance_decline, pass_tolerance, max_iterations, max_passes, prune,
-                   singleton_guard, subrounds, colour_classes)
+                   singleton_guard, subrounds, colour_classes, stop_rule)
 
 
 def _load():
@@ -119,19 +119,22 @@ class Result:
 
 def louvain(off, col, w, mode=SYNC, tolerance=0.01, tolerance_decline=10.0, pass_tolerance=0.0,
             max_iterations=20, max_passes=10, prune=0, singleton_guard=1, subrounds=1,
-            record_levels=False, initial=None, colour_classes=0) -> Result:
+            record_levels=False, initial=None, colour_classes=0, stop_rule=0) -> Result:
     """Run the oracle Louvain; exact integers for every recorded quantity.
 
     singleton_guard, subrounds and colour_classes apply to the synchronous
     mode only (colour_classes: the classes are colour_classes() of every pass
     graph instead of i mod subrounds).
     initial: a membership of the input (values in [0, n)) that pass 0 starts
-    from instead of singletons (an incremental re-run)."""
+    from instead of singletons (an incremental re-run).
+    stop_rule: what an iteration's "total change in modularity" (Section 3.2)
+    is: 0 = 2S/M^2, S the sum of the movers' gains; 1 = the exact change of
+    the Q numerator over the iteration, recomputed from the membership, / M^2."""
     lib = _load()
     off, col, w = _arrs(off, col, w)
     n = len(off) - 1
     opt = Options.make(mode, tolerance, tolerance_decline, pass_tolerance, max_iterations, max_passes, prune,
-                       singleton_guard, subrounds, int(colour_classes))
+                       singleton_guard, subrounds, int(colour_classes), int(stop_rule))
     init = None
     if initial is not None:
         init = np.ascontiguousarray(initial, dtype=np.int32)

@@ -42,7 +42,12 @@
  *   - "total change in modularity" of an iteration is the sum of the gains
  *     of the vertices that moved, S; the phase stops when
  *     (2.0 * dbl(S)) / dbl(M^2) <= tolerance, dbl() being the correctly
- *     rounded conversion of the exact integer;
+ *     rounded conversion of the exact integer.  In sequential (asynchronous)
+ *     order 2S is exactly the change of the Q numerator N over the iteration;
+ *     in synchronous order it is not (decisions taken together overlap), so
+ *     stop_rule 1 reads the phrase as that exact change instead: the phase
+ *     stops when dbl(N_after_iteration - N_before_iteration) / dbl(M^2) <=
+ *     tolerance, N recomputed from the membership;
  *   - at most max_iterations iterations per pass and max_passes passes;
  *   - a pass with no move ends the run; otherwise its level is kept, and the
  *     run ends when dbl(N_after - N_before) / dbl(M^2) <= pass_tolerance
@@ -83,6 +88,8 @@ typedef struct {
   int singleton_guard; /* synchronous only: see decide() */
   int subrounds;       /* synchronous only: vertex classes i mod P run in sequence */
   int colour_classes;  /* synchronous only: vertex classes from colour_classes() instead of i mod P */
+  int stop_rule;       /* 0: an iteration's change is S, the sum of its movers' gains; 1: the exact
+                          change of the Q numerator over the iteration, recomputed from the membership */
 } or_options;
 
 /* ------------------------------------------------------------ helpers */
@@ -433,6 +440,7 @@ or_result *or_louvain_from(int64_t n, const int64_t *off, const int32_t *col, co
       size[memb[i]] += 1;
     }
     i128 Nbefore = Qnum;
+    i128 Nprev = Nbefore;   /* Q numerator before the current iteration (stop_rule 1) */
     scratch s;
     s.n = np;
     s.acc = (int64_t *)calloc((size_t)(np ? np : 1), 8);
@@ -494,7 +502,16 @@ or_result *or_louvain_from(int64_t n, const int64_t *off, const int32_t *col, co
           active[i] = a;
         }
       }
-      if ((2.0 * (double)S) / (double)M2 <= tol) break;
+      int settled;
+      if (opt->stop_rule == 1) {
+        int64_t Mx;
+        const i128 Nit = q_numerator(np, g.off, g.col, g.w, memb, &Mx);
+        settled = dbl_ratio(Nit - Nprev, M2) <= tol;
+        Nprev = Nit;
+      } else {
+        settled = (2.0 * (double)S) / (double)M2 <= tol;
+      }
+      if (settled) break;
     }
     r->pass_n[p] = np;
     r->pass_nnz[p] = g.nnz;

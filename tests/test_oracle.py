@@ -312,6 +312,43 @@ def test_async_gains_sum_to_the_exact_modularity_change():
         assert 2 * total_S == r.passes[0].n_after - r.passes[0].n_before
 
 
+def test_recomputed_stop_rule_equals_sum_of_gains_in_sequential_order():
+    """stop_rule 1 (the exact Q change of each iteration, recomputed) and
+    stop_rule 0 (2S) agree in sequential asynchronous order, where every gain
+    is the true change: same traces, memberships and Q on random and SBM
+    graphs.  A ΔN taken over the wrong span (say since the pass began) or
+    without the factor of two would stop at other iterations."""
+    rng = random.Random(14)
+    graphs = [gg.sbm(13, 600, 10, 0.12, 0.01, wmin=1, wmax=7), gg.rmat(15, 11, 8, wmin=1, wmax=5)]
+    graphs += [random_graph(rng, rng.randint(5, 12), 0.4) for _ in range(20)]
+    for g in graphs:
+        for tol in (0.01, 0.001, 0.05):
+            a = run(g, mode=oracle.ASYNC, prune=1, tolerance=tol)
+            b = run(g, mode=oracle.ASYNC, prune=1, tolerance=tol, stop_rule=1)
+            assert a.iterations == b.iterations
+            assert np.array_equal(a.top, b.top) and a.q_num == b.q_num
+
+
+def test_recomputed_stop_rule_in_synchronous_order():
+    """In synchronous order the recomputed change is what the moves did:
+    each pass's iterations end at the first iteration whose own exact change
+    N(after) - N(before) is at most tolerance * M^2 (replayed here iteration by
+    iteration, with max_iterations cut, from runs of the oracle itself)."""
+    g = gg.sbm(16, 900, 12, 0.1, 0.01, wmin=1, wmax=4)
+    full = run(g, mode=oracle.SYNC, stop_rule=1, max_passes=1, tolerance=0.01)
+    M2 = full.M * full.M
+    n_prev = full.passes[0].n_before
+    for t in range(1, full.passes[0].iterations + 1):
+        r = run(g, mode=oracle.SYNC, stop_rule=1, max_passes=1, tolerance=0.01, max_iterations=t)
+        n_t = r.passes[0].n_after
+        settled = float(n_t - n_prev) / float(M2) <= 0.01
+        assert settled == (t == full.passes[0].iterations and t < 20), t
+        n_prev = n_t
+    # and the sum-of-gains rule over-counts here: 2 * sum S exceeds the pass's exact change
+    s0 = run(g, mode=oracle.SYNC, max_passes=1, tolerance=0.01)
+    assert 2 * sum(S for (_, _, S) in s0.iterations) > s0.passes[0].n_after - s0.passes[0].n_before
+
+
 def test_modularity_range_and_sync_async_quality():
     """Q stays in [-1/2, 1] (Section 1); sync and async reach equivalent quality (Section 3.2)."""
     g = gg.sbm(0x5EED, 2048, 16, 0.1, 0.002)
