@@ -111,7 +111,12 @@ typedef struct {
                                  0..62 that no preceding neighbour holds, else 63.  The pass has (largest
                                  class + 1) classes.  Synchronous: deterministic, equal to the oracle's
                                  colour-class mode.  0 (default): subrounds / reclass */
-  int32_t reserved_i[1];
+  int32_t stop_rule;          /* what an iteration's "total change in modularity" (Section 3.2) is:
+                                 0 (default) = 2S/M^2, S the sum of the gains of its moves (exactly the
+                                 change in sequential order); 1 = the exact change of the Q numerator over
+                                 the iteration, recomputed from the membership after it (costs one scan of
+                                 the pass graph per iteration), / M^2.  The two differ in synchronous
+                                 order, where decisions taken together overlap */
   double reserved_d[4];
 } louvain_options;
 
@@ -294,9 +299,12 @@ int louvain_modularity(louvain_ctx *ctx, const int32_t *memb, int64_t n, int ptr
  * share the array and each clears what it needs: calls that overlap on the
  * GPU race and must not be issued.  Outputs are host pointers; num_hi,
  * num_lo, M may be NULL.  The call synchronises `cuda_stream`.
- * Errors: CAPACITY (n > LOUVAIN_STATIC_MAX_VERTICES), INVALID_ARG (null
- * pointer, negative n, a membership outside [0, n)), OVERFLOW (M >= 2^62),
- * CUDA. */
+ * Errors: CAPACITY (n > LOUVAIN_STATIC_MAX_VERTICES), INVALID_ARG (a null
+ * pointer with n > 0, negative n, a membership outside [0, n)), BAD_CSR (a
+ * row whose offsets are negative or decreasing, a column outside [0, n); the
+ * kernels check both before they index with them), OVERFLOW (M >= 2^62),
+ * CUDA.  The offsets must lie within the caller's cols / weights buffers
+ * (offsets[n] <= their length): the call cannot see those lengths. */
 int louvain_modularity_static(int64_t n, const int64_t *offsets, const int32_t *cols, const int32_t *weights,
                               const int32_t *memb, void *cuda_stream, double *q, int64_t *num_hi, uint64_t *num_lo,
                               int64_t *M);

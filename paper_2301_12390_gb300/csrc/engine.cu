@@ -274,6 +274,7 @@ int check_options(const louvain_options* o) {
   if (o->reclass < 0 || o->reclass > 3) return 1;
   if (o->bucket_streams < 0 || o->bucket_streams > 1) return 1;
   if (o->colour_classes < 0 || o->colour_classes > 1) return 1;
+  if (o->stop_rule < 0 || o->stop_rule > 1) return 1;
   return 0;
 }
 
@@ -344,6 +345,9 @@ int colour_pass(louvain_ctx* c, const PassState& g, int pass, int* ncls) {
   *ncls = m + 1;
   return 0;
 }
+
+template <typename W>
+int q_numerators(louvain_ctx* c, const PassState& g, std::vector<i128>& out);
 
 template <typename W>
 int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool wide, int* iters_out,
@@ -591,6 +595,14 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
     return 0;
   };
 
+  // stop_rule 1: each graph's Q numerator before the current iteration
+  const bool recompute = c->opt.stop_rule == 1;
+  std::vector<i128> nprev, nnow;
+  if (recompute) {
+    nprev.resize(G);
+    nnow.resize(G);
+    for (int64_t q = 0; q < G; ++q) nprev[q] = c->gst[q].qnum;
+  }
   bool filtered = false;     // the lists hold only the last iteration's visits
   int64_t last_visited = 0;  // vertices the last iteration visited (all graphs)
   cudaGraph_t graph = nullptr;
@@ -662,13 +674,20 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
     last_visited = (int64_t)c->h_ctr->visited;
     cands_total += (int64_t)c->h_ctr->cands;
     bool any_on = false;
+    if (recompute)
+      if ((rc = q_numerators<W>(c, g, nnow))) break;
     if (!multi) {
       const u128 S = ((u128)c->h_ctr->s_hi << 64) | (u128)c->h_ctr->s_lo;
       const int64_t mv = (int64_t)c->h_ctr->moves;
       c->iters.push_back(IterRec{pass, mv, S});
       c->gst[0].pass_moves += mv;
       c->gst[0].pass_iters++;
-      any_on = !((2.0 * (double)S) / dbl((i128)c->M * c->M) <= tol);
+      if (recompute) {
+        any_on = !(dbl(nnow[0] - nprev[0]) / dbl((i128)c->M * c->M) <= tol);
+        nprev[0] = nnow[0];
+      } else {
+        any_on = !((2.0 * (double)S) / dbl((i128)c->M * c->M) <= tol);
+      }
     } else {
       u128 Stot = 0;
       int64_t mvtot = 0;
@@ -682,7 +701,14 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
         st.pass_iters++;
         Stot += S;
         mvtot += mv;
-        if ((2.0 * (double)S) / dbl((i128)st.M * st.M) <= tol) c->h_gon[q] = 0;
+        bool settled;
+        if (recompute) {
+          settled = dbl(nnow[q] - nprev[q]) / dbl((i128)st.M * st.M) <= tol;
+          nprev[q] = nnow[q];
+        } else {
+          settled = (2.0 * (double)S) / dbl((i128)st.M * st.M) <= tol;
+        }
+        if (settled) c->h_gon[q] = 0;
         else any_on = true;
       }
       c->iters.push_back(IterRec{pass, mvtot, Stot});
@@ -1280,6 +1306,7 @@ int louvain_default_options(louvain_options* o) {
   o->reclass = 3;
   o->bucket_streams = 1;
   o->colour_classes = 0;
+  o->stop_rule = 0;
   return 0;
 }
 

@@ -53,15 +53,21 @@ int scratch_address(void** out) {
   return 0;
 }
 
-// One warp per row: K[u] = row sum; M += K[u]; loops are not needed here.
+// One warp per row: K[u] = row sum; M += K[u].  A row whose offsets are
+// negative or decreasing sets a flag and is not read.
 template <typename W>
 __global__ void static_row_sums_k(const int64_t* __restrict__ off, const W* __restrict__ wt, int64_t n,
                                   long long* K, unsigned long long* acc) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < n; u += warps) {
+    const int64_t x0 = off[u], x1 = off[u + 1];
+    if (x0 < 0 || x1 < x0) {   // not a CSR: flag it, read nothing of the row
+      if (lane == 0) atomicOr(&acc[6], 2ull);
+      continue;
+    }
     unsigned long long s = 0;
-    for (int64_t x = off[u] + lane; x < off[u + 1]; x += 32) s += (unsigned long long)wt[x];
+    for (int64_t x = x0 + lane; x < x1; x += 32) s += (unsigned long long)wt[x];
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
     if (lane == 0) {
@@ -81,7 +87,8 @@ __global__ void static_totals_k(const long long* K, const int32_t* __restrict__ 
   }
 }
 
-// L += weights of entries whose ends share a community (one warp per row).
+// L += weights of entries whose ends share a community (one warp per row);
+// a column outside [0, n) sets a flag instead.
 template <typename W>
 __global__ void static_intra_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
                                const W* __restrict__ wt, int64_t n, const int32_t* __restrict__ memb,
@@ -91,8 +98,16 @@ __global__ void static_intra_k(const int64_t* __restrict__ off, const int32_t* _
   unsigned long long L = 0;
   for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < n; u += warps) {
     const int32_t cu = memb[u];
-    for (int64_t x = off[u] + lane; x < off[u + 1]; x += 32)
-      if (memb[col[x]] == cu) L += (unsigned long long)wt[x];
+    const int64_t x0 = off[u], x1 = off[u + 1];
+    if (x0 < 0 || x1 < x0) continue;   // flagged by static_row_sums_k
+    for (int64_t x = x0 + lane; x < x1; x += 32) {
+      const int32_t v = col[x];
+      if (v < 0 || v >= n) {   // a column outside [0, n): flag it, do not index memb with it
+        atomicOr(&acc[6], 4ull);
+        continue;
+      }
+      if (memb[v] == cu) L += (unsigned long long)wt[x];
+    }
   }
 #pragma unroll
   for (int m = 16; m >= 1; m >>= 1) L += __shfl_xor_sync(0xffffffffu, L, m);
@@ -123,7 +138,7 @@ extern "C" int louvain_modularity_static(int64_t n, const int64_t* offsets, cons
                                          const int32_t* weights, const int32_t* memb, void* cuda_stream, double* q,
                                          int64_t* num_hi, uint64_t* num_lo, int64_t* M_out) {
   if (n > kMaxV) return LOUVAIN_ERR_CAPACITY;
-  if (n < 0 || !q || (n > 0 && (!offsets || !memb))) return LOUVAIN_ERR_INVALID_ARG;
+  if (n < 0 || !q || (n > 0 && (!offsets || !cols || !weights || !memb))) return LOUVAIN_ERR_INVALID_ARG;
   if (n == 0) {
     *q = 0.0;
     if (num_hi) *num_hi = 0;
@@ -150,7 +165,8 @@ extern "C" int louvain_modularity_static(int64_t n, const int64_t* offsets, cons
       cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return LOUVAIN_ERR_CUDA;
-  if (h[6]) return LOUVAIN_ERR_INVALID_ARG;
+  if (h[6] & 1) return LOUVAIN_ERR_INVALID_ARG;   // a membership outside [0, n)
+  if (h[6] & 6) return LOUVAIN_ERR_BAD_CSR;       // decreasing offsets or a column outside [0, n)
   if (h[1] != 0 || h[0] >= (1ull << 62)) return LOUVAIN_ERR_OVERFLOW;
   const int64_t M = (int64_t)h[0];
   const u128 L = ((u128)h[3] << 64) | (u128)h[2];

@@ -39,7 +39,7 @@ class Options(ctypes.Structure):
                 ("max_passes", ctypes.c_int32), ("prune", ctypes.c_int32), ("singleton_guard", ctypes.c_int32),
                 ("subrounds", ctypes.c_int32), ("validate", ctypes.c_int32), ("record_levels", ctypes.c_int32),
                 ("cuda_graphs", ctypes.c_int32), ("reclass", ctypes.c_int32), ("bucket_streams", ctypes.c_int32),
-                ("colour_classes", ctypes.c_int32), ("reserved_i", ctypes.c_int32 * 1),
+                ("colour_classes", ctypes.c_int32), ("stop_rule", ctypes.c_int32),
                 ("reserved_d", ctypes.c_double * 4)]
 
 
@@ -384,11 +384,31 @@ class Louvain:
 def modularity_static(off, col, w, memb, stream=None):
     """louvain_modularity_static on CUDA tensors (device pointers): (Q, exact numerator, M).
 
-    Allocates no device memory; see include/louvain.h for who needs that and
-    for the limits (fixed capacity, calls must not overlap on the GPU)."""
+    offsets int64 (n + 1), cols / weights / memb int32, contiguous, on the
+    device that is current.  `stream` is a torch.cuda.Stream, a raw
+    cudaStream_t handle (int) or None (the default stream).  Allocates no
+    device memory; include/louvain.h says who needs that and gives the limits
+    (fixed capacity, calls must not overlap on the GPU)."""
     lib = load_library()
-    q, hi, lo, M = ctypes.c_double(), ctypes.c_int64(), ctypes.c_uint64(), ctypes.c_int64()
+    want = (("offsets", off, "torch.int64"), ("cols", col, "torch.int32"), ("weights", w, "torch.int32"),
+            ("memb", memb, "torch.int32"))
+    dev = None
+    for name, t, dt in want:
+        if not hasattr(t, "is_cuda") or not t.is_cuda:
+            raise TypeError(f"modularity_static: {name} must be a CUDA tensor")
+        if str(t.dtype) != dt:
+            raise TypeError(f"modularity_static: {name} must be {dt}, not {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"modularity_static: {name} must be contiguous")
+        if dev is not None and t.device != dev:
+            raise ValueError("modularity_static: all tensors must be on one device")
+        dev = t.device
     n = len(off) - 1
+    if len(memb) != n:
+        raise ValueError("modularity_static: memb must have one entry per vertex")
+    if stream is not None and not isinstance(stream, int):
+        stream = stream.cuda_stream   # a torch.cuda.Stream
+    q, hi, lo, M = ctypes.c_double(), ctypes.c_int64(), ctypes.c_uint64(), ctypes.c_int64()
     rc = lib.louvain_modularity_static(n, _ptr(off), _ptr(col), _ptr(w), _ptr(memb), stream or None,
                                        ctypes.byref(q), ctypes.byref(hi), ctypes.byref(lo), ctypes.byref(M))
     if rc:

@@ -52,7 +52,7 @@ def assert_sync_parity(g, **opt):
                          subrounds=kw.get("subrounds", 1), max_iterations=kw.get("max_iterations", 20),
                          max_passes=kw.get("max_passes", 10), tolerance=kw.get("tolerance", 0.01),
                          tolerance_decline=kw.get("tolerance_decline", 10.0),
-                         colour_classes=kw.get("colour_classes", 0))
+                         colour_classes=kw.get("colour_classes", 0), stop_rule=kw.get("stop_rule", 0))
     assert got["iters"] == list(ref.iterations), "per-iteration (pass, moves, S) differ"
     assert len(got["passes"]) == len(ref.passes)
     for p, (gp, rp) in enumerate(zip(got["passes"], ref.passes)):

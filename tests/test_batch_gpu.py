@@ -78,6 +78,19 @@ def test_sync_batch_with_colour_classes_equals_each_graph_alone():
         assert np.array_equal(membs[g], ref.top) and nums[g] == ref.q_num, g
 
 
+def test_sync_batch_with_recomputed_stop_rule_equals_each_graph_alone():
+    """stop_rule 1 keeps each graph's own iteration stop in a batch: every
+    graph's recomputed Q change is its own, so its result equals its result
+    alone and the oracle's."""
+    membs, q, nums, Ms, iters = run_batch(GS, mode=0, prune=1, stop_rule=1)
+    for g, graph in enumerate(GS):
+        m1, q1, (num1, M1), it1 = run_alone(graph, mode=0, prune=1, stop_rule=1)
+        assert np.array_equal(membs[g], m1), g
+        assert (nums[g], Ms[g]) == (num1, M1) and iters[g] == it1, g
+        ref = oracle.louvain(graph.off, graph.col, graph.w, mode=oracle.SYNC, prune=1, stop_rule=1)
+        assert np.array_equal(membs[g], ref.top) and nums[g] == ref.q_num, g
+
+
 def test_async_batch_quality_per_graph():
     membs, q, nums, Ms, iters = run_batch(GS, mode=1, prune=1)
     for g, graph in enumerate(GS):

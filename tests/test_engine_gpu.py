@@ -82,6 +82,25 @@ def test_sync_parity_subrounds(name, subrounds):
     assert_sync_parity(G[name], prune=1, subrounds=subrounds)
 
 
+@pytest.mark.parametrize("name", list(G))
+@pytest.mark.parametrize("prune", [0, 1])
+def test_sync_parity_recomputed_stop_rule(name, prune):
+    """stop_rule 1: an iteration's change is the exact change of the Q
+    numerator over it (recomputed on the device after every iteration);
+    bit-exact with the oracle's same reading."""
+    assert_sync_parity(G[name], prune=prune, stop_rule=1)
+
+
+@pytest.mark.parametrize("name", ["sbm600", "rmat16", "road128"])
+def test_async_quality_recomputed_stop_rule(name):
+    g = G[name]
+    got = engine_run(g, mode=1, prune=1, stop_rule=1)
+    ref = oracle.louvain(g.off, g.col, g.w, mode=oracle.ASYNC, prune=1)
+    assert got["q"] >= ref.Q - 0.01, (got["q"], ref.Q)
+    _, num, M = oracle.modularity(g.off, g.col, g.w, got["top"])
+    assert got["exact"] == (num, M)
+
+
 @pytest.mark.parametrize("name", ["road128", "sbm8192"])
 @pytest.mark.parametrize("graphs", [0, 1])
 def test_sync_parity_with_and_without_cuda_graphs(name, graphs):
