@@ -522,3 +522,25 @@ def test_colour_classes_on_a_clique_are_the_sequential_order():
     assert a.iterations == b.iterations                  # every iteration's moves and gain sum
     pairs = {(int(a.top[v]), int(b.top[cls[v]])) for v in range(n)}
     assert len(pairs) == len({x for x, _ in pairs}) == len({y for _, y in pairs})   # the same partition
+
+
+def test_relabelled_graph_keeps_modularity_and_async_reference():
+    """The relabelling used for the asynchronous reference (engine_util) is a
+    graph isomorphism: same M, same modularity of the correspondingly renamed
+    membership, still symmetric; and a run at the id-order Q meets it."""
+    from engine_util import relabelled, async_within_tolerance
+    g = gg.sbm(21, 500, 9, 0.1, 0.01, wmin=1, wmax=6)
+    memb = np.random.default_rng(3).integers(0, 9, g.n).astype(np.int32)
+    off, col, w = relabelled(g.off, g.col, g.w, 7)
+    perm = np.random.default_rng(7).permutation(g.n)
+    memb2 = np.empty_like(memb)
+    memb2[perm] = memb
+    assert oracle.modularity(off, col, w, memb2) == oracle.modularity(g.off, g.col, g.w, memb)
+    A = {}
+    for u in range(g.n):
+        for e in range(off[u], off[u + 1]):
+            A[(u, int(col[e]))] = int(w[e])
+    assert all(A.get((v, u)) == x for (u, v), x in A.items())
+    q_id = oracle.louvain(g.off, g.col, g.w, mode=oracle.ASYNC, prune=1).Q
+    assert async_within_tolerance(g.off, g.col, g.w, q_id)[0]
+    assert not async_within_tolerance(g.off, g.col, g.w, -1.0)[0]
