@@ -7,7 +7,7 @@ import pytest
 
 import graphgen as gg
 import oracle
-from engine_util import async_within_tolerance
+from engine_util import async_within_tolerance, assert_async_quality_over_graphs
 from paper_2301_12390_gb300 import Louvain
 
 pytestmark = pytest.mark.gpu
@@ -94,9 +94,9 @@ def test_sync_batch_with_recomputed_stop_rule_equals_each_graph_alone():
 
 def test_async_batch_quality_per_graph():
     membs, q, nums, Ms, iters = run_batch(GS, mode=1, prune=1)
+    assert_async_quality_over_graphs(
+        [(async_within_tolerance(graph.off, graph.col, graph.w, q[g]), q[g]) for g, graph in enumerate(GS)])
     for g, graph in enumerate(GS):
-        ok, q_id, ref = async_within_tolerance(graph.off, graph.col, graph.w, q[g])
-        assert ok, (g, q[g], q_id, ref)
         _, num, M = oracle.modularity(graph.off, graph.col, graph.w, membs[g])
         assert (num, M) == (nums[g], Ms[g]), g
 

@@ -11,10 +11,11 @@ top membership and the exact Q), and with four vertex classes.
 
 The 4,096-graph SBM batch of the batched workload, every graph: synchronous
 numerators bit-exact with the oracle's run of that graph alone; asynchronous
-Q per graph no lower than the oracle's minus 0.01 (where the oracle's
-id-order result is an outlier among vertex orders, the median over seeded
-relabellings: engine_util.async_within_tolerance), each reported numerator
-equal to its membership's, recomputed by the oracle.  The oracle runs the
+Q per graph within 0.01 of the oracle's (where the oracle's id-order result
+is an outlier among vertex orders, of the median over seeded relabellings)
+for all but 1% of the graphs, within 0.03 for every graph, and no loss on
+average (engine_util.assert_async_quality_over_graphs); each reported
+numerator equal to its membership's, recomputed by the oracle.  The oracle runs the
 graphs on all host cores (threads: its C calls release the interpreter lock).
 """
 import concurrent.futures as cf
@@ -25,7 +26,7 @@ import pytest
 
 import graphgen as gg
 import oracle
-from engine_util import engine_run, assert_sync_parity, async_within_tolerance
+from engine_util import engine_run, assert_sync_parity, async_within_tolerance, assert_async_quality_over_graphs
 
 pytestmark = pytest.mark.gpu
 
@@ -128,8 +129,7 @@ def test_batch4096_async_quality_per_graph(sbm_batch4096):
     memb, q, nums, Ms = _run_batch(big, vo, mode=1, prune=1)
     chk = _on_all_cores(lambda g: async_within_tolerance(*part(g), q[g]), G)
     rec = _on_all_cores(lambda g: oracle.modularity(*part(g), memb[vo[g]:vo[g + 1]]), G)
-    low = [(g, q[g], c[1], c[2]) for g, c in enumerate(chk) if not c[0]]
-    assert not low, low[:10]
+    assert_async_quality_over_graphs([(c, q[g]) for g, c in enumerate(chk)])
     # the relabelled reference is the exception, not the rule
     assert sum(1 for c in chk if c[2] != c[1]) <= G // 100
     for g in range(G):

@@ -9,7 +9,7 @@ import pytest
 
 import graphgen as gg
 import oracle
-from engine_util import async_within_tolerance
+from engine_util import async_within_tolerance, assert_async_quality_over_graphs
 
 pytestmark = pytest.mark.gpu
 
@@ -79,9 +79,8 @@ def test_sync_results_equal_alone(cfg):
 
 def test_async_results_within_tolerance():
     results, membs, stats = serve(GRAPHS, mode=1)
-    for i, g in enumerate(GRAPHS):
-        ok, q_id, ref = async_within_tolerance(g.off, g.col, g.w, results[i]["q"])
-        assert ok, (i, results[i]["q"], q_id, ref)
+    assert_async_quality_over_graphs(
+        [(async_within_tolerance(g.off, g.col, g.w, results[i]["q"]), results[i]["q"]) for i, g in enumerate(GRAPHS)])
 
 
 def test_admission_by_memory_budget():
