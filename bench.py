@@ -177,6 +177,29 @@ ORACLE_SAMPLE_ENTRIES = 1.0e9
 ORACLE_SAMPLE_MIN_S = 10.0
 
 
+class OneCore:
+    """Pins the calling thread to one host core while the oracle runs, and
+    restores its affinity afterwards, so that the single-threaded CPU baseline
+    does not drift with scheduler placement.  The last allowed core is taken
+    (core 0 serves most interrupts)."""
+
+    def __enter__(self):
+        self.prev = None
+        self.core = None
+        try:
+            self.prev = os.sched_getaffinity(0)
+            self.core = max(self.prev)
+            os.sched_setaffinity(0, {self.core})
+        except (AttributeError, OSError):
+            self.prev = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.prev is not None:
+            os.sched_setaffinity(0, self.prev)
+        return False
+
+
 def oracle_sample_plan(g):
     """(max_passes, max_iterations, description) of the bounded oracle sample."""
     if g.nnz * 40 <= ORACLE_SAMPLE_ENTRIES:
@@ -214,14 +237,15 @@ def bench_reference_graphs(args):
         graphs = [pool[p] for p in pick if pool[p].n <= 200_000][:32]
         metric = "graphs/sec (p50/p99 latency) served with continuous batching vs serial plain runs, at equal Q"
         what = "the first 32 requests whose graph has at most 200,000 vertices"
-    for g in graphs[:max(1, args.warmup)]:
-        oracle.louvain(g.off, g.col, g.w, mode=mode, prune=1)
     lat, tot_t = [], 0.0
-    for _ in range(args.steps):
-        for g in graphs:
-            t = time.perf_counter()
+    with OneCore() as pin:
+        for g in graphs[:max(1, args.warmup)]:
             oracle.louvain(g.off, g.col, g.w, mode=mode, prune=1)
-            lat.append(time.perf_counter() - t)
+        for _ in range(args.steps):
+            for g in graphs:
+                t = time.perf_counter()
+                oracle.louvain(g.off, g.col, g.w, mode=mode, prune=1)
+                lat.append(time.perf_counter() - t)
     tot_t = float(np.sum(lat))
     value = len(lat) / tot_t
     line = {
@@ -230,7 +254,7 @@ def bench_reference_graphs(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": args.workload, "mode": args.mode, "graphs_per_step": len(graphs)},
         "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)), "latency_ms_p99": 1e3 * float(np.percentile(lat, 99)),
-        "cpu_baseline": {"value": value, "unit": "graphs/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "graphs/s", "cores": 1, "kind": "oracle", "pinned_core": pin.core,
                          "sample": f"full oracle runs ({args.mode}, prune on) of {what}, per step"},
         "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -250,13 +274,14 @@ def bench_reference(args):
         return
     g = WORKLOADS[args.workload][0]()
     mode = oracle.ASYNC if args.mode == "async" else oracle.SYNC
-    for _ in range(args.warmup):
-        run_oracle_sample(g, mode, max_passes=1, max_iterations=1)
     tot_e, tot_t, q = 0, 0.0, None
-    for _ in range(args.steps):
-        e, dt, q = run_oracle_sample(g, mode, max_passes=1, max_iterations=1)
-        tot_e += e
-        tot_t += dt
+    with OneCore() as pin:
+        for _ in range(args.warmup):
+            run_oracle_sample(g, mode, max_passes=1, max_iterations=1)
+        for _ in range(args.steps):
+            e, dt, q = run_oracle_sample(g, mode, max_passes=1, max_iterations=1)
+            tot_e += e
+            tot_t += dt
     value = tot_e / tot_t
     sample = f"first local-moving iteration (pass 0) over all {g.n} vertices / {g.nnz} entries, per step"
     line = {
@@ -265,7 +290,8 @@ def bench_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": args.workload, "description": WORKLOADS[args.workload][1], "mode": args.mode,
                    "n": g.n, "nnz": g.nnz},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "pinned_core": pin.core,
+                         "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -365,13 +391,14 @@ def bench_ours(args):
         mp, mi, what = oracle_sample_plan(g)
         e = dt = 0
         runs = 0
-        while runs == 0 or dt < ORACLE_SAMPLE_MIN_S:
-            e1, dt1, q_or = run_oracle_sample(g, oracle.ASYNC if mode == ASYNC else oracle.SYNC, max_passes=mp,
-                                              max_iterations=mi)
-            e, dt, runs = e + e1, dt + dt1, runs + 1
+        with OneCore() as pin:
+            while runs == 0 or dt < ORACLE_SAMPLE_MIN_S:
+                e1, dt1, q_or = run_oracle_sample(g, oracle.ASYNC if mode == ASYNC else oracle.SYNC, max_passes=mp,
+                                                  max_iterations=mi)
+                e, dt, runs = e + e1, dt + dt1, runs + 1
         if runs > 1:
             what = f"{what}, repeated {runs} times,"
-        cpu = {"value": e / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": e / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "pinned_core": pin.core,
                "sample": f"{what} ({args.mode}, prune off) of the same graph: "
                          f"{e} local-moving entries in {dt:.1f} s, Q {q_or:.5f}"}
     if rank == 0:

@@ -50,3 +50,13 @@ def test_serving_pool_is_seeded_and_in_range():
 def gg_rows(rows):
     import numpy as np
     return np.repeat(np.arange(len(rows), dtype=np.int64), rows)
+
+
+def test_oracle_baseline_runs_on_one_pinned_core_and_restores_affinity():
+    import os
+    import bench
+    before = os.sched_getaffinity(0)
+    with bench.OneCore() as pin:
+        assert os.sched_getaffinity(0) == {pin.core}
+        assert pin.core in before
+    assert os.sched_getaffinity(0) == before
