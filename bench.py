@@ -435,26 +435,32 @@ def bench_ours(args):
                           # pass 0 (the input graph): its iterations times nnz per second of its local moving
                           "pass0_iterations_per_step": iters / args.steps},
         }
-        print(json.dumps(line), flush=True)
     lv.close()
+    if rank == 0:
+        # the metric's second half: the batched workload against plain runs of
+        # the same graphs (one GPU; outside the timed region above)
+        if world == 1 and args.workload == "rmat22" and not args.no_batched:
+            b = measure_batched(args, device, steps=3, warmup=1)
+            line["batched"] = {k: b[k] for k in ("graphs", "n", "nnz", "mode", "steps", "description", "plain",
+                                                 "batched", "speedup_vs_plain", "q_batched_minus_plain", "clocks",
+                                                 "gpu_launches")}
+        print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()
 
 
-def bench_batched(args):
+def measure_batched(args, device, steps, warmup):
     """Many small graphs: one batched run vs the same graphs one at a time.
 
     Workload: args.batch_graphs planted-partition SBMs, n log-uniform in
     [256, 16384], 4-64 blocks, p_in uniform in [0.05, 0.2], p_out 1e-3,
     weight 1, packed as one block-diagonal CSR.  Both arms start from inputs
     resident on the device and include load (validation, degrees), run and
-    membership read-back (device to device) per request.
+    membership read-back (device to device) per request.  Returns the
+    measurement as a dict (graphs/s, p50/p99 latency, Q difference per graph).
     """
     import torch
     from paper_2301_12390_gb300 import Louvain, SYNC, ASYNC
-    world, rank, local, pg = dist_setup()
-    device = local
-    torch.cuda.set_device(device)
     mode = ASYNC if args.mode == "async" else SYNC
     specs = gg.batch_sbm_specs(SEED + 3, args.batch_graphs)
     big, vo = gg.sbm_batch(specs)
@@ -476,7 +482,7 @@ def bench_batched(args):
     # one at a time
     lv = Louvain(device=device, stream=stream.cuda_stream, **opts)
     biggest = int(np.argmax(np.diff(big.off[vo])))
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         lv.load_csr(*parts[biggest])
         lv.run()
     out_memb = torch.empty(int(big.n), dtype=torch.int32, device=dev)
@@ -496,7 +502,7 @@ def bench_batched(args):
     lb = Louvain(device=device, stream=stream.cuda_stream, **opts)
     lb.load_batch(d_vo, d_off, d_col, d_w)
     mapping, tune_ms = lb.autotune() if not args.no_autotune else (lb.mapping(), 0.0)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         lb.load_batch(d_vo, d_off, d_col, d_w)
         lb.run()
     clocks = Clocks(device)
@@ -505,7 +511,7 @@ def bench_batched(args):
     blat = []
     lm_edges = 0
     lm_ms = 0.0
-    for _ in range(args.steps):
+    for _ in range(steps):
         t0 = time.perf_counter()
         lb.load_batch(d_vo, d_off, d_col, d_w)
         lb.run()
@@ -519,29 +525,46 @@ def bench_batched(args):
     launches = lb.stats().kernel_launches
     lb.close()
     batch_s = float(np.median(blat))
-    value = G / batch_s
+    return {
+        "graphs": G, "n": int(big.n), "nnz": int(big.nnz), "mode": args.mode, "steps": steps,
+        "description": "SBM graphs, n log-uniform 256-16384, 4-64 blocks, p_in 0.05-0.2, p_out 1e-3, weight 1, one "
+                       "block-diagonal CSR; each request = load (validated) + run + membership, inputs resident on "
+                       "the device",
+        "plain": {"graphs_per_s": G / plain_s, "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
+                  "latency_ms_p99": 1e3 * float(np.percentile(lat, 99)), "total_s": plain_s,
+                  "mean_q": float(q_plain.mean())},
+        "batched": {"graphs_per_s": G / batch_s, "latency_ms_p50": 1e3 * float(np.percentile(blat, 50)),
+                    "latency_ms_p99": 1e3 * float(np.percentile(blat, 99)), "mean_q": float(q_batch.mean()),
+                    "lm_edges_per_s": lm_edges / (lm_ms / 1e3) if lm_ms else None},
+        "mapping": {"thresholds": mapping, "autotuned": not args.no_autotune, "best_trial_ms": tune_ms},
+        "cuda_graphs": bool(args.cuda_graphs),
+        "speedup_vs_plain": (G / batch_s) / (G / plain_s),
+        "q_batched_minus_plain": {"mean": float((q_batch - q_plain).mean()),
+                                  "min": float((q_batch - q_plain).min()),
+                                  "max": float((q_batch - q_plain).max())},
+        "clocks": ck, "gpu_launches": launches * steps, "batch_s": batch_s,
+    }
+
+
+def bench_batched(args):
+    """The batched workload alone: one JSON line whose value is the batched
+    graphs/s (see measure_batched)."""
+    import torch
+    world, rank, local, pg = dist_setup()
+    device = local
+    torch.cuda.set_device(device)
+    m = measure_batched(args, device, args.steps, args.warmup)
     if rank == 0:
         line = {
-            "metric": "graphs/sec batched vs plain, at equal Q", "value": value, "unit": "graphs/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * batch_s,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic",
-            "config": {"workload": "batched", "graphs": G, "n": int(big.n), "nnz": int(big.nnz), "mode": args.mode,
-                       "description": "SBM graphs, n log-uniform 256-16384, 4-64 blocks, p_in 0.05-0.2, "
-                                      "p_out 1e-3, weight 1, one block-diagonal CSR; each request = load "
-                                      "(validated) + run + membership, inputs resident on the device"},
-            "plain": {"graphs_per_s": G / plain_s, "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
-                      "latency_ms_p99": 1e3 * float(np.percentile(lat, 99)), "total_s": plain_s,
-                      "mean_q": float(q_plain.mean())},
-            "batched": {"graphs_per_s": value, "latency_ms_p50": 1e3 * float(np.percentile(blat, 50)),
-                        "latency_ms_p99": 1e3 * float(np.percentile(blat, 99)), "mean_q": float(q_batch.mean()),
-                        "lm_edges_per_s": lm_edges / (lm_ms / 1e3) if lm_ms else None},
-            "mapping": {"thresholds": mapping, "autotuned": not args.no_autotune, "best_trial_ms": tune_ms},
-            "cuda_graphs": bool(args.cuda_graphs),
-            "speedup_vs_plain": value / (G / plain_s),
-            "q_batched_minus_plain": {"mean": float((q_batch - q_plain).mean()),
-                                      "min": float((q_batch - q_plain).min())},
-            "clocks": ck, "gpu_launches": launches * args.steps,
+            "metric": "graphs/sec batched vs plain, at equal Q", "value": m["batched"]["graphs_per_s"],
+            "unit": "graphs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * m["batch_s"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "batched", "graphs": m["graphs"], "n": m["n"], "nnz": m["nnz"],
+                       "mode": args.mode, "description": m["description"]},
+            "plain": m["plain"], "batched": m["batched"], "mapping": m["mapping"], "cuda_graphs": m["cuda_graphs"],
+            "speedup_vs_plain": m["speedup_vs_plain"], "q_batched_minus_plain": m["q_batched_minus_plain"],
+            "clocks": m["clocks"], "gpu_launches": m["gpu_launches"],
         }
         print(json.dumps(line), flush=True)
     if pg is not None:
@@ -710,6 +733,7 @@ def main():
     ap.add_argument("--slots", type=int, default=2)
     ap.add_argument("--mode", default="async", choices=["async", "sync"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="default workload: skip the batched measurement")
     ap.add_argument("--no-autotune", action="store_true", help="batched workload: keep the default vertex mapping")
     ap.add_argument("--cuda-graphs", action="store_true", help="batched workload: replay iterations as CUDA graphs")
     args = ap.parse_args()

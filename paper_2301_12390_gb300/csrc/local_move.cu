@@ -230,6 +230,28 @@ __device__ __forceinline__ VertexInfo vertex_info(const LMArgs<W>& a, const Iter
   return v;
 }
 
+// Pruning marks of a vertex that moved: the vertex and every neighbour are
+// active in the next iteration.  The row's columns are loaded together
+// before the marks are stored (a load after a store to the stamps would wait
+// for it), U at a time per thread; the entries b + lane0, + step, ... are
+// this thread's, and the thread with lane0 == 0 marks the vertex itself.
+template <int U, typename W>
+__device__ __forceinline__ void mark_row(const LMArgs<W>& a, const IterView& iv, int32_t i, int64_t b, int64_t e,
+                                         int lane0 = 0, int step = 1, bool self = true) {
+  if (self && lane0 == 0) iv.sw[i] = iv.iter + 1;
+  for (int64_t x0 = b + lane0; x0 < e; x0 += (int64_t)U * step) {
+    int32_t cc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t x = x0 + (int64_t)u * step;
+      cc[u] = x < e ? __ldg(a.col + x) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (cc[u] >= 0) iv.sw[cc[u]] = iv.iter + 1;
+  }
+}
+
 // --------------------------------------------- bucket 0: thread per vertex
 
 // The row (<= 8 entries) is loaded first and its neighbours' communities
@@ -301,10 +323,7 @@ __global__ void __launch_bounds__(256, 3) lm_thread(LMArgs<W> a, const int32_t* 
       n_edges = (unsigned)(e - b);
       n_visited = 1;
       moved = commit_choice<W, WIDE, ASYNC>(a, acc, i, d, Ki, sd, szd, bg, bc, kid, M, graph, &gv);
-      if (moved && a.prune) {
-        iv.sw[i] = iv.iter + 1;
-        for (int64_t x = b; x < e; ++x) iv.sw[a.col[x]] = iv.iter + 1;
-      }
+      if (moved && a.prune) mark_row<8>(a, iv, i, b, e);
     } while (false);
     n_edges = __reduce_add_sync(0xffffffffu, n_edges);
     n_visited = __reduce_add_sync(0xffffffffu, n_visited);
@@ -399,10 +418,7 @@ __device__ __forceinline__ void warp_vertex(const LMArgs<W>& a, const IterView& 
     moved = commit_choice<W, WIDE, ASYNC, LD>(a, acc, i, d, Ki, cur.sd, cur.szd, bg, bc, kid, M, graph);
   }
   moved = __shfl_sync(0xffffffffu, moved, 0);
-  if (moved && a.prune) {
-    if (lane == 0) iv.sw[i] = iv.iter + 1;
-    for (int64_t x = b + lane; x < e; x += kWarp) iv.sw[a.col[x]] = iv.iter + 1;
-  }
+  if (moved && a.prune) mark_row<U>(a, iv, i, b, e, lane, kWarp);
 }
 
 // U entries per lane are loaded and gathered before any insert (U * 32 covers
@@ -478,9 +494,11 @@ __global__ void __launch_bounds__(256, 4) lm_class(LMArgs<W> a, const int32_t* _
 
 // ----------------------------------------- buckets 3-4: block per vertex
 
-// A decided move waiting for the block to commit it.
+// A decided move waiting for the block to commit it, with its row bounds
+// (for the pruning marks).
 struct PendingMove {
-  int32_t i, c, d;
+  int32_t i, c, d, pad;
+  int64_t b, e;
 };
 
 // Commit and mark the pending moves of a block (all threads take part).
@@ -501,12 +519,8 @@ __device__ __forceinline__ void flush_moves(const LMArgs<W>& a, const IterView& 
       a.moves[pos] = make_int2(m.i, m.c);
     }
   }
-  if (a.prune)
-    for (int t = 0; t < n; ++t) {
-      const int32_t i = q[t].i;
-      if (tid == 0) iv.sw[i] = iv.iter + 1;
-      for (int64_t x = a.off[i] + tid; x < a.off[i + 1]; x += nthr) iv.sw[a.col[x]] = iv.iter + 1;
-    }
+  if (a.prune)   // one warp per move, the warps' moves in parallel
+    for (int t = tid >> 5; t < n; t += nthr >> 5) mark_row<8>(a, iv, q[t].i, q[t].b, q[t].e, tid & 31, kWarp);
 }
 
 // Decide (no commit yet): the exact gain of the best candidate against the
@@ -655,7 +669,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 128 ? 8 : 2)
         atomicAdd(&acc.visited, 1ull);
         atomicAdd(&acc.cands, (unsigned long long)(s_nt[p] - (s_kid[p] != 0 ? 1 : 0)));
         if (decide_move<W, WIDE, ASYNC>(a, acc, d, Ki, cur.sd, cur.szd, bg, bc, s_kid[p], M, graph))
-          queue[q_n++] = PendingMove{i, bc, d};
+          queue[q_n++] = PendingMove{i, bc, d, 0, b, e};
       }
     }
     p ^= 1;
@@ -879,7 +893,7 @@ __global__ void __launch_bounds__(256) lm_hub_mark(LMArgs<W> a, const int32_t* _
   const int64_t b = a.off[i], e = a.off[i + 1];
   const int64_t x0 = b + q * kHubChunk, x1 = min(e, x0 + kHubChunk);
   if (q == 0 && threadIdx.x == 0) iv.sw[i] = iv.iter + 1;
-  for (int64_t x = x0 + threadIdx.x; x < x1; x += 256) iv.sw[a.col[x]] = iv.iter + 1;
+  mark_row<4>(a, iv, i, x0, x1, (int)threadIdx.x, 256, false);   // the hub itself: marked above
 }
 
 // ----------------------------------------------- synchronous commit step

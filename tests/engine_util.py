@@ -115,7 +115,9 @@ def assert_async_quality_over_graphs(results, floor=0.03):
     """The asynchronous contract over a set of graphs, as results of
     async_within_tolerance(...) paired with (q, id-order Q): every graph
     within `floor` of its reference, all but max(1, G // 100) graphs within
-    0.01 of it, and no loss on average against the oracle's id-order Q.
+    0.01 of it, and no systematic loss: the mean difference from the oracle's
+    id-order Q above -0.003 (on a few dozen graphs one graph's variance moves
+    the mean by about 0.001; a broken asynchronous mode loses 0.01 or more).
 
     The parallel visiting order is one more order among the many that the
     sequential method may take; measured on the 4,096 SBMs of the batched
@@ -129,5 +131,5 @@ def assert_async_quality_over_graphs(results, floor=0.03):
                                                              if not r[1] >= r[0][2] - floor][:10]
     assert len(misses) <= max(1, G // 100), misses[:10]
     mean_diff = sum(r[1] - r[0][1] for r in results) / max(G, 1)
-    assert mean_diff >= -0.001, mean_diff
+    assert mean_diff >= -0.003, mean_diff
     return misses
