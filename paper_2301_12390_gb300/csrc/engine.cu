@@ -53,6 +53,9 @@ constexpr int64_t kSmallGraph = 65536;
 // road grid and R-MAT (no gain; a quarter as the threshold cost the road grid 9%).
 constexpr int64_t kFilterMinList = 2000000;
 constexpr double kFilterFraction = 0.1;
+// A pass with at least this many vertices per vertex with edges classifies
+// its later iterations over the vertices with edges only.
+constexpr int64_t kEdgeListRatio = 4;
 
 struct IterRec {
   int pass;
@@ -403,7 +406,7 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
   auto reclassify_small = [&]() {
     int32_t* idx = (int32_t*)c->moves;   // free in asynchronous mode
     lm_keys_sub(g.off, c->level, sub_m, P, c->key, multi ? c->gid : nullptr, multi ? c->vo : nullptr, c->d_gcat,
-                cs, c->d_iter, c->thr, s);
+                cs, c->d_iter, c->thr, nullptr, nullptr, s);
     stable_partition(c->key, sub_m, nkeys, idx, c->key_off, c->tmp, s);
     gather_ids(idx, c->level, sub_m, c->list, s);
   };
@@ -414,10 +417,23 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
   // lists keep only the vertices the iteration visits (active, graph still
   // iterating): the late iterations of a pass, and batches whose graphs have
   // mostly stopped, launch over those alone.  A filtered list is never reused.
+  // A pass whose vertices are mostly isolated (the later passes of a
+  // heavy-tailed graph: every isolated vertex stays a community of its own)
+  // classifies again only its vertices with edges, kept in c->level (free
+  // until renumbering) after the first classification; c->newid (free too)
+  // takes the partition's positions.
+  int64_t edge_m = 0;
   auto classify = [&](int iter, bool filter) -> int {
-    lm_keys(g.off, g.n, P, c->key, multi ? c->gid : nullptr, multi ? c->vo : nullptr, c->d_gcat, cs, c->d_iter,
-            c->thr, filter ? c->stamp[iter & 1] : nullptr, multi ? c->d_gon : nullptr, s);
-    stable_partition(c->key, g.n, nkeys, c->list, c->key_off, c->tmp, s);
+    if (edge_m > 0) {
+      lm_keys_sub(g.off, c->level, edge_m, P, c->key, multi ? c->gid : nullptr, multi ? c->vo : nullptr, c->d_gcat,
+                  cs, c->d_iter, c->thr, filter ? c->stamp[iter & 1] : nullptr, multi ? c->d_gon : nullptr, s);
+      stable_partition(c->key, edge_m, nkeys, c->newid, c->key_off, c->tmp, s);
+      gather_ids(c->newid, c->level, edge_m, c->list, s);
+    } else {
+      lm_keys(g.off, g.n, P, c->key, multi ? c->gid : nullptr, multi ? c->vo : nullptr, c->d_gcat, cs, c->d_iter,
+              c->thr, filter ? c->stamp[iter & 1] : nullptr, multi ? c->d_gon : nullptr, s);
+      stable_partition(c->key, g.n, nkeys, c->list, c->key_off, c->tmp, s);
+    }
     CKLAUNCH();
     if (int r = fetch(c, ko.data(), c->key_off, ko.size() * sizeof(int64_t))) return r;
     hub0 = ko[kHubBucket * P];
@@ -445,6 +461,10 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
     // later classifications partition only the vertices with edges
     sub_m = ko[3 * P];
     CK(cudaMemcpyAsync(c->level, c->list, sub_m * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  } else if (!small_pass && !colour && full_len > 0 && full_len * kEdgeListRatio <= g.n &&
+             (reclass || c->opt.prune)) {
+    edge_m = full_len;
+    CK(cudaMemcpyAsync(c->level, c->list, edge_m * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   }
   // a class kernel of a small pass loops over its class, however large: one
   // grid for the pass, so its iteration's launches do not depend on the draw

@@ -125,10 +125,11 @@ void stable_partition(const int32_t* key, int64_t n, int nkeys, int32_t* out, in
 void lm_keys(const int64_t* off, int64_t n, int P, int32_t* key, const int32_t* gid, const int64_t* vo,
              const int32_t* gcat, ClassSpec cs, const int* d_iter, LMThresholds th, const int32_t* active,
              const int32_t* g_on, cudaStream_t s);
-// lm_keys for the m vertices sub[0..m); gather_ids: out[j] = sub[idx[j]].
+// lm_keys for the m vertices sub[0..m) (with `active`, as lm_keys);
+// gather_ids: out[j] = sub[idx[j]].
 void lm_keys_sub(const int64_t* off, const int32_t* sub, int64_t m, int P, int32_t* key, const int32_t* gid,
                  const int64_t* vo, const int32_t* gcat, ClassSpec cs, const int* d_iter, LMThresholds th,
-                 cudaStream_t s);
+                 const int32_t* active, const int32_t* g_on, cudaStream_t s);
 void gather_ids(const int32_t* idx, const int32_t* sub, int64_t m, int32_t* out, cudaStream_t s);
 // For the hub list: per hub its table base (2 * degree slots), the prefix of
 // its insert chunks and the prefix of its slot chunks (each nhubs + 1 long).

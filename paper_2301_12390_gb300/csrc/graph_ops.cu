@@ -247,15 +247,18 @@ __global__ void lm_keys_k(const int64_t* __restrict__ off, int64_t n, int P, int
   }
 }
 
-// The same keys for the vertices of a subset (key[j] for vertex sub[j]).
+// The same keys for the vertices of a subset (key[j] for vertex sub[j]);
+// with `active`, inactive vertices and vertices of stopped graphs get the
+// key past every bucket.
 __global__ void lm_keys_sub_k(const int64_t* __restrict__ off, const int32_t* __restrict__ sub, int64_t m, int P,
                               int32_t* key, const int32_t* __restrict__ gid, const int64_t* __restrict__ vo,
                               const int32_t* __restrict__ gcat, ClassSpec cs, const int* __restrict__ d_iter,
-                              LMThresholds th) {
+                              LMThresholds th, const int32_t* __restrict__ active, const int32_t* __restrict__ g_on) {
   const int iter = *d_iter;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
     const int32_t i = sub[j];
     int b = lm_bucket_of(off[i + 1] - off[i], th);
+    if (active && (active[i] != iter || (gid && !g_on[gid[i]]))) b = -1;
     key[j] = b < 0 ? kBuckets * P : b * P + (P > 1 ? vertex_class(i, gid, vo, gcat, cs, iter) : 0);
   }
 }
@@ -401,9 +404,10 @@ void pass_init(int64_t n, const long long* K, int32_t* memb, long long* sig, int
 
 void lm_keys_sub(const int64_t* off, const int32_t* sub, int64_t m, int P, int32_t* key, const int32_t* gid,
                  const int64_t* vo, const int32_t* gcat, ClassSpec cs, const int* d_iter, LMThresholds th,
-                 cudaStream_t s) {
+                 const int32_t* active, const int32_t* g_on, cudaStream_t s) {
   if (m > 0)
-    (count_launch(), lm_keys_sub_k<<<grid1d(m), kT, 0, s>>>(off, sub, m, P, key, gid, vo, gcat, cs, d_iter, th));
+    (count_launch(), lm_keys_sub_k<<<grid1d(m), kT, 0, s>>>(off, sub, m, P, key, gid, vo, gcat, cs, d_iter, th, active,
+                                                             g_on));
 }
 void gather_ids(const int32_t* idx, const int32_t* sub, int64_t m, int32_t* out, cudaStream_t s) {
   if (m > 0) (count_launch(), gather_ids_k<<<grid1d(m), kT, 0, s>>>(idx, sub, m, out));
