@@ -385,7 +385,7 @@ def bench_ours(args):
     d2h = memb.nbytes
     lv_e2e.close()
     # CPU baseline: the oracle, as it stands, on rank 0 at N=1 only
-    cpu = None
+    cpu = cpu_mt = None
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         mp, mi, what = oracle_sample_plan(g)
@@ -401,6 +401,21 @@ def bench_ours(args):
         cpu = {"value": e / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "pinned_core": pin.core,
                "sample": f"{what} ({args.mode}, prune off) of the same graph: "
                          f"{e} local-moving entries in {dt:.1f} s, Q {q_or:.5f}"}
+        # the paper's multi-threaded design on all host cores, same sample
+        cpu_mt = None
+        if args.mode == "async":
+            e = dt = 0
+            runs = 0
+            while runs == 0 or dt < ORACLE_SAMPLE_MIN_S / 2:
+                t = time.perf_counter()
+                r = oracle.louvain_mt(g.off, g.col, g.w, max_passes=mp, max_iterations=mi)
+                dt += time.perf_counter() - t
+                e += r.scanned
+                runs += 1
+            cpu_mt = {"value": e / dt, "unit": UNIT, "cores": r.threads,
+                      "kind": "multi-threaded CPU Louvain (asynchronous, a hashtable per thread; not the oracle)",
+                      "sample": f"the same sample, repeated {runs} times: {e} local-moving entries in {dt:.1f} s, "
+                                f"Q {r.Q:.5f}"}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -422,6 +437,7 @@ def bench_ours(args):
                          "kernel": "local-moving phase (all its kernels, CUDA events)",
                          "peak_source": peak_src},
             "cpu_baseline": cpu,
+            "cpu_baseline_multithreaded": cpu_mt,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps, "host_buffers": "pinned",
                     "step": "louvain_load_csr (H2D, validation, degrees) + louvain_run + louvain_get_membership (D2H)"},
@@ -591,8 +607,19 @@ def serving_pool(seed: int, count: int, nmin: int, nmax: int):
 
 
 def bench_serving(args):
-    """A Poisson stream of requests served two ways: one request per run on one
-    slot (serial plain runs) and the continuous-batching server."""
+    """Requests served by the continuous-batching server against serial plain
+    runs (one request per run), on a stream of args.requests requests drawn
+    from a seeded pool of SBM and R-MAT graphs.
+
+    - Serial capacity: every pool graph run alone through the C ABI (host CSR
+      in, membership out), the median of two timed runs; over the request mix
+      the serial arm serves requests / sum of their service times.
+    - Served capacity (the value): every request submitted at once, so the
+      server is saturated; requests / makespan.
+    - Latency: Poisson arrivals at 0.5, 1 and 2 times the serial capacity
+      (args.latency_requests each), p50/p99 of submit-to-result.
+    Equal Q: each served request's Q against its graph's plain run.
+    """
     import torch
     from paper_2301_12390_gb300 import Louvain, Server, SYNC, ASYNC
     torch.cuda.set_device(0)
@@ -600,73 +627,96 @@ def bench_serving(args):
     pool = serving_pool(SEED + 4, args.pool, args.serve_nmin, args.serve_nmax)
     R = args.requests
     pick = [int(gg.uniform(SEED + 4, 32, r) * len(pool)) for r in range(R)]
-    # serial capacity: each pool graph alone through the C ABI (host inputs)
+    # serial plain runs: each pool graph alone
     lv = Louvain(device=0, mode=mode, prune=1)
     lv.load_csr(pool[0].off, pool[0].col, pool[0].w)
     lv.run()
-    svc = []
+    svc, q_pool = [], []
     for g in pool:
-        t0 = time.perf_counter()
-        lv.load_csr(g.off, g.col, g.w)
-        lv.run()
-        lv.membership()
-        svc.append(time.perf_counter() - t0)
+        ts = []
+        for _ in range(2):
+            t0 = time.perf_counter()
+            lv.load_csr(g.off, g.col, g.w)
+            lv.run()
+            lv.membership()
+            ts.append(time.perf_counter() - t0)
+        svc.append(float(np.median(ts)))
+        q_pool.append(lv.modularity())
     lv.close()
-    mean_svc = float(np.mean([svc[p] for p in pick]))
-    rate = args.rate_factor / mean_svc           # requests per second
-    gaps = [-np.log(1.0 - gg.uniform(SEED + 4, 33, r)) / rate for r in range(R)]
-    arrivals = np.cumsum(gaps)
+    serial_s = float(sum(svc[p] for p in pick))
+    serial_cap = R / serial_s
+    q_plain = np.array([q_pool[p] for p in pick])
 
-    def run_arm(**cfg):
+    def run_arm(reqs, arrivals, **cfg):
         results = {}
         with Server(device=0, mode=mode, prune=1, **cfg) as srv:
             t0 = time.perf_counter()
-            for r in range(R):
-                while time.perf_counter() - t0 < arrivals[r]:
-                    for x in srv.poll():
-                        results[x["id"]] = x
-                    time.sleep(0.0002)
+            for k, r in enumerate(reqs):
+                if arrivals is not None:
+                    while time.perf_counter() - t0 < arrivals[k]:
+                        for x in srv.poll():
+                            results[x["id"]] = x
+                        time.sleep(0.0002)
                 g = pool[pick[r]]
                 srv.submit(r, g.off, g.col, g.w)
-            while len(results) < R:
+            while len(results) < len(reqs):
                 for x in srv.poll(wait_ms=100):
                     results[x["id"]] = x
             st = srv.stats()
             tm = srv.timings()
-        lat = np.array([results[r]["done_s"] - results[r]["submit_s"] for r in range(R)])
-        span = max(results[r]["done_s"] for r in range(R)) - min(results[r]["submit_s"] for r in range(R))
-        q = np.array([results[r]["q"] for r in range(R)])
-        bsz = np.array([results[r]["batch_size"] for r in range(R)])
-        ok = all(results[r]["status"] == 0 for r in range(R))
-        return {"graphs_per_s": R / span, "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
+        lat = np.array([results[r]["done_s"] - results[r]["submit_s"] for r in reqs])
+        span = max(results[r]["done_s"] for r in reqs) - min(results[r]["submit_s"] for r in reqs)
+        q = np.array([results[r]["q"] for r in reqs])
+        bsz = np.array([results[r]["batch_size"] for r in reqs])
+        ok = all(results[r]["status"] == 0 for r in reqs)
+        return {"graphs_per_s": len(reqs) / span, "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
                 "latency_ms_p99": 1e3 * float(np.percentile(lat, 99)), "makespan_s": span, "runs": st["runs"],
                 "mean_q": float(q.mean()), "all_ok": ok, "peak_reserved_gb": st["peak_reserved_bytes"] / 1e9,
                 "mean_batch": float(bsz.mean()), "slot_seconds": {k: round(v, 3) for k, v in tm.items()}}, q
 
+    cfg = dict(slots=args.slots)
+    if args.batch_max_entries >= 0:
+        cfg["batch_max_entries"] = args.batch_max_entries
     clocks = Clocks(0)
-    plain, q_plain = run_arm(slots=1, batch_max_entries=0)
     clocks.start()
-    served, q_served = run_arm(slots=args.slots)
+    served, q_served = run_arm(list(range(R)), None, **cfg)
     ck = clocks.stop()
+    latency = {}
+    L = min(R, args.latency_requests)
+    for f in (0.5, 1.0, 2.0):
+        rate = f * serial_cap
+        gaps = [-np.log(1.0 - gg.uniform(SEED + 4, 33, r)) / rate for r in range(L)]
+        res, _ = run_arm(list(range(L)), np.cumsum(gaps), **cfg)
+        latency[f"{f:g}x_serial_capacity"] = {"arrival_rate_per_s": rate, "graphs_per_s": res["graphs_per_s"],
+                                              "latency_ms_p50": res["latency_ms_p50"],
+                                              "latency_ms_p99": res["latency_ms_p99"], "requests": L}
+    svc_req = np.array([svc[p] for p in pick])
+    d = q_served - q_plain
     line = {
         "metric": "graphs/sec (p50/p99 latency) served with continuous batching vs serial plain runs, at equal Q",
         "value": served["graphs_per_s"], "unit": "graphs/s", "n_gpus": 1, "steps": 1, "warmup": 1,
         "ms_per_step": 1e3 * served["makespan_s"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int64", "data": "synthetic",
         "config": {"workload": "serving", "requests": R, "pool_graphs": len(pool), "mode": args.mode,
-                   "arrival_rate_per_s": rate, "rate_factor_of_serial_capacity": args.rate_factor,
-                   "description": f"Poisson arrivals; each request a graph drawn from {len(pool)} seeded graphs, "
-                                  f"half SBM half R-MAT, n log-uniform {args.serve_nmin}-{args.serve_nmax}, "
-                                  "average degree 8-32, weights 1..8; host CSR in, membership out",
-                   "pool_nnz_mean": float(np.mean([g.nnz for g in pool]))},
-        "served": served, "plain_serial": plain,
-        "speedup_vs_plain": served["graphs_per_s"] / plain["graphs_per_s"],
-        "q_served_minus_plain": {"mean": float((q_served - q_plain).mean()), "min": float((q_served - q_plain).min()),
-                                 "max": float((q_served - q_plain).max()),
-                                 "worst": {"request": int(np.argmin(q_served - q_plain)),
-                                           "pool_graph": int(pick[int(np.argmin(q_served - q_plain))]),
-                                           "q_served": float(q_served[np.argmin(q_served - q_plain)]),
-                                           "q_plain": float(q_plain[np.argmin(q_served - q_plain)])}},
+                   "slots": args.slots, "batch_max_entries": args.batch_max_entries,
+                   "description": f"each request a graph drawn from {len(pool)} seeded graphs, half SBM half R-MAT, "
+                                  f"n log-uniform {args.serve_nmin}-{args.serve_nmax}, average degree 8-32, weights "
+                                  "1..8; host CSR in, membership out; served arm saturated (every request submitted "
+                                  "at once)",
+                   "pool_nnz_mean": float(np.mean([g.nnz for g in pool])),
+                   "request_nnz_mean": float(np.mean([pool[p].nnz for p in pick]))},
+        "served": served,
+        "plain_serial": {"graphs_per_s": serial_cap, "total_s": serial_s,
+                         "latency_ms_p50": 1e3 * float(np.percentile(svc_req, 50)),
+                         "latency_ms_p99": 1e3 * float(np.percentile(svc_req, 99)),
+                         "how": "each pool graph alone (load from host, run, membership), median of two runs, "
+                                "summed over the requests"},
+        "latency_at_load": latency,
+        "speedup_vs_plain": served["graphs_per_s"] / serial_cap,
+        "q_served_minus_plain": {"mean": float(d.mean()), "min": float(d.min()), "max": float(d.max()),
+                                 "worst": {"request": int(np.argmin(d)), "pool_graph": int(pick[int(np.argmin(d))]),
+                                           "q_served": float(q_served[np.argmin(d)]),
+                                           "q_plain": float(q_plain[np.argmin(d)])}},
         "clocks": ck,
     }
     print(json.dumps(line), flush=True)
@@ -725,11 +775,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS) + ["batched", "serving", "tolerance"])
     ap.add_argument("--batch-graphs", type=int, default=4096)
-    ap.add_argument("--requests", type=int, default=1000)
+    ap.add_argument("--requests", type=int, default=10000)
+    ap.add_argument("--latency-requests", type=int, default=1000,
+                    help="serving workload: requests per latency point (0.5, 1, 2 x serial capacity)")
+    ap.add_argument("--batch-max-entries", type=int, default=-1,
+                    help="serving workload: entries per batch (-1: the server's default)")
     ap.add_argument("--pool", type=int, default=64)
     ap.add_argument("--serve-nmin", type=int, default=1000)
     ap.add_argument("--serve-nmax", type=int, default=2_000_000)
-    ap.add_argument("--rate-factor", type=float, default=3.0)
     ap.add_argument("--slots", type=int, default=2)
     ap.add_argument("--mode", default="async", choices=["async", "sync"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -28,13 +28,26 @@ _lib = None
 SYNC, ASYNC = 0, 1
 
 
+_MT_SRC = os.path.join(_HERE, "louvain_mt.c")
+_MT_LIB = os.path.join(_HERE, "liblouvain_mt.so")
+_mt_lib = None
+
+
 def build(force: bool = False) -> str:
-    """Compile louvain_oracle.c into liboracle.so (gcc; no FMA contraction)."""
+    """Compile louvain_oracle.c into liboracle.so (gcc; no FMA contraction), and
+    the multi-threaded CPU baseline louvain_mt.c into liblouvain_mt.so (OpenMP
+    where the compiler has it, else one thread)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
                                "-fno-fast-math", "-o", tmp, _SRC])
         os.replace(tmp, _LIB)
+    if force or not os.path.exists(_MT_LIB) or os.path.getmtime(_MT_LIB) < os.path.getmtime(_MT_SRC):
+        tmp = _MT_LIB + f".tmp{os.getpid()}"
+        base = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, _MT_SRC]
+        if subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True).returncode != 0:
+            subprocess.check_call(base)
+        os.replace(tmp, _MT_LIB)
     return _LIB
 
 
@@ -249,3 +262,64 @@ def brute_best(off, col, w):
     if rc != 0:
         raise ValueError("oracle.brute_best: n must be in [1, 12]")
     return _i128(hi.value, lo.value), memb[:n].copy(), cnt.value
+
+
+# ------------------------------------------------ multi-threaded baseline
+
+class _MTOptions(ctypes.Structure):
+    _fields_ = [("tolerance", ctypes.c_double), ("tolerance_decline", ctypes.c_double),
+                ("pass_tolerance", ctypes.c_double), ("max_iterations", ctypes.c_int),
+                ("max_passes", ctypes.c_int), ("threads", ctypes.c_int)]
+
+
+@dataclass
+class MTResult:
+    top: np.ndarray
+    M: int
+    q_num: int
+    Q: float
+    passes: int
+    iterations: int
+    moves: int
+    scanned: int     # CSR entries scanned by local moving (every vertex every iteration)
+    threads: int
+
+
+def _load_mt():
+    global _mt_lib
+    if _mt_lib is None:
+        build()
+        lib = ctypes.CDLL(_MT_LIB)
+        lib.mt_louvain.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.POINTER(_MTOptions), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.mt_louvain.restype = ctypes.c_int
+        lib.mt_threads_available.restype = ctypes.c_int
+        _mt_lib = lib
+    return _mt_lib
+
+
+def threads_available() -> int:
+    """Threads the multi-threaded baseline can use (1 without OpenMP)."""
+    return int(_load_mt().mt_threads_available())
+
+
+def louvain_mt(off, col, w, threads=None, tolerance=0.01, tolerance_decline=10.0, pass_tolerance=0.0,
+               max_iterations=20, max_passes=10) -> MTResult:
+    """Multi-threaded CPU Louvain (louvain_mt.c): the paper's shared-memory
+    asynchronous design with a hashtable per thread.  A CPU baseline for the
+    benchmark, not the oracle; with one thread it is the oracle's sequential
+    asynchronous run without pruning."""
+    lib = _load_mt()
+    off, col, w = _arrs(off, col, w)
+    n = len(off) - 1
+    t = threads_available() if threads is None else int(threads)
+    opt = _MTOptions(tolerance, tolerance_decline, pass_tolerance, max_iterations, max_passes, t)
+    top = np.empty(n, np.int32)
+    out = np.zeros(8, np.int64)
+    q = ctypes.c_double()
+    used = lib.mt_louvain(n, off.ctypes.data, col.ctypes.data, w.ctypes.data, ctypes.byref(opt), top.ctypes.data,
+                          out.ctypes.data, ctypes.byref(q))
+    if used < 0:
+        raise ValueError("louvain_mt: invalid options")
+    return MTResult(top=top, M=int(out[6]), q_num=_i128(out[4], out[5]), Q=q.value, passes=int(out[0]),
+                    iterations=int(out[1]), moves=int(out[2]), scanned=int(out[3]), threads=int(used))
