@@ -625,6 +625,17 @@ def bench_serving(args):
     torch.cuda.set_device(0)
     mode = ASYNC if args.mode == "async" else SYNC
     pool = serving_pool(SEED + 4, args.pool, args.serve_nmin, args.serve_nmax)
+    # the requests' host CSRs sit in pinned memory (both arms load from it)
+    pinned = []
+    for g in pool:
+        arrs = []
+        for a in (g.off, g.col, g.w):
+            t = torch.empty(a.shape, dtype=torch.from_numpy(a[:0]).dtype, pin_memory=True)
+            t.numpy()[...] = a
+            arrs.append(t)
+        pinned.append(arrs)
+    pool = [gg.CSR(n=g.n, off=p[0].numpy(), col=p[1].numpy(), w=p[2].numpy())
+            for g, p in zip(pool, pinned)]
     R = args.requests
     pick = [int(gg.uniform(SEED + 4, 32, r) * len(pool)) for r in range(R)]
     # serial plain runs: each pool graph alone
@@ -674,7 +685,7 @@ def bench_serving(args):
                 "mean_q": float(q.mean()), "all_ok": ok, "peak_reserved_gb": st["peak_reserved_bytes"] / 1e9,
                 "mean_batch": float(bsz.mean()), "slot_seconds": {k: round(v, 3) for k, v in tm.items()}}, q
 
-    cfg = dict(slots=args.slots)
+    cfg = dict(slots=args.slots, borrow_inputs=not args.copy_inputs)
     if args.batch_max_entries >= 0:
         cfg["batch_max_entries"] = args.batch_max_entries
     clocks = Clocks(0)
@@ -691,6 +702,13 @@ def bench_serving(args):
                                               "latency_ms_p50": res["latency_ms_p50"],
                                               "latency_ms_p99": res["latency_ms_p99"], "requests": L}
     svc_req = np.array([svc[p] for p in pick])
+    cnt = np.bincount(np.array(pick), minlength=len(pool))
+    # serial time by request size: what a single large graph's run costs against the many small ones
+    share = {}
+    for lo, hi in ((0, 1 << 20), (1 << 20, 1 << 24), (1 << 24, 1 << 40)):
+        sel = [i for i, g in enumerate(pool) if lo <= g.nnz < hi]
+        share[f"nnz {lo}-{hi}"] = {"requests": int(sum(cnt[i] for i in sel)),
+                                  "serial_s": float(sum(cnt[i] * svc[i] for i in sel))}
     d = q_served - q_plain
     line = {
         "metric": "graphs/sec (p50/p99 latency) served with continuous batching vs serial plain runs, at equal Q",
@@ -699,6 +717,7 @@ def bench_serving(args):
         "dtype": "int64", "data": "synthetic",
         "config": {"workload": "serving", "requests": R, "pool_graphs": len(pool), "mode": args.mode,
                    "slots": args.slots, "batch_max_entries": args.batch_max_entries,
+                   "inputs": "copied at submit" if args.copy_inputs else "borrowed (the slots copy them to the device)",
                    "description": f"each request a graph drawn from {len(pool)} seeded graphs, half SBM half R-MAT, "
                                   f"n log-uniform {args.serve_nmin}-{args.serve_nmax}, average degree 8-32, weights "
                                   "1..8; host CSR in, membership out; served arm saturated (every request submitted "
@@ -709,8 +728,11 @@ def bench_serving(args):
         "plain_serial": {"graphs_per_s": serial_cap, "total_s": serial_s,
                          "latency_ms_p50": 1e3 * float(np.percentile(svc_req, 50)),
                          "latency_ms_p99": 1e3 * float(np.percentile(svc_req, 99)),
-                         "how": "each pool graph alone (load from host, run, membership), median of two runs, "
-                                "summed over the requests"},
+                         "how": "each pool graph alone (load from pinned host memory, run, membership), median of "
+                                "two runs, summed over the requests",
+                         "share_of_time_by_size": share},
+        "pool": [{"n": g.n, "nnz": g.nnz, "serial_ms": 1e3 * svc[i], "requests": int(cnt[i])}
+                 for i, g in enumerate(pool)],
         "latency_at_load": latency,
         "speedup_vs_plain": served["graphs_per_s"] / serial_cap,
         "q_served_minus_plain": {"mean": float(d.mean()), "min": float(d.min()), "max": float(d.max()),
@@ -783,7 +805,9 @@ def main():
     ap.add_argument("--pool", type=int, default=64)
     ap.add_argument("--serve-nmin", type=int, default=1000)
     ap.add_argument("--serve-nmax", type=int, default=2_000_000)
-    ap.add_argument("--slots", type=int, default=2)
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--copy-inputs", action="store_true",
+                    help="serving workload: the server copies every request at submit instead of borrowing it")
     ap.add_argument("--mode", default="async", choices=["async", "sync"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="default workload: skip the batched measurement")

@@ -349,7 +349,12 @@ typedef struct {
   int32_t batch_max_graphs;   /* at most this many requests per run, default 1024 */
   int64_t batch_max_entries;  /* at most this many CSR entries per run, default 64 Mi; 0 = one request per run */
   int64_t hbm_budget_bytes;   /* device bytes all slots' arenas may hold; 0 = 90% of free memory at creation */
-  int64_t reserved[5];
+  int64_t borrow_inputs;      /* 0 (default): louvain_server_submit copies the graph (into a reused pinned
+                                 host pool); 1: it keeps the caller's pointers, the caller keeps the arrays
+                                 alive and unchanged until the request's result has been polled, and the
+                                 worker slots copy them to the device themselves (no host copy on the
+                                 submitting thread) */
+  int64_t reserved[4];
 } louvain_server_config;
 
 typedef struct {
@@ -369,7 +374,8 @@ int louvain_server_default_config(louvain_server_config *cfg);
 /* opt: the engine options every slot runs with (NULL = defaults). */
 int louvain_server_create(louvain_server **out, const louvain_options *opt, const louvain_server_config *cfg,
                           int device);
-/* Submit graph `request_id` (host CSR as in louvain_load_csr; copied). */
+/* Submit graph `request_id` (host CSR as in louvain_load_csr; copied, or
+ * borrowed with borrow_inputs = 1). */
 int louvain_server_submit(louvain_server *srv, int64_t request_id, int64_t n, int64_t nnz, const int64_t *offsets,
                           const int32_t *cols, const int32_t *weights);
 /* Up to cap finished results into out (host); waits up to wait_ms for the

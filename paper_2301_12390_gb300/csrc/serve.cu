@@ -333,7 +333,7 @@ int louvain_server_create(louvain_server** out, const louvain_options* opt, cons
   if (opt) S->opt = *opt; else louvain_default_options(&S->opt);
   if (cfg) S->cfg = *cfg; else louvain_server_default_config(&S->cfg);
   if (S->cfg.slots < 1 || S->cfg.slots > 64 || S->cfg.batch_max_entries < 0 || S->cfg.batch_max_graphs < 1 ||
-      S->cfg.hbm_budget_bytes < 0) {
+      S->cfg.hbm_budget_bytes < 0 || S->cfg.borrow_inputs < 0 || S->cfg.borrow_inputs > 1) {
     delete S;
     return LOUVAIN_ERR_INVALID_ARG;
   }
@@ -368,6 +368,19 @@ int louvain_server_submit(louvain_server* S, int64_t request_id, int64_t n, int6
   r.id = request_id;
   r.n = n;
   r.nnz = nnz;
+  if (S->cfg.borrow_inputs) {   // the caller keeps the arrays until the result is polled
+    r.off = offsets;
+    r.col = cols;
+    r.w = weights;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stopping) return LOUVAIN_ERR_STATE;
+    if (S->memberships.count(request_id)) return LOUVAIN_ERR_INVALID_ARG;   // id still holds a result
+    r.submit_s = now_s(S->t0);
+    S->queue.push_back(std::move(r));
+    S->submitted++;
+    S->cv_work.notify_one();
+    return 0;
+  }
   // one block: offsets, then columns and weights (16-byte aligned)
   const size_t b_off = (size_t)(n + 1) * sizeof(int64_t);
   const size_t at_col = (b_off + 15) & ~(size_t)15;

@@ -418,7 +418,8 @@ def modularity_static(off, col, w, memb, stream=None):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("batch_max_graphs", ctypes.c_int32), ("batch_max_entries", ctypes.c_int64),
-                ("hbm_budget_bytes", ctypes.c_int64), ("reserved", ctypes.c_int64 * 5)]
+                ("hbm_budget_bytes", ctypes.c_int64), ("borrow_inputs", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 4)]
 
 
 class ServerResult(ctypes.Structure):
@@ -456,7 +457,7 @@ class Server:
     time, poll finished results; each result equals the graph's result alone."""
 
     def __init__(self, device: int = 0, slots: int = 2, batch_max_entries=None, batch_max_graphs=None,
-                 hbm_budget_bytes=None, **options):
+                 hbm_budget_bytes=None, borrow_inputs=False, **options):
         self.lib = load_library()
         self.opt = default_options(**options)
         cfg = ServerConfig()
@@ -468,6 +469,9 @@ class Server:
             cfg.batch_max_graphs = batch_max_graphs
         if hbm_budget_bytes is not None:
             cfg.hbm_budget_bytes = hbm_budget_bytes
+        cfg.borrow_inputs = 1 if borrow_inputs else 0
+        self.cfg_borrow = bool(borrow_inputs)
+        self._borrowed = {}   # borrowed inputs stay referenced until their result is polled
         h = ctypes.c_void_p()
         rc = self.lib.louvain_server_create(ctypes.byref(h), ctypes.byref(self.opt), ctypes.byref(cfg), device)
         if rc:
@@ -484,6 +488,8 @@ class Server:
         if rc:
             raise LouvainError(rc, f"submit of request {request_id} failed")
         self._n[request_id] = len(off) - 1
+        if self.cfg_borrow:
+            self._borrowed[request_id] = (off, col, w)
 
     def poll(self, wait_ms: int = 0, cap: int = 1024):
         buf = (ServerResult * cap)()
@@ -491,6 +497,7 @@ class Server:
         self.lib.louvain_server_poll(self.h, buf, cap, ctypes.byref(cnt), wait_ms)
         out = []
         for r in buf[:cnt.value]:
+            self._borrowed.pop(r.request_id, None)
             out.append({"id": r.request_id, "status": r.status, "batch_size": r.batch_size, "n": r.n,
                         "communities": r.communities, "q": r.q, "num": _i128(r.num_hi, r.num_lo), "M": r.M,
                         "submit_s": r.submit_s, "start_s": r.start_s, "done_s": r.done_s})

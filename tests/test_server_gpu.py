@@ -64,7 +64,7 @@ def serve(graphs, mode, gap_s=0.0, **cfg):
 
 
 @pytest.mark.parametrize("cfg", [dict(slots=2), dict(slots=3, batch_max_entries=50_000),
-                                 dict(slots=1, batch_max_entries=0)])
+                                 dict(slots=1, batch_max_entries=0), dict(slots=4, borrow_inputs=True)])
 def test_sync_results_equal_alone(cfg):
     results, membs, stats = serve(GRAPHS, mode=0, gap_s=0.002, **cfg)
     assert stats["finished"] == len(GRAPHS)
