@@ -182,6 +182,17 @@ struct louvain_ctx {
   int64_t* vo = nullptr;               // first pass-graph vertex of each graph
   int64_t* vo_next = nullptr;
   int64_t* vo_top = nullptr;           // first community id of each graph in the top membership
+  // Isolated communities leave the pass graphs after pass 0 (communities of
+  // vertices without edges: singletons that never move); later passes run on
+  // the other vertices only, in the same order (compact ids).
+  int64_t iso0 = 0;                    // empty rows of the loaded graph
+  bool compacted = false;              // this run's pass graphs are compact
+  int64_t iso_z = 0;                   // isolated communities left out (all graphs)
+  std::vector<int64_t> h_zg;           // ... per graph
+  int32_t* isob[2] = {nullptr, nullptr};   // per compact vertex: isolated communities before it
+  int isob_cur = 0;                    // isob[isob_cur] belongs to the current pass graph
+  int64_t kc_top = 0;                  // the compact ids in top[] lie below this
+  int64_t* d_zpre = nullptr;           // per graph: isolated communities of the graphs before it
   int64_t* kcount = nullptr;
   long long* d_Mg = nullptr;
   int32_t* d_gon = nullptr;
@@ -302,9 +313,14 @@ struct PassState {
 // Colour classes of the pass graph (option colour_classes) into c->members,
 // the aggregation's member list, which is free until the pass aggregates;
 // c->inv (predecessor counts) and c->mdeg / c->fill (the two frontiers) are
-// free too.  Rounds run kColourRoundsPerCheck at a time between host checks
-// of the frontier (a round with an empty frontier does nothing).  *ncls =
-// the number of classes (largest class + 1).
+// free too, and so are the aggregation's c->tcol (the two hub frontiers) and
+// local moving's hub partials c->hpart / c->hpart_c (the hubs' masks and item
+// counters; nothing keeps state in them from one iteration to the next; the
+// global tables c->gkeys / c->gvals must stay cleared, so they are not
+// borrowed).  Rounds run
+// kColourRoundsPerCheck at a time between host checks of the frontiers (a
+// round with empty frontiers does nothing).  *ncls = the number of classes
+// (largest class + 1).
 constexpr int kColourRoundsPerCheck = 8;
 int colour_pass(louvain_ctx* c, const PassState& g, int pass, int* ncls) {
   cudaStream_t s = c->stream;
@@ -315,23 +331,38 @@ int colour_pass(louvain_ctx* c, const PassState& g, int pass, int* ncls) {
   int32_t* cls = c->members;
   int32_t* cnt = c->inv;
   int32_t* front[2] = {(int32_t*)c->mdeg, (int32_t*)c->fill};
-  unsigned long long* sz = (unsigned long long*)(c->scal + 4);   // [0], [1]: frontier sizes; [2]: coloured
+  const int64_t hslots = g.nnz / kColourHubDegree + 1;
+  int32_t* hfront[2] = {c->tcol, c->tcol + hslots};
+  unsigned long long* hmask = (unsigned long long*)c->hpart;
+  int32_t* hdone = c->hpart_c;
+  if (hslots > c->npart) return fail(c, LOUVAIN_ERR_INTERNAL, "colouring: hub slots exceed the partial buffer");
+  // [0], [1]: frontier sizes; [2]: coloured; [3], [4]: hub frontier sizes (c->scal + 8)
+  unsigned long long* sz = (unsigned long long*)(c->scal + 4);
+  unsigned long long* hsz = (unsigned long long*)(c->scal + 8);
   int* cmax = (int*)(c->scal + 7);
   CK(cudaMemsetAsync(sz, 0, 3 * sizeof(unsigned long long), s));
+  CK(cudaMemsetAsync(hsz, 0, 2 * sizeof(unsigned long long), s));
+  CK(cudaMemsetAsync(hmask, 0, hslots * sizeof(unsigned long long), s));
+  CK(cudaMemsetAsync(hdone, 0, hslots * sizeof(int32_t), s));
   CK(cudaMemsetAsync(c->flags, 0, sizeof(int), s));
-  colour_init(g.off, g.col, g.n, gid, vo, salt, cnt, cls, front[0], sz, s);
+  const int32_t* isob = c->compacted ? c->isob[c->isob_cur] : nullptr;
+  const int64_t* zpre = c->compacted ? c->d_zpre : nullptr;
+  colour_init(g.off, g.col, g.n, gid, vo, isob, zpre, salt, cnt, cls, front[0], sz, hfront[0], hsz, s);
   int64_t r = 0;
   for (;;) {
     for (int k = 0; k < kColourRoundsPerCheck; ++k, ++r) {
       const int a = (int)(r & 1), b = a ^ 1;
       CK(cudaMemsetAsync(sz + b, 0, sizeof(unsigned long long), s));
-      colour_round(g.off, g.col, g.n, gid, vo, salt, front[a], sz + a, cnt, cls, front[b], sz + b, sz + 2, c->flags,
-                   s);
+      CK(cudaMemsetAsync(hsz + b, 0, sizeof(unsigned long long), s));
+      colour_round(g.off, g.col, g.n, gid, vo, isob, zpre, salt, front[a], sz + a, hfront[a], hsz + a, cnt, cls,
+                   front[b],
+                   sz + b, hfront[b], hsz + b, sz + 2, hmask, hdone, c->flags, s);
     }
     CKLAUNCH();
-    unsigned long long left = 0;
-    if (int e = fetch(c, &left, sz + (r & 1), sizeof(left))) return e;
-    if (left == 0) break;
+    unsigned long long left[2] = {0, 0};
+    if (int e = fetch(c, &left[0], sz + (r & 1), sizeof(unsigned long long))) return e;
+    if (int e = fetch(c, &left[1], hsz + (r & 1), sizeof(unsigned long long))) return e;
+    if (left[0] + left[1] == 0) break;
     if (r > g.n + kColourRoundsPerCheck) return fail(c, LOUVAIN_ERR_INTERNAL, "colouring did not end");
   }
   unsigned long long coloured = 0;
@@ -370,7 +401,8 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
   bool any_cat[3] = {false, false, false};
   for (int64_t q = 0; q < c->G; ++q) any_cat[c->hgcat[q]] = true;
   const bool any_small = any_cat[kCatSmall], any_big = any_cat[kCatLarge] || any_cat[kCatSparse];
-  ClassSpec cs{1, 1, 1, 0, 0, pass, c->G == 1 ? c->hgcat[0] : kCatLarge, nullptr};
+  ClassSpec cs{1, 1, 1, 0, 0, pass, c->G == 1 ? c->hgcat[0] : kCatLarge, nullptr,
+               c->compacted ? c->isob[c->isob_cur] : nullptr, c->compacted ? c->d_zpre : nullptr};
   if (colour) {
     cs.Ps = cs.Pb = cs.Pl = ncls;
     cs.colour = c->members;
@@ -896,6 +928,108 @@ int record_coarse(louvain_ctx* c, PassRec& pr, const PassState& h) {
   return 0;
 }
 
+// After pass 0: if enough communities of the coarse graph are isolated
+// (empty rows: communities of vertices without entries, which never move),
+// the later pass graphs leave them out.  Every other coarse vertex keeps its
+// order (compact id = rank among the non-empty rows); the columns are
+// renumbered in place, the offsets, degrees (c->Knext) and graph ids (batch)
+// compacted, top[] takes compact ids (an isolated community: -1 - its rank
+// among the isolated ones) and isob the isolated count before each compact
+// vertex.  finalize_top puts top[] back in the full numbering at the end.
+constexpr int64_t kCompactMinIsolated = 1024;   // and at least 1/16 of the coarse vertices
+int compact_coarse(louvain_ctx* c, PassState* next, int64_t k, const std::vector<int64_t>& vo_full) {
+  cudaStream_t s = c->stream;
+  const bool multi = c->G > 1;
+  const int64_t G = c->G;
+  int32_t* flag = c->used;    // free: the renumbering and the coarse degrees are done
+  int32_t* pos = c->newid;
+  nonempty_rows(next->off, k, flag, s);
+  scan_i32(flag, pos, k, c->scal, c->tmp, s);
+  CKLAUNCH();
+  int64_t kc = 0;
+  if (int r = fetch(c, &kc, c->scal, sizeof(int64_t))) return r;
+  const int64_t z = k - kc;
+  if (z < kCompactMinIsolated || z * 16 < k) return 0;
+  compact_rows(next->off, k, next->nnz, flag, pos, c->Knext, multi ? c->gid_next : nullptr, c->cnt, c->K,
+               multi ? c->gid : nullptr, c->isob[0], next->col, c->top, c->n0, s);
+  c->h_scal[0] = next->nnz;
+  CK(cudaMemcpyAsync(c->cnt + kc, c->h_scal, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(next->off, c->cnt, (kc + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  std::swap(c->K, c->Knext);   // the run swaps them back: the next pass's degrees are the compact ones
+  c->h_zg.assign(G, 0);
+  if (multi) {
+    std::swap(c->gid, c->gid_next);   // the pass swaps them back: gid_next holds the compact graph ids
+    compact_vo(c->vo_next, G, pos, k, kc, c->vo, s);
+    CKLAUNCH();
+    std::vector<int64_t> vo_c(G + 1), zpre(G + 1);
+    if (int r = fetch(c, vo_c.data(), c->vo, (G + 1) * sizeof(int64_t))) return r;
+    for (int64_t q = 0; q <= G; ++q) zpre[q] = vo_full[q] - vo_c[q];
+    for (int64_t q = 0; q < G; ++q) c->h_zg[q] = zpre[q + 1] - zpre[q];
+    CK(cudaMemcpyAsync(c->d_zpre, zpre.data(), (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->vo_next, c->vo, (G + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c->vo_top, c->vo, (G + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  } else {
+    c->h_zg[0] = z;
+  }
+  CKLAUNCH();
+  next->n = kc;
+  c->compacted = true;
+  c->iso_z = z;
+  c->isob_cur = 0;
+  c->kc_top = kc;
+  return 0;
+}
+
+// A compact pass's recorded level and coarse graph in the full numbering
+// (parity dumps only): the pass graph had n compact vertices, its level k
+// compact communities; isob[isob_cur ^ 1] and isob[isob_cur] hold the
+// isolated counts before them.
+int record_full_numbering(louvain_ctx* c, PassRec& pr, int64_t n, int64_t k) {
+  const int64_t z = c->iso_z;
+  std::vector<int32_t> before(n), after(k);
+  if (n) CK(cudaMemcpyAsync(before.data(), c->isob[c->isob_cur ^ 1], n * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            c->stream));
+  if (k) CK(cudaMemcpyAsync(after.data(), c->isob[c->isob_cur], k * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  // full id of the r-th isolated community after the renumbering
+  auto iso_id = [&](int64_t r) -> int32_t {
+    const int64_t j = std::upper_bound(after.begin(), after.end(), (int32_t)r) - after.begin();
+    return (int32_t)(j + r);
+  };
+  if (!pr.level.empty()) {
+    std::vector<int32_t> full(n + z);
+    int64_t j = 0;
+    for (int64_t x = 0; x < n + z; ++x) {
+      if (j < n && j + before[j] == x) {
+        const int32_t L = pr.level[j++];
+        full[x] = L + after[L];
+      } else {
+        full[x] = iso_id(x - j);
+      }
+    }
+    pr.level.swap(full);
+  }
+  if (pr.info.coarse_built) {
+    std::vector<int64_t> off(k + z + 1, 0);
+    std::vector<int32_t> col(pr.ccol.size());
+    int64_t j = 0;
+    for (int64_t R = 0; R < k + z; ++R) {
+      int64_t len = 0;
+      if (j < k && j + after[j] == R) {
+        len = pr.coff[j + 1] - pr.coff[j];
+        for (int64_t x = pr.coff[j]; x < pr.coff[j + 1]; ++x) col[x] = pr.ccol[x] + after[pr.ccol[x]];
+        ++j;
+      }
+      off[R + 1] = off[R] + len;
+    }
+    pr.coff.swap(off);
+    pr.ccol.swap(col);
+  }
+  return 0;
+}
+
 // One pass on graph g (weights W), coarse graphs use W2.  Every graph that
 // has not stopped takes part; a graph stops after a pass with no move, a
 // pass whose gain is <= pass_tolerance, or the last pass.  Returns 0 and sets
@@ -907,7 +1041,8 @@ int run_pass(louvain_ctx* c, const PassState& g, int pass, double* tol, bool wid
   const int64_t G = c->G;
   PassRec pr;
   memset(&pr.info, 0, sizeof(pr.info));
-  pr.info.n = g.n;
+  const int64_t iso = c->compacted ? c->iso_z : 0;   // isolated communities outside the pass graph
+  pr.info.n = g.n + iso;
   pr.info.nnz = g.nnz;
   CK(cudaEventRecord(c->ev[0], s));
   // pass 0 of louvain_run_from starts from the caller's membership (in memb)
@@ -960,7 +1095,7 @@ int run_pass(louvain_ctx* c, const PassState& g, int pass, double* tol, bool wid
     CK(cudaEventSynchronize(c->ev[2]));
     cudaEventElapsedTime(&ms_init, c->ev[0], c->ev[1]);
     cudaEventElapsedTime(&ms_lm, c->ev[1], c->ev[2]);
-    pr.info.k = g.n;
+    pr.info.k = g.n + iso;
     pr.info.n_after_hi = pr.info.n_before_hi;
     pr.info.n_after_lo = pr.info.n_before_lo;
     pr.info.lm_ms = ms_lm;
@@ -983,9 +1118,14 @@ int run_pass(louvain_ctx* c, const PassState& g, int pass, double* tol, bool wid
     scan_i64(c->kcount, c->vo_next, G, c->vo_next + G, c->tmp, s);
     CK(cudaMemcpyAsync(c->vo_top, c->vo_next, (G + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
   }
+  if (c->compacted) {
+    carry_isob(c->used, c->newid, c->isob[c->isob_cur], g.n, c->isob[c->isob_cur ^ 1], s);
+    c->isob_cur ^= 1;
+  }
   CKLAUNCH();
   int64_t k = 0;
   if (int r = fetch(c, &k, c->scal, sizeof(int64_t))) return r;
+  if (c->compacted) c->kc_top = k;
   std::vector<int64_t> vo_next;
   if (multi) {
     vo_next.resize(G + 1);
@@ -1012,12 +1152,12 @@ int run_pass(louvain_ctx* c, const PassState& g, int pass, double* tol, bool wid
     } else {
       const i128 gain = nafter[q] - st.qnum;
       st.qnum = nafter[q];
-      st.k = multi ? vo_next[q + 1] - vo_next[q] : k;
+      st.k = (multi ? vo_next[q + 1] - vo_next[q] : k) + (c->compacted ? c->h_zg[q] : 0);
       st.stopped = dbl(gain) / dbl((i128)st.M * st.M) <= c->opt.pass_tolerance || pass + 1 == c->opt.max_passes;
     }
     all_stopped = all_stopped && st.stopped;
   }
-  pr.info.k = k;
+  pr.info.k = k + iso;
   pr.info.n_after_hi = (int64_t)(c->gst[0].qnum >> 64);
   pr.info.n_after_lo = (uint64_t)c->gst[0].qnum;
   pr.info.level_recorded = c->opt.record_levels ? 1 : 0;
@@ -1036,11 +1176,15 @@ int run_pass(louvain_ctx* c, const PassState& g, int pass, double* tol, bool wid
     if (c->opt.record_levels)
       if (int r = record_coarse<W2>(c, pr, *next)) return r;
     *tol = *tol / c->opt.tolerance_decline;
+    if (pass == 0 && !c->compacted && c->iso0 >= kCompactMinIsolated)
+      if (int r = compact_coarse(c, next, k, vo_next)) return r;
     if (multi) {
       std::swap(c->gid, c->gid_next);
       std::swap(c->vo, c->vo_next);
     }
   }
+  if (c->opt.record_levels && iso > 0)
+    if (int r = record_full_numbering(c, pr, g.n, k)) return r;
   cudaEventElapsedTime(&ms_init, c->ev[0], c->ev[1]);
   cudaEventElapsedTime(&ms_lm, c->ev[1], c->ev[2]);
   pr.info.lm_ms = ms_lm;
@@ -1092,6 +1236,11 @@ int run_all(louvain_ctx* c) {
   CK(cudaEventRecord(c->ev[6], s));
   iota_i32(c->top, c->n0, s);
   if (int r = init_run_state(c)) return r;
+  c->compacted = false;
+  c->iso_z = 0;
+  c->isob_cur = 0;
+  c->kc_top = 0;
+  c->h_zg.assign(G, 0);
   const bool wide = c->M >= (1ll << 31);           // M^2 >= 2^62: 128-bit gains
   const bool coarse64 = c->M >= (1ll << 31) - 1;   // coarse weights can exceed int32
   PassState g{c->n0, c->nnz0, c->off0, c->col0, (void*)c->w0, -1};
@@ -1115,6 +1264,10 @@ int run_all(louvain_ctx* c) {
     if (stop) break;
     std::swap(c->K, c->Knext);
     g = next;
+  }
+  if (c->compacted) {   // top[] back in the full numbering
+    finalize_top(c->top, c->n0, c->isob[c->isob_cur], c->kc_top, G > 1 ? c->vo_top : nullptr, c->d_zpre, G, s);
+    CKLAUNCH();
   }
   CK(cudaEventRecord(c->ev[7], s));
   CK(cudaEventSynchronize(c->ev[7]));
@@ -1256,7 +1409,10 @@ int alloc_arena(louvain_ctx* c, int64_t n, int64_t nnz) {
   ALLOC(c->acc, 8);
   ALLOC(c->flags, 4);
   ALLOC(c->d_iter, 4);
-  ALLOC(c->scal, 8);
+  ALLOC(c->scal, 16);
+  ALLOC(c->isob[0], n);
+  ALLOC(c->isob[1], n);
+  ALLOC(c->d_zpre, N1 + 1);
   ALLOC(c->gid0, n);
   ALLOC(c->gid_a, n);
   ALLOC(c->gid_b, n);
@@ -1488,6 +1644,14 @@ int load_graphs(louvain_ctx* c, int64_t G, const int64_t* vo, int64_t n, int64_t
     if (int r = fetch(c, c->h_acc, c->acc, 2 * sizeof(unsigned long long))) return r;
     const u128 SS = ((u128)c->h_acc[1] << 64) | (u128)c->h_acc[0];
     c->qnum0 = (i128)c->M0 * (i128)loops - (i128)SS;
+  }
+  {
+    // vertices without entries: their communities may leave the later passes
+    CK(cudaMemsetAsync(c->acc, 0, sizeof(unsigned long long), s));
+    count_empty_rows(c->off0, n, c->acc, s);
+    CKLAUNCH();
+    if (int r = fetch(c, c->h_acc, c->acc, sizeof(unsigned long long))) return r;
+    c->iso0 = (int64_t)c->h_acc[0];
   }
   // per graph: M, vertices, singleton numerator
   if (int r = host_graph_buffers(c, G)) return r;

@@ -54,6 +54,11 @@ struct ClassSpec {
   int32_t pass;
   int32_t single_cat;
   const int32_t* colour;   // colour classes of the pass graph's vertices, or null
+  // a compact pass graph (isolated communities left out): the isolated count
+  // before each vertex and, per graph, before the graph's first vertex, so
+  // that classes follow the full numbering (null: the ids are full)
+  const int32_t* isob;
+  const int64_t* zpre;
 };
 // splitmix64 finaliser of (pass, iteration), folded to 32 bits, never 0.
 __host__ __device__ inline uint32_t class_salt(int pass, int iter) {
@@ -74,6 +79,9 @@ __device__ __forceinline__ int vertex_class(int64_t i, const int32_t* gid, const
     const int g = gid[i];
     local = i - vo[g];
     cat = gcat[g];
+    if (cs.isob) local += cs.isob[i] - cs.zpre[g];
+  } else if (cs.isob) {
+    local += cs.isob[i];
   }
   const uint32_t Pg = (uint32_t)(cat == kCatSmall ? cs.Ps : (cat == kCatSparse ? cs.Pl : cs.Pb));
   const int mode = cat == kCatSmall ? cs.mode_s : cs.mode_b;
@@ -248,12 +256,38 @@ void localize_membership(const int32_t* top, const int32_t* gid0, const int64_t*
                          cudaStream_t s);
 void graph_entries(const int64_t* off, const int64_t* vo, int64_t G, int64_t* out, cudaStream_t s);
 // Colour classes: capped greedy colouring of a pass graph (graph_ops.cu).
+// Isolated communities leave the pass graphs after pass 0 (graph_ops.cu):
+// flags of non-empty rows; the compacted offsets, degrees, graph ids and
+// isolated counts (isob), columns renumbered in place and top[] rewritten;
+// the counts carried through a pass's renumbering; top[] back in the full
+// numbering at the end (and the per-graph offsets vo_top shifted by zpre).
+void nonempty_rows(const int64_t* off, int64_t k, int32_t* flag, cudaStream_t s);
+void compact_rows(const int64_t* off, int64_t k, int64_t nnz, const int32_t* flag, const int32_t* pos,
+                  const long long* Kin, const int32_t* gid_in, int64_t* off_out, long long* K_out, int32_t* gid_out,
+                  int32_t* isob, int32_t* col, int32_t* top, int64_t n0, cudaStream_t s);
+void carry_isob(const int32_t* used, const int32_t* newid, const int32_t* isob, int64_t n, int32_t* isob_next,
+                cudaStream_t s);
+void finalize_top(int32_t* top, int64_t n0, const int32_t* isob, int64_t kc, int64_t* vo_top, const int64_t* zpre,
+                  int64_t G, cudaStream_t s);
+void count_empty_rows(const int64_t* off, int64_t n, unsigned long long* out, cudaStream_t s);
+void compact_vo(const int64_t* vo_full, int64_t G, const int32_t* pos, int64_t k, int64_t kc, int64_t* vo_c,
+                cudaStream_t s);
+
+// Colouring frontiers: vertices of degree above kColourHubDegree go to the
+// hub frontier (hfront / hnext), whose rows many blocks share; hmask / hdone
+// hold a zeroed mask and item counter per hub-frontier slot (at most
+// nnz / kColourHubDegree + 1 slots), left zeroed after every round.
+constexpr int64_t kColourHubDegree = 2048;
+// isob / zpre: as in ClassSpec (priorities follow the full numbering).
 void colour_init(const int64_t* off, const int32_t* col, int64_t n, const int32_t* gid, const int64_t* vo,
-                 uint32_t salt, int32_t* cnt, int32_t* cls, int32_t* front, unsigned long long* nfront,
-                 cudaStream_t s);
+                 const int32_t* isob, const int64_t* zpre, uint32_t salt, int32_t* cnt, int32_t* cls, int32_t* front,
+                 unsigned long long* nfront, int32_t* hfront, unsigned long long* nhfront, cudaStream_t s);
 void colour_round(const int64_t* off, const int32_t* col, int64_t n, const int32_t* gid, const int64_t* vo,
-                  uint32_t salt, const int32_t* front, const unsigned long long* nfront, int32_t* cnt, int32_t* cls,
-                  int32_t* next, unsigned long long* nnext, unsigned long long* total, int* flags, cudaStream_t s);
+                  const int32_t* isob, const int64_t* zpre, uint32_t salt, const int32_t* front,
+                  const unsigned long long* nfront, const int32_t* hfront,
+                  const unsigned long long* nhfront, int32_t* cnt, int32_t* cls, int32_t* next,
+                  unsigned long long* nnext, int32_t* hnext, unsigned long long* nhnext, unsigned long long* total,
+                  unsigned long long* hmask, int32_t* hdone, int* flags, cudaStream_t s);
 void class_max(const int32_t* cls, int64_t n, int* out, cudaStream_t s);
 void graph_ids(const int64_t* vo, int G, int64_t n, int32_t* gid, const int64_t* off, const int32_t* col, int* flags,
                cudaStream_t s);

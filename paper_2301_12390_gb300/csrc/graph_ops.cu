@@ -615,9 +615,13 @@ void apply_level(const int32_t* memb, const int32_t* newid, int64_t n, int32_t* 
   if (n > 0) (count_launch(), apply_level_k<<<grid1d(n), kT, 0, s>>>(memb, newid, n, level));
 }
 
+// top[v] = level[top[v]]; a negative entry (a vertex whose community left
+// the pass graphs with the isolated vertices, see compact_rows) stays.
 __global__ void compose_top_k(int32_t* top, int64_t n0, const int32_t* level) {
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n0; v += (int64_t)gridDim.x * blockDim.x)
-    top[v] = level[top[v]];
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n0; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t t = top[v];
+    if (t >= 0) top[v] = level[t];
+  }
 }
 void compose_top(int32_t* top, int64_t n0, const int32_t* level, cudaStream_t s) {
   if (n0 > 0) (count_launch(), compose_top_k<<<grid1d(n0), kT, 0, s>>>(top, n0, level));
@@ -631,6 +635,120 @@ __global__ void coarse_degrees_k(const int32_t* used, const int32_t* newid, cons
 void coarse_degrees(const int32_t* used, const int32_t* newid, const long long* sig, int64_t n, long long* Knext,
                     cudaStream_t s) {
   if (n > 0) (count_launch(), coarse_degrees_k<<<grid1d(n), kT, 0, s>>>(used, newid, sig, n, Knext));
+}
+
+// ------------------------------------------- isolated communities leave
+//
+// After pass 0 the communities of isolated vertices (empty coarse rows) are
+// singletons that can never move; the later pass graphs keep only the other
+// vertices, in the same order (compact ids).  isob[j] counts the isolated
+// vertices before compact vertex j in the full numbering, so that full id =
+// j + isob[j]; a vertex of the input whose community is isolated keeps in
+// top[] -1 - (its rank among the isolated ones) until finalize_top.
+
+__global__ void nonempty_rows_k(const int64_t* __restrict__ off, int64_t k, int32_t* __restrict__ flag) {
+  for (int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; C < k; C += (int64_t)gridDim.x * blockDim.x)
+    flag[C] = off[C + 1] > off[C] ? 1 : 0;
+}
+void nonempty_rows(const int64_t* off, int64_t k, int32_t* flag, cudaStream_t s) {
+  if (k > 0) (count_launch(), nonempty_rows_k<<<grid1d(k), kT, 0, s>>>(off, k, flag));
+}
+
+__global__ void compact_rows_k(const int64_t* __restrict__ off, const int32_t* __restrict__ flag,
+                               const int32_t* __restrict__ pos, int64_t k, const long long* __restrict__ Kin,
+                               const int32_t* __restrict__ gid_in, int64_t* __restrict__ off_out,
+                               long long* __restrict__ K_out, int32_t* __restrict__ gid_out,
+                               int32_t* __restrict__ isob) {
+  for (int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; C < k; C += (int64_t)gridDim.x * blockDim.x)
+    if (flag[C]) {
+      const int32_t j = pos[C];
+      off_out[j] = off[C];
+      K_out[j] = Kin[C];
+      if (gid_in) gid_out[j] = gid_in[C];
+      isob[j] = (int32_t)(C - j);
+    }
+}
+__global__ void compact_cols_k(int32_t* __restrict__ col, int64_t nnz, const int32_t* __restrict__ pos) {
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nnz; x += (int64_t)gridDim.x * blockDim.x)
+    col[x] = pos[col[x]];
+}
+__global__ void compact_top_k(int32_t* __restrict__ top, int64_t n0, const int32_t* __restrict__ flag,
+                              const int32_t* __restrict__ pos) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n0; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t y = top[v];
+    top[v] = flag[y] ? pos[y] : -1 - (y - pos[y]);
+  }
+}
+void compact_rows(const int64_t* off, int64_t k, int64_t nnz, const int32_t* flag, const int32_t* pos,
+                  const long long* Kin, const int32_t* gid_in, int64_t* off_out, long long* K_out, int32_t* gid_out,
+                  int32_t* isob, int32_t* col, int32_t* top, int64_t n0, cudaStream_t s) {
+  if (k > 0)
+    (count_launch(), compact_rows_k<<<grid1d(k), kT, 0, s>>>(off, flag, pos, k, Kin, gid_in, off_out, K_out, gid_out,
+                                                              isob));
+  if (nnz > 0) (count_launch(), compact_cols_k<<<grid1d(nnz), kT, 0, s>>>(col, nnz, pos));
+  if (n0 > 0) (count_launch(), compact_top_k<<<grid1d(n0), kT, 0, s>>>(top, n0, flag, pos));
+}
+
+// After a pass's renumbering: the isolated count before each new community.
+__global__ void carry_isob_k(const int32_t* __restrict__ used, const int32_t* __restrict__ newid,
+                             const int32_t* __restrict__ isob, int64_t n, int32_t* __restrict__ isob_next) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+    if (used[c]) isob_next[newid[c]] = isob[c];
+}
+void carry_isob(const int32_t* used, const int32_t* newid, const int32_t* isob, int64_t n, int32_t* isob_next,
+                cudaStream_t s) {
+  if (n > 0) (count_launch(), carry_isob_k<<<grid1d(n), kT, 0, s>>>(used, newid, isob, n, isob_next));
+}
+
+// The top membership in the full numbering: a compact community j is
+// j + isob[j]; the r-th isolated community follows the compact communities
+// with at most r isolated ones before them (isob is non-decreasing).
+__global__ void finalize_top_k(int32_t* __restrict__ top, int64_t n0, const int32_t* __restrict__ isob, int64_t kc) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n0; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t t = top[v];
+    if (t >= 0) {
+      top[v] = t + isob[t];
+    } else {
+      const int32_t r = -1 - t;
+      int64_t lo = 0, hi = kc;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (isob[mid] <= r) lo = mid + 1; else hi = mid;
+      }
+      top[v] = (int32_t)(lo + r);
+    }
+  }
+}
+__global__ void shift_vo_k(int64_t* vo, const int64_t* __restrict__ zpre, int64_t m) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < m; g += (int64_t)gridDim.x * blockDim.x)
+    vo[g] += zpre[g];
+}
+void finalize_top(int32_t* top, int64_t n0, const int32_t* isob, int64_t kc, int64_t* vo_top, const int64_t* zpre,
+                  int64_t G, cudaStream_t s) {
+  if (n0 > 0) (count_launch(), finalize_top_k<<<grid1d(n0), kT, 0, s>>>(top, n0, isob, kc));
+  if (vo_top) (count_launch(), shift_vo_k<<<grid1d(G + 1), kT, 0, s>>>(vo_top, zpre, G + 1));
+}
+
+// Per-graph first compact vertex: vo_c[g] = pos[vo_full[g]] (kc at the end).
+__global__ void compact_vo_k(const int64_t* __restrict__ vo_full, int64_t m, const int32_t* __restrict__ pos,
+                             int64_t k, int64_t kc, int64_t* __restrict__ vo_c) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < m; g += (int64_t)gridDim.x * blockDim.x)
+    vo_c[g] = vo_full[g] < k ? pos[vo_full[g]] : kc;
+}
+void compact_vo(const int64_t* vo_full, int64_t G, const int32_t* pos, int64_t k, int64_t kc, int64_t* vo_c,
+                cudaStream_t s) {
+  (count_launch(), compact_vo_k<<<grid1d(G + 1), kT, 0, s>>>(vo_full, G + 1, pos, k, kc, vo_c));
+}
+
+__global__ void count_empty_rows_k(const int64_t* __restrict__ off, int64_t n, unsigned long long* out) {
+  unsigned c = 0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    c += off[v + 1] == off[v] ? 1u : 0u;
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, (unsigned long long)c);
+}
+void count_empty_rows(const int64_t* off, int64_t n, unsigned long long* out, cudaStream_t s) {
+  if (n > 0) (count_launch(), count_empty_rows_k<<<grid1d(n), kT, 0, s>>>(off, n, out));
 }
 
 // ------------------------------------------------------------ aggregation
@@ -1381,79 +1499,172 @@ void graph_entries(const int64_t* off, const int64_t* vo, int64_t G, int64_t* ou
 // Edges never join two graphs of a batch, so global ids order ties as local
 // ones do.
 
-__device__ __forceinline__ uint32_t colour_pri(int64_t v, const int32_t* gid, const int64_t* vo, uint32_t salt) {
-  const int64_t local = gid ? v - vo[gid[v]] : v;
+__device__ __forceinline__ uint32_t colour_pri(int64_t v, const int32_t* gid, const int64_t* vo, const int32_t* isob,
+                                               const int64_t* zpre, uint32_t salt) {
+  int64_t local = gid ? v - vo[gid[v]] : v;
+  if (isob) local += isob[v] - (gid ? zpre[gid[v]] : 0);   // the full numbering's id
   return hash32((uint32_t)local ^ salt);
+}
+
+// Frontier lists of the colouring: a vertex of degree above kColourHubDeg
+// (a hub) goes to the hub frontier, whose rows are split over many blocks.
+constexpr int64_t kColourHubDeg = kColourHubDegree;
+constexpr int64_t kColourChunk = 4096;   // entries of a hub row per block item
+constexpr int kColourHubBlocks = 152 * 4;
+
+__device__ __forceinline__ void colour_push(const int64_t* __restrict__ off, int32_t u, int32_t* front,
+                                            unsigned long long* nfront, int32_t* hfront,
+                                            unsigned long long* nhfront) {
+  if (off[u + 1] - off[u] > kColourHubDeg) hfront[atomicAdd(nhfront, 1ull)] = u;
+  else front[atomicAdd(nfront, 1ull)] = u;
 }
 
 // Warp per vertex: cnt[v] = its preceding neighbours; those with none start.
 __global__ void colour_init_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col, int64_t n,
-                              const int32_t* __restrict__ gid, const int64_t* __restrict__ vo, uint32_t salt,
+                              const int32_t* __restrict__ gid, const int64_t* __restrict__ vo,
+                              const int32_t* __restrict__ isob, const int64_t* __restrict__ zpre, uint32_t salt,
                               int32_t* __restrict__ cnt, int32_t* __restrict__ cls, int32_t* __restrict__ front,
-                              unsigned long long* __restrict__ nfront) {
+                              unsigned long long* __restrict__ nfront, int32_t* __restrict__ hfront,
+                              unsigned long long* __restrict__ nhfront) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t ws = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t v = w0; v < n; v += ws) {   // uniform across the warp
-    const uint32_t pv = colour_pri(v, gid, vo, salt);
+    const uint32_t pv = colour_pri(v, gid, vo, isob, zpre, salt);
     unsigned c = 0;
     for (int64_t x = off[v] + lane; x < off[v + 1]; x += kWarp) {
       const int32_t u = col[x];
       if (u == v) continue;
-      const uint32_t pu = colour_pri(u, gid, vo, salt);
+      const uint32_t pu = colour_pri(u, gid, vo, isob, zpre, salt);
       if (pu > pv || (pu == pv && u < v)) ++c;
     }
     c = __reduce_add_sync(0xffffffffu, c);
     if (lane == 0) {
       cnt[v] = (int32_t)c;
       cls[v] = -1;
-      if (c == 0) front[atomicAdd(nfront, 1ull)] = (int32_t)v;
+      if (c == 0) colour_push(off, (int32_t)v, front, nfront, hfront, nhfront);
     }
   }
 }
 
-// Warp per frontier vertex: its class from its preceding neighbours' classes,
-// then one predecessor fewer for each succeeding neighbour; those left with
-// none form the next frontier.  A class outside 0..63 (a preceding neighbour
-// without one) sets flags bit 1 and is not used.
+// One Jones-Plassmann round.  Blocks below gridDim.x - kColourHubBlocks:
+// a warp per frontier vertex takes its class from its preceding neighbours'
+// classes, then counts itself off its succeeding neighbours; those left with
+// no predecessor form the next frontier (hubs apart).  The last
+// kColourHubBlocks blocks do the same for the hub frontier with each hub row
+// split into kColourChunk-entry items: an item ORs its preceding neighbours'
+// classes into the hub's mask (hmask) and counts itself off its succeeding
+// neighbours; the block that finishes a hub's last item (hdone, after a
+// fence) takes the class from the complete mask and clears the mask and
+// counter for the next round.  No block waits for another.  Frontier
+// vertices are never neighbours, so the items of one round are independent.
+// A class outside 0..63 (a preceding neighbour without one) sets flags bit 1
+// and is not used.
 __global__ void colour_round_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                               const int32_t* __restrict__ gid, const int64_t* __restrict__ vo, uint32_t salt,
+                               const int32_t* __restrict__ gid, const int64_t* __restrict__ vo,
+                               const int32_t* __restrict__ isob, const int64_t* __restrict__ zpre, uint32_t salt,
                                const int32_t* __restrict__ front, const unsigned long long* __restrict__ nfront,
+                               const int32_t* __restrict__ hfront, const unsigned long long* __restrict__ nhfront,
                                int32_t* __restrict__ cnt, int32_t* __restrict__ cls, int32_t* __restrict__ next,
-                               unsigned long long* __restrict__ nnext, unsigned long long* __restrict__ total,
+                               unsigned long long* __restrict__ nnext, int32_t* __restrict__ hnext,
+                               unsigned long long* __restrict__ nhnext, unsigned long long* __restrict__ total,
+                               unsigned long long* __restrict__ hmask, int32_t* __restrict__ hdone,
                                int* __restrict__ flags) {
   const int lane = threadIdx.x & 31;
-  const int64_t nf = (int64_t)*nfront;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *total += (unsigned long long)nf;
-  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t ws = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t t = w0; t < nf; t += ws) {   // uniform across the warp
-    const int32_t v = front[t];
-    const uint32_t pv = colour_pri(v, gid, vo, salt);
+  const int64_t nf = (int64_t)*nfront, nh = (int64_t)*nhfront;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *total += (unsigned long long)(nf + nh);
+  const int64_t wblocks = (int64_t)gridDim.x - kColourHubBlocks;
+  if ((int64_t)blockIdx.x < wblocks) {
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t ws = (wblocks * blockDim.x) >> 5;
+    for (int64_t t = w0; t < nf; t += ws) {   // uniform across the warp
+      const int32_t v = front[t];
+      const uint32_t pv = colour_pri(v, gid, vo, isob, zpre, salt);
+      unsigned long long used = 0;
+      bool bad = false;
+      for (int64_t x = off[v] + lane; x < off[v + 1]; x += kWarp) {
+        const int32_t u = col[x];
+        if (u == v) continue;
+        const uint32_t pu = colour_pri(u, gid, vo, isob, zpre, salt);
+        if (pu > pv || (pu == pv && u < v)) {
+          const int32_t cu = cls[u];
+          if (cu >= 0 && cu < 64) used |= 1ull << cu;
+          else bad = true;
+        }
+      }
+      const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)used);
+      const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(used >> 32));
+      const unsigned long long free_cls = ~(((unsigned long long)hi << 32) | lo) & 0x7fffffffffffffffull;
+      if (lane == 0) cls[v] = free_cls ? __ffsll((long long)free_cls) - 1 : 63;
+      if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flags, 2);
+      for (int64_t x = off[v] + lane; x < off[v + 1]; x += kWarp) {
+        const int32_t u = col[x];
+        if (u == v) continue;
+        const uint32_t pu = colour_pri(u, gid, vo, isob, zpre, salt);
+        if (pv > pu || (pv == pu && v < u))
+          if (atomicSub(cnt + u, 1) == 1) colour_push(off, u, next, nnext, hnext, nhnext);
+      }
+    }
+    return;
+  }
+  // hub items: (hub slot, chunk) in hub-frontier order
+  __shared__ unsigned long long s_mask[8];
+  __shared__ int s_bad;
+  const int64_t hb = (int64_t)blockIdx.x - wblocks;
+  int64_t h = 0, h_first = 0;   // hub slot h owns items [h_first, h_first + chunks(h))
+  for (int64_t item = hb;; item += kColourHubBlocks) {
+    int64_t nc = 0;
+    while (h < nh) {
+      const int32_t v = hfront[h];
+      nc = (off[v + 1] - off[v] + kColourChunk - 1) / kColourChunk;
+      if (item < h_first + nc) break;
+      h_first += nc;
+      ++h;
+    }
+    if (h >= nh) break;   // uniform across the block
+    const int32_t v = hfront[h];
+    const uint32_t pv = colour_pri(v, gid, vo, isob, zpre, salt);
+    const int64_t x0 = off[v] + (item - h_first) * kColourChunk, x1 = min(off[v + 1], x0 + kColourChunk);
     unsigned long long used = 0;
     bool bad = false;
-    for (int64_t x = off[v] + lane; x < off[v + 1]; x += kWarp) {
+    for (int64_t x = x0 + threadIdx.x; x < x1; x += blockDim.x) {
       const int32_t u = col[x];
       if (u == v) continue;
-      const uint32_t pu = colour_pri(u, gid, vo, salt);
+      const uint32_t pu = colour_pri(u, gid, vo, isob, zpre, salt);
       if (pu > pv || (pu == pv && u < v)) {
         const int32_t cu = cls[u];
         if (cu >= 0 && cu < 64) used |= 1ull << cu;
         else bad = true;
+      } else if (atomicSub(cnt + u, 1) == 1) {
+        colour_push(off, u, next, nnext, hnext, nhnext);
       }
     }
     const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)used);
     const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(used >> 32));
-    const unsigned long long free_cls = ~(((unsigned long long)hi << 32) | lo) & 0x7fffffffffffffffull;
-    if (lane == 0) cls[v] = free_cls ? __ffsll((long long)free_cls) - 1 : 63;
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flags, 2);
-    for (int64_t x = off[v] + lane; x < off[v + 1]; x += kWarp) {
-      const int32_t u = col[x];
-      if (u == v) continue;
-      const uint32_t pu = colour_pri(u, gid, vo, salt);
-      if (pv > pu || (pv == pu && v < u))
-        if (atomicSub(cnt + u, 1) == 1) next[atomicAdd(nnext, 1ull)] = u;
+    const bool wbad = __any_sync(0xffffffffu, bad);
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    if (lane == 0) {
+      s_mask[threadIdx.x >> 5] = ((unsigned long long)hi << 32) | lo;
+      if (wbad) s_bad = 1;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long m = 0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m |= s_mask[k];
+      if (s_bad) atomicOr(flags, 2);
+      if (m) atomicOr(hmask + h, m);
+      __threadfence();
+      if (atomicAdd(hdone + h, 1) == (int)nc - 1) {   // this hub's last item: its mask is complete
+        __threadfence();
+        const unsigned long long full = atomicOr(hmask + h, 0ull);
+        const unsigned long long free_cls = ~full & 0x7fffffffffffffffull;
+        cls[v] = free_cls ? __ffsll((long long)free_cls) - 1 : 63;
+        hmask[h] = 0;
+        hdone[h] = 0;
+      }
+    }
+    __syncthreads();   // s_mask and s_bad are reused by the next item
   }
 }
 
@@ -1471,16 +1682,20 @@ static unsigned warp_grid(int64_t items) {
 }
 
 void colour_init(const int64_t* off, const int32_t* col, int64_t n, const int32_t* gid, const int64_t* vo,
-                 uint32_t salt, int32_t* cnt, int32_t* cls, int32_t* front, unsigned long long* nfront,
-                 cudaStream_t s) {
-  if (n > 0) (count_launch(), colour_init_k<<<warp_grid(n), 256, 0, s>>>(off, col, n, gid, vo, salt, cnt, cls, front,
-                                                                         nfront));
+                 const int32_t* isob, const int64_t* zpre, uint32_t salt, int32_t* cnt, int32_t* cls, int32_t* front,
+                 unsigned long long* nfront, int32_t* hfront, unsigned long long* nhfront, cudaStream_t s) {
+  if (n > 0) (count_launch(), colour_init_k<<<warp_grid(n), 256, 0, s>>>(off, col, n, gid, vo, isob, zpre, salt, cnt,
+                                                                         cls, front, nfront, hfront, nhfront));
 }
 void colour_round(const int64_t* off, const int32_t* col, int64_t n, const int32_t* gid, const int64_t* vo,
-                  uint32_t salt, const int32_t* front, const unsigned long long* nfront, int32_t* cnt, int32_t* cls,
-                  int32_t* next, unsigned long long* nnext, unsigned long long* total, int* flags, cudaStream_t s) {
-  (count_launch(), colour_round_k<<<warp_grid(n), 256, 0, s>>>(off, col, gid, vo, salt, front, nfront, cnt, cls,
-                                                                next, nnext, total, flags));
+                  const int32_t* isob, const int64_t* zpre, uint32_t salt, const int32_t* front,
+                  const unsigned long long* nfront, const int32_t* hfront,
+                  const unsigned long long* nhfront, int32_t* cnt, int32_t* cls, int32_t* next,
+                  unsigned long long* nnext, int32_t* hnext, unsigned long long* nhnext, unsigned long long* total,
+                  unsigned long long* hmask, int32_t* hdone, int* flags, cudaStream_t s) {
+  (count_launch(), colour_round_k<<<warp_grid(n) + kColourHubBlocks, 256, 0, s>>>(
+                       off, col, gid, vo, isob, zpre, salt, front, nfront, hfront, nhfront, cnt, cls, next, nnext,
+                       hnext, nhnext, total, hmask, hdone, flags));
 }
 void class_max(const int32_t* cls, int64_t n, int* out, cudaStream_t s) {
   if (n > 0) (count_launch(), class_max_k<<<grid1d(n), kT, 0, s>>>(cls, n, out));
