@@ -46,11 +46,11 @@ WORKLOADS = {
 METRIC = "edges/sec in local-moving"
 L2_BYTES = 126 << 20   # GB300 L2 (about 126 MB)
 # DRAM bytes the local-moving phase moves per algorithmic byte, from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum) of every local-moving
-# launch of an asynchronous R-MAT s22 run with L2 kept between launches:
-# 13.85 GB for 8.86 GB of algorithmic bytes.  Taken on the current kernels;
-# None where no capture was taken.
-LM_TRAFFIC_PER_BYTE = {("rmat22", "async"): 1.56}
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of every
+# local-moving launch of an asynchronous R-MAT s22 run with L2 kept between
+# launches: 13.07 GB for 4.66 GB of algorithmic bytes.  Taken on the current
+# kernels; None where no capture was taken.
+LM_TRAFFIC_PER_BYTE = {("rmat22", "async"): 2.81}
 UNIT = "edges/s"
 
 
