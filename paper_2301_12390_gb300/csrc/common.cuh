@@ -283,6 +283,7 @@ struct LMArgs {
   const int64_t* hbase;      // table offset of hub h (the class's first hub at hbase[0])
   const int64_t* spre;       // first slot chunk of hub h (absolute within the pass)
   unsigned long long* hkid;  // K_{i->d} of hub h, looked up before the scan clears the table
+  int32_t* hdone;            // scan blocks of hub h finished so far (back to 0 by the last one)
   int32_t* hmoved;           // iteration + 1 when hub h moved in that iteration
   long long* hpart;          // per slot chunk: best gain (lo, hi)
   int32_t* hpart_c;          // per slot chunk: its community

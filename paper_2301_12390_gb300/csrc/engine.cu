@@ -145,6 +145,7 @@ struct louvain_ctx {
   louvain_ctx* sub = nullptr;  // louvain_run_partitioned: the parts' context (same device and stream)
   int32_t* crow = nullptr;     // aggregation: first row of each relabel chunk      // aggregation: direct-table first key per global community, or -1
   unsigned long long* hkid = nullptr;
+  int32_t* hdone = nullptr;            // local moving: finished scan chunks per hub (zero between uses)
   long long* hpart = nullptr;
   int32_t* hpart_c = nullptr;
   int64_t npart = 0;
@@ -521,6 +522,7 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
   a.hvals = c->gvals;
   a.hpart = c->hpart;
   a.hpart_c = c->hpart_c;
+  a.hdone = c->hdone;
   a.d_iter = c->d_iter;
   a.stamps[0] = c->stamp[0];
   a.stamps[1] = c->stamp[1];
@@ -586,6 +588,7 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
           ah.hbase = c->gbase + h0;
           ah.spre = c->spre + h0;
           ah.hkid = c->hkid + h0;
+          ah.hdone = c->hdone + h0;
           ah.hmoved = c->hmoved + h0;
           lm_launch_hubs<W>(ah, wide, async, c->list + hub0 + h0, (int)(h1 - h0), c->chunk_pre + h0,
                             hchunks[h1] - hchunks[h0], c->spre + h0, hschunks[h1] - hschunks[h0], c->aux[kHubBucket]);
@@ -617,6 +620,7 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
         ah.hbase = c->gbase + h0;
         ah.spre = c->spre + h0;
         ah.hkid = c->hkid + h0;
+        ah.hdone = c->hdone + h0;
         ah.hmoved = c->hmoved + h0;
         lm_launch_hubs<W>(ah, wide, async, c->list + hub0 + h0, (int)(h1 - h0), c->chunk_pre + h0,
                           hchunks[h1] - hchunks[h0], c->spre + h0, hschunks[h1] - hschunks[h0], c->aux[kHubBucket]);
@@ -1393,6 +1397,7 @@ int alloc_arena(louvain_ctx* c, int64_t n, int64_t nnz) {
   ALLOC(c->spre, N1);
   ALLOC(c->glo, N1);
   ALLOC(c->hkid, N1);
+  ALLOC(c->hdone, N1);
   ALLOC(c->hmoved, N1);
   // slot chunks of all hubs: sum of ceil(2 deg / kSlotChunk) <= 2 nnz / kSlotChunk + #hubs
   c->npart = 2 * nnz / kSlotChunk + n + 16;   // every hub has at least one slot chunk
@@ -1613,6 +1618,7 @@ int load_graphs(louvain_ctx* c, int64_t G, const int64_t* vo, int64_t n, int64_t
     CK(cudaMemsetAsync(c->gkeys, 0xff, 2 * c->cap_nnz * sizeof(int32_t), s));
     CK(cudaMemsetAsync(c->gvals, 0, 2 * c->cap_nnz * sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(c->hkid, 0, (c->cap_n + 1) * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(c->hdone, 0, (c->cap_n + 1) * sizeof(int32_t), s));
     c->tables_dirty = false;
   }
   if (c->opt.validate) {

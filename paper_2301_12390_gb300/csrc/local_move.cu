@@ -691,9 +691,9 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 128 ? 8 : 2)
 //    to the hub's global table;
 // 2. scan: blocks are (hub, 4096-slot chunk) pairs; each evaluates the gain
 //    of every occupied slot, clears it, and leaves its chunk's best (and
-//    K_{i->d} of the slot holding d);
-// 3. final: one block per hub reduces the chunk bests and commits;
-// 4. mark (once per iteration, all classes): neighbours of the hubs that moved.
+//    K_{i->d} of the slot holding d); the last block of a hub reduces the
+//    chunk bests and commits;
+// 3. mark (once per iteration, all classes): neighbours of the hubs that moved.
 
 constexpr int kHubChunk = (int)kHubChunkEntries;
 
@@ -767,6 +767,11 @@ __global__ void __launch_bounds__(256) lm_hub_insert(LMArgs<W> a, const int32_t*
   if (!ok) atomicOr(&a.ctr->error, kErrProbe);
 }
 
+// Scan blocks are (hub, kSlotChunk-slot chunk) pairs: each evaluates the
+// gain of every occupied slot of its chunk, clears it, and leaves its chunk's
+// best; the block that finishes a hub's last chunk (a per-hub counter after a
+// fence) reduces the hub's chunk bests and commits the hub's move, so the
+// decision needs no launch of its own.  No block waits for another.
 template <typename W, bool WIDE, bool ASYNC>
 __global__ void __launch_bounds__(256) lm_hub_scan(LMArgs<W> a, const int32_t* __restrict__ hubs, int nhubs) {
   const IterView iv = iter_view(a);
@@ -775,6 +780,8 @@ __global__ void __launch_bounds__(256) lm_hub_scan(LMArgs<W> a, const int32_t* _
   __shared__ S red_g[NW];
   __shared__ int32_t red_c[NW];
   __shared__ unsigned red_n[NW];
+  __shared__ BlockAcc acc;
+  __shared__ int s_last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int h = find_item(a.spre, nhubs, blockIdx.x);
   const int32_t i = hubs[h];
@@ -782,6 +789,7 @@ __global__ void __launch_bounds__(256) lm_hub_scan(LMArgs<W> a, const int32_t* _
   long long M;
   int graph;
   if (!graph_of(a, i, &M, &graph)) return;
+  acc_init(acc);
   const int64_t q = (int64_t)blockIdx.x - (a.spre[h] - a.spre[0]);
   const int64_t b = a.off[i], e = a.off[i + 1];
   const int64_t cap = 2 * (e - b);
@@ -829,50 +837,38 @@ __global__ void __launch_bounds__(256) lm_hub_scan(LMArgs<W> a, const int32_t* _
     bc = lane < NW ? red_c[lane] : -1;
     warp_argmax(bg, bc);
     ncand = __reduce_add_sync(0xffffffffu, lane < NW ? red_n[lane] : 0u);
-    if (lane == 0 && ncand) atomicAdd(&a.ctr->cands, (unsigned long long)ncand);
     if (lane == 0) {
+      if (ncand) atomicAdd(&a.ctr->cands, (unsigned long long)ncand);
       const int64_t slot = a.spre[h] + q;
       u128 gu = (u128)(i128)bg;
       a.hpart[2 * slot] = (long long)(unsigned long long)gu;
       a.hpart[2 * slot + 1] = (long long)(unsigned long long)(gu >> 64);
       a.hpart_c[slot] = bc;
+      __threadfence();   // the chunk best (and K_{i->d}) before the count
+      const int nck = (int)(a.spre[h + 1] - a.spre[h]);
+      s_last = atomicAdd(a.hdone + h, 1) == nck - 1;
     }
   }
-}
-
-template <typename W, bool WIDE, bool ASYNC>
-__global__ void __launch_bounds__(256) lm_hub_final(LMArgs<W> a, const int32_t* __restrict__ hubs, int nhubs) {
-  const IterView iv = iter_view(a);
-  typedef typename Arith<WIDE>::S S;
-  __shared__ BlockAcc acc;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  acc_init(acc);
   __syncthreads();
-  for (int h = blockIdx.x; h < nhubs; h += gridDim.x) {
-    const int32_t i = hubs[h];
-    if (!is_active(a, iv, i)) continue;
-    long long M;
-    int graph;
-    if (!graph_of(a, i, &M, &graph)) continue;
-    const int64_t b = a.off[i], e = a.off[i + 1];
-    if (wid == 0) {
-      S bg = Arith<WIDE>::lowest();
-      int32_t bc = -1;
-      for (int64_t t = a.spre[h] + lane; t < a.spre[h + 1]; t += kWarp) {
-        i128 g = ((i128)a.hpart[2 * t + 1] << 64) | (i128)(unsigned long long)a.hpart[2 * t];
-        int32_t c = a.hpart_c[t];
-        if (c >= 0 && better((S)g, c, bg, bc)) { bg = (S)g; bc = c; }
-      }
-      warp_argmax(bg, bc);
-      if (lane == 0) {
-        atomicAdd(&acc.edges, (unsigned long long)(e - b));
-        atomicAdd(&acc.visited, 1ull);
-        const int32_t d = a.memb[i];
-        const bool moved = commit_choice<W, WIDE, ASYNC>(a, acc, i, d, a.K[i], ld_sig<ASYNC>(a.sig + d),
-                                                         ld_size<ASYNC>(a.csize + d), bg, bc, a.hkid[h], M, graph);
-        a.hkid[h] = 0;
-        if (moved && a.prune) a.hmoved[h] = iv.iter + 1;   // lm_hub_mark marks its neighbours
-      }
+  if (s_last && wid == 0) {   // every chunk of this hub is done: decide
+    __threadfence();
+    S hg = Arith<WIDE>::lowest();
+    int32_t hc = -1;
+    for (int64_t t = a.spre[h] + lane; t < a.spre[h + 1]; t += kWarp) {
+      const i128 g = ((i128)__ldcg(a.hpart + 2 * t + 1) << 64) | (i128)(unsigned long long)__ldcg(a.hpart + 2 * t);
+      const int32_t c = __ldcg(a.hpart_c + t);
+      if (c >= 0 && better((S)g, c, hg, hc)) { hg = (S)g; hc = c; }
+    }
+    warp_argmax(hg, hc);
+    if (lane == 0) {
+      atomicAdd(&acc.edges, (unsigned long long)(e - b));
+      atomicAdd(&acc.visited, 1ull);
+      const bool moved = commit_choice<W, WIDE, ASYNC>(a, acc, i, d, Ki, ld_sig<ASYNC>(a.sig + d),
+                                                       ld_size<ASYNC>(a.csize + d), hg, hc, __ldcg(a.hkid + h), M,
+                                                       graph);
+      a.hkid[h] = 0;
+      a.hdone[h] = 0;
+      if (moved && a.prune) a.hmoved[h] = iv.iter + 1;   // lm_hub_mark marks its neighbours
     }
   }
   __syncthreads();
@@ -1004,23 +1000,12 @@ void lm_launch_hubs(const LMArgs<W>& a, bool wide, bool async, const int32_t* hu
     if (async) (count_launch(), lm_hub_insert<W, false, true><<<(unsigned)nchunks, 256, smem, s>>>(a, hubs, nhubs, chunk_pre));
     else (count_launch(), lm_hub_insert<W, false, false><<<(unsigned)nchunks, 256, smem, s>>>(a, hubs, nhubs, chunk_pre));
   }
-  const int g = nhubs < 4096 ? nhubs : 4096;
   if (wide) {
-    if (async) {
-      (count_launch(), lm_hub_scan<W, true, true><<<(unsigned)nslotchunks, 256, 0, s>>>(a, hubs, nhubs));
-      (count_launch(), lm_hub_final<W, true, true><<<g, 256, 0, s>>>(a, hubs, nhubs));
-    } else {
-      (count_launch(), lm_hub_scan<W, true, false><<<(unsigned)nslotchunks, 256, 0, s>>>(a, hubs, nhubs));
-      (count_launch(), lm_hub_final<W, true, false><<<g, 256, 0, s>>>(a, hubs, nhubs));
-    }
+    if (async) (count_launch(), lm_hub_scan<W, true, true><<<(unsigned)nslotchunks, 256, 0, s>>>(a, hubs, nhubs));
+    else (count_launch(), lm_hub_scan<W, true, false><<<(unsigned)nslotchunks, 256, 0, s>>>(a, hubs, nhubs));
   } else {
-    if (async) {
-      (count_launch(), lm_hub_scan<W, false, true><<<(unsigned)nslotchunks, 256, 0, s>>>(a, hubs, nhubs));
-      (count_launch(), lm_hub_final<W, false, true><<<g, 256, 0, s>>>(a, hubs, nhubs));
-    } else {
-      (count_launch(), lm_hub_scan<W, false, false><<<(unsigned)nslotchunks, 256, 0, s>>>(a, hubs, nhubs));
-      (count_launch(), lm_hub_final<W, false, false><<<g, 256, 0, s>>>(a, hubs, nhubs));
-    }
+    if (async) (count_launch(), lm_hub_scan<W, false, true><<<(unsigned)nslotchunks, 256, 0, s>>>(a, hubs, nhubs));
+    else (count_launch(), lm_hub_scan<W, false, false><<<(unsigned)nslotchunks, 256, 0, s>>>(a, hubs, nhubs));
   }
 }
 
