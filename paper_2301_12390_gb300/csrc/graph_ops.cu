@@ -669,8 +669,23 @@ __global__ void compact_rows_k(const int64_t* __restrict__ off, const int32_t* _
     }
 }
 __global__ void compact_cols_k(int32_t* __restrict__ col, int64_t nnz, const int32_t* __restrict__ pos) {
-  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nnz; x += (int64_t)gridDim.x * blockDim.x)
-    col[x] = pos[col[x]];
+  constexpr int U = 4;   // four gathers in flight per thread
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t x0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x0 < nnz; x0 += U * stride) {
+    int32_t c[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t x = x0 + u * stride;
+      c[u] = x < nnz ? col[x] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) c[u] = pos[c[u]];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t x = x0 + u * stride;
+      if (x < nnz) col[x] = c[u];
+    }
+  }
 }
 __global__ void compact_top_k(int32_t* __restrict__ top, int64_t n0, const int32_t* __restrict__ flag,
                               const int32_t* __restrict__ pos) {
@@ -753,17 +768,36 @@ void count_empty_rows(const int64_t* off, int64_t n, unsigned long long* out, cu
 
 // ------------------------------------------------------------ aggregation
 
+// Counting sort of the vertices by community.  The lanes of a warp that hold
+// the same community share one atomic (a community of a million members
+// would otherwise serialise a million atomics on one address).
 __global__ void count_members_k(const int32_t* level, int64_t n, int64_t* cnt) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd((unsigned long long*)(cnt + level[i]), 1ull);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < n; i0 += stride) {
+    const int64_t i = i0 + (threadIdx.x & 31);
+    const int32_t C = i < n ? level[i] : -1;
+    const unsigned grp = __match_any_sync(0xffffffffu, C);
+    if (C >= 0 && (int)(threadIdx.x & 31) == __ffs(grp) - 1)
+      atomicAdd((unsigned long long*)(cnt + C), (unsigned long long)__popc(grp));
+  }
 }
 __global__ void place_members_k(const int32_t* level, int64_t n, const int64_t* cstart, int64_t* fill,
                                 int32_t* members, int32_t* inv) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    int32_t C = level[i];
-    int64_t pos = cstart[C] + (int64_t)atomicAdd((unsigned long long*)(fill + C), 1ull);
-    members[pos] = (int32_t)i;
-    inv[i] = (int32_t)pos;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < n; i0 += stride) {
+    const int64_t i = i0 + lane;
+    const int32_t C = i < n ? level[i] : -1;
+    const unsigned grp = __match_any_sync(0xffffffffu, C);
+    const int leader = __ffs(grp) - 1;
+    unsigned long long base = 0;
+    if (C >= 0 && lane == leader) base = atomicAdd((unsigned long long*)(fill + C), (unsigned long long)__popc(grp));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (C >= 0) {
+      const int64_t pos = cstart[C] + (int64_t)base + __popc(grp & ((1u << lane) - 1u));
+      members[pos] = (int32_t)i;
+      inv[i] = (int32_t)pos;
+    }
   }
 }
 
