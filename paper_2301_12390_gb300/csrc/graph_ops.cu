@@ -840,6 +840,45 @@ __device__ __forceinline__ void add_self_loop(const AggArgs& a, int32_t C, unsig
   else atomicAdd(a.lsum, w);
 }
 
+// The same sums held by each thread while it walks many communities (one
+// atomic per thread and graph run instead of one per community: a pass of
+// millions of small communities would otherwise queue millions of atomics on
+// one address).  Communities are visited in increasing id order per thread,
+// and a graph's communities are a contiguous id range, so a thread flushes
+// when its graph changes.
+struct SelfLoops {
+  int g;
+  unsigned long long v;
+  __device__ __forceinline__ SelfLoops() : g(-1), v(0) {}
+  __device__ __forceinline__ void flush(const AggArgs& a) {
+    if (v) {
+      if (a.cgid) atomic_add_u128(a.glsum + 2 * g, a.glsum + 2 * g + 1, (u128)v);
+      else atomicAdd(a.lsum, v);
+    }
+    v = 0;
+  }
+  __device__ __forceinline__ void add(const AggArgs& a, int32_t C, unsigned long long w) {
+    if (a.cgid) {
+      const int gc = a.cgid[C];
+      if (gc != g) { flush(a); g = gc; }
+    }
+    v += w;
+  }
+};
+
+// Adds a warp's self-loop sums (all 32 lanes call it): one atomic per warp
+// with one graph, else one per lane and graph.
+__device__ __forceinline__ void selfloops_finish(const AggArgs& a, SelfLoops& sl) {
+  if (a.cgid) {
+    sl.flush(a);
+    return;
+  }
+  unsigned long long v = sl.v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(a.lsum, v);
+}
+
 // ---- relabel: every CSR entry x = (u, v, w) of the pass graph is written to
 // the tmp rows, which hold the communities' member rows back to back:
 // position mpre[inv[u]] + (x - off[u]) gets (level[v], w).  The hash kernels
@@ -957,6 +996,74 @@ __device__ __forceinline__ void load_entries(const AggArgs& a, int64_t t0, int64
   }
 }
 
+// Communities with at most CAP / 2 member entries, G lanes each (several
+// communities per warp, so that the dependent loads of several communities'
+// bounds and entries are in flight at once).  Each group's table lives in
+// shared memory with the list of the slots it filled; the coarse row is
+// written back over the community's tmp entries, which the group's lanes hold
+// in registers before the first write.  The row comes out in the order its
+// keys were first inserted.
+template <typename W2, int G, int CAP>
+__global__ void __launch_bounds__(256) agg_group_k(AggArgs a, const int32_t* __restrict__ comms, int ncomms) {
+  typedef AggVal<W2> V;
+  static_assert(G == 4 || G == 8 || G == 16 || G == 32, "group of 4 to 32 lanes");
+  static_assert(CAP <= 256 && CAP / 2 % G == 0, "slot ids fit a byte; whole rows per lane set");
+  constexpr int GPB = 256 / G;
+  constexpr int U = CAP / 2 / G;
+  __shared__ int32_t skeys[GPB][CAP];
+  __shared__ V svals[GPB][CAP];
+  __shared__ uint8_t sfill[GPB][CAP / 2];
+  __shared__ int scnt[GPB];
+  const int lane = threadIdx.x & 31;
+  const int gib = threadIdx.x / G, l = threadIdx.x % G;
+  const unsigned gm = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (lane & ~(G - 1));
+  int32_t* keys = skeys[gib];
+  V* vals = svals[gib];
+  uint8_t* fill = sfill[gib];
+  for (int t = l; t < CAP; t += G) { keys[t] = kEmpty; vals[t] = 0; }
+  if (l == 0) scnt[gib] = 0;
+  __syncwarp(gm);
+  bool ok = true;
+  SelfLoops sl;
+  for (int ci = blockIdx.x * GPB + gib; ci < ncomms; ci += gridDim.x * GPB) {
+    const int32_t C = comms[ci];
+    int64_t b = 0;
+    if (l < 2) b = a.mpre[a.cstart[C + l]];
+    const int64_t vs = __shfl_sync(gm, b, 0, G), ve = __shfl_sync(gm, b, 1, G);
+    int32_t D[U];
+    unsigned long long w[U];
+    load_entries<W2, U>(a, vs + l, ve, G, D, w);
+#pragma unroll
+    for (int k = 0; k < U; ++k)
+      if (D[k] != kEmpty) {
+        bool fresh;
+        const int h = table_add_pow2_slot<CAP, V>(keys, vals, D[k], w[k], &fresh);
+        if (h < 0) ok = false;
+        else if (fresh) fill[atomicAdd(&scnt[gib], 1)] = (uint8_t)h;
+      }
+    __syncwarp(gm);
+    const int cnt = scnt[gib];
+    for (int j = l; j < cnt; j += G) {
+      const int h = fill[j];
+      const int32_t key = keys[h];
+      const V v = vals[h];
+      a.tcol[vs + j] = key;
+      ((W2*)a.tw)[vs + j] = (W2)v;
+      if (key == C) sl.add(a, C, v);
+      keys[h] = kEmpty;
+      vals[h] = 0;
+    }
+    __syncwarp(gm);
+    if (l == 0) {
+      a.rlen[C] = cnt;
+      scnt[gib] = 0;
+    }
+    __syncwarp(gm);
+  }
+  selfloops_finish(a, sl);
+  if (!ok) atomicOr(a.error, kErrProbe);
+}
+
 // Communities with at most CAP / 2 member entries: a warp each, table in
 // shared memory; the coarse row is written back over the community's tmp
 // entries (all of them are read before the first write).
@@ -973,6 +1080,7 @@ __global__ void __launch_bounds__(256) agg_warp_k(AggArgs a, const int32_t* __re
   for (int t = lane; t < CAP; t += kWarp) { keys[t] = kEmpty; vals[t] = 0; }
   __syncwarp();
   bool ok = true;
+  SelfLoops sl;
   for (int ci = blockIdx.x * WPB + wib; ci < ncomms; ci += gridDim.x * WPB) {
     int32_t C = comms[ci];
     const int64_t vs = a.mpre[a.cstart[C]], ve = a.mpre[a.cstart[C + 1]];
@@ -994,7 +1102,7 @@ __global__ void __launch_bounds__(256) agg_warp_k(AggArgs a, const int32_t* __re
         int64_t pos = vs + base + __popc(m & lanemask_lt());
         a.tcol[pos] = key;
         ((W2*)a.tw)[pos] = (W2)vals[t];
-        if (key == C) add_self_loop(a, C, vals[t]);
+        if (key == C) sl.add(a, C, vals[t]);
         keys[t] = kEmpty;
         vals[t] = 0;
       }
@@ -1003,6 +1111,7 @@ __global__ void __launch_bounds__(256) agg_warp_k(AggArgs a, const int32_t* __re
     if (lane == 0) a.rlen[C] = base;
     __syncwarp();
   }
+  selfloops_finish(a, sl);
   if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicOr(a.error, kErrProbe);
 }
 
@@ -1020,6 +1129,7 @@ __global__ void __launch_bounds__(THREADS) agg_block_k(AggArgs a, const int32_t*
   for (int t = threadIdx.x; t < CAP; t += THREADS) { keys[t] = kEmpty; vals[t] = 0; }
   __syncthreads();
   bool ok = true;
+  SelfLoops sl;
   for (int ci = blockIdx.x; ci < ncomms; ci += gridDim.x) {
     int32_t C = comms[ci];
     const int64_t vs = a.mpre[a.cstart[C]], ve = a.mpre[a.cstart[C + 1]];
@@ -1049,7 +1159,7 @@ __global__ void __launch_bounds__(THREADS) agg_block_k(AggArgs a, const int32_t*
         int64_t pos = vs + base + before + __popc(m & lanemask_lt());
         a.tcol[pos] = key;
         ((W2*)a.tw)[pos] = (W2)vals[t];
-        if (key == C) add_self_loop(a, C, vals[t]);
+        if (key == C) sl.add(a, C, vals[t]);
         keys[t] = kEmpty;
         vals[t] = 0;
       }
@@ -1058,6 +1168,7 @@ __global__ void __launch_bounds__(THREADS) agg_block_k(AggArgs a, const int32_t*
     }
     if (threadIdx.x == 0) a.rlen[C] = base;
   }
+  selfloops_finish(a, sl);
   if (!ok) atomicOr(a.error, kErrProbe);
 }
 
@@ -1187,8 +1298,8 @@ void agg_launch_bucket(const AggArgs& a, int bucket, const int32_t* comms, int n
   if (ncomms <= 0) return;
   switch (bucket) {
     case 0: {
-      auto k = agg_warp_k<W2, 64>;
-      (count_launch(), k<<<agrid(k, 256, 0, (ncomms + 7) / 8), 256, 0, s>>>(a, comms, ncomms));
+      auto k = agg_group_k<W2, 8, 64>;
+      (count_launch(), k<<<agrid(k, 256, 0, (ncomms + 31) / 32), 256, 0, s>>>(a, comms, ncomms));
       break;
     }
     case 1: {
