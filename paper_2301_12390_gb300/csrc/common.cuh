@@ -110,6 +110,18 @@ __device__ __forceinline__ void warp_argmax(S& g, int32_t& c) {
   }
 }
 
+// The same with a payload that travels with the winner.
+template <typename S>
+__device__ __forceinline__ void warp_argmax_carry(S& g, int32_t& c, int32_t& pay) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    S g2 = shfl_xor_s(g, m);
+    int32_t c2 = __shfl_xor_sync(0xffffffffu, c, m);
+    int32_t p2 = __shfl_xor_sync(0xffffffffu, pay, m);
+    if (better(g2, c2, g, c)) { g = g2; c = c2; pay = p2; }
+  }
+}
+
 // ---------------------------------------------------------------- hashing
 
 __device__ __forceinline__ uint32_t hash32(uint32_t x) {
@@ -127,9 +139,19 @@ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
 template <bool WIDE> struct TableVal { typedef unsigned long long T; };
 template <> struct TableVal<false> { typedef unsigned int T; };
 
+// Home slot of a key in a power-of-two shared table: multiplicative
+// (Fibonacci) hashing, the top log2(CAP) bits of key * 2^32 / golden ratio
+// (two instructions; consecutive community ids land far apart).
+constexpr int log2_pow2(int x) { return x <= 1 ? 0 : 1 + log2_pow2(x >> 1); }
+template <int CAP>
+__device__ __forceinline__ uint32_t table_home(int32_t key) {
+  static_assert(CAP >= 2 && (CAP & (CAP - 1)) == 0, "power-of-two table");
+  return ((uint32_t)key * 0x9E3779B9u) >> (32 - log2_pow2(CAP));
+}
+
 template <int CAP, typename V>
 __device__ __forceinline__ bool table_add_pow2(int32_t* keys, V* vals, int32_t key, unsigned long long w) {
-  uint32_t h = hash32((uint32_t)key) & (CAP - 1);
+  uint32_t h = table_home<CAP>(key);
 #pragma unroll 1
   for (int probe = 0; probe < CAP; ++probe) {
     int32_t k = keys[h];
@@ -148,7 +170,7 @@ __device__ __forceinline__ bool table_add_pow2(int32_t* keys, V* vals, int32_t k
 template <int CAP, typename V>
 __device__ __forceinline__ int table_add_pow2_slot(int32_t* keys, V* vals, int32_t key, unsigned long long w,
                                                    bool* fresh) {
-  uint32_t h = hash32((uint32_t)key) & (CAP - 1);
+  uint32_t h = table_home<CAP>(key);
   *fresh = false;
 #pragma unroll 1
   for (int probe = 0; probe < CAP; ++probe) {
@@ -169,7 +191,7 @@ __device__ __forceinline__ int table_add_pow2_slot(int32_t* keys, V* vals, int32
 // Lookup in a power-of-two table; 0 if absent.
 template <int CAP, typename V>
 __device__ __forceinline__ unsigned long long table_get_pow2(const int32_t* keys, const V* vals, int32_t key) {
-  uint32_t h = hash32((uint32_t)key) & (CAP - 1);
+  uint32_t h = table_home<CAP>(key);
 #pragma unroll 1
   for (int probe = 0; probe < CAP; ++probe) {
     int32_t k = keys[h];

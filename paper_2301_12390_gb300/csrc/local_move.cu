@@ -125,17 +125,18 @@ __device__ __forceinline__ void warp_move_totals(const LMArgs<W>& a, BlockAcc& a
 // needs gain = best - score_d > 0.
 // sd, szd: Sigma_d and the size of d, loaded with the vertex's row (constant
 // within a synchronous class; an asynchronous decision may use any recent
-// value).
+// value).  size_c: the size of c when the caller loaded it with the
+// candidates (the guard's test), else -1 and it is loaded here.
 template <typename W, bool WIDE, bool ASYNC, int LD = (ASYNC ? 1 : 0)>
 __device__ __forceinline__ bool commit_choice(const LMArgs<W>& a, BlockAcc& acc, int32_t i, int32_t d, long long Ki,
                                               long long sd, int32_t szd, typename Arith<WIDE>::S best, int32_t c,
                                               unsigned long long kid, long long M, int graph,
-                                              u128* defer_gain = nullptr) {
+                                              u128* defer_gain = nullptr, int32_t size_c = -1) {
   if (c < 0) return false;
   typedef typename Arith<WIDE>::S S;
   const S g = best - Arith<WIDE>::score(M, (long long)kid, Ki, sd - Ki);
   if (!(g > 0)) return false;
-  if (a.guard && c > d && szd == 1 && ld_state<LD>(a.csize + c) == 1) return false;
+  if (a.guard && c > d && szd == 1 && (size_c >= 0 ? size_c : ld_state<LD>(a.csize + c)) == 1) return false;
   if (ASYNC) {
     a.memb[i] = c;
     atomicAdd((unsigned long long*)(a.sig + d), (unsigned long long)(-Ki));
@@ -275,12 +276,14 @@ __global__ void __launch_bounds__(256, 3) lm_thread(LMArgs<W> a, const int32_t* 
     do {
       if (vi >= nverts) break;
       int32_t i = verts[vi];
-      if (!is_active(a, iv, i)) break;
-      long long M;
-      if (!graph_of(a, i, &M, &graph)) break;
+      // the vertex's row bounds, community and degree are loaded together
+      // with its stamp, before the activity test
       const int64_t b = a.off[i], e = a.off[i + 1];
       const int32_t d = a.memb[i];
       const long long Ki = a.K[i];
+      if (!is_active(a, iv, i)) break;
+      long long M;
+      if (!graph_of(a, i, &M, &graph)) break;
       const long long sd = ld_sig<ASYNC>(a.sig + d);
       const int32_t szd = ld_size<ASYNC>(a.csize + d);
       int32_t cc[8];
@@ -305,24 +308,32 @@ __global__ void __launch_bounds__(256, 3) lm_thread(LMArgs<W> a, const int32_t* 
 #pragma unroll
       for (int k = 0; k < 8; ++k)
         if (cc[k] == d) kid = ww[k];
+      // the candidates' totals, and for a singleton under the guard their
+      // sizes too (loaded with the totals instead of after the choice)
+      const bool want_size = a.guard && szd == 1;
       long long sg[8];
+      int32_t sz[8];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) sg[k] = (cc[k] != kEmpty && cc[k] != d) ? ld_sig<ASYNC>(a.sig + cc[k]) : 0;
+      for (int k = 0; k < 8; ++k) {
+        const bool cand = cc[k] != kEmpty && cc[k] != d;
+        sg[k] = cand ? ld_sig<ASYNC>(a.sig + cc[k]) : 0;
+        sz[k] = cand && want_size && cc[k] > d ? ld_size<ASYNC>(a.csize + cc[k]) : 0;
+      }
       S bg = Arith<WIDE>::lowest();
-      int32_t bc = -1;
+      int32_t bc = -1, bsz = 0;
       unsigned ncand = 0;
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         if (cc[k] != kEmpty && cc[k] != d) {
           ++ncand;
           S g = Arith<WIDE>::score(M, (long long)ww[k], Ki, sg[k]);
-          if (better(g, cc[k], bg, bc)) { bg = g; bc = cc[k]; }
+          if (better(g, cc[k], bg, bc)) { bg = g; bc = cc[k]; bsz = sz[k]; }
         }
       }
       n_cand = ncand;
       n_edges = (unsigned)(e - b);
       n_visited = 1;
-      moved = commit_choice<W, WIDE, ASYNC>(a, acc, i, d, Ki, sd, szd, bg, bc, kid, M, graph, &gv);
+      moved = commit_choice<W, WIDE, ASYNC>(a, acc, i, d, Ki, sd, szd, bg, bc, kid, M, graph, &gv, bsz);
       if (moved && a.prune) mark_row<8>(a, iv, i, b, e);
     } while (false);
     n_edges = __reduce_add_sync(0xffffffffu, n_edges);
@@ -344,7 +355,10 @@ __global__ void __launch_bounds__(256, 3) lm_thread(LMArgs<W> a, const int32_t* 
 // One vertex of degree <= U * 32 by one warp: its neighbour communities summed
 // in the warp's shared table (CAP slots, left empty again), the best score
 // against its own community's, the move committed and its neighbours marked.
-template <typename W, bool WIDE, bool ASYNC, int CAP, int U, int LD>
+// SIZES: a singleton under the guard loads its candidates' sizes with their
+// totals (one dependent load less before the decision; off where the
+// registers would spill).
+template <typename W, bool WIDE, bool ASYNC, int CAP, int U, int LD, bool SIZES>
 __device__ __forceinline__ void warp_vertex(const LMArgs<W>& a, const IterView& iv, BlockAcc& acc, int32_t* keys,
                                             typename TableVal<WIDE>::T* vals, const VertexInfo& cur, int lane,
                                             bool& ok) {
@@ -355,14 +369,21 @@ __device__ __forceinline__ void warp_vertex(const LMArgs<W>& a, const IterView& 
   const long long Ki = cur.Ki, M = cur.M;
   const int graph = cur.graph;
   for (int64_t x0 = b; x0 < e; x0 += U * kWarp) {
+    // rounds of 32 entries that hold at least one (the rest are skipped)
+    const int nu = (int)min((int64_t)U, (e - x0 + kWarp - 1) / kWarp);
     int32_t cc[U];
     unsigned long long ww[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int64_t x = x0 + u * kWarp + lane;
-      const bool v = x < e;
-      cc[u] = v ? a.col[x] : i;
-      ww[u] = v ? (unsigned long long)a.wt[x] : 0ull;
+      cc[u] = i;
+      ww[u] = 0ull;
+      if (u < nu) {
+        const int64_t x = x0 + u * kWarp + lane;
+        if (x < e) {
+          cc[u] = a.col[x];
+          ww[u] = (unsigned long long)a.wt[x];
+        }
+      }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) cc[u] = cc[u] != i ? ld_state<LD>(a.memb + cc[u]) : kEmpty;
@@ -371,9 +392,12 @@ __device__ __forceinline__ void warp_vertex(const LMArgs<W>& a, const IterView& 
       if (cc[u] != kEmpty) ok &= table_add_pow2<CAP, V>(keys, vals, cc[u], ww[u]);
   }
   __syncwarp();
+  // a singleton under the guard loads its candidates' sizes with their
+  // totals and carries the best one's through the reduction
+  const bool want_size = SIZES && a.guard && cur.szd == 1;
   unsigned long long kid = 0;
   S bg = Arith<WIDE>::lowest();
-  int32_t bc = -1;
+  int32_t bc = -1, bsz = 0;
   unsigned ncand = 0;
 #pragma unroll
   for (int t0 = 0; t0 < CAP; t0 += kWarp * 4) {
@@ -386,8 +410,13 @@ __device__ __forceinline__ void warp_vertex(const LMArgs<W>& a, const IterView& 
       cs[u] = t < CAP ? keys[t] : kEmpty;
       vs[u] = t < CAP ? vals[t] : 0ull;
     }
+    bool one[4];   // the candidate is a singleton (asked only for the guard)
 #pragma unroll
-    for (int u = 0; u < 4; ++u) sg[u] = (cs[u] != kEmpty && cs[u] != d) ? ld_state<LD>(a.sig + cs[u]) : 0;
+    for (int u = 0; u < 4; ++u) {
+      const bool cand = cs[u] != kEmpty && cs[u] != d;
+      sg[u] = cand ? ld_state<LD>(a.sig + cs[u]) : 0;
+      one[u] = cand && want_size && cs[u] > d && ld_state<LD>(a.csize + cs[u]) == 1;
+    }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int t = t0 + u * kWarp + lane;
@@ -395,7 +424,7 @@ __device__ __forceinline__ void warp_vertex(const LMArgs<W>& a, const IterView& 
         if (cs[u] != d) {
           ++ncand;
           S g = Arith<WIDE>::score(M, (long long)vs[u], Ki, sg[u]);
-          if (better(g, cs[u], bg, bc)) { bg = g; bc = cs[u]; }
+          if (better(g, cs[u], bg, bc)) { bg = g; bc = cs[u]; bsz = one[u] ? 1 : 0; }
         } else {
           kid = vs[u];
         }
@@ -404,7 +433,8 @@ __device__ __forceinline__ void warp_vertex(const LMArgs<W>& a, const IterView& 
       }
     }
   }
-  warp_argmax(bg, bc);
+  if (want_size) warp_argmax_carry(bg, bc, bsz);
+  else warp_argmax(bg, bc);
   ncand = __reduce_add_sync(0xffffffffu, ncand);
   {
     const unsigned has = __ballot_sync(0xffffffffu, kid != 0);
@@ -415,7 +445,8 @@ __device__ __forceinline__ void warp_vertex(const LMArgs<W>& a, const IterView& 
     atomicAdd(&acc.cands, (unsigned long long)ncand);
     atomicAdd(&acc.edges, (unsigned long long)(e - b));
     atomicAdd(&acc.visited, 1ull);
-    moved = commit_choice<W, WIDE, ASYNC, LD>(a, acc, i, d, Ki, cur.sd, cur.szd, bg, bc, kid, M, graph);
+    moved = commit_choice<W, WIDE, ASYNC, LD>(a, acc, i, d, Ki, cur.sd, cur.szd, bg, bc, kid, M, graph, nullptr,
+                                              want_size ? bsz : -1);
   }
   moved = __shfl_sync(0xffffffffu, moved, 0);
   if (moved && a.prune) mark_row<U>(a, iv, i, b, e, lane, kWarp);
@@ -445,7 +476,8 @@ __global__ void __launch_bounds__(256, 4) lm_warp(LMArgs<W> a, const int32_t* __
     const VertexInfo cur = nx;
     nx = vertex_info<W, ASYNC>(a, iv, verts, nverts, vi + stride);
     if (!cur.on) continue;
-    warp_vertex<W, WIDE, ASYNC, CAP, U, (ASYNC ? 1 : 0)>(a, iv, acc, keys, vals, cur, lane, ok);
+    warp_vertex<W, WIDE, ASYNC, CAP, U, (ASYNC ? 1 : 0), (CAP <= 64 && !WIDE)>(a, iv, acc, keys, vals, cur, lane,
+                                                                                 ok);
     __syncwarp();
   }
   if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicOr(&acc.error, kErrProbe);
@@ -484,7 +516,7 @@ __global__ void __launch_bounds__(256, 4) lm_class(LMArgs<W> a, const int32_t* _
     const int64_t idx = t < n0 ? r0 + t : (t < n0 + n1 ? r1 + (t - n0) : r2 + (t - n0 - n1));
     const VertexInfo cur = vertex_info<W, ASYNC>(a, iv, list + idx, 1, 0);
     if (!cur.on) continue;
-    warp_vertex<W, WIDE, ASYNC, CAP, U, (ASYNC ? 1 : 0)>(a, iv, acc, keys, vals, cur, lane, ok);
+    warp_vertex<W, WIDE, ASYNC, CAP, U, (ASYNC ? 1 : 0), !WIDE>(a, iv, acc, keys, vals, cur, lane, ok);
     __syncwarp();
   }
   if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicOr(&acc.error, kErrProbe);
@@ -594,19 +626,28 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 128 ? 8 : 2)
     const long long Ki = cur.Ki, M = cur.M;
     const int graph = cur.graph;
     for (int64_t x0 = b; x0 < e; x0 += U * THREADS) {
+      // this warp's rounds that hold at least one entry (the rest skipped)
+      const int64_t rem = e - x0 - wid * kWarp;
+      const int nu = rem <= 0 ? 0 : (int)min((int64_t)U, (rem + THREADS - 1) / THREADS);
       int32_t cc[U];
       unsigned long long ww[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int64_t x = x0 + u * THREADS + threadIdx.x;
-        const bool v = x < e;
-        cc[u] = v ? a.col[x] : i;
-        ww[u] = v ? (unsigned long long)a.wt[x] : 0ull;
+        cc[u] = i;
+        ww[u] = 0ull;
+        if (u < nu) {
+          const int64_t x = x0 + u * THREADS + threadIdx.x;
+          if (x < e) {
+            cc[u] = a.col[x];
+            ww[u] = (unsigned long long)a.wt[x];
+          }
+        }
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) cc[u] = cc[u] != i ? ld_memb<ASYNC>(a.memb + cc[u]) : kEmpty;
 #pragma unroll
       for (int u = 0; u < U; ++u) {
+        if (u >= nu) break;
         bool fresh = false;
         int h = -1;
         if (cc[u] != kEmpty) {
@@ -633,13 +674,15 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 128 ? 8 : 2)
     S bg = Arith<WIDE>::lowest();
     int32_t bc = -1;
     for (int t0 = 0; t0 < nt; t0 += U * THREADS) {
+      const int rem = nt - t0 - wid * kWarp;
+      const int nu = rem <= 0 ? 0 : min(U, (rem + THREADS - 1) / THREADS);
       int hs[U];
       int32_t cs[U];
       long long sg[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int t = t0 + u * THREADS + threadIdx.x;
-        hs[u] = t < nt ? (int)touched[t] : -1;
+        hs[u] = u < nu && t < nt ? (int)touched[t] : -1;
         cs[u] = hs[u] >= 0 ? keys[hs[u]] : kEmpty;
       }
 #pragma unroll
