@@ -257,18 +257,15 @@ __device__ __forceinline__ void mark_row(const LMArgs<W>& a, const IterView& iv,
 
 // The row (<= 8 entries) is loaded first and its neighbours' communities
 // gathered with all loads in flight; duplicates are then merged in registers.
+// Lane l of the calling warp takes list entry vi (none if vi >= nverts); all
+// 32 lanes call it.  Whole warps sum their counters, moves and gains over the
+// warp: per-lane atomics on the block's counters serialise (measured: a third
+// of the thread kernel's time).
 template <typename W, bool WIDE, bool ASYNC>
-__global__ void __launch_bounds__(256, 3) lm_thread(LMArgs<W> a, const int32_t* __restrict__ verts, int nverts) {
-  const IterView iv = iter_view(a);
+__device__ __forceinline__ void thread_vertex(const LMArgs<W>& a, const IterView& iv, BlockAcc& acc,
+                                              const int32_t* __restrict__ verts, int64_t nverts, int64_t vi) {
   typedef typename Arith<WIDE>::S S;
-  __shared__ BlockAcc acc;
-  acc_init(acc);
-  __syncthreads();
-  // Whole warps iterate together and sum their counters, moves and gains
-  // over the warp: per-lane atomics on the block's counters serialise
-  // (measured: a third of this kernel's time).
-  for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < nverts; base += gridDim.x * blockDim.x) {
-    const int vi = base + (int)(threadIdx.x & 31);
+  {
     bool moved = false;
     u128 gv = 0;
     int graph = 0;
@@ -346,6 +343,16 @@ __global__ void __launch_bounds__(256, 3) lm_thread(LMArgs<W> a, const int32_t* 
     }
     warp_move_totals(a, acc, moved, graph, gv);
   }
+}
+
+template <typename W, bool WIDE, bool ASYNC>
+__global__ void __launch_bounds__(256, 3) lm_thread(LMArgs<W> a, const int32_t* __restrict__ verts, int nverts) {
+  const IterView iv = iter_view(a);
+  __shared__ BlockAcc acc;
+  acc_init(acc);
+  __syncthreads();
+  for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < nverts; base += gridDim.x * blockDim.x)
+    thread_vertex<W, WIDE, ASYNC>(a, iv, acc, verts, nverts, base + (int)(threadIdx.x & 31));
   __syncthreads();
   acc_flush(acc, a.ctr);
 }
@@ -489,11 +496,12 @@ __global__ void __launch_bounds__(256, 4) lm_warp(LMArgs<W> a, const int32_t* __
 //
 // When no vertex of the pass graph has degree above 128 and the graph is
 // small, the launches of a class are few microseconds of work each: one
-// kernel then takes the whole class, a warp per vertex of buckets 0-2 (as
-// lm_warp, 256-slot tables), instead of one kernel per bucket on forked
-// streams.  ko = the bucket offsets of the class lists (device).
+// kernel then takes the whole class instead of one kernel per bucket on
+// forked streams: a lane per vertex of bucket 0 (as lm_thread), a warp per
+// vertex of buckets 1-2 (as lm_warp, 256-slot tables).  ko = the bucket
+// offsets of the class lists (device).
 template <typename W, bool WIDE, bool ASYNC>
-__global__ void __launch_bounds__(256, 4) lm_class(LMArgs<W> a, const int32_t* __restrict__ list,
+__global__ void __launch_bounds__(256, 3) lm_class(LMArgs<W> a, const int32_t* __restrict__ list,
                                                    const int64_t* __restrict__ ko, int P, int ch) {
   const IterView iv = iter_view(a);
   typedef typename TableVal<WIDE>::T V;
@@ -511,9 +519,17 @@ __global__ void __launch_bounds__(256, 4) lm_class(LMArgs<W> a, const int32_t* _
   const int64_t r0 = ko[ch], n0 = ko[ch + 1] - r0;
   const int64_t r1 = ko[P + ch], n1 = ko[P + ch + 1] - r1;
   const int64_t r2 = ko[2 * P + ch], n2 = ko[2 * P + ch + 1] - r2;
-  const int64_t tot = n0 + n1 + n2;
+  // work items of a warp: 32 degree-<=8 vertices (a lane each, as the thread
+  // kernel), then one vertex of degree 9-128 each
+  const int64_t m0 = (n0 + kWarp - 1) / kWarp;
+  const int64_t tot = m0 + n1 + n2;
   for (int64_t t = (int64_t)blockIdx.x * WPB + wib; t < tot; t += (int64_t)gridDim.x * WPB) {
-    const int64_t idx = t < n0 ? r0 + t : (t < n0 + n1 ? r1 + (t - n0) : r2 + (t - n0 - n1));
+    if (t < m0) {
+      thread_vertex<W, WIDE, ASYNC>(a, iv, acc, list + r0, n0, t * kWarp + lane);
+      continue;
+    }
+    const int64_t u = t - m0;
+    const int64_t idx = u < n1 ? r1 + u : r2 + (u - n1);
     const VertexInfo cur = vertex_info<W, ASYNC>(a, iv, list + idx, 1, 0);
     if (!cur.on) continue;
     warp_vertex<W, WIDE, ASYNC, CAP, U, (ASYNC ? 1 : 0), !WIDE>(a, iv, acc, keys, vals, cur, lane, ok);
@@ -1057,7 +1073,7 @@ void lm_launch_class(const LMArgs<W>& a, bool wide, bool async, const int32_t* l
                      int ch, int64_t nverts, cudaStream_t s) {
   if (nverts <= 0) return;
   int64_t blocks = (nverts + 7) / 8;
-  if (blocks > 152 * 4) blocks = 152 * 4;
+  if (blocks > 152 * 3) blocks = 152 * 3;   // resident blocks (three per SM)
   const unsigned g = (unsigned)blocks;
   if (wide) {
     if (async) (count_launch(), lm_class<W, true, true><<<g, 256, 0, s>>>(a, list, ko, P, ch));
