@@ -1217,12 +1217,14 @@ __global__ void __launch_bounds__(256) agg_global_insert_k(AggArgs a, const int3
   unsigned long long* vals = a.gvals + base;
   const int64_t lo = a.glo[h];
   if (lo >= 0) {   // direct table: slot Dk - lo (same-value key stores may race)
+    // the key is stored without reading the slot first: no load waits, so a
+    // thread's slots go out back to back
     for (int t = threadIdx.x; t < CAP; t += blockDim.x) {
       const int32_t Dk = skeys[t];
       if (Dk == kEmpty) continue;
       const int64_t y = (int64_t)Dk - lo;
       if (y < 0 || y >= (int64_t)cap) { ok = false; continue; }
-      if (keys[y] != Dk) keys[y] = Dk;
+      keys[y] = Dk;
       atomicAdd(&vals[y], (unsigned long long)svals[t]);
     }
   } else {
@@ -1242,36 +1244,64 @@ __global__ void __launch_bounds__(256) agg_global_insert_k(AggArgs a, const int3
 }
 
 // Blocks are (community, 4096-slot chunk) pairs: every occupied slot is
-// appended to the community's tmp row (positions claimed once per warp) and
-// cleared.
+// appended to the community's tmp row and cleared.  A thread holds its
+// kSlotChunk / 256 keys in registers; the block counts them, claims its
+// positions with one atomic on the row length and writes (one round trip
+// per block instead of one per warp and 256 slots).
 template <typename W2>
 __global__ void __launch_bounds__(256) agg_global_write_k(AggArgs a, const int32_t* __restrict__ comms, int ncomms,
                                                           const int64_t* __restrict__ gbase,
                                                           const int64_t* __restrict__ spre) {
-  const int lane = threadIdx.x & 31;
+  constexpr int J = (int)kSlotChunk / 256;
+  constexpr int NW = 256 / kWarp;
+  __shared__ int wsum[NW];
+  __shared__ long long sbase;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int h = find_item(spre, ncomms, blockIdx.x);
   const int32_t C = comms[h];
-  const int64_t vs = a.mpre[a.cstart[C]];
   const int64_t base = gbase[h];
   const int64_t cap = gbase[h + 1] - base;
   const int64_t q = (int64_t)blockIdx.x - spre[h];
   const int64_t t0 = q * kSlotChunk, t1 = min(cap, t0 + kSlotChunk);
-  for (int64_t y = t0; y < t1; y += blockDim.x) {
-    const int64_t t = y + threadIdx.x;
-    int32_t D = t < t1 ? a.gkeys[base + t] : kEmpty;
-    const bool occ = D != kEmpty;
-    const unsigned m = __ballot_sync(0xffffffffu, occ);
-    int64_t wbase = 0;
-    if (lane == 0 && m) wbase = (int64_t)atomicAdd((unsigned long long*)(a.rlen + C), (unsigned long long)__popc(m));
-    wbase = __shfl_sync(0xffffffffu, wbase, 0);
-    if (occ) {
-      const int64_t pos = vs + wbase + __popc(m & lanemask_lt());
-      a.tcol[pos] = D;
-      ((W2*)a.tw)[pos] = (W2)a.gvals[base + t];
-      if (D == C) add_self_loop(a, C, a.gvals[base + t]);
-      a.gkeys[base + t] = kEmpty;
-      a.gvals[base + t] = 0;
-    }
+  int32_t D[J];
+  int mine = 0;
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const int64_t t = t0 + j * 256 + threadIdx.x;
+    D[j] = t < t1 ? a.gkeys[base + t] : kEmpty;
+    mine += D[j] != kEmpty ? 1 : 0;
+  }
+  // exclusive prefix of the threads' counts over the block
+  int incl = mine;
+#pragma unroll
+  for (int o = 1; o < kWarp; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == kWarp - 1) wsum[wid] = incl;
+  __syncthreads();
+  int before = 0, total = 0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    before += w < wid ? wsum[w] : 0;
+    total += wsum[w];
+  }
+  if (threadIdx.x == 0)
+    sbase = total ? (long long)atomicAdd((unsigned long long*)(a.rlen + C), (unsigned long long)total) : 0;
+  __syncthreads();
+  if (!mine) return;
+  int64_t pos = a.mpre[a.cstart[C]] + sbase + before + (incl - mine);
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    if (D[j] == kEmpty) continue;
+    const int64_t t = base + t0 + j * 256 + threadIdx.x;
+    const unsigned long long v = a.gvals[t];
+    a.tcol[pos] = D[j];
+    ((W2*)a.tw)[pos] = (W2)v;
+    if (D[j] == C) add_self_loop(a, C, v);
+    a.gkeys[t] = kEmpty;
+    a.gvals[t] = 0;
+    ++pos;
   }
 }
 
