@@ -122,6 +122,32 @@ __device__ __forceinline__ void warp_argmax_carry(S& g, int32_t& c, int32_t& pay
   }
 }
 
+// ------------------------------------------------- block-to-item maps
+
+// Blocks are handed out to items by prefix sums: item h owns blocks
+// [pre[h] - pre[0], pre[h + 1] - pre[0]).  The item of block blk is the last
+// h with pre[h] - pre[0] <= blk.  With at most CACHE items the block first
+// copies pre into shared memory (`cache`, CACHE + 1 entries): one coalesced
+// load instead of log2(nitems) dependent global loads at the head of every
+// block.  Every thread of the block calls it (it holds a barrier).
+template <int CACHE>
+__device__ __forceinline__ int block_item(const int64_t* __restrict__ pre, int nitems, int64_t blk,
+                                          int64_t* cache) {
+  const int64_t* p = pre;
+  if (nitems <= CACHE) {
+    for (int t = threadIdx.x; t <= nitems; t += blockDim.x) cache[t] = pre[t];
+    __syncthreads();
+    p = cache;
+  }
+  const int64_t p0 = p[0];
+  int lo = 0, hi = nitems;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (p[mid] - p0 <= blk) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 // ---------------------------------------------------------------- hashing
 
 __device__ __forceinline__ uint32_t hash32(uint32_t x) {

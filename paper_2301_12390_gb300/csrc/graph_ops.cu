@@ -1176,14 +1176,7 @@ __global__ void __launch_bounds__(THREADS) agg_block_k(AggArgs a, const int32_t*
 // pairs; each sums its chunk per neighbour community in shared memory, then
 // adds each distinct one to the community's global table (hashed, 2 x its
 // entries slots, or direct-indexed by community id).
-__device__ __forceinline__ int find_item(const int64_t* __restrict__ pre, int nitems, int64_t blk) {
-  int lo = 0, hi = nitems;
-  while (hi - lo > 1) {
-    int mid = (lo + hi) >> 1;
-    if (pre[mid] <= blk) lo = mid; else hi = mid;
-  }
-  return lo;
-}
+constexpr int kAggItemCache = 2048;   // community prefix entries a block copies to shared memory
 
 template <typename W2>
 __global__ void __launch_bounds__(256) agg_global_insert_k(AggArgs a, const int32_t* __restrict__ comms, int ncomms,
@@ -1196,7 +1189,8 @@ __global__ void __launch_bounds__(256) agg_global_insert_k(AggArgs a, const int3
   extern __shared__ unsigned long long gdyn[];
   V* svals = (V*)gdyn;
   int32_t* skeys = (int32_t*)(svals + CAP);
-  const int h = find_item(chunk_pre, ncomms, blockIdx.x);
+  __shared__ int64_t s_pre[kAggItemCache + 1];
+  const int h = block_item<kAggItemCache>(chunk_pre, ncomms, blockIdx.x, s_pre);
   const int32_t C = comms[h];
   const int64_t vs = a.mpre[a.cstart[C]], ve = a.mpre[a.cstart[C + 1]];
   const int64_t q = (int64_t)blockIdx.x - chunk_pre[h];
@@ -1257,7 +1251,8 @@ __global__ void __launch_bounds__(256) agg_global_write_k(AggArgs a, const int32
   __shared__ int wsum[NW];
   __shared__ long long sbase;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int h = find_item(spre, ncomms, blockIdx.x);
+  __shared__ int64_t s_pre[kAggItemCache + 1];
+  const int h = block_item<kAggItemCache>(spre, ncomms, blockIdx.x, s_pre);
   const int32_t C = comms[h];
   const int64_t base = gbase[h];
   const int64_t cap = gbase[h + 1] - base;

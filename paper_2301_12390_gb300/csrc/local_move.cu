@@ -756,16 +756,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 128 ? 8 : 2)
 
 constexpr int kHubChunk = (int)kHubChunkEntries;
 
-__device__ __forceinline__ int find_item(const int64_t* __restrict__ pre, int nitems, int64_t blk) {
-  // last h with pre[h] - pre[0] <= blk
-  const int64_t p0 = pre[0];
-  int lo = 0, hi = nitems;
-  while (hi - lo > 1) {
-    int mid = (lo + hi) >> 1;
-    if (pre[mid] - p0 <= blk) lo = mid; else hi = mid;
-  }
-  return lo;
-}
+constexpr int kItemCache = 512;   // hub prefix entries a block copies to shared memory
 
 template <typename W, bool WIDE, bool ASYNC>
 __global__ void __launch_bounds__(256) lm_hub_insert(LMArgs<W> a, const int32_t* __restrict__ hubs, int nhubs,
@@ -776,7 +767,8 @@ __global__ void __launch_bounds__(256) lm_hub_insert(LMArgs<W> a, const int32_t*
   extern __shared__ unsigned long long hdyn[];
   V* svals = (V*)hdyn;
   int32_t* skeys = (int32_t*)(svals + CAP);
-  const int h = find_item(chunk_pre, nhubs, blockIdx.x);
+  __shared__ int64_t s_pre[kItemCache + 1];
+  const int h = block_item<kItemCache>(chunk_pre, nhubs, blockIdx.x, s_pre);
   const int32_t i = hubs[h];
   if (!is_active(a, iv, i)) return;   // uniform across the block
   {
@@ -842,7 +834,8 @@ __global__ void __launch_bounds__(256) lm_hub_scan(LMArgs<W> a, const int32_t* _
   __shared__ BlockAcc acc;
   __shared__ int s_last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int h = find_item(a.spre, nhubs, blockIdx.x);
+  __shared__ int64_t s_pre[kItemCache + 1];
+  const int h = block_item<kItemCache>(a.spre, nhubs, blockIdx.x, s_pre);
   const int32_t i = hubs[h];
   if (!is_active(a, iv, i)) return;   // uniform across the block
   long long M;
@@ -941,7 +934,8 @@ template <typename W>
 __global__ void __launch_bounds__(256) lm_hub_mark(LMArgs<W> a, const int32_t* __restrict__ hubs, int nhubs,
                                                    const int64_t* __restrict__ chunk_pre) {
   const IterView iv = iter_view(a);
-  const int h = find_item(chunk_pre, nhubs, blockIdx.x);
+  __shared__ int64_t s_pre[kItemCache + 1];
+  const int h = block_item<kItemCache>(chunk_pre, nhubs, blockIdx.x, s_pre);
   if (a.hmoved[h] != iv.iter + 1) return;
   const int32_t i = hubs[h];
   const int64_t q = (int64_t)blockIdx.x - (chunk_pre[h] - chunk_pre[0]);
