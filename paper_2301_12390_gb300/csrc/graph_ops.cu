@@ -1115,58 +1115,67 @@ __global__ void __launch_bounds__(256) agg_warp_k(AggArgs a, const int32_t* __re
   if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicOr(a.error, kErrProbe);
 }
 
-// Communities with at most CAP / 2 member entries, a block each.
+// Communities with at most CAP / 2 member entries, a block each.  Each key
+// seen for the first time appends its slot to a fill list (one shared atomic
+// per warp), so writing the row costs its distinct keys, not the table's
+// CAP slots; the row comes out in first-insert order.
 template <typename W2, int CAP, int THREADS>
 __global__ void __launch_bounds__(THREADS) agg_block_k(AggArgs a, const int32_t* __restrict__ comms, int ncomms) {
   typedef AggVal<W2> V;
+  static_assert(CAP <= 65536, "slot ids fit 16 bits");
   constexpr int U = 4;
-  // dynamic shared memory: values (CAP V), keys (CAP i32)
+  // dynamic shared memory: values (CAP V), keys (CAP i32), fill list (CAP / 2 u16)
   extern __shared__ unsigned long long adyn[];
   V* vals = (V*)adyn;
   int32_t* keys = (int32_t*)(vals + CAP);
-  __shared__ int wtot[THREADS / kWarp];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint16_t* fill = (uint16_t*)(keys + CAP);
+  __shared__ int scnt;
+  const int lane = threadIdx.x & 31;
   for (int t = threadIdx.x; t < CAP; t += THREADS) { keys[t] = kEmpty; vals[t] = 0; }
+  if (threadIdx.x == 0) scnt = 0;
   __syncthreads();
   bool ok = true;
   SelfLoops sl;
   for (int ci = blockIdx.x; ci < ncomms; ci += gridDim.x) {
     int32_t C = comms[ci];
     const int64_t vs = a.mpre[a.cstart[C]], ve = a.mpre[a.cstart[C + 1]];
-    for (int64_t t0 = vs + threadIdx.x; t0 < ve; t0 += U * THREADS) {
+    for (int64_t r0 = vs; r0 < ve; r0 += U * THREADS) {   // same trip count for every thread
       int32_t D[U];
       unsigned long long w[U];
-      load_entries<W2, U>(a, t0, ve, THREADS, D, w);
+      load_entries<W2, U>(a, r0 + threadIdx.x, ve, THREADS, D, w);
 #pragma unroll
-      for (int k = 0; k < U; ++k)
-        if (D[k] != kEmpty) ok &= table_add_pow2<CAP, V>(keys, vals, D[k], w[k]);
+      for (int k = 0; k < U; ++k) {
+        bool fresh = false;
+        int h = -1;
+        if (D[k] != kEmpty) {
+          h = table_add_pow2_slot<CAP, V>(keys, vals, D[k], w[k], &fresh);
+          if (h < 0) ok = false;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, fresh);
+        int base = 0;
+        if (lane == 0 && m) base = atomicAdd(&scnt, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (fresh) fill[base + __popc(m & lanemask_lt())] = (uint16_t)h;
+      }
     }
     __syncthreads();
-    int64_t base = 0;
-    for (int t0 = 0; t0 < CAP; t0 += THREADS) {
-      int t = t0 + threadIdx.x;
-      int32_t key = keys[t];
-      bool occ = key != kEmpty;
-      unsigned m = __ballot_sync(0xffffffffu, occ);
-      if (lane == 0) wtot[wid] = __popc(m);
-      __syncthreads();
-      int before = 0, all = 0;
-      for (int w = 0; w < THREADS / kWarp; ++w) {
-        if (w < wid) before += wtot[w];
-        all += wtot[w];
-      }
-      if (occ) {
-        int64_t pos = vs + base + before + __popc(m & lanemask_lt());
-        a.tcol[pos] = key;
-        ((W2*)a.tw)[pos] = (W2)vals[t];
-        if (key == C) sl.add(a, C, vals[t]);
-        keys[t] = kEmpty;
-        vals[t] = 0;
-      }
-      base += all;
-      __syncthreads();
+    const int cnt = scnt;
+    for (int j = threadIdx.x; j < cnt; j += THREADS) {
+      const int h = fill[j];
+      const int32_t key = keys[h];
+      const V v = vals[h];
+      a.tcol[vs + j] = key;
+      ((W2*)a.tw)[vs + j] = (W2)v;
+      if (key == C) sl.add(a, C, v);
+      keys[h] = kEmpty;
+      vals[h] = 0;
     }
-    if (threadIdx.x == 0) a.rlen[C] = base;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      a.rlen[C] = cnt;
+      scnt = 0;
+    }
+    __syncthreads();
   }
   selfloops_finish(a, sl);
   if (!ok) atomicOr(a.error, kErrProbe);
@@ -1334,14 +1343,14 @@ void agg_launch_bucket(const AggArgs& a, int bucket, const int32_t* comms, int n
     }
     case 2: {
       constexpr int CAP = 2048;
-      size_t smem = (size_t)CAP * (4 + sizeof(AggVal<W2>));
+      size_t smem = (size_t)CAP * (4 + sizeof(AggVal<W2>) + 1);
       auto k = agg_block_k<W2, CAP, 128>;
       (count_launch(), k<<<agrid(k, 128, smem, ncomms), 128, smem, s>>>(a, comms, ncomms));
       break;
     }
     case 3: {
       constexpr int CAP = 8192;
-      size_t smem = (size_t)CAP * (4 + sizeof(AggVal<W2>));
+      size_t smem = (size_t)CAP * (4 + sizeof(AggVal<W2>) + 1);
       auto k = agg_block_k<W2, CAP, 256>;
       static bool attr = false;
       if (!attr) {
