@@ -33,10 +33,13 @@ constexpr int64_t kHubChunkEntries = 1024;   // entries per insert block of a hu
 constexpr int64_t kSlotChunk = 4096;         // table slots per scan block (hubs and large communities)
 
 // Community classes of the aggregation phase by total member degree.
-constexpr int kAggBuckets = 5;       // 0 warp/64, 1 warp/256, 2 block/2k, 3 block/8k, 4 global
-constexpr int kAggGlobal = 4;
+constexpr int kAggBuckets = 6;   // 0 thread/16, 1 thread/32, 2 warp/256, 3 block/2k, 4 block/8k, 5 global
+constexpr int kAggGlobal = 5;
+constexpr int kAggThreadEntries = 16;   // bucket 0: a thread sorts up to this many entries in registers
 __host__ __device__ inline int agg_bucket_of(int64_t dsum) {
-  return dsum <= 0 ? -1 : dsum <= 32 ? 0 : dsum <= 128 ? 1 : dsum <= 1024 ? 2 : dsum <= 4096 ? 3 : 4;
+  return dsum <= 0 ? -1
+         : dsum <= kAggThreadEntries ? 0
+         : dsum <= 32 ? 1 : dsum <= 128 ? 2 : dsum <= 1024 ? 3 : dsum <= 4096 ? 4 : 5;
 }
 constexpr int64_t kAggChunkEntries = 2048;
 constexpr int64_t kRelabelChunk = 1024;     // CSR entries per warp of the relabel kernel

@@ -996,72 +996,69 @@ __device__ __forceinline__ void load_entries(const AggArgs& a, int64_t t0, int64
   }
 }
 
-// Communities with at most CAP / 2 member entries, G lanes each (several
-// communities per warp, so that the dependent loads of several communities'
-// bounds and entries are in flight at once).  Each group's table lives in
-// shared memory with the list of the slots it filled; the coarse row is
-// written back over the community's tmp entries, which the group's lanes hold
-// in registers before the first write.  The row comes out in the order its
-// keys were first inserted.
-template <typename W2, int G, int CAP>
-__global__ void __launch_bounds__(256) agg_group_k(AggArgs a, const int32_t* __restrict__ comms, int ncomms) {
+// Communities with at most D member entries, a thread each: the entries are
+// loaded into registers together, sorted by neighbour community with a
+// bitonic network (static indices, no shared memory) and each run of equal
+// keys summed into one coarse entry, written back over the community's tmp
+// entries.
+template <typename W2, int D>
+__global__ void __launch_bounds__(256) agg_thread_k(AggArgs a, const int32_t* __restrict__ comms, int ncomms) {
   typedef AggVal<W2> V;
-  static_assert(G == 4 || G == 8 || G == 16 || G == 32, "group of 4 to 32 lanes");
-  static_assert(CAP <= 256 && CAP / 2 % G == 0, "slot ids fit a byte; whole rows per lane set");
-  constexpr int GPB = 256 / G;
-  constexpr int U = CAP / 2 / G;
-  __shared__ int32_t skeys[GPB][CAP];
-  __shared__ V svals[GPB][CAP];
-  __shared__ uint8_t sfill[GPB][CAP / 2];
-  __shared__ int scnt[GPB];
-  const int lane = threadIdx.x & 31;
-  const int gib = threadIdx.x / G, l = threadIdx.x % G;
-  const unsigned gm = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (lane & ~(G - 1));
-  int32_t* keys = skeys[gib];
-  V* vals = svals[gib];
-  uint8_t* fill = sfill[gib];
-  for (int t = l; t < CAP; t += G) { keys[t] = kEmpty; vals[t] = 0; }
-  if (l == 0) scnt[gib] = 0;
-  __syncwarp(gm);
-  bool ok = true;
+  static_assert((D & (D - 1)) == 0, "power-of-two network");
+  constexpr int32_t kPast = 0x7fffffff;   // sorts after every community id
   SelfLoops sl;
-  for (int ci = blockIdx.x * GPB + gib; ci < ncomms; ci += gridDim.x * GPB) {
+  for (int ci = blockIdx.x * blockDim.x + threadIdx.x; ci < ncomms; ci += gridDim.x * blockDim.x) {
     const int32_t C = comms[ci];
-    int64_t b = 0;
-    if (l < 2) b = a.mpre[a.cstart[C + l]];
-    const int64_t vs = __shfl_sync(gm, b, 0, G), ve = __shfl_sync(gm, b, 1, G);
-    int32_t D[U];
-    unsigned long long w[U];
-    load_entries<W2, U>(a, vs + l, ve, G, D, w);
+    const int64_t vs = a.mpre[a.cstart[C]], ve = a.mpre[a.cstart[C + 1]];
+    int32_t k[D];
+    V w[D];
 #pragma unroll
-    for (int k = 0; k < U; ++k)
-      if (D[k] != kEmpty) {
-        bool fresh;
-        const int h = table_add_pow2_slot<CAP, V>(keys, vals, D[k], w[k], &fresh);
-        if (h < 0) ok = false;
-        else if (fresh) fill[atomicAdd(&scnt[gib], 1)] = (uint8_t)h;
+    for (int j = 0; j < D; ++j) {
+      const int64_t x = vs + j;
+      k[j] = x < ve ? a.tcol[x] : kPast;
+      w[j] = x < ve ? (V)((const W2*)a.tw)[x] : (V)0;
+    }
+#pragma unroll
+    for (int kk = 2; kk <= D; kk <<= 1) {
+#pragma unroll
+      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          const int l = i ^ jj;
+          if (l > i) {
+            const bool up = (i & kk) == 0;
+            if ((k[i] > k[l]) == up) {
+              const int32_t tk = k[i]; k[i] = k[l]; k[l] = tk;
+              const V tw = w[i]; w[i] = w[l]; w[l] = tw;
+            }
+          }
+        }
       }
-    __syncwarp(gm);
-    const int cnt = scnt[gib];
-    for (int j = l; j < cnt; j += G) {
-      const int h = fill[j];
-      const int32_t key = keys[h];
-      const V v = vals[h];
-      a.tcol[vs + j] = key;
-      ((W2*)a.tw)[vs + j] = (W2)v;
-      if (key == C) sl.add(a, C, v);
-      keys[h] = kEmpty;
-      vals[h] = 0;
     }
-    __syncwarp(gm);
-    if (l == 0) {
-      a.rlen[C] = cnt;
-      scnt[gib] = 0;
+    int cnt = 0;
+    int32_t ck = k[0];
+    V cs = w[0];
+#pragma unroll
+    for (int j = 1; j <= D; ++j) {
+      const int32_t kj = j < D ? k[j] : kPast;
+      if (j < D && kj == ck) {
+        cs += w[j];
+      } else {
+        if (ck != kPast) {
+          a.tcol[vs + cnt] = ck;
+          ((W2*)a.tw)[vs + cnt] = (W2)cs;
+          if (ck == C) sl.add(a, C, cs);
+          ++cnt;
+        }
+        if (j < D) {
+          ck = kj;
+          cs = w[j];
+        }
+      }
     }
-    __syncwarp(gm);
+    a.rlen[C] = cnt;
   }
   selfloops_finish(a, sl);
-  if (!ok) atomicOr(a.error, kErrProbe);
 }
 
 // Communities with at most CAP / 2 member entries: a warp each, table in
@@ -1081,17 +1078,34 @@ __global__ void __launch_bounds__(256) agg_warp_k(AggArgs a, const int32_t* __re
   __syncwarp();
   bool ok = true;
   SelfLoops sl;
-  for (int ci = blockIdx.x * WPB + wib; ci < ncomms; ci += gridDim.x * WPB) {
-    int32_t C = comms[ci];
-    const int64_t vs = a.mpre[a.cstart[C]], ve = a.mpre[a.cstart[C + 1]];
+  // the next community's id and ranges are fetched while the current one is
+  // summed (lanes 0 and 1 load the two bounds)
+  const int stride = gridDim.x * WPB;
+  int ci = blockIdx.x * WPB + wib;
+  int32_t C = ci < ncomms ? comms[ci] : 0;
+  int64_t bnd = 0;
+  if (ci < ncomms && lane < 2) bnd = a.mpre[a.cstart[C + lane]];
+  for (; ci < ncomms; ci += stride) {
+    const int64_t vs = __shfl_sync(0xffffffffu, bnd, 0), ve = __shfl_sync(0xffffffffu, bnd, 1);
+    const int ci2 = ci + stride;
+    const bool more = ci2 < ncomms;
+    const int32_t C2 = more ? comms[ci2] : 0;
+    int64_t st2 = 0;
+    bool got = false;   // st2 issued (after the first entries' loads)
     for (int64_t t0 = vs + lane; t0 < ve; t0 += U * kWarp) {
       int32_t D[U];
       unsigned long long w[U];
       load_entries<W2, U>(a, t0, ve, kWarp, D, w);
+      if (!got) {
+        if (more && lane < 2) st2 = a.cstart[C2 + lane];
+        got = true;
+      }
 #pragma unroll
       for (int k = 0; k < U; ++k)
         if (D[k] != kEmpty) ok &= table_add_pow2<CAP, V>(keys, vals, D[k], w[k]);
     }
+    if (!got && more && lane < 2) st2 = a.cstart[C2 + lane];
+    const int64_t b2 = more && lane < 2 ? a.mpre[st2] : 0;
     __syncwarp();
     int64_t base = 0;
     for (int t = lane; t < CAP; t += kWarp) {
@@ -1110,6 +1124,8 @@ __global__ void __launch_bounds__(256) agg_warp_k(AggArgs a, const int32_t* __re
     }
     if (lane == 0) a.rlen[C] = base;
     __syncwarp();
+    C = C2;
+    bnd = b2;
   }
   selfloops_finish(a, sl);
   if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicOr(a.error, kErrProbe);
@@ -1332,23 +1348,28 @@ void agg_launch_bucket(const AggArgs& a, int bucket, const int32_t* comms, int n
   if (ncomms <= 0) return;
   switch (bucket) {
     case 0: {
-      auto k = agg_group_k<W2, 8, 64>;
-      (count_launch(), k<<<agrid(k, 256, 0, (ncomms + 31) / 32), 256, 0, s>>>(a, comms, ncomms));
+      auto k = agg_thread_k<W2, kAggThreadEntries>;
+      (count_launch(), k<<<agrid(k, 256, 0, (ncomms + 255) / 256), 256, 0, s>>>(a, comms, ncomms));
       break;
     }
     case 1: {
+      auto k = agg_thread_k<W2, 32>;
+      (count_launch(), k<<<agrid(k, 256, 0, (ncomms + 255) / 256), 256, 0, s>>>(a, comms, ncomms));
+      break;
+    }
+    case 2: {
       auto k = agg_warp_k<W2, 256>;
       (count_launch(), k<<<agrid(k, 256, 0, (ncomms + 7) / 8), 256, 0, s>>>(a, comms, ncomms));
       break;
     }
-    case 2: {
+    case 3: {
       constexpr int CAP = 2048;
       size_t smem = (size_t)CAP * (4 + sizeof(AggVal<W2>) + 1);
       auto k = agg_block_k<W2, CAP, 128>;
       (count_launch(), k<<<agrid(k, 128, smem, ncomms), 128, smem, s>>>(a, comms, ncomms));
       break;
     }
-    case 3: {
+    case 4: {
       constexpr int CAP = 8192;
       size_t smem = (size_t)CAP * (4 + sizeof(AggVal<W2>) + 1);
       auto k = agg_block_k<W2, CAP, 256>;
