@@ -357,6 +357,137 @@ __global__ void __launch_bounds__(256, 3) lm_thread(LMArgs<W> a, const int32_t* 
   acc_flush(acc, a.ctr);
 }
 
+// --------------------- bucket 1, narrow arithmetic: thread per vertex, sorted
+
+// A vertex of degree <= D by one lane: its row is loaded and the neighbours'
+// communities gathered with all loads in flight, the (community, weight)
+// pairs sorted by community with a bitonic network in registers (static
+// indices), each run of one community summed into its first position, and the
+// runs' totals gathered in two halves (bounded registers).  Same decisions as
+// the warp kernel it replaces for narrow sums (K_{i->c} < 2^31).  All 32
+// lanes call it.
+template <typename W, bool ASYNC, int D>
+__device__ __forceinline__ void thread_vertex_sorted(const LMArgs<W>& a, const IterView& iv, BlockAcc& acc,
+                                                     const int32_t* __restrict__ verts, int64_t nverts, int64_t vi) {
+  typedef typename Arith<false>::S S;
+  static_assert((D & (D - 1)) == 0 && D <= 32, "power-of-two network of at most 32");
+  constexpr int32_t kPast = 0x7fffffff;   // sorts after every community id
+  constexpr int H = D / 2;
+  bool moved = false;
+  u128 gv = 0;
+  int graph = 0;
+  unsigned n_edges = 0, n_visited = 0, n_cand = 0;
+  do {
+    if (vi >= nverts) break;
+    const int32_t i = verts[vi];
+    const int64_t b = a.off[i], e = a.off[i + 1];
+    const int32_t d = a.memb[i];
+    const long long Ki = a.K[i];
+    if (!is_active(a, iv, i)) break;
+    long long M;
+    if (!graph_of(a, i, &M, &graph)) break;
+    const long long sd = ld_sig<ASYNC>(a.sig + d);
+    const int32_t szd = ld_size<ASYNC>(a.csize + d);
+    int32_t k[D];
+    unsigned w[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const bool v = b + j < e;
+      k[j] = v ? a.col[b + j] : i;
+      w[j] = v ? (unsigned)a.wt[b + j] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const bool other = k[j] != i;   // a self-loop adds to no K_{i->c}
+      k[j] = other ? ld_memb<ASYNC>(a.memb + k[j]) : kPast;
+      if (!other) w[j] = 0u;
+    }
+#pragma unroll
+    for (int kk = 2; kk <= D; kk <<= 1) {
+#pragma unroll
+      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+#pragma unroll
+        for (int x = 0; x < D; ++x) {
+          const int y = x ^ jj;
+          if (y > x) {
+            const bool up = (x & kk) == 0;
+            if ((k[x] > k[y]) == up) {
+              const int32_t tk = k[x]; k[x] = k[y]; k[y] = tk;
+              const unsigned tw = w[x]; w[x] = w[y]; w[y] = tw;
+            }
+          }
+        }
+      }
+    }
+    // run heads (first position of each community) carry the run's sum
+    unsigned heads = 0u, run = 0u;
+#pragma unroll
+    for (int j = D - 1; j >= 0; --j) {
+      run += w[j];
+      if (k[j] != kPast && (j == 0 || k[j] != k[j - 1])) {
+        heads |= 1u << j;
+        w[j] = run;
+        run = 0u;
+      }
+    }
+    unsigned long long kid = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+      if (((heads >> j) & 1u) && k[j] == d) kid = w[j];
+    const bool want_size = a.guard && szd == 1;
+    S bg = Arith<false>::lowest();
+    int32_t bc = -1, bsz = 0;
+    unsigned ncand = 0;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      long long sg[H];
+      bool one[H];
+#pragma unroll
+      for (int t = 0; t < H; ++t) {
+        const int j = half * H + t;
+        const bool cand = ((heads >> j) & 1u) && k[j] != d;
+        sg[t] = cand ? ld_sig<ASYNC>(a.sig + k[j]) : 0;
+        one[t] = cand && want_size && k[j] > d && ld_size<ASYNC>(a.csize + k[j]) == 1;
+      }
+#pragma unroll
+      for (int t = 0; t < H; ++t) {
+        const int j = half * H + t;
+        if (((heads >> j) & 1u) && k[j] != d) {
+          ++ncand;
+          const S g = Arith<false>::score(M, (long long)w[j], Ki, sg[t]);
+          if (better(g, k[j], bg, bc)) { bg = g; bc = k[j]; bsz = one[t] ? 1 : 0; }
+        }
+      }
+    }
+    n_cand = ncand;
+    n_edges = (unsigned)(e - b);
+    n_visited = 1;
+    moved = commit_choice<W, false, ASYNC>(a, acc, i, d, Ki, sd, szd, bg, bc, kid, M, graph, &gv, bsz);
+    if (moved && a.prune) mark_row<8>(a, iv, i, b, e);
+  } while (false);
+  n_edges = __reduce_add_sync(0xffffffffu, n_edges);
+  n_visited = __reduce_add_sync(0xffffffffu, n_visited);
+  n_cand = __reduce_add_sync(0xffffffffu, n_cand);
+  if ((threadIdx.x & 31) == 0 && n_visited) {
+    atomicAdd(&acc.edges, (unsigned long long)n_edges);
+    atomicAdd(&acc.visited, (unsigned long long)n_visited);
+    atomicAdd(&acc.cands, (unsigned long long)n_cand);
+  }
+  warp_move_totals(a, acc, moved, graph, gv);
+}
+
+template <typename W, bool ASYNC, int D>
+__global__ void __launch_bounds__(128) lm_thread_sorted(LMArgs<W> a, const int32_t* __restrict__ verts, int nverts) {
+  const IterView iv = iter_view(a);
+  __shared__ BlockAcc acc;
+  acc_init(acc);
+  __syncthreads();
+  for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < nverts; base += gridDim.x * blockDim.x)
+    thread_vertex_sorted<W, ASYNC, D>(a, iv, acc, verts, nverts, base + (int)(threadIdx.x & 31));
+  __syncthreads();
+  acc_flush(acc, a.ctr);
+}
+
 // ------------------------------------------ buckets 1-2: warp per vertex
 
 // One vertex of degree <= U * 32 by one warp: its neighbour communities summed
@@ -994,8 +1125,13 @@ void launch_bucket_t(const LMArgs<W>& a, int bucket, const int32_t* verts, int n
       break;
     }
     case 1: {
-      auto k = lm_warp<W, WIDE, ASYNC, 64, 1>;
-      (count_launch(), k<<<grid_for(k, 256, 0, (nverts + 7) / 8), 256, 0, s>>>(a, verts, nverts));
+      if (!WIDE) {   // narrow sums: a lane per vertex, its row sorted in registers
+        auto k = lm_thread_sorted<W, ASYNC, 32>;
+        (count_launch(), k<<<grid_for(k, 128, 0, (nverts + 127) / 128), 128, 0, s>>>(a, verts, nverts));
+      } else {
+        auto k = lm_warp<W, WIDE, ASYNC, 64, 1>;
+        (count_launch(), k<<<grid_for(k, 256, 0, (nverts + 7) / 8), 256, 0, s>>>(a, verts, nverts));
+      }
       break;
     }
     case 2: {
