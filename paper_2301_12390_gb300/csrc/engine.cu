@@ -166,6 +166,8 @@ struct louvain_ctx {
   DevCounters* h_ctr = nullptr;
   unsigned long long* h_acc = nullptr;
   int64_t* h_scal = nullptr;
+  void* h_pair = nullptr;   // pinned staging of fetch_pair (grown on demand)
+  size_t h_pair_cap = 0;
 
   // several graphs (block-diagonal CSR): G graphs, vertex ranges vo0
   int64_t G = 1;
@@ -297,6 +299,27 @@ int check_options(const louvain_options* o) {
 int fetch(louvain_ctx* c, void* host, const void* dev, size_t bytes) {
   CK(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  return 0;
+}
+
+// Two small device arrays to host with one synchronisation (through pinned
+// staging, so both copies are queued before the stream is waited for).
+int fetch_pair(louvain_ctx* c, void* h1, const void* d1, size_t b1, void* h2, const void* d2, size_t b2) {
+  const size_t o2 = (b1 + 15) & ~(size_t)15, need = o2 + b2;
+  if (need > c->h_pair_cap) {
+    if (c->h_pair) cudaFreeHost(c->h_pair);
+    c->h_pair = nullptr;
+    c->h_pair_cap = 0;
+    const size_t cap = need < 4096 ? 4096 : 2 * need;
+    CK(cudaMallocHost(&c->h_pair, cap));
+    c->h_pair_cap = cap;
+  }
+  char* p = (char*)c->h_pair;
+  CK(cudaMemcpyAsync(p, d1, b1, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(p + o2, d2, b2, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  memcpy(h1, p, b1);
+  memcpy(h2, p + o2, b2);
   return 0;
 }
 
@@ -477,8 +500,9 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
       CKLAUNCH();
       hchunks.resize(nhubs + 1);
       hschunks.resize(nhubs + 1);
-      if (int r = fetch(c, hchunks.data(), c->chunk_pre, hchunks.size() * sizeof(int64_t))) return r;
-      if (int r = fetch(c, hschunks.data(), c->spre, hschunks.size() * sizeof(int64_t))) return r;
+      if (int r = fetch_pair(c, hchunks.data(), c->chunk_pre, hchunks.size() * sizeof(int64_t), hschunks.data(),
+                             c->spre, hschunks.size() * sizeof(int64_t)))
+        return r;
       if (hschunks[nhubs] > c->npart) return fail(c, LOUVAIN_ERR_INTERNAL, "hub partial buffer too small");
     }
     return 0;
@@ -876,8 +900,8 @@ int aggregate(louvain_ctx* c, const PassState& g, int64_t k, PassState* next, st
                       multi ? c->vo_next : nullptr, c->gbase, c->chunk_pre, c->spre, c->glo, c->tmp, s);
     int64_t nchunks = 0, nschunks = 0;
     CKLAUNCH();
-    if (int r = fetch(c, &nchunks, c->chunk_pre + ng, sizeof(int64_t))) return r;
-    if (int r = fetch(c, &nschunks, c->spre + ng, sizeof(int64_t))) return r;
+    if (int r = fetch_pair(c, &nchunks, c->chunk_pre + ng, sizeof(int64_t), &nschunks, c->spre + ng, sizeof(int64_t)))
+      return r;
     agg_launch_global<W, W2>(a, c->list + ko[kAggGlobal], (int)ng, c->gbase, c->chunk_pre, nchunks, c->spre,
                              nschunks, s);
   }
@@ -886,9 +910,8 @@ int aggregate(louvain_ctx* c, const PassState& g, int64_t k, PassState* next, st
   scan_i64(c->rlen, c->offX[dst], k, c->offX[dst] + k, c->tmp, s);
   CKLAUNCH();
   int64_t nnz2 = 0;
-  if (int r = fetch(c, &nnz2, c->offX[dst] + k, sizeof(int64_t))) return r;
   int flag = 0;
-  if (int r = fetch(c, &flag, c->flags, sizeof(int))) return r;
+  if (int r = fetch_pair(c, &nnz2, c->offX[dst] + k, sizeof(int64_t), &flag, c->flags, sizeof(int))) return r;
   if (flag) return fail(c, LOUVAIN_ERR_INTERNAL, "aggregation: hash table overflow");
   agg_compact<W2>(c->cstart, c->mpre, c->offX[dst], k, nnz2, c->crow, c->tcol, (const W2*)c->tw, c->colX[dst],
                   (W2*)c->wX[dst], s);
@@ -2106,6 +2129,7 @@ void louvain_destroy(louvain_ctx* c) {
   if (c->h_ctr) cudaFreeHost(c->h_ctr);
   if (c->h_acc) cudaFreeHost(c->h_acc);
   if (c->h_scal) cudaFreeHost(c->h_scal);
+  if (c->h_pair) cudaFreeHost(c->h_pair);
   if (c->h_iter) cudaFreeHost(c->h_iter);
   free_host_graph_buffers(c);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
