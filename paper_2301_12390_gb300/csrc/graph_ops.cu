@@ -1252,9 +1252,10 @@ __global__ void __launch_bounds__(256) agg_global_insert_k(AggArgs a, const int3
       int32_t kk[J];
       unsigned long long vv[J];
 #pragma unroll
-      for (int j = 0; j < J; ++j) {
-        kk[j] = skeys[t0 + j * 256 + threadIdx.x];
-        vv[j] = (unsigned long long)svals[t0 + j * 256 + threadIdx.x];
+      for (int j = 0; j < J; ++j) {   // slots past CAP (a table smaller than J * 256) read as empty
+        const int t = t0 + j * 256 + (int)threadIdx.x;
+        kk[j] = t < CAP ? skeys[t] : kEmpty;
+        vv[j] = t < CAP ? (unsigned long long)svals[t] : 0ull;
       }
       ok &= gtable_add_many<J>(keys, vals, cap, kk, vv);
     }

@@ -916,6 +916,7 @@ __global__ void __launch_bounds__(256) lm_hub_insert(LMArgs<W> a, const int32_t*
   const int64_t x0 = b + q * kHubChunk, x1 = min(e, x0 + kHubChunk);
   bool ok = true;
   constexpr int U = kHubChunk / 256;
+  static_assert(U >= 1 && kHubChunk % 256 == 0, "a chunk covers whole rounds of 256 threads");
   for (int64_t y = x0; y < x1; y += U * 256) {
     int32_t cc[U];
     unsigned long long ww[U];
@@ -940,9 +941,10 @@ __global__ void __launch_bounds__(256) lm_hub_insert(LMArgs<W> a, const int32_t*
     int32_t kk[J];
     unsigned long long vv[J];
 #pragma unroll
-    for (int j = 0; j < J; ++j) {
-      kk[j] = skeys[t0 + j * 256 + threadIdx.x];
-      vv[j] = (unsigned long long)svals[t0 + j * 256 + threadIdx.x];
+    for (int j = 0; j < J; ++j) {   // slots past CAP (a table smaller than J * 256) read as empty
+      const int t = t0 + j * 256 + (int)threadIdx.x;
+      kk[j] = t < CAP ? skeys[t] : kEmpty;
+      vv[j] = t < CAP ? (unsigned long long)svals[t] : 0ull;
     }
     ok &= gtable_add_many<J>(keys, vals, cap, kk, vv);
   }
