@@ -50,7 +50,7 @@ L2_BYTES = 126 << 20   # GB300 L2 (about 126 MB)
 # local-moving launch of an asynchronous R-MAT s22 run with L2 kept between
 # launches: 13.07 GB for 4.66 GB of algorithmic bytes.  Taken on the current
 # kernels; None where no capture was taken.
-LM_TRAFFIC_PER_BYTE = {("rmat22", "async"): 2.81}
+LM_TRAFFIC_PER_BYTE = {("rmat22", "async"): 1.94}
 UNIT = "edges/s"
 
 
@@ -432,8 +432,9 @@ def bench_ours(args):
                          "traffic": (LM_TRAFFIC_PER_BYTE[(args.workload, args.mode)] * lm_bytes / args.steps
                                      if (args.workload, args.mode) in LM_TRAFFIC_PER_BYTE else None),
                          "traffic_unit": "bytes per step (local-moving phase)",
-                         "traffic_source": "ncu DRAM bytes of every local-moving launch of one run, L2 kept between "
-                                           "launches, scaled to this step by its algorithmic bytes",
+                         "traffic_source": "ncu DRAM bytes of every local-moving launch of pass 0 of one run (two "
+                                           "iterations, L2 kept between launches) per algorithmic byte of that run, "
+                                           "applied to this step's algorithmic bytes",
                          "kernel": "local-moving phase (all its kernels, CUDA events)",
                          "peak_source": peak_src},
             "cpu_baseline": cpu,
