@@ -1645,7 +1645,7 @@ int load_graphs(louvain_ctx* c, int64_t G, const int64_t* vo, int64_t n, int64_t
     c->tables_dirty = false;
   }
   if (c->opt.validate) {
-    validate_csr(c->off0, c->col0, c->w0, n, nnz, c->flags, c->acc, s);
+    validate_csr(c->off0, c->col0, c->w0, n, nnz, c->flags, c->acc, c->crow, s);
     CKLAUNCH();
     int flags = 0;
     unsigned long long h[2];
@@ -1658,7 +1658,7 @@ int load_graphs(louvain_ctx* c, int64_t G, const int64_t* vo, int64_t n, int64_t
   }
   // input degrees (for louvain_modularity)
   CK(cudaMemsetAsync(c->acc, 0, 8 * sizeof(unsigned long long), s));
-  row_sums<int32_t>(c->off0, c->col0, c->w0, n, c->K0, c->acc, s);
+  row_sums<int32_t>(c->off0, c->col0, c->w0, n, nnz, c->crow, c->K0, c->acc, s);
   CKLAUNCH();
   if (int r = fetch(c, c->h_acc, c->acc, 4 * sizeof(unsigned long long))) return r;
   if (c->h_acc[1] != 0 || c->h_acc[0] >= (1ull << 62))

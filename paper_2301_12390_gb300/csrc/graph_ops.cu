@@ -324,62 +324,85 @@ __device__ __forceinline__ int row_of(const int64_t* soff, int nr, int64_t x) {
   return lo;
 }
 
-// Row sums: warps take consecutive 32-entry chunks of the block's rows; a
-// segmented scan across the warp (rows are non-decreasing along the chunk)
-// leaves each row's chunk total on the row's last lane, which adds it to the
-// row in shared memory — one atomic per (row, chunk) instead of per entry.
+__global__ void chunk_rows_k(const int64_t* __restrict__ off, int64_t n, int64_t nchunks, int32_t* crow);
+
+// Row sums over merge-path chunks (crow from chunk_rows_k: every warp gets
+// kRelabelChunk rows + entries, however skewed the rows are).  A warp walks
+// its chunk's rows 32 at a time; each lane finds its entry's row by a shuffle
+// search over the 32 row starts; a segmented scan across the warp (rows are
+// non-decreasing along the lanes) leaves each row's total on its last lane,
+// which adds it to K (zeroed before).  M and the self-loop total are summed
+// per lane and added once per warp.
 template <typename W>
-__global__ void __launch_bounds__(kT) row_sums_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                                                 const W* __restrict__ wt, int64_t n, long long* K,
-                                                 unsigned long long* acc) {
-  __shared__ int64_t soff[kT + 1];
-  __shared__ unsigned long long ks[kT];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t v0 = (int64_t)blockIdx.x * kT;
-  const int nr = (int)min((int64_t)kT, n - v0);
-  for (int t = threadIdx.x; t <= nr; t += kT) soff[t] = off[v0 + t];
-  ks[threadIdx.x] = 0;
-  __syncthreads();
-  unsigned long long loops = 0;
-  const int64_t e0 = soff[0], e1 = soff[nr];
-  for (int64_t c0 = e0 + (int64_t)wid * kWarp; c0 < e1; c0 += (int64_t)(kT / kWarp) * kWarp) {
-    const int64_t x = c0 + lane;
-    int r = -1;
-    unsigned long long v = 0;
-    if (x < e1) {
-      r = row_of(soff, nr, x);
-      v = (unsigned long long)wt[x];
-      if (col[x] == v0 + r) loops += v;
-    }
+__global__ void __launch_bounds__(256) row_sums_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                                                 const W* __restrict__ wt, int64_t n, int64_t nnz,
+                                                 const int32_t* __restrict__ crow, int64_t nchunks,
+                                                 unsigned long long* K, unsigned long long* acc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  u128 mtot = 0, ltot = 0;   // this lane's share of M and of the self-loop total
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += warps) {
+    const int64_t X0 = c * kRelabelChunk - crow[c];
+    const int64_t X1 = min(nnz, (c + 1) * kRelabelChunk - crow[c + 1]);
+    for (int64_t r = crow[c];; r += kWarp) {
+      const int64_t u = r + lane;
+      const int64_t o = off[min(u, n)];
+      const int64_t wend = __shfl_sync(0xffffffffu, off[min(r + kWarp, n)], 0);
+      const int64_t xs = max(X0, __shfl_sync(0xffffffffu, o, 0)), xe = min(X1, wend);
+      for (int64_t x = xs + lane; x - lane < xe; x += kWarp) {
+        int rr = 0;
 #pragma unroll
-    for (int d = 1; d < kWarp; d <<= 1) {
-      unsigned long long u = __shfl_up_sync(0xffffffffu, v, d);
-      int ru = __shfl_up_sync(0xffffffffu, r, d);
-      if (lane >= d && ru == r) v += u;
+        for (int step = 16; step >= 1; step >>= 1) {
+          const int cand = rr + step;
+          if (__shfl_sync(0xffffffffu, o, cand) <= x) rr = cand;
+        }
+        const bool in = x < xe;
+        unsigned long long v = in ? (unsigned long long)wt[x] : 0ull;
+        if (in && col[x] == r + rr) ltot += v;
+        mtot += v;
+        const int row = in ? rr : -1;
+#pragma unroll
+        for (int d = 1; d < kWarp; d <<= 1) {
+          const unsigned long long up = __shfl_up_sync(0xffffffffu, v, d);
+          const int ru = __shfl_up_sync(0xffffffffu, row, d);
+          if (lane >= d && ru == row) v += up;
+        }
+        const int rn = __shfl_down_sync(0xffffffffu, row, 1);
+        if (row >= 0 && (lane == kWarp - 1 || rn != row)) atomicAdd(K + (r + row), v);
+      }
+      if (wend >= X1) break;
     }
-    int rn = __shfl_down_sync(0xffffffffu, r, 1);
-    if (r >= 0 && (lane == kWarp - 1 || rn != r)) atomicAdd(&ks[r], v);
   }
-  __syncthreads();
-  u128 mine = 0;
-  if (threadIdx.x < nr) {
-    K[v0 + threadIdx.x] = (long long)ks[threadIdx.x];
-    mine = ks[threadIdx.x];
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    mtot += ((u128)__shfl_xor_sync(0xffffffffu, (unsigned long long)(mtot >> 64), m) << 64) |
+            (u128)__shfl_xor_sync(0xffffffffu, (unsigned long long)mtot, m);
+    ltot += ((u128)__shfl_xor_sync(0xffffffffu, (unsigned long long)(ltot >> 64), m) << 64) |
+            (u128)__shfl_xor_sync(0xffffffffu, (unsigned long long)ltot, m);
   }
-  block_add_u128(mine, acc, acc + 1);
-  block_add_u128((u128)loops, acc + 2, acc + 3);
+  if (lane == 0) {
+    if (mtot) atomic_add_u128(acc, acc + 1, mtot);
+    if (ltot) atomic_add_u128(acc + 2, acc + 3, ltot);
+  }
 }
 
 template <typename W>
-void row_sums(const int64_t* off, const int32_t* col, const W* wt, int64_t n, long long* K, unsigned long long* acc,
-              cudaStream_t s) {
+void row_sums(const int64_t* off, const int32_t* col, const W* wt, int64_t n, int64_t nnz, int32_t* crow,
+              long long* K, unsigned long long* acc, cudaStream_t s) {
   if (n <= 0) return;
-  (count_launch(), row_sums_k<W><<<(unsigned)((n + kT - 1) / kT), kT, 0, s>>>(off, col, wt, n, K, acc));
+  cudaMemsetAsync(K, 0, n * sizeof(long long), s);
+  if (nnz <= 0) return;
+  const int64_t nchunks = (n + nnz + kRelabelChunk - 1) / kRelabelChunk;
+  (count_launch(), chunk_rows_k<<<grid1d(nchunks + 1), kT, 0, s>>>(off, n, nchunks, crow));
+  int64_t blocks = (nchunks + 7) / 8;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  (count_launch(), row_sums_k<W><<<(unsigned)blocks, 256, 0, s>>>(off, col, wt, n, nnz, crow, nchunks,
+                                                                  (unsigned long long*)K, acc));
 }
-template void row_sums<int32_t>(const int64_t*, const int32_t*, const int32_t*, int64_t, long long*,
-                                unsigned long long*, cudaStream_t);
-template void row_sums<int64_t>(const int64_t*, const int32_t*, const int64_t*, int64_t, long long*,
-                                unsigned long long*, cudaStream_t);
+template void row_sums<int32_t>(const int64_t*, const int32_t*, const int32_t*, int64_t, int64_t, int32_t*,
+                                long long*, unsigned long long*, cudaStream_t);
+template void row_sums<int64_t>(const int64_t*, const int32_t*, const int64_t*, int64_t, int64_t, int32_t*,
+                                long long*, unsigned long long*, cudaStream_t);
 
 __global__ void pass_init_k(int64_t n, const long long* K, int32_t* memb, long long* sig, int32_t* csize,
                             int32_t* sa, int32_t* sb) {
@@ -1920,32 +1943,62 @@ __global__ void validate_off_k(const int64_t* off, int64_t n, int64_t nnz, int* 
   if (blockIdx.x == 0 && threadIdx.x == 0 && (off[0] != 0 || off[n] != nnz)) atomicOr(flags, 1);
 }
 
-__global__ void __launch_bounds__(kT) validate_rows_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                                                      const int32_t* __restrict__ wt, int64_t n, int* flags,
+// Column range, weights and the two symmetry fingerprints over merge-path
+// chunks (crow from chunk_rows_k), walked as in row_sums_k: every warp gets
+// the same number of rows + entries however skewed the rows are.  The sums
+// wrap modulo 2^64 on both sides alike.
+__global__ void __launch_bounds__(256) validate_rows_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                                                      const int32_t* __restrict__ wt, int64_t n, int64_t nnz,
+                                                      const int32_t* __restrict__ crow, int64_t nchunks, int* flags,
                                                       unsigned long long* hashes) {
-  __shared__ int64_t soff[kT + 1];
-  const int64_t v0 = (int64_t)blockIdx.x * kT;
-  const int nr = (int)min((int64_t)kT, n - v0);
-  for (int t = threadIdx.x; t <= nr; t += kT) soff[t] = off[v0 + t];
-  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   unsigned long long h1 = 0, h2 = 0;
   int f = 0;
-  for (int64_t x = soff[0] + threadIdx.x; x < soff[nr]; x += kT) {
-    int r = row_of(soff, nr, x);
-    int32_t v = col[x], w = wt[x];
-    if (v < 0 || v >= n) { f |= 2; continue; }
-    if (w <= 0) f |= 4;
-    uint32_t u = (uint32_t)(v0 + r);
-    h1 += entry_hash(u, (uint32_t)v, (uint32_t)w);
-    h2 += entry_hash((uint32_t)v, u, (uint32_t)w);
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += warps) {
+    const int64_t X0 = c * kRelabelChunk - crow[c];
+    const int64_t X1 = min(nnz, (c + 1) * kRelabelChunk - crow[c + 1]);
+    for (int64_t r = crow[c];; r += kWarp) {
+      const int64_t o = off[min(r + lane, n)];
+      const int64_t wend = __shfl_sync(0xffffffffu, off[min(r + kWarp, n)], 0);
+      const int64_t xs = max(X0, __shfl_sync(0xffffffffu, o, 0)), xe = min(X1, wend);
+      for (int64_t x = xs + lane; x - lane < xe; x += kWarp) {
+        int rr = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+          const int cand = rr + step;
+          if (__shfl_sync(0xffffffffu, o, cand) <= x) rr = cand;
+        }
+        if (x < xe) {
+          const int32_t v = col[x], w = wt[x];
+          if (v < 0 || v >= n) {
+            f |= 2;
+          } else {
+            if (w <= 0) f |= 4;
+            const uint32_t u = (uint32_t)(r + rr);
+            h1 += entry_hash(u, (uint32_t)v, (uint32_t)w);
+            h2 += entry_hash((uint32_t)v, u, (uint32_t)w);
+          }
+        }
+      }
+      if (wend >= X1) break;
+    }
   }
-  if (f) atomicOr(flags, f);
-  atomicAdd(hashes, h1);
-  atomicAdd(hashes + 1, h2);
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    h1 += __shfl_xor_sync(0xffffffffu, h1, m);
+    h2 += __shfl_xor_sync(0xffffffffu, h2, m);
+    f |= __shfl_xor_sync(0xffffffffu, f, m);
+  }
+  if (lane == 0) {
+    if (f) atomicOr(flags, f);
+    atomicAdd(hashes, h1);
+    atomicAdd(hashes + 1, h2);
+  }
 }
 
 void validate_csr(const int64_t* off, const int32_t* col, const int32_t* wt, int64_t n, int64_t nnz, int* flags,
-                  unsigned long long* hashes, cudaStream_t s) {
+                  unsigned long long* hashes, int32_t* crow, cudaStream_t s) {
   cudaMemsetAsync(flags, 0, sizeof(int), s);
   cudaMemsetAsync(hashes, 0, 2 * sizeof(unsigned long long), s);
   if (n <= 0) return;
@@ -1953,8 +2006,13 @@ void validate_csr(const int64_t* off, const int32_t* col, const int32_t* wt, int
   int hf = 0;
   cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
-  if (hf) return;
-  (count_launch(), validate_rows_k<<<(unsigned)((n + kT - 1) / kT), kT, 0, s>>>(off, col, wt, n, flags, hashes));
+  if (hf || nnz <= 0) return;   // the chunks below need monotone offsets
+  const int64_t nchunks = (n + nnz + kRelabelChunk - 1) / kRelabelChunk;
+  (count_launch(), chunk_rows_k<<<grid1d(nchunks + 1), kT, 0, s>>>(off, n, nchunks, crow));
+  int64_t blocks = (nchunks + 7) / 8;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  (count_launch(), validate_rows_k<<<(unsigned)blocks, 256, 0, s>>>(off, col, wt, n, nnz, crow, nchunks, flags,
+                                                                    hashes));
 }
 
 // ------------------------------------------------------------ conversions
