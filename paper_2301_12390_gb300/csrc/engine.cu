@@ -1645,22 +1645,27 @@ int load_graphs(louvain_ctx* c, int64_t G, const int64_t* vo, int64_t n, int64_t
     c->tables_dirty = false;
   }
   if (c->opt.validate) {
-    validate_csr(c->off0, c->col0, c->w0, n, nnz, c->flags, c->acc, c->crow, s);
+    // offsets first: the entry checks below walk chunks found from them
+    validate_offsets(c->off0, n, nnz, c->flags, s);
     CKLAUNCH();
     int flags = 0;
-    unsigned long long h[2];
     if (int r = fetch(c, &flags, c->flags, sizeof(int))) return r;
-    if (int r = fetch(c, h, c->acc, sizeof(h))) return r;
     if (flags & 1) return fail(c, LOUVAIN_ERR_BAD_CSR, "offsets not monotone or wrong ends");
+  }
+  // input degrees (for louvain_modularity); with validation the same pass
+  // checks the entries (acc[4..5]: the symmetry fingerprints)
+  CK(cudaMemsetAsync(c->acc, 0, 8 * sizeof(unsigned long long), s));
+  row_sums<int32_t>(c->off0, c->col0, c->w0, n, nnz, c->crow, c->K0, c->acc, c->opt.validate ? c->flags : nullptr,
+                    c->acc + 4, s);
+  CKLAUNCH();
+  if (int r = fetch(c, c->h_acc, c->acc, 6 * sizeof(unsigned long long))) return r;
+  if (c->opt.validate) {
+    int flags = 0;
+    if (int r = fetch(c, &flags, c->flags, sizeof(int))) return r;
     if (flags & 2) return fail(c, LOUVAIN_ERR_BAD_CSR, "column index out of range");
     if (flags & 4) return fail(c, LOUVAIN_ERR_BAD_CSR, "weight <= 0");
-    if (h[0] != h[1]) return fail(c, LOUVAIN_ERR_NOT_SYMMETRIC, "CSR is not symmetric");
+    if (c->h_acc[4] != c->h_acc[5]) return fail(c, LOUVAIN_ERR_NOT_SYMMETRIC, "CSR is not symmetric");
   }
-  // input degrees (for louvain_modularity)
-  CK(cudaMemsetAsync(c->acc, 0, 8 * sizeof(unsigned long long), s));
-  row_sums<int32_t>(c->off0, c->col0, c->w0, n, nnz, c->crow, c->K0, c->acc, s);
-  CKLAUNCH();
-  if (int r = fetch(c, c->h_acc, c->acc, 4 * sizeof(unsigned long long))) return r;
   if (c->h_acc[1] != 0 || c->h_acc[0] >= (1ull << 62))
     return fail(c, LOUVAIN_ERR_OVERFLOW, "total weight M must be below 2^62");
   c->M0 = (int64_t)c->h_acc[0];

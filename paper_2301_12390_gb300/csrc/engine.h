@@ -149,10 +149,14 @@ void hub_layout(const int64_t* off, const int32_t* hubs, int64_t nhubs, int64_t*
 
 // Row sums K (int64) of a CSR, the total M (u128 lo/hi) and the self-loop
 // total (u128 at acc[2..3]); crow: (n + nnz) / kRelabelChunk + 2 ints of
-// scratch for the merge-path chunks.
+// scratch for the merge-path chunks.  With flags non-null the same pass
+// checks the entries: flags |= 2 column out of range, 4 weight <= 0;
+// hashes[0..1] += sums of mix(u,v,w) and mix(v,u,w) (the offsets must have
+// passed validate_offsets).
 template <typename W>
 void row_sums(const int64_t* off, const int32_t* col, const W* wt, int64_t n, int64_t nnz, int32_t* crow,
-              long long* K, unsigned long long* acc /* [0..1] M lo/hi, [2..3] self-loop total */, cudaStream_t s);
+              long long* K, unsigned long long* acc /* [0..1] M lo/hi, [2..3] self-loop total */, int* flags,
+              unsigned long long* hashes, cudaStream_t s);
 
 // Pass set-up: memb = identity, Sigma = K, sizes 1, stamps -1.
 void pass_init(int64_t n, const long long* K, int32_t* memb, long long* sig, int32_t* csize, int32_t* stampA,
@@ -299,9 +303,8 @@ void graph_ids(const int64_t* vo, int G, int64_t n, int32_t* gid, const int64_t*
 
 // Input checks: flags |= 1 offsets not monotone / bad ends, 2 col out of
 // range, 4 weight <= 0; hashes[0..1] = sums of mix(u,v,w) and mix(v,u,w).
-// crow: merge-path scratch as for row_sums.
-void validate_csr(const int64_t* off, const int32_t* col, const int32_t* wt, int64_t n, int64_t nnz, int* flags,
-                  unsigned long long* hashes, int32_t* crow, cudaStream_t s);
+// flags = 1 if the offsets decrease or have the wrong ends (else 0).
+void validate_offsets(const int64_t* off, int64_t n, int64_t nnz, int* flags, cudaStream_t s);
 
 // Copies with conversion.
 void widen_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);

@@ -328,47 +328,92 @@ __global__ void chunk_rows_k(const int64_t* __restrict__ off, int64_t n, int64_t
 
 // Row sums over merge-path chunks (crow from chunk_rows_k: every warp gets
 // kRelabelChunk rows + entries, however skewed the rows are).  A warp walks
-// its chunk's rows 32 at a time; each lane finds its entry's row by a shuffle
-// search over the 32 row starts; a segmented scan across the warp (rows are
+// its chunk's rows 32 at a time and each lane finds its entry's row by a
+// shuffle search over the 32 row starts; U rounds of 32 entries are loaded
+// together.  Per round a segmented scan across the warp (rows are
 // non-decreasing along the lanes) leaves each row's total on its last lane,
 // which adds it to K (zeroed before).  M and the self-loop total are summed
-// per lane and added once per warp.
-template <typename W>
+// per lane and added once per warp.  With CHECK the same pass checks the
+// columns' range and the weights' sign (flags 2 and 4; an entry out of range
+// is not used further) and sums the two symmetry fingerprints (they wrap
+// modulo 2^64 on both sides alike).
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ unsigned long long entry_hash(uint32_t u, uint32_t v, uint32_t w) {
+  return mix64((((unsigned long long)u << 32) | v) ^ mix64(0xC0FFEEull + w));
+}
+
+template <typename W, bool CHECK>
 __global__ void __launch_bounds__(256) row_sums_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
                                                  const W* __restrict__ wt, int64_t n, int64_t nnz,
                                                  const int32_t* __restrict__ crow, int64_t nchunks,
-                                                 unsigned long long* K, unsigned long long* acc) {
+                                                 unsigned long long* K, unsigned long long* acc, int* flags,
+                                                 unsigned long long* hashes) {
+  constexpr int U = 4;
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   u128 mtot = 0, ltot = 0;   // this lane's share of M and of the self-loop total
+  unsigned long long h1 = 0, h2 = 0;
+  int f = 0;
   for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += warps) {
     const int64_t X0 = c * kRelabelChunk - crow[c];
     const int64_t X1 = min(nnz, (c + 1) * kRelabelChunk - crow[c + 1]);
     for (int64_t r = crow[c];; r += kWarp) {
-      const int64_t u = r + lane;
-      const int64_t o = off[min(u, n)];
+      const int64_t o = off[min(r + lane, n)];
       const int64_t wend = __shfl_sync(0xffffffffu, off[min(r + kWarp, n)], 0);
       const int64_t xs = max(X0, __shfl_sync(0xffffffffu, o, 0)), xe = min(X1, wend);
-      for (int64_t x = xs + lane; x - lane < xe; x += kWarp) {
-        int rr = 0;
+      for (int64_t x0 = xs; x0 < xe; x0 += U * kWarp) {
+        int rr[U];
+        int32_t v[U];
+        unsigned long long w[U];
 #pragma unroll
-        for (int step = 16; step >= 1; step >>= 1) {
-          const int cand = rr + step;
-          if (__shfl_sync(0xffffffffu, o, cand) <= x) rr = cand;
-        }
-        const bool in = x < xe;
-        unsigned long long v = in ? (unsigned long long)wt[x] : 0ull;
-        if (in && col[x] == r + rr) ltot += v;
-        mtot += v;
-        const int row = in ? rr : -1;
+        for (int k = 0; k < U; ++k) {
+          const int64_t x = x0 + k * kWarp + lane;
+          int q = 0;
 #pragma unroll
-        for (int d = 1; d < kWarp; d <<= 1) {
-          const unsigned long long up = __shfl_up_sync(0xffffffffu, v, d);
-          const int ru = __shfl_up_sync(0xffffffffu, row, d);
-          if (lane >= d && ru == row) v += up;
+          for (int step = 16; step >= 1; step >>= 1) {
+            const int cand = q + step;
+            if (__shfl_sync(0xffffffffu, o, cand) <= x) q = cand;
+          }
+          rr[k] = x < xe ? q : -1;
         }
-        const int rn = __shfl_down_sync(0xffffffffu, row, 1);
-        if (row >= 0 && (lane == kWarp - 1 || rn != row)) atomicAdd(K + (r + row), v);
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          const int64_t x = x0 + k * kWarp + lane;
+          v[k] = rr[k] >= 0 ? col[x] : -1;
+          w[k] = rr[k] >= 0 ? (unsigned long long)wt[x] : 0ull;
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          const int64_t u = r + rr[k];
+          if (rr[k] >= 0) {
+            mtot += w[k];
+            if (v[k] == u) ltot += w[k];
+            if (CHECK) {
+              if (v[k] < 0 || v[k] >= n) {
+                f |= 2;
+              } else {
+                if ((long long)(W)w[k] <= 0) f |= 4;
+                h1 += entry_hash((uint32_t)u, (uint32_t)v[k], (uint32_t)w[k]);
+                h2 += entry_hash((uint32_t)v[k], (uint32_t)u, (uint32_t)w[k]);
+              }
+            }
+          }
+          unsigned long long sum = w[k];
+          const int row = rr[k];
+#pragma unroll
+          for (int d = 1; d < kWarp; d <<= 1) {
+            const unsigned long long up = __shfl_up_sync(0xffffffffu, sum, d);
+            const int ru = __shfl_up_sync(0xffffffffu, row, d);
+            if (lane >= d && ru == row) sum += up;
+          }
+          const int rn = __shfl_down_sync(0xffffffffu, row, 1);
+          if (row >= 0 && (lane == kWarp - 1 || rn != row)) atomicAdd(K + (r + row), sum);
+        }
       }
       if (wend >= X1) break;
     }
@@ -379,16 +424,26 @@ __global__ void __launch_bounds__(256) row_sums_k(const int64_t* __restrict__ of
             (u128)__shfl_xor_sync(0xffffffffu, (unsigned long long)mtot, m);
     ltot += ((u128)__shfl_xor_sync(0xffffffffu, (unsigned long long)(ltot >> 64), m) << 64) |
             (u128)__shfl_xor_sync(0xffffffffu, (unsigned long long)ltot, m);
+    if (CHECK) {
+      h1 += __shfl_xor_sync(0xffffffffu, h1, m);
+      h2 += __shfl_xor_sync(0xffffffffu, h2, m);
+      f |= __shfl_xor_sync(0xffffffffu, f, m);
+    }
   }
   if (lane == 0) {
     if (mtot) atomic_add_u128(acc, acc + 1, mtot);
     if (ltot) atomic_add_u128(acc + 2, acc + 3, ltot);
+    if (CHECK) {
+      if (f) atomicOr(flags, f);
+      atomicAdd(hashes, h1);
+      atomicAdd(hashes + 1, h2);
+    }
   }
 }
 
 template <typename W>
 void row_sums(const int64_t* off, const int32_t* col, const W* wt, int64_t n, int64_t nnz, int32_t* crow,
-              long long* K, unsigned long long* acc, cudaStream_t s) {
+              long long* K, unsigned long long* acc, int* flags, unsigned long long* hashes, cudaStream_t s) {
   if (n <= 0) return;
   cudaMemsetAsync(K, 0, n * sizeof(long long), s);
   if (nnz <= 0) return;
@@ -396,13 +451,18 @@ void row_sums(const int64_t* off, const int32_t* col, const W* wt, int64_t n, in
   (count_launch(), chunk_rows_k<<<grid1d(nchunks + 1), kT, 0, s>>>(off, n, nchunks, crow));
   int64_t blocks = (nchunks + 7) / 8;
   if (blocks > 152 * 8) blocks = 152 * 8;
-  (count_launch(), row_sums_k<W><<<(unsigned)blocks, 256, 0, s>>>(off, col, wt, n, nnz, crow, nchunks,
-                                                                  (unsigned long long*)K, acc));
+  if (flags)
+    (count_launch(), row_sums_k<W, true><<<(unsigned)blocks, 256, 0, s>>>(off, col, wt, n, nnz, crow, nchunks,
+                                                                         (unsigned long long*)K, acc, flags, hashes));
+  else
+    (count_launch(), row_sums_k<W, false><<<(unsigned)blocks, 256, 0, s>>>(off, col, wt, n, nnz, crow, nchunks,
+                                                                          (unsigned long long*)K, acc, nullptr,
+                                                                          nullptr));
 }
 template void row_sums<int32_t>(const int64_t*, const int32_t*, const int32_t*, int64_t, int64_t, int32_t*,
-                                long long*, unsigned long long*, cudaStream_t);
+                                long long*, unsigned long long*, int*, unsigned long long*, cudaStream_t);
 template void row_sums<int64_t>(const int64_t*, const int32_t*, const int64_t*, int64_t, int64_t, int32_t*,
-                                long long*, unsigned long long*, cudaStream_t);
+                                long long*, unsigned long long*, int*, unsigned long long*, cudaStream_t);
 
 __global__ void pass_init_k(int64_t n, const long long* K, int32_t* memb, long long* sig, int32_t* csize,
                             int32_t* sa, int32_t* sb) {
@@ -1927,92 +1987,18 @@ void class_max(const int32_t* cls, int64_t n, int* out, cudaStream_t s) {
 
 // -------------------------------------------------------------- validation
 
-__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
-  z += 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-__device__ __forceinline__ unsigned long long entry_hash(uint32_t u, uint32_t v, uint32_t w) {
-  return mix64((((unsigned long long)u << 32) | v) ^ mix64(0xC0FFEEull + w));
-}
-
 __global__ void validate_off_k(const int64_t* off, int64_t n, int64_t nnz, int* flags) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     if (off[i] > off[i + 1]) atomicOr(flags, 1);
   if (blockIdx.x == 0 && threadIdx.x == 0 && (off[0] != 0 || off[n] != nnz)) atomicOr(flags, 1);
 }
 
-// Column range, weights and the two symmetry fingerprints over merge-path
-// chunks (crow from chunk_rows_k), walked as in row_sums_k: every warp gets
-// the same number of rows + entries however skewed the rows are.  The sums
-// wrap modulo 2^64 on both sides alike.
-__global__ void __launch_bounds__(256) validate_rows_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                                                      const int32_t* __restrict__ wt, int64_t n, int64_t nnz,
-                                                      const int32_t* __restrict__ crow, int64_t nchunks, int* flags,
-                                                      unsigned long long* hashes) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  unsigned long long h1 = 0, h2 = 0;
-  int f = 0;
-  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += warps) {
-    const int64_t X0 = c * kRelabelChunk - crow[c];
-    const int64_t X1 = min(nnz, (c + 1) * kRelabelChunk - crow[c + 1]);
-    for (int64_t r = crow[c];; r += kWarp) {
-      const int64_t o = off[min(r + lane, n)];
-      const int64_t wend = __shfl_sync(0xffffffffu, off[min(r + kWarp, n)], 0);
-      const int64_t xs = max(X0, __shfl_sync(0xffffffffu, o, 0)), xe = min(X1, wend);
-      for (int64_t x = xs + lane; x - lane < xe; x += kWarp) {
-        int rr = 0;
-#pragma unroll
-        for (int step = 16; step >= 1; step >>= 1) {
-          const int cand = rr + step;
-          if (__shfl_sync(0xffffffffu, o, cand) <= x) rr = cand;
-        }
-        if (x < xe) {
-          const int32_t v = col[x], w = wt[x];
-          if (v < 0 || v >= n) {
-            f |= 2;
-          } else {
-            if (w <= 0) f |= 4;
-            const uint32_t u = (uint32_t)(r + rr);
-            h1 += entry_hash(u, (uint32_t)v, (uint32_t)w);
-            h2 += entry_hash((uint32_t)v, u, (uint32_t)w);
-          }
-        }
-      }
-      if (wend >= X1) break;
-    }
-  }
-#pragma unroll
-  for (int m = 16; m >= 1; m >>= 1) {
-    h1 += __shfl_xor_sync(0xffffffffu, h1, m);
-    h2 += __shfl_xor_sync(0xffffffffu, h2, m);
-    f |= __shfl_xor_sync(0xffffffffu, f, m);
-  }
-  if (lane == 0) {
-    if (f) atomicOr(flags, f);
-    atomicAdd(hashes, h1);
-    atomicAdd(hashes + 1, h2);
-  }
-}
-
-void validate_csr(const int64_t* off, const int32_t* col, const int32_t* wt, int64_t n, int64_t nnz, int* flags,
-                  unsigned long long* hashes, int32_t* crow, cudaStream_t s) {
+// Offsets monotone with the right ends (flag 1); the entries are checked by
+// row_sums with its check on, which needs monotone offsets for its chunks.
+void validate_offsets(const int64_t* off, int64_t n, int64_t nnz, int* flags, cudaStream_t s) {
   cudaMemsetAsync(flags, 0, sizeof(int), s);
-  cudaMemsetAsync(hashes, 0, 2 * sizeof(unsigned long long), s);
   if (n <= 0) return;
   (count_launch(), validate_off_k<<<grid1d(n), kT, 0, s>>>(off, n, nnz, flags));
-  int hf = 0;
-  cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, s);
-  cudaStreamSynchronize(s);
-  if (hf || nnz <= 0) return;   // the chunks below need monotone offsets
-  const int64_t nchunks = (n + nnz + kRelabelChunk - 1) / kRelabelChunk;
-  (count_launch(), chunk_rows_k<<<grid1d(nchunks + 1), kT, 0, s>>>(off, n, nchunks, crow));
-  int64_t blocks = (nchunks + 7) / 8;
-  if (blocks > 152 * 8) blocks = 152 * 8;
-  (count_launch(), validate_rows_k<<<(unsigned)blocks, 256, 0, s>>>(off, col, wt, n, nnz, crow, nchunks, flags,
-                                                                    hashes));
 }
 
 // ------------------------------------------------------------ conversions
