@@ -347,7 +347,7 @@ typedef struct louvain_server louvain_server;
 typedef struct {
   int32_t slots;              /* worker slots (contexts), default 2 */
   int32_t batch_max_graphs;   /* at most this many requests per run, default 1024 */
-  int64_t batch_max_entries;  /* at most this many CSR entries per run, default 64 Mi; 0 = one request per run */
+  int64_t batch_max_entries;  /* at most this many CSR entries per run, default 256 Mi; 0 = one request per run */
   int64_t hbm_budget_bytes;   /* device bytes all slots' arenas may hold; 0 = 90% of free memory at creation */
   int64_t borrow_inputs;      /* 0 (default): louvain_server_submit copies the graph (into a reused pinned
                                  host pool); 1: it keeps the caller's pointers, the caller keeps the arrays

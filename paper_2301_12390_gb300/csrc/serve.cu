@@ -320,7 +320,7 @@ int louvain_server_default_config(louvain_server_config* cfg) {
   memset(cfg, 0, sizeof(*cfg));
   cfg->slots = 2;
   cfg->hbm_budget_bytes = 0;
-  cfg->batch_max_entries = 64ll << 20;
+  cfg->batch_max_entries = 256ll << 20;   // measured best of 16M-1G on the 10,000-request stream
   cfg->batch_max_graphs = 1024;
   return 0;
 }
