@@ -137,11 +137,13 @@ def test_sync_parity_max_iterations_and_passes():
 # ------------------------------------------------- vertex mapping, autotuner
 
 @pytest.mark.parametrize("name", ["rmat16", "sbm8192"])
-@pytest.mark.parametrize("thresholds", [[4, 16, 64, 256, 2048], [8, 32, 128, 1024, 4096], [1, 2, 3, 4, 5]])
+@pytest.mark.parametrize("thresholds", [[4, 16, 64, 256, 2048], [8, 32, 128, 1024, 4096], [1, 2, 3, 4, 5],
+                                        [1, 32, 128, 1024, 4096]])
 def test_sync_parity_under_any_mapping(name, thresholds):
     """Which kernel handles a vertex never changes the result: bit-exact sync
-    parity with the oracle under non-default degree thresholds (the last one
-    sends almost every vertex to the hub path)."""
+    parity with the oracle under non-default degree thresholds (the third
+    sends almost every vertex to the hub path, the fourth every vertex of
+    degree 2-32 to the lane-per-vertex sorting kernel)."""
     g = G[name]
     with Louvain(device=0, mode=0, prune=1) as lv:
         lv.set_mapping(thresholds)
