@@ -127,6 +127,21 @@ def test_sync_parity_wide_arithmetic():
     assert ref.M >= 2**31
 
 
+def test_sync_parity_wide_arithmetic_large_communities():
+    """Wide sums with communities above 4,096 member entries: the aggregation
+    takes its global-table path with 64-bit shared sums (three blocks of
+    1,000 vertices, about 22,000 entries each)."""
+    base = gg.sbm(11, 3000, 3, 0.02, 0.0007)
+    rows = np.repeat(np.arange(base.n), np.diff(base.off))
+    lo, hi = np.minimum(rows, base.col), np.maximum(rows, base.col)
+    w = (2**31 - 1 - ((lo.astype(np.int64) * 131 + hi) % 1000)).astype(np.int32)
+    g = gg.CSR(base.n, base.off, base.col, w)
+    got, ref = assert_sync_parity(g, prune=1)
+    assert ref.M >= 2**31
+    dsum = np.bincount(ref.passes[0].level, weights=np.diff(g.off))   # member entries per pass-0 community
+    assert dsum.max() > 4096
+
+
 def test_sync_parity_max_iterations_and_passes():
     g = G["sbm8192"]
     assert_sync_parity(g, max_iterations=1)
