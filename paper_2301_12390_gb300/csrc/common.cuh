@@ -5,6 +5,7 @@
 // increase), hashing for per-vertex community-weight tables, and warp
 // reductions.  Nothing here is shared with the CPU oracle.
 #pragma once
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -40,6 +41,19 @@ struct DevCounters {
   int error;
   int pad;
 };
+
+// Raises a kernel's dynamic shared-memory limit on the current device the
+// first time a call site launches it there (`done`: the call site's bit per
+// device; several host threads may race to set it, which is harmless).
+template <typename K>
+inline void smem_limit_once(std::atomic<unsigned long long>& done, K kernel, size_t smem) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (bit) done.fetch_or(bit, std::memory_order_acq_rel);
+}
 
 // ---------------------------------------------------------- 128-bit sums
 

@@ -1457,11 +1457,8 @@ void agg_launch_bucket(const AggArgs& a, int bucket, const int32_t* comms, int n
       constexpr int CAP = 8192;
       size_t smem = (size_t)CAP * (4 + sizeof(AggVal<W2>) + 1);
       auto k = agg_block_k<W2, CAP, 256>;
-      static bool attr = false;
-      if (!attr) {
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-      }
+      static std::atomic<unsigned long long> attr{0};
+      smem_limit_once(attr, k, smem);
       (count_launch(), k<<<agrid(k, 256, smem, ncomms), 256, smem, s>>>(a, comms, ncomms));
       break;
     }
@@ -1475,11 +1472,8 @@ void agg_launch_global(const AggArgs& a, const int32_t* comms, int ncomms, const
                        cudaStream_t s) {
   if (ncomms <= 0 || nchunks <= 0) return;
   const size_t smem = (size_t)(2 * kAggChunkEntries) * (4 + sizeof(AggVal<W2>));
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(agg_global_insert_k<W2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  smem_limit_once(attr, agg_global_insert_k<W2>, smem);
   (count_launch(), agg_global_insert_k<W2><<<(unsigned)nchunks, 256, smem, s>>>(a, comms, ncomms, gbase, chunk_pre));
   (count_launch(), agg_global_write_k<W2><<<(unsigned)nslotchunks, 256, 0, s>>>(a, comms, ncomms, gbase, spre));
 }

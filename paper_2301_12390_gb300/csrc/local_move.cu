@@ -1152,11 +1152,8 @@ void launch_bucket_t(const LMArgs<W>& a, int bucket, const int32_t* verts, int n
       constexpr int CAP = 8192;
       size_t smem = (size_t)CAP * (sizeof(typename TableVal<WIDE>::T) + 4 + 1);
       auto k = lm_block<W, WIDE, ASYNC, CAP, 512>;
-      static bool attr = false;
-      if (!attr) {
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-      }
+      static std::atomic<unsigned long long> attr{0};
+      smem_limit_once(attr, k, smem);
       (count_launch(), k<<<grid_for(k, 512, smem, nverts), 512, smem, s>>>(a, verts, nverts));
       break;
     }
