@@ -821,7 +821,7 @@ int q_numerators(louvain_ctx* c, const PassState& g, std::vector<i128>& out) {
   cudaStream_t s = c->stream;
   if (c->G == 1) {
     CK(cudaMemsetAsync(c->acc, 0, 4 * sizeof(unsigned long long), s));
-    modularity_parts<W>(g.off, g.col, (const W*)g.w, g.n, c->memb, c->sig, c->acc, s);
+    modularity_parts<W>(g.off, g.col, (const W*)g.w, g.n, g.nnz, c->memb, c->sig, c->acc, c->crow, s);
     CKLAUNCH();
     if (int r = fetch(c, c->h_acc, c->acc, 4 * sizeof(unsigned long long))) return r;
     u128 L = ((u128)c->h_acc[3] << 64) | (u128)c->h_acc[0];
@@ -1985,7 +1985,7 @@ int louvain_modularity(louvain_ctx* c, const int32_t* memb, int64_t n, int ptr_k
   if (n) CK(cudaMemcpyAsync(c->used, memb, n * sizeof(int32_t), kind, s));
   community_totals(c->K0, c->used, n, c->Knext, s);
   CK(cudaMemsetAsync(c->acc, 0, 8 * sizeof(unsigned long long), s));
-  modularity_parts<int32_t>(c->off0, c->col0, c->w0, n, c->used, c->Knext, c->acc, s);
+  modularity_parts<int32_t>(c->off0, c->col0, c->w0, n, c->nnz0, c->used, c->Knext, c->acc, c->crow, s);
   CKLAUNCH();
   if (int r = fetch(c, c->h_acc, c->acc, 4 * sizeof(unsigned long long))) return r;
   const int64_t M = c->M0;

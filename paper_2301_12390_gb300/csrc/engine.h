@@ -183,9 +183,11 @@ void pass_init_from(int64_t n, const long long* K, int32_t* memb, long long* sig
 
 // Modularity numerator parts: sumL (u64) += weights inside communities,
 // ss (u128 lo/hi) += sum over c < n of sig[c]^2.
+// crow: merge-path scratch ((n + nnz) / kRelabelChunk + 2 ints).
 template <typename W>
-void modularity_parts(const int64_t* off, const int32_t* col, const W* wt, int64_t n, const int32_t* memb,
-                      const long long* sig, unsigned long long* acc /* [0] L, [1..2] ss lo/hi */, cudaStream_t s);
+void modularity_parts(const int64_t* off, const int32_t* col, const W* wt, int64_t n, int64_t nnz,
+                      const int32_t* memb, const long long* sig,
+                      unsigned long long* acc /* [0], [3] L lo/hi, [1..2] ss lo/hi */, int32_t* crow, cudaStream_t s);
 // ss (u128 lo/hi at acc[0..1]) += sum over i < n of v[i]^2.
 void sum_squares(const long long* v, int64_t n, unsigned long long* acc, cudaStream_t s);
 // Community totals for an arbitrary membership (Sigma_c = sum K_i over c).

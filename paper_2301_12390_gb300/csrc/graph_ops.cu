@@ -625,21 +625,57 @@ void pass_init_from(int64_t n, const long long* K, int32_t* memb, long long* sig
   (count_launch(), community_sizes_k<<<grid1d(n), kT, 0, s>>>(K, memb, n, sig, csize));
 }
 
+// L = sum of the weights of entries whose two ends share a community, over
+// merge-path chunks of rows + entries (crow from chunk_rows_k, the walk of
+// row_sums_k): every warp the same work however skewed the rows are.  A lane
+// loads the community of one row of the warp's 32-row window; each entry
+// takes its row's by a shuffle.
 template <typename W>
-__global__ void __launch_bounds__(kT) intra_weight_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                                                     const W* __restrict__ wt, int64_t n,
-                                                     const int32_t* __restrict__ memb, unsigned long long* acc) {
-  __shared__ int64_t soff[kT + 1];
-  const int64_t v0 = (int64_t)blockIdx.x * kT;
-  const int nr = (int)min((int64_t)kT, n - v0);
-  for (int t = threadIdx.x; t <= nr; t += kT) soff[t] = off[v0 + t];
-  __syncthreads();
-  unsigned long long L = 0;
-  for (int64_t x = soff[0] + threadIdx.x; x < soff[nr]; x += kT) {
-    int r = row_of(soff, nr, x);
-    if (memb[col[x]] == memb[v0 + r]) L += (unsigned long long)wt[x];
+__global__ void __launch_bounds__(256) intra_weight_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                                                     const W* __restrict__ wt, int64_t n, int64_t nnz,
+                                                     const int32_t* __restrict__ memb,
+                                                     const int32_t* __restrict__ crow, int64_t nchunks,
+                                                     unsigned long long* acc) {
+  constexpr int U = 4;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  u128 L = 0;
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += warps) {
+    const int64_t X0 = c * kRelabelChunk - crow[c];
+    const int64_t X1 = min(nnz, (c + 1) * kRelabelChunk - crow[c + 1]);
+    for (int64_t r = crow[c];; r += kWarp) {
+      const int64_t o = off[min(r + lane, n)];
+      const int32_t mr = r + lane < n ? memb[r + lane] : -1;
+      const int64_t wend = __shfl_sync(0xffffffffu, off[min(r + kWarp, n)], 0);
+      const int64_t xs = max(X0, __shfl_sync(0xffffffffu, o, 0)), xe = min(X1, wend);
+      for (int64_t x0 = xs; x0 < xe; x0 += U * kWarp) {
+        int32_t cm[U], v[U];
+        unsigned long long w[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          const int64_t x = x0 + k * kWarp + lane;
+          int q = 0;
+#pragma unroll
+          for (int step = 16; step >= 1; step >>= 1) {
+            const int cand = q + step;
+            if (__shfl_sync(0xffffffffu, o, cand) <= x) q = cand;
+          }
+          cm[k] = __shfl_sync(0xffffffffu, mr, q);
+          v[k] = x < xe ? col[x] : -1;
+          w[k] = x < xe ? (unsigned long long)wt[x] : 0ull;
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k)
+          if (v[k] >= 0 && memb[v[k]] == cm[k]) L += w[k];
+      }
+      if (wend >= X1) break;
+    }
   }
-  block_add_u128((u128)L, acc, acc + 3);   // acc[0] lo; hi unused beyond 2^64 (L <= M < 2^62)
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1)
+    L += ((u128)__shfl_xor_sync(0xffffffffu, (unsigned long long)(L >> 64), m) << 64) |
+         (u128)__shfl_xor_sync(0xffffffffu, (unsigned long long)L, m);
+  if (lane == 0 && L) atomic_add_u128(acc, acc + 3, L);   // acc[0] lo, acc[3] hi
 }
 
 __global__ void __launch_bounds__(kT) sum_squares_k(const long long* __restrict__ sig, int64_t n,
@@ -653,16 +689,26 @@ __global__ void __launch_bounds__(kT) sum_squares_k(const long long* __restrict_
 }
 
 template <typename W>
-void modularity_parts(const int64_t* off, const int32_t* col, const W* wt, int64_t n, const int32_t* memb,
-                      const long long* sig, unsigned long long* acc, cudaStream_t s) {
+void modularity_parts(const int64_t* off, const int32_t* col, const W* wt, int64_t n, int64_t nnz,
+                      const int32_t* memb, const long long* sig, unsigned long long* acc, int32_t* crow,
+                      cudaStream_t s) {
   if (n <= 0) return;
-  (count_launch(), intra_weight_k<W><<<(unsigned)((n + kT - 1) / kT), kT, 0, s>>>(off, col, wt, n, memb, acc));
+  if (nnz > 0) {
+    const int64_t nchunks = (n + nnz + kRelabelChunk - 1) / kRelabelChunk;
+    (count_launch(), chunk_rows_k<<<grid1d(nchunks + 1), kT, 0, s>>>(off, n, nchunks, crow));
+    int64_t blocks = (nchunks + 7) / 8;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    (count_launch(), intra_weight_k<W><<<(unsigned)blocks, 256, 0, s>>>(off, col, wt, n, nnz, memb, crow, nchunks,
+                                                                       acc));
+  }
   (count_launch(), sum_squares_k<<<grid1d(n), kT, 0, s>>>(sig, n, acc + 1, acc + 2));
 }
-template void modularity_parts<int32_t>(const int64_t*, const int32_t*, const int32_t*, int64_t, const int32_t*,
-                                        const long long*, unsigned long long*, cudaStream_t);
-template void modularity_parts<int64_t>(const int64_t*, const int32_t*, const int64_t*, int64_t, const int32_t*,
-                                        const long long*, unsigned long long*, cudaStream_t);
+template void modularity_parts<int32_t>(const int64_t*, const int32_t*, const int32_t*, int64_t, int64_t,
+                                        const int32_t*, const long long*, unsigned long long*, int32_t*,
+                                        cudaStream_t);
+template void modularity_parts<int64_t>(const int64_t*, const int32_t*, const int64_t*, int64_t, int64_t,
+                                        const int32_t*, const long long*, unsigned long long*, int32_t*,
+                                        cudaStream_t);
 
 __global__ void community_totals_k(const long long* K, const int32_t* memb, int64_t n, long long* sig) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
