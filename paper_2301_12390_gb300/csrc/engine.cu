@@ -832,7 +832,8 @@ int q_numerators(louvain_ctx* c, const PassState& g, std::vector<i128>& out) {
   const int64_t G = c->G;
   CK(cudaMemsetAsync(c->d_gL, 0, 2 * G * sizeof(unsigned long long), s));
   CK(cudaMemsetAsync(c->d_gSS, 0, 2 * G * sizeof(unsigned long long), s));
-  graph_modularity_parts<W>(g.off, g.col, (const W*)g.w, g.n, c->memb, c->sig, c->gid, c->d_gL, c->d_gSS, s);
+  graph_modularity_parts<W>(g.off, g.col, (const W*)g.w, g.n, g.nnz, c->memb, c->sig, c->gid, c->d_gL, c->d_gSS,
+                            c->crow, s);
   CKLAUNCH();
   if (int r = fetch(c, c->h_gL, c->d_gL, 2 * G * sizeof(unsigned long long))) return r;
   if (int r = fetch(c, c->h_gSS, c->d_gSS, 2 * G * sizeof(unsigned long long))) return r;
@@ -1719,7 +1720,7 @@ int load_graphs(louvain_ctx* c, int64_t G, const int64_t* vo, int64_t n, int64_t
     c->gqnum0[0] = c->qnum0;
   } else {
     CK(cudaMemsetAsync(c->flags, 0, sizeof(int), s));
-    graph_ids(c->vo0, (int)G, n, c->gid0, c->off0, c->col0, c->flags, s);
+    graph_ids(c->vo0, (int)G, n, nnz, c->gid0, c->off0, c->col0, c->crow, c->flags, s);
     int flags = 0;
     CKLAUNCH();
     if (int r = fetch(c, &flags, c->flags, sizeof(int))) return r;
@@ -1729,7 +1730,8 @@ int load_graphs(louvain_ctx* c, int64_t G, const int64_t* vo, int64_t n, int64_t
     CK(cudaMemsetAsync(c->d_gSS, 0, 2 * G * sizeof(unsigned long long), s));
     graph_totals(c->K0, c->gid0, n, c->d_gs, s);
     iota_i32(c->memb, n, s);
-    graph_modularity_parts<int32_t>(c->off0, c->col0, c->w0, n, c->memb, c->K0, c->gid0, c->d_gL, c->d_gSS, s);
+    graph_modularity_parts<int32_t>(c->off0, c->col0, c->w0, n, nnz, c->memb, c->K0, c->gid0, c->d_gL, c->d_gSS,
+                                    c->crow, s);
     CKLAUNCH();
     if (int r = fetch(c, c->h_gs, c->d_gs, 2 * G * sizeof(unsigned long long))) return r;
     if (int r = fetch(c, c->h_gL, c->d_gL, 2 * G * sizeof(unsigned long long))) return r;

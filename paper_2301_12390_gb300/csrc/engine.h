@@ -257,9 +257,9 @@ void agg_compact(const int64_t* cstart, const int64_t* mpre, const int64_t* coff
 // Several graphs in one CSR (contiguous vertex ranges per graph).
 void graph_totals(const long long* K, const int32_t* gid, int64_t n, unsigned long long* Mg, cudaStream_t s);
 template <typename W>
-void graph_modularity_parts(const int64_t* off, const int32_t* col, const W* wt, int64_t n, const int32_t* memb,
-                            const long long* sig, const int32_t* gid, unsigned long long* Lg, unsigned long long* SSg,
-                            cudaStream_t s);
+void graph_modularity_parts(const int64_t* off, const int32_t* col, const W* wt, int64_t n, int64_t nnz,
+                            const int32_t* memb, const long long* sig, const int32_t* gid, unsigned long long* Lg,
+                            unsigned long long* SSg, int32_t* crow /* merge-path scratch */, cudaStream_t s);
 void graph_squares(const long long* sig, const int32_t* gid, int64_t n, unsigned long long* SSg, cudaStream_t s);
 void graph_renumber(const int32_t* used, const int32_t* newid, const int32_t* gid, int64_t n, int64_t* kcount,
                     int32_t* gid_next, cudaStream_t s);
@@ -300,8 +300,8 @@ void colour_round(const int64_t* off, const int32_t* col, int64_t n, const int32
                   unsigned long long* nnext, int32_t* hnext, unsigned long long* nhnext, unsigned long long* total,
                   unsigned long long* hmask, int32_t* hdone, int* flags, cudaStream_t s);
 void class_max(const int32_t* cls, int64_t n, int* out, cudaStream_t s);
-void graph_ids(const int64_t* vo, int G, int64_t n, int32_t* gid, const int64_t* off, const int32_t* col, int* flags,
-               cudaStream_t s);
+void graph_ids(const int64_t* vo, int G, int64_t n, int64_t nnz, int32_t* gid, const int64_t* off, const int32_t* col,
+               int32_t* crow /* merge-path scratch */, int* flags, cudaStream_t s);
 
 // Input checks: flags |= 1 offsets not monotone / bad ends, 2 col out of
 // range, 4 weight <= 0; hashes[0..1] = sums of mix(u,v,w) and mix(v,u,w).

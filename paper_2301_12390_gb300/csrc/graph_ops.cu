@@ -1682,29 +1682,50 @@ void graph_totals(const long long* K, const int32_t* gid, int64_t n, unsigned lo
 }
 
 // Per-graph modularity parts: L_g (lo, hi) over intra-community entries of
-// the graph's rows and SS_g (lo, hi) over its communities' Sigma^2.
+// the graph's rows (merge-path chunks as in intra_weight_k; a lane's entries
+// come in increasing row order, so it sums a run of one graph in registers
+// and adds it when the graph changes) and SS_g (lo, hi) over its
+// communities' Sigma^2.
 template <typename W>
-__global__ void __launch_bounds__(kT) graph_intra_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                                                    const W* __restrict__ wt, int64_t n, const int32_t* __restrict__ memb,
-                                                    const int32_t* __restrict__ gid, unsigned long long* Lg) {
-  __shared__ int64_t soff[kT + 1];
-  __shared__ unsigned long long lo[kT], hi[kT];
-  const int64_t v0 = (int64_t)blockIdx.x * kT;
-  const int nr = (int)min((int64_t)kT, n - v0);
-  for (int t = threadIdx.x; t <= nr; t += kT) soff[t] = off[v0 + t];
-  lo[threadIdx.x] = 0;
-  hi[threadIdx.x] = 0;
-  const int g0 = gid[v0], ng = gid[v0 + nr - 1] - g0 + 1;
-  __syncthreads();
-  for (int64_t x = soff[0] + threadIdx.x; x < soff[nr]; x += kT) {
-    int r = row_of(soff, nr, x);
-    if (memb[col[x]] == memb[v0 + r]) {
-      const int slot = gid[v0 + r] - g0;
-      atomic_add_u128(&lo[slot], &hi[slot], (u128)(unsigned long long)wt[x]);
+__global__ void __launch_bounds__(256) graph_intra_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                                                    const W* __restrict__ wt, int64_t n, int64_t nnz,
+                                                    const int32_t* __restrict__ memb, const int32_t* __restrict__ gid,
+                                                    const int32_t* __restrict__ crow, int64_t nchunks,
+                                                    unsigned long long* Lg) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  int g = -1;
+  u128 L = 0;
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += warps) {
+    const int64_t X0 = c * kRelabelChunk - crow[c];
+    const int64_t X1 = min(nnz, (c + 1) * kRelabelChunk - crow[c + 1]);
+    for (int64_t r = crow[c];; r += kWarp) {
+      const int64_t o = off[min(r + lane, n)];
+      const int32_t mr = r + lane < n ? memb[r + lane] : -1;
+      const int32_t gr = r + lane < n ? gid[r + lane] : -1;
+      const int64_t wend = __shfl_sync(0xffffffffu, off[min(r + kWarp, n)], 0);
+      const int64_t xs = max(X0, __shfl_sync(0xffffffffu, o, 0)), xe = min(X1, wend);
+      for (int64_t x = xs + lane; x - lane < xe; x += kWarp) {
+        int q = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+          const int cand = q + step;
+          if (__shfl_sync(0xffffffffu, o, cand) <= x) q = cand;
+        }
+        const int32_t cm = __shfl_sync(0xffffffffu, mr, q), cg = __shfl_sync(0xffffffffu, gr, q);
+        if (x < xe && memb[col[x]] == cm) {
+          if (cg != g) {
+            if (L) atomic_add_u128(Lg + 2 * g, Lg + 2 * g + 1, L);
+            g = cg;
+            L = 0;
+          }
+          L += (unsigned long long)wt[x];
+        }
+      }
+      if (wend >= X1) break;
     }
   }
-  __syncthreads();
-  flush_graph_sums(lo, hi, g0, ng, Lg);
+  if (L) atomic_add_u128(Lg + 2 * g, Lg + 2 * g + 1, L);
 }
 
 __global__ void __launch_bounds__(kT) graph_squares_k(const long long* __restrict__ sig, const int32_t* __restrict__ gid,
@@ -1727,20 +1748,27 @@ __global__ void __launch_bounds__(kT) graph_squares_k(const long long* __restric
 }
 
 template <typename W>
-void graph_modularity_parts(const int64_t* off, const int32_t* col, const W* wt, int64_t n, const int32_t* memb,
-                            const long long* sig, const int32_t* gid, unsigned long long* Lg, unsigned long long* SSg,
-                            cudaStream_t s) {
+void graph_modularity_parts(const int64_t* off, const int32_t* col, const W* wt, int64_t n, int64_t nnz,
+                            const int32_t* memb, const long long* sig, const int32_t* gid, unsigned long long* Lg,
+                            unsigned long long* SSg, int32_t* crow, cudaStream_t s) {
   if (n <= 0) return;
+  if (nnz > 0) {
+    const int64_t nchunks = (n + nnz + kRelabelChunk - 1) / kRelabelChunk;
+    (count_launch(), chunk_rows_k<<<grid1d(nchunks + 1), kT, 0, s>>>(off, n, nchunks, crow));
+    int64_t blocks = (nchunks + 7) / 8;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    (count_launch(), graph_intra_k<W><<<(unsigned)blocks, 256, 0, s>>>(off, col, wt, n, nnz, memb, gid, crow, nchunks,
+                                                                      Lg));
+  }
   const unsigned nb = (unsigned)((n + kT - 1) / kT);
-  (count_launch(), graph_intra_k<W><<<nb, kT, 0, s>>>(off, col, wt, n, memb, gid, Lg));
   (count_launch(), graph_squares_k<<<nb, kT, 0, s>>>(sig, gid, n, SSg));
 }
-template void graph_modularity_parts<int32_t>(const int64_t*, const int32_t*, const int32_t*, int64_t, const int32_t*,
-                                              const long long*, const int32_t*, unsigned long long*,
-                                              unsigned long long*, cudaStream_t);
-template void graph_modularity_parts<int64_t>(const int64_t*, const int32_t*, const int64_t*, int64_t, const int32_t*,
-                                              const long long*, const int32_t*, unsigned long long*,
-                                              unsigned long long*, cudaStream_t);
+template void graph_modularity_parts<int32_t>(const int64_t*, const int32_t*, const int32_t*, int64_t, int64_t,
+                                              const int32_t*, const long long*, const int32_t*, unsigned long long*,
+                                              unsigned long long*, int32_t*, cudaStream_t);
+template void graph_modularity_parts<int64_t>(const int64_t*, const int32_t*, const int64_t*, int64_t, int64_t,
+                                              const int32_t*, const long long*, const int32_t*, unsigned long long*,
+                                              unsigned long long*, int32_t*, cudaStream_t);
 
 void graph_squares(const long long* sig, const int32_t* gid, int64_t n, unsigned long long* SSg, cudaStream_t s) {
   if (n > 0) (count_launch(), graph_squares_k<<<(unsigned)((n + kT - 1) / kT), kT, 0, s>>>(sig, gid, n, SSg));
@@ -1778,26 +1806,48 @@ __global__ void graph_ids_k(const int64_t* __restrict__ vo, int G, int64_t n, in
   for (int g = blockIdx.x; g < G; g += gridDim.x)
     for (int64_t v = vo[g] + threadIdx.x; v < vo[g + 1]; v += blockDim.x) gid[v] = g;
 }
-__global__ void __launch_bounds__(kT) graph_check_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                                                    const int32_t* __restrict__ gid, int64_t n, int* flags) {
-  __shared__ int64_t soff[kT + 1];
-  const int64_t v0 = (int64_t)blockIdx.x * kT;
-  const int nr = (int)min((int64_t)kT, n - v0);
-  for (int t = threadIdx.x; t <= nr; t += kT) soff[t] = off[v0 + t];
-  __syncthreads();
+__global__ void __launch_bounds__(256) graph_check_k(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                                                    const int32_t* __restrict__ gid, int64_t n, int64_t nnz,
+                                                    const int32_t* __restrict__ crow, int64_t nchunks, int* flags) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   int f = 0;
-  for (int64_t x = soff[0] + threadIdx.x; x < soff[nr]; x += kT) {
-    int r = row_of(soff, nr, x);
-    const int32_t v = col[x];
-    if (v < 0 || v >= n || gid[v] != gid[v0 + r]) f = 8;
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += warps) {
+    const int64_t X0 = c * kRelabelChunk - crow[c];
+    const int64_t X1 = min(nnz, (c + 1) * kRelabelChunk - crow[c + 1]);
+    for (int64_t r = crow[c];; r += kWarp) {
+      const int64_t o = off[min(r + lane, n)];
+      const int32_t gr = r + lane < n ? gid[r + lane] : -1;
+      const int64_t wend = __shfl_sync(0xffffffffu, off[min(r + kWarp, n)], 0);
+      const int64_t xs = max(X0, __shfl_sync(0xffffffffu, o, 0)), xe = min(X1, wend);
+      for (int64_t x = xs + lane; x - lane < xe; x += kWarp) {
+        int q = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+          const int cand = q + step;
+          if (__shfl_sync(0xffffffffu, o, cand) <= x) q = cand;
+        }
+        const int32_t cg = __shfl_sync(0xffffffffu, gr, q);
+        if (x < xe) {
+          const int32_t v = col[x];
+          if (v < 0 || v >= n || gid[v] != cg) f = 8;
+        }
+      }
+      if (wend >= X1) break;
+    }
   }
   if (f) atomicOr(flags, f);
 }
-void graph_ids(const int64_t* vo, int G, int64_t n, int32_t* gid, const int64_t* off, const int32_t* col, int* flags,
-               cudaStream_t s) {
+void graph_ids(const int64_t* vo, int G, int64_t n, int64_t nnz, int32_t* gid, const int64_t* off, const int32_t* col,
+               int32_t* crow, int* flags, cudaStream_t s) {
   if (G <= 0 || n <= 0) return;
   (count_launch(), graph_ids_k<<<G < 65535 ? G : 65535, 256, 0, s>>>(vo, G, n, gid));
-  (count_launch(), graph_check_k<<<(unsigned)((n + kT - 1) / kT), kT, 0, s>>>(off, col, gid, n, flags));
+  if (nnz <= 0) return;
+  const int64_t nchunks = (n + nnz + kRelabelChunk - 1) / kRelabelChunk;
+  (count_launch(), chunk_rows_k<<<grid1d(nchunks + 1), kT, 0, s>>>(off, n, nchunks, crow));
+  int64_t blocks = (nchunks + 7) / 8;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  (count_launch(), graph_check_k<<<(unsigned)blocks, 256, 0, s>>>(off, col, gid, n, nnz, crow, nchunks, flags));
 }
 
 // Entries of every graph of a batch: off[vo[q + 1]] - off[vo[q]].
