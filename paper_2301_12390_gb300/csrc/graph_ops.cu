@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kT) part_scatter_k(const int32_t* __restrict__
   long long* running = psm;               // nkeys
   long long* wcnt = psm + nkeys;          // (kT / 32) * nkeys
   constexpr int NW = kT / kWarp;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int wid = threadIdx.x >> 5;
   for (int t = threadIdx.x; t < nkeys; t += kT) running[t] = offs[(int64_t)t * nblk + blockIdx.x];
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
   for (int r = 0; r < kScanTile / kT; ++r) {
@@ -311,18 +311,6 @@ void hub_layout(const int64_t* off, const int32_t* hubs, int64_t nhubs, int64_t*
 }
 
 // -------------------------------------------- row-range load balancing
-
-// A block takes rows [v0, v0 + kT); its threads stride over the rows'
-// entries and find each entry's row by binary search in a shared copy of
-// the offsets, so a hub row is spread over all threads of its block.
-__device__ __forceinline__ int row_of(const int64_t* soff, int nr, int64_t x) {
-  int lo = 0, hi = nr;  // soff[lo] <= x < soff[hi]
-  while (hi - lo > 1) {
-    int mid = (lo + hi) >> 1;
-    if (soff[mid] <= x) lo = mid; else hi = mid;
-  }
-  return lo;
-}
 
 __global__ void chunk_rows_k(const int64_t* __restrict__ off, int64_t n, int64_t nchunks, int32_t* crow);
 
