@@ -142,6 +142,27 @@ def test_sync_parity_wide_arithmetic_large_communities():
     assert dsum.max() > 4096
 
 
+@pytest.mark.parametrize("opt", [dict(prune=1), dict(prune=0, subrounds=4), dict(prune=1, singleton_guard=0)])
+def test_sync_parity_graph_of_block_vertices(opt):
+    """A graph whose every vertex has degree 129-1,024 (checked below), so
+    that all of pass 0 runs in the block-per-vertex kernel with its
+    2,048-slot table: bit-exact with the oracle under pruning, four classes
+    and no singleton guard."""
+    g = gg.sbm(21, 3000, 4, 0.3, 0.01, wmin=1, wmax=9)
+    deg = np.diff(g.off)
+    assert deg.min() > 128 and deg.max() <= 1024
+    assert_sync_parity(g, **opt)
+
+
+def test_async_quality_graph_of_block_vertices():
+    g = gg.sbm(21, 3000, 4, 0.3, 0.01, wmin=1, wmax=9)
+    got = engine_run(g, mode=1, prune=1)
+    ref = oracle.louvain(g.off, g.col, g.w, mode=oracle.ASYNC, prune=1)
+    assert got["q"] >= ref.Q - 0.01, (got["q"], ref.Q)
+    _, num, M = oracle.modularity(g.off, g.col, g.w, got["top"])
+    assert got["exact"] == (num, M)
+
+
 def test_sync_parity_max_iterations_and_passes():
     g = G["sbm8192"]
     assert_sync_parity(g, max_iterations=1)
