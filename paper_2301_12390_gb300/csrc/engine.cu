@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <initializer_list>
 #include <vector>
 #include "engine.h"
 #include "../../include/louvain.h"
@@ -302,10 +303,16 @@ int fetch(louvain_ctx* c, void* host, const void* dev, size_t bytes) {
   return 0;
 }
 
-// Two small device arrays to host with one synchronisation (through pinned
-// staging, so both copies are queued before the stream is waited for).
-int fetch_pair(louvain_ctx* c, void* h1, const void* d1, size_t b1, void* h2, const void* d2, size_t b2) {
-  const size_t o2 = (b1 + 15) & ~(size_t)15, need = o2 + b2;
+// Several small device arrays to host with one synchronisation (through
+// pinned staging, so all copies are queued before the stream is waited for).
+struct FetchPiece {
+  void* host;
+  const void* dev;
+  size_t bytes;
+};
+int fetch_many(louvain_ctx* c, std::initializer_list<FetchPiece> pieces) {
+  size_t need = 0;
+  for (const FetchPiece& f : pieces) need = ((need + 15) & ~(size_t)15) + f.bytes;
   if (need > c->h_pair_cap) {
     if (c->h_pair) cudaFreeHost(c->h_pair);
     c->h_pair = nullptr;
@@ -315,12 +322,24 @@ int fetch_pair(louvain_ctx* c, void* h1, const void* d1, size_t b1, void* h2, co
     c->h_pair_cap = cap;
   }
   char* p = (char*)c->h_pair;
-  CK(cudaMemcpyAsync(p, d1, b1, cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaMemcpyAsync(p + o2, d2, b2, cudaMemcpyDeviceToHost, c->stream));
+  size_t o = 0;
+  for (const FetchPiece& f : pieces) {
+    o = (o + 15) & ~(size_t)15;
+    if (f.bytes) CK(cudaMemcpyAsync(p + o, f.dev, f.bytes, cudaMemcpyDeviceToHost, c->stream));
+    o += f.bytes;
+  }
   CK(cudaStreamSynchronize(c->stream));
-  memcpy(h1, p, b1);
-  memcpy(h2, p + o2, b2);
+  o = 0;
+  for (const FetchPiece& f : pieces) {
+    o = (o + 15) & ~(size_t)15;
+    if (f.bytes) memcpy(f.host, p + o, f.bytes);
+    o += f.bytes;
+  }
   return 0;
+}
+
+int fetch_pair(louvain_ctx* c, void* h1, const void* d1, size_t b1, void* h2, const void* d2, size_t b2) {
+  return fetch_many(c, {{h1, d1, b1}, {h2, d2, b2}});
 }
 
 // --------------------------------------------------------------- a pass
@@ -835,8 +854,9 @@ int q_numerators(louvain_ctx* c, const PassState& g, std::vector<i128>& out) {
   graph_modularity_parts<W>(g.off, g.col, (const W*)g.w, g.n, g.nnz, c->memb, c->sig, c->gid, c->d_gL, c->d_gSS,
                             c->crow, s);
   CKLAUNCH();
-  if (int r = fetch(c, c->h_gL, c->d_gL, 2 * G * sizeof(unsigned long long))) return r;
-  if (int r = fetch(c, c->h_gSS, c->d_gSS, 2 * G * sizeof(unsigned long long))) return r;
+  if (int r = fetch_pair(c, c->h_gL, c->d_gL, 2 * G * sizeof(unsigned long long), c->h_gSS, c->d_gSS,
+                         2 * G * sizeof(unsigned long long)))
+    return r;
   for (int64_t q = 0; q < G; ++q) {
     u128 L = ((u128)c->h_gL[2 * q + 1] << 64) | (u128)c->h_gL[2 * q];
     u128 SS = ((u128)c->h_gSS[2 * q + 1] << 64) | (u128)c->h_gSS[2 * q];
@@ -910,21 +930,29 @@ int aggregate(louvain_ctx* c, const PassState& g, int64_t k, PassState* next, st
   // coarse offsets = scan of row lengths, written straight into the next graph
   scan_i64(c->rlen, c->offX[dst], k, c->offX[dst] + k, c->tmp, s);
   CKLAUNCH();
+  // the coarse row count, the overflow flag and the Q numerator's parts
+  // (complete: the kernels that sum them ran before the scan) in one read
   int64_t nnz2 = 0;
   int flag = 0;
-  if (int r = fetch_pair(c, &nnz2, c->offX[dst] + k, sizeof(int64_t), &flag, c->flags, sizeof(int))) return r;
+  if (!multi) {
+    if (int r = fetch_many(c, {{&nnz2, c->offX[dst] + k, sizeof(int64_t)}, {&flag, c->flags, sizeof(int)},
+                               {c->h_acc, c->acc, 8 * sizeof(unsigned long long)}}))
+      return r;
+  } else {
+    if (int r = fetch_many(c, {{&nnz2, c->offX[dst] + k, sizeof(int64_t)}, {&flag, c->flags, sizeof(int)},
+                               {c->h_gL, c->d_gL, 2 * G * sizeof(unsigned long long)},
+                               {c->h_gSS, c->d_gSS, 2 * G * sizeof(unsigned long long)}}))
+      return r;
+  }
   if (flag) return fail(c, LOUVAIN_ERR_INTERNAL, "aggregation: hash table overflow");
   agg_compact<W2>(c->cstart, c->mpre, c->offX[dst], k, nnz2, c->crow, c->tcol, (const W2*)c->tw, c->colX[dst],
                   (W2*)c->wX[dst], s);
   CKLAUNCH();
   // Q numerator after the pass: M * sum_C L_C (coarse self-loops) - sum_c Sigma_c^2
   if (!multi) {
-    if (int r = fetch(c, c->h_acc, c->acc, 8 * sizeof(unsigned long long))) return r;
     u128 SS = ((u128)c->h_acc[5] << 64) | (u128)c->h_acc[4];
     nafter[0] = (i128)c->M * (i128)c->h_acc[6] - (i128)SS;
   } else {
-    if (int r = fetch(c, c->h_gL, c->d_gL, 2 * G * sizeof(unsigned long long))) return r;
-    if (int r = fetch(c, c->h_gSS, c->d_gSS, 2 * G * sizeof(unsigned long long))) return r;
     for (int64_t q = 0; q < G; ++q) {
       u128 L = ((u128)c->h_gL[2 * q + 1] << 64) | (u128)c->h_gL[2 * q];
       u128 SS = ((u128)c->h_gSS[2 * q + 1] << 64) | (u128)c->h_gSS[2 * q];
@@ -1152,13 +1180,15 @@ int run_pass(louvain_ctx* c, const PassState& g, int pass, double* tol, bool wid
   }
   CKLAUNCH();
   int64_t k = 0;
-  if (int r = fetch(c, &k, c->scal, sizeof(int64_t))) return r;
-  if (c->compacted) c->kc_top = k;
   std::vector<int64_t> vo_next;
   if (multi) {
     vo_next.resize(G + 1);
-    if (int r = fetch(c, vo_next.data(), c->vo_next, (G + 1) * sizeof(int64_t))) return r;
+    if (int r = fetch_pair(c, &k, c->scal, sizeof(int64_t), vo_next.data(), c->vo_next, (G + 1) * sizeof(int64_t)))
+      return r;
+  } else {
+    if (int r = fetch(c, &k, c->scal, sizeof(int64_t))) return r;
   }
+  if (c->compacted) c->kc_top = k;
   // If another pass may follow, aggregate first: the coarse self-loops give
   // sum_C L_C, so the pass's Q numerators cost no extra scan of the graph; a
   // coarse graph built for a pass after which every graph stops is dropped.
@@ -1733,9 +1763,10 @@ int load_graphs(louvain_ctx* c, int64_t G, const int64_t* vo, int64_t n, int64_t
     graph_modularity_parts<int32_t>(c->off0, c->col0, c->w0, n, nnz, c->memb, c->K0, c->gid0, c->d_gL, c->d_gSS,
                                     c->crow, s);
     CKLAUNCH();
-    if (int r = fetch(c, c->h_gs, c->d_gs, 2 * G * sizeof(unsigned long long))) return r;
-    if (int r = fetch(c, c->h_gL, c->d_gL, 2 * G * sizeof(unsigned long long))) return r;
-    if (int r = fetch(c, c->h_gSS, c->d_gSS, 2 * G * sizeof(unsigned long long))) return r;
+    if (int r = fetch_many(c, {{c->h_gs, c->d_gs, 2 * G * sizeof(unsigned long long)},
+                               {c->h_gL, c->d_gL, 2 * G * sizeof(unsigned long long)},
+                               {c->h_gSS, c->d_gSS, 2 * G * sizeof(unsigned long long)}}))
+      return r;
     std::vector<long long> Mg(G);
     for (int64_t q = 0; q < G; ++q) {
       const u128 M = ((u128)c->h_gs[2 * q + 1] << 64) | (u128)c->h_gs[2 * q];
