@@ -526,6 +526,9 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
     }
     return 0;
   };
+  // the first classification draws iteration 0's classes
+  *c->h_iter = 0;
+  CK(cudaMemcpyAsync(c->d_iter, c->h_iter, sizeof(int), cudaMemcpyHostToDevice, s));
   if (int r = classify(0, false)) return r;
   const int64_t full_len = ko[kBuckets * P];   // vertices with edges
   // A small pass graph without vertices above degree 128 takes one launch per
@@ -545,8 +548,9 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
   // a class kernel of a small pass loops over its class, however large: one
   // grid for the pass, so its iteration's launches do not depend on the draw
   const int64_t class_grid_verts = (ko[3 * P] + P - 1) / P + 1;
-  // hub move stamps are iteration numbers of this pass
-  CK(cudaMemsetAsync(c->hmoved, 0, (size_t)g.n * sizeof(int32_t), s));
+  // hub move stamps are iteration numbers of this pass (by position in the
+  // first hub list; later lists are subsets of it)
+  if (nhubs > 0) CK(cudaMemsetAsync(c->hmoved, 0, (size_t)nhubs * sizeof(int32_t), s));
   LMArgs<W> a;
   memset(&a, 0, sizeof(a));
   a.off = g.off;
@@ -589,8 +593,12 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
   // forked onto their streams and joined (synchronous: then committed), and
   // the counters copied to pinned host memory.  The sequence depends on the
   // iteration only through *d_iter (and, for several graphs, the device copy
-  // of which graphs still iterate), so after two direct iterations a pass
-  // captures it once into a CUDA graph and replays that.
+  // of which graphs still iterate), so a pass can capture it once into a CUDA
+  // graph and replay that (a small pass from its second iteration, others
+  // with the cuda_graphs option from the third).  A small pass whose classes
+  // are drawn anew every iteration draws them inside the sequence, except in
+  // iteration 0, whose classes the first classification drew.
+  bool drawn = true;
   auto iteration = [&]() -> int {
     CK(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), s));
     if (multi) {
@@ -599,7 +607,8 @@ int local_moving(louvain_ctx* c, const PassState& g, int pass, double tol, bool 
     }
     // a small pass graph without vertices above degree 128: one launch per
     // class on the main stream (and the new draw of its classes first)
-    if (small_pass && sub_m > 0) reclassify_small();
+    if (small_pass && sub_m > 0 && !drawn) reclassify_small();
+    drawn = false;
     for (int ch = 0; ch < P && small_pass; ++ch) {
       lm_launch_class<W>(a, wide, async, c->list, c->key_off, P, ch, class_grid_verts, s);
       if (!async) lm_launch_commit<W>(a, ko[3 * P], s);
