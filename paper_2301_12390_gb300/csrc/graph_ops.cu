@@ -122,6 +122,41 @@ __global__ void __launch_bounds__(kT) scan_final_k(const Tin* in, Tout* out, int
   }
 }
 
+// A short input (at most kScanOneTiles tiles) in one launch: one block takes
+// the tiles in order, each offset by the sum of those before it (the three
+// kernels above cost more in launches than in work at these sizes).
+constexpr int64_t kScanOneTiles = 4;
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(kT) scan_one_k(const Tin* in, Tout* out, int64_t n, int64_t* total) {
+  __shared__ long long tile[kScanTile];
+  constexpr int PER = kScanTile / kT;
+  long long carry = 0;
+  for (int64_t base = 0; base < n; base += kScanTile) {
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int64_t idx = base + k * kT + threadIdx.x;
+      tile[k * kT + threadIdx.x] = idx < n ? (long long)in[idx] : 0;
+    }
+    __syncthreads();
+    long long loc[PER], v = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) { loc[k] = v; v += tile[threadIdx.x * PER + k]; }
+    long long tot;
+    const long long ex = block_inclusive_scan(v, &tot) - v + carry;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) tile[threadIdx.x * PER + k] = ex + loc[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int64_t idx = base + k * kT + threadIdx.x;
+      if (idx < n) out[idx] = (Tout)tile[k * kT + threadIdx.x];
+    }
+    carry += tot;
+    __syncthreads();   // the tile is loaded again
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
 size_t scan_tmp_bytes(int64_t n) { return (size_t)((n + kScanTile - 1) / kScanTile + 1) * sizeof(long long); }
 
 template <typename Tin, typename Tout>
@@ -131,6 +166,10 @@ static void scan_any(const Tin* in, Tout* out, int64_t n, int64_t* total, void* 
     return;
   }
   int64_t nb = (n + kScanTile - 1) / kScanTile;
+  if (nb <= kScanOneTiles) {
+    (count_launch(), scan_one_k<Tin, Tout><<<1, kT, 0, s>>>(in, out, n, total));
+    return;
+  }
   long long* bsum = (long long*)tmp;
   (count_launch(), scan_reduce_k<Tin><<<(unsigned)nb, kT, 0, s>>>(in, n, bsum));
   (count_launch(), scan_bsums_k<<<1, kT, 0, s>>>(bsum, nb, total));
@@ -202,6 +241,58 @@ __global__ void __launch_bounds__(kT) part_scatter_k(const int32_t* __restrict__
   }
 }
 
+// One tile (n <= kScanTile) in one launch: the counts, their scan over the
+// keys, the key offsets and the stable scatter above, in the same order.
+__global__ void __launch_bounds__(kT) part_one_k(const int32_t* __restrict__ key, int64_t n, int nkeys,
+                                                 int64_t* key_off, int32_t* out) {
+  extern __shared__ long long psm[];
+  long long* running = psm;               // nkeys
+  long long* wcnt = psm + nkeys;          // (kT / 32) * nkeys
+  constexpr int NW = kT / kWarp;
+  const int wid = threadIdx.x >> 5;
+  for (int t = threadIdx.x; t < nkeys; t += kT) running[t] = 0;
+  __syncthreads();
+  for (int64_t idx = threadIdx.x; idx < n; idx += kT) atomicAdd((unsigned long long*)&running[key[idx]], 1ull);
+  __syncthreads();
+  long long carry = 0;   // exclusive scan of the counts over the keys
+  for (int c0 = 0; c0 < nkeys; c0 += kT) {
+    const int t = c0 + threadIdx.x;
+    const long long v = t < nkeys ? running[t] : 0;
+    long long tot;
+    const long long ex = block_inclusive_scan(v, &tot) - v + carry;
+    if (t < nkeys) {
+      running[t] = ex;
+      key_off[t] = ex;
+    }
+    carry += tot;
+  }
+  if (threadIdx.x == 0) key_off[nkeys] = n;
+  __syncthreads();
+  for (int64_t base = 0; base < n; base += kT) {
+    for (int t = threadIdx.x; t < NW * nkeys; t += kT) wcnt[t] = 0;
+    __syncthreads();
+    const int64_t idx = base + threadIdx.x;
+    const bool valid = idx < n;
+    const int k = valid ? key[idx] : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, k);
+    const int rank = __popc(peers & lanemask_lt());
+    if (valid && rank == 0) wcnt[wid * nkeys + k] = __popc(peers);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nkeys; t += kT) {
+      long long b = running[t];
+      for (int w = 0; w < NW; ++w) {
+        const long long c = wcnt[w * nkeys + t];
+        wcnt[w * nkeys + t] = b;
+        b += c;
+      }
+      running[t] = b;
+    }
+    __syncthreads();
+    if (valid) out[wcnt[wid * nkeys + k] + rank] = (int32_t)idx;
+    __syncthreads();
+  }
+}
+
 size_t partition_tmp_bytes(int64_t n, int nkeys) {
   int64_t nblk = (n + kScanTile - 1) / kScanTile;
   if (nblk < 1) nblk = 1;
@@ -217,6 +308,11 @@ void stable_partition(const int32_t* key, int64_t n, int nkeys, int32_t* out, in
   int64_t* counts = (int64_t*)tmp;
   int64_t* offs = counts + m;
   void* stmp = (void*)(offs + m);
+  if (n > 0 && n <= kScanTile) {
+    const size_t smem = (size_t)nkeys * (1 + kT / kWarp) * sizeof(long long);
+    (count_launch(), part_one_k<<<1, kT, smem, s>>>(key, n, nkeys, key_off, out));
+    return;
+  }
   if (n > 0) {
     (count_launch(), part_count_k<<<(unsigned)nblk, kT, nkeys * sizeof(int), s>>>(key, n, nkeys, counts, nblk));
     scan_i64(counts, offs, m, nullptr, stmp, s);
