@@ -1,4 +1,4 @@
-"""Host-side choices of bench.py (no GPU): the bounded CPU-baseline sample."""
+"""Host-side parts of bench.py (no GPU): the bounded CPU-baseline sample, the serving pool and the clock record."""
 import sys
 import os
 
@@ -60,3 +60,41 @@ def test_oracle_baseline_runs_on_one_pinned_core_and_restores_affinity():
         assert os.sched_getaffinity(0) == {pin.core}
         assert pin.core in before
     assert os.sched_getaffinity(0) == before
+
+
+def test_clock_samples_give_median_max_and_throttle_reasons(tmp_path):
+    """The clock record of the timed region: median SM clock under load, the
+    maximum, and every throttle reason seen active in any sample (the sampler
+    writes nvidia-smi's CSV; a malformed line is skipped)."""
+    ck = bench.Clocks(0)
+    ck.path = str(tmp_path / "clocks.csv")
+    rows = [
+        "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1200.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070",
+        "0, 1500, 2070, 1000.0, 0x8, Active, Not Active, Not Active, Not Active",
+    ]
+    with open(ck.path, "w") as f:
+        f.write("\n".join(rows) + "\n")
+
+    class _Done:   # the sampler process has already ended
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    ck.proc = _Done()
+    got = ck.stop()
+    assert got["samples"] == 4
+    assert got["sm_mhz"] == 2025.0 and got["sm_max_mhz"] == 2070.0
+    assert got["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    assert not os.path.exists(ck.path)
+
+
+def test_clocks_without_nvidia_smi_say_so():
+    ck = bench.Clocks(0)
+    ck.proc = None
+    got = ck.stop()
+    assert got["sm_mhz"] is None and got["reasons"] == ["nvidia-smi unavailable"]
